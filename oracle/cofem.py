@@ -1,0 +1,347 @@
+"""Plain FP64 reference for exact EM and covariance-free EM (CoFEM) on the clustered
+multi-task compressive sensing model (Lin & Ba, "An efficient algorithm for clustered
+multi-task compressive sensing").
+
+TEST INFRASTRUCTURE ONLY: this is the slow, obviously-correct CPU oracle the CUDA path is
+checked against.  Only the tests, the smoke check and the benchmark's CPU-baseline leg may
+import it; the library itself never does, and nothing here is shared with the CUDA code.
+
+Everything is float64 numpy.  Library primitives used as single steps: matrix products,
+Cholesky (numpy.linalg.cholesky), triangular solves (scipy.linalg.solve_triangular) and the
+symmetric eigensolver (numpy.linalg.eigh).  Inputs Phi_t and y_t arrive as the FP32 values
+the GPU sees and are promoted to float64 exactly.
+
+Conventions: T tasks, C clusters, D signal dimension, N_t rows of Phi_t, K probes per
+(t, c).  The paper also uses K for the number of clusters in Eq. 1 and Sec. 4; here C is
+always the cluster count and K the probe count.
+
+Readings where the paper leaves a choice (each applied identically on the GPU):
+* CG stopping (Alg. 1 runs "until convergence"): system i stops after the first step u with
+  ||r_{u+1}||_2 <= tol * ||b||_2, or after max_iter steps, or when r'r == 0 or d'Ad <= 0.
+  U_i is the number of completed steps; the Lanczos matrix of Eq. 9 uses gamma_1..gamma_U
+  and xi_1..xi_{U-1}.
+* Probes are fresh for every (EM iteration, t, c, k) (Alg. 2 samples them inside the loop).
+* M-step (Eq. 5 with diag Sigma replaced by s): the per-task term max(mu^2 + s, 0), then
+  alpha = clamp(num / den, alpha_min, alpha_max); den <= num / alpha_max gives alpha_max; a
+  cluster whose total responsibility is below 1e-300 keeps its previous alpha.
+* The returned responsibilities and means are those of the last E-step (Alg. 2 returns
+  mu_{t, a_t} after the loop); ties in argmax go to the lowest cluster index.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+from scipy.linalg import solve_triangular
+
+from . import philox
+
+LOG_2PI = float(np.log(2.0 * np.pi))
+
+
+# --------------------------------------------------------------------------------------
+# model pieces (Eqs. 1, 3, 5)
+# --------------------------------------------------------------------------------------
+
+def rhs_mean(Phi_t: np.ndarray, y_t: np.ndarray, beta: float) -> np.ndarray:
+    """b0 = beta * Phi_t^T y_t, the right-hand side of the posterior-mean system (Eq. 7)."""
+    return beta * (Phi_t.T @ y_t)
+
+
+def apply_A(Phi_t: np.ndarray, beta: float, alpha_c: np.ndarray, V: np.ndarray) -> np.ndarray:
+    """A V with A = beta Phi_t^T Phi_t + diag(alpha_c) (Eq. 7), V of shape [D] or [D, m]."""
+    if V.ndim == 1:
+        return beta * (Phi_t.T @ (Phi_t @ V)) + alpha_c * V
+    return beta * (Phi_t.T @ (Phi_t @ V)) + alpha_c[:, None] * V
+
+
+def task_const(y_t: np.ndarray, beta: float) -> float:
+    """The c-independent part of log p(y_t | alpha_c):  log p = ell/2 - task_const, with
+    task_const = (N log 2pi - N log beta + beta ||y||^2) / 2 (from Eqs. 1 and 3)."""
+    N = y_t.shape[0]
+    return 0.5 * (N * LOG_2PI - N * np.log(beta) + beta * float(y_t @ y_t))
+
+
+def ell(logdet_sigma: float, alpha_c: np.ndarray, b0: np.ndarray, mu: np.ndarray) -> float:
+    """ell_{t,c} = log det Sigma + sum_d log alpha_cd + beta y^T Phi mu  (Eq. 3), where
+    beta y^T Phi mu is written as b0^T mu."""
+    return float(logdet_sigma) + float(np.sum(np.log(alpha_c))) + float(b0 @ mu)
+
+
+def responsibilities(ell_tc: np.ndarray, pi: np.ndarray) -> np.ndarray:
+    """q_t = softmax_c(ell_tc / 2 + log pi_c)  (Eq. 3), max-shifted log-sum-exp, [T, C]."""
+    z = 0.5 * ell_tc + np.log(pi)[None, :]
+    z = z - z.max(axis=1, keepdims=True)
+    e = np.exp(z)
+    return e / e.sum(axis=1, keepdims=True)
+
+
+def log_likelihood(ell_tc: np.ndarray, pi: np.ndarray, consts: np.ndarray) -> float:
+    """L(theta) = (1/T) sum_t log sum_c pi_c p(y_t | alpha_c)  (Sec. 2), using
+    log p(y_t | alpha_c) = ell_tc / 2 - consts[t]."""
+    z = 0.5 * ell_tc + np.log(pi)[None, :]
+    m = z.max(axis=1)
+    lse = m + np.log(np.exp(z - m[:, None]).sum(axis=1))
+    return float(np.mean(lse - consts))
+
+
+def m_step(q: np.ndarray, mu: np.ndarray, s: np.ndarray, alpha_prev: np.ndarray,
+           alpha_min: float = 1e-10, alpha_max: float = 1e10) -> np.ndarray:
+    """Eq. 5: alpha_cd = sum_t q_tc / sum_t q_tc (mu_tcd^2 + s_tcd), with the clamps above.
+    q [T, C], mu and s [T, C, D], alpha_prev [C, D]."""
+    num = q.sum(axis=0)                                                   # [C]
+    den = np.einsum("tc,tcd->cd", q, np.maximum(mu * mu + s, 0.0))        # [C, D]
+    out = np.empty_like(alpha_prev)
+    for c in range(q.shape[1]):
+        if num[c] < 1e-300:
+            out[c] = alpha_prev[c]
+            continue
+        with np.errstate(divide="ignore"):
+            a = num[c] / den[c]
+        a = np.where(den[c] <= num[c] / alpha_max, alpha_max, a)
+        out[c] = np.clip(a, alpha_min, alpha_max)
+    return out
+
+
+# --------------------------------------------------------------------------------------
+# Alg. 1: conjugate gradient, run side by side over the columns of B
+# --------------------------------------------------------------------------------------
+
+@dataclass
+class CGResult:
+    x: np.ndarray        # [D, m]
+    gamma: np.ndarray    # [m, max_iter]  step sizes gamma_u
+    xi: np.ndarray       # [m, max_iter]  direction coefficients xi_u
+    steps: np.ndarray    # [m] completed steps U_i
+    rel_resid: np.ndarray  # [m] ||r_{U+1}|| / ||b|| of the recursive residual
+
+
+def cg(apply, B: np.ndarray, tol: float, max_iter: int, steps: np.ndarray = None) -> CGResult:
+    """Alg. 1 with x_1 = 0, r_1 = d_1 = b, for every column of B (independent systems).
+
+    apply(V) returns A V for the columns given.  If ``steps`` is given, column i runs exactly
+    steps[i] steps (replay of a step count measured elsewhere) instead of the tol test."""
+    D, m = B.shape
+    X = np.zeros((D, m))
+    R = B.astype(np.float64).copy()
+    Dd = R.copy()
+    rr = np.einsum("ij,ij->j", R, R)
+    bb = rr.copy()
+    gam = np.zeros((m, max_iter))
+    xi = np.zeros((m, max_iter))
+    U = np.zeros(m, dtype=np.int64)
+    if steps is None:
+        active = rr > 0.0
+    else:
+        active = (np.asarray(steps) > 0) & (rr > 0.0)
+    for u in range(max_iter):
+        idx = np.nonzero(active)[0]
+        if idx.size == 0:
+            break
+        Dd_a = Dd[:, idx]
+        AD = apply(Dd_a, idx)
+        dAd = np.einsum("ij,ij->j", Dd_a, AD)
+        ok = dAd > 0.0
+        if not ok.all():
+            active[idx[~ok]] = False
+            idx, Dd_a, AD, dAd = idx[ok], Dd_a[:, ok], AD[:, ok], dAd[ok]
+            if idx.size == 0:
+                break
+        g = rr[idx] / dAd                                   # gamma_u
+        X[:, idx] += g * Dd_a                               # x_{u+1}
+        R_a = R[:, idx] - g * AD                            # r_{u+1}
+        rr_new = np.einsum("ij,ij->j", R_a, R_a)
+        x_u = rr_new / rr[idx]                              # xi_u
+        R[:, idx] = R_a
+        Dd[:, idx] = R_a + x_u * Dd_a                       # d_{u+1}
+        gam[idx, u] = g
+        xi[idx, u] = x_u
+        U[idx] += 1
+        rr[idx] = rr_new
+        if steps is None:
+            done = (rr_new <= (tol * tol) * bb[idx]) | (rr_new == 0.0)
+        else:
+            done = U[idx] >= np.asarray(steps)[idx]
+        active[idx[done]] = False
+    rel = np.sqrt(rr / np.where(bb > 0, bb, 1.0))
+    return CGResult(X, gam, xi, U, rel)
+
+
+def refine(apply, B: np.ndarray, X: np.ndarray, tol: float, max_iter: int, refine_tol: float,
+           refine_max: int):
+    """Iterative refinement of the CG solutions X of A X = B: each sweep forms the residual
+    B - A X, solves A delta = residual by Alg. 1 (x_1 = 0, same tol and step cap) and adds
+    delta; column i stops once ||delta_i|| <= refine_tol * ||x_i||.  Returns (X, sweeps [m])."""
+    X = X.copy()
+    m = B.shape[1]
+    sweeps = np.zeros(m, dtype=np.int64)
+    active = np.ones(m, dtype=bool)
+    for _ in range(refine_max):
+        idx = np.nonzero(active)[0]
+        if idx.size == 0:
+            break
+        Rres = B[:, idx] - apply(X[:, idx], idx)
+        res = cg(lambda V, sub: apply(V, idx[sub]), Rres, tol, max_iter)
+        X[:, idx] += res.x
+        sweeps[idx] += 1
+        dn = np.linalg.norm(res.x, axis=0)
+        xn = np.linalg.norm(X[:, idx], axis=0)
+        active[idx[dn <= refine_tol * xn]] = False
+    return X, sweeps
+
+
+# --------------------------------------------------------------------------------------
+# Eqs. 9-11: Lanczos quadrature of p^T log(A) p from the CG coefficients
+# --------------------------------------------------------------------------------------
+
+def lanczos_tridiag(gamma: np.ndarray, xi: np.ndarray, U: int) -> np.ndarray:
+    """The U x U matrix of Eq. 9: G_11 = 1/gamma_1, G_uu = 1/gamma_u + xi_{u-1}/gamma_{u-1},
+    G_{u,u-1} = G_{u-1,u} = sqrt(xi_{u-1}) / gamma_{u-1} (1-based indices as in the paper)."""
+    G = np.zeros((U, U))
+    G[0, 0] = 1.0 / gamma[0]
+    for u in range(1, U):
+        G[u, u] = 1.0 / gamma[u] + xi[u - 1] / gamma[u - 1]
+        G[u, u - 1] = G[u - 1, u] = np.sqrt(xi[u - 1]) / gamma[u - 1]
+    return G
+
+
+def lanczos_log_quadrature(gamma: np.ndarray, xi: np.ndarray, U: int, pnorm2: float) -> float:
+    """Eq. 10 restricted to the U x U Lanczos matrix (the inner sum of Eq. 11):
+    ||p||^2 * sum_u S_{u,1}^2 log lambda_u, with the eigenpairs of G = S^T diag(lambda) S."""
+    if U <= 0:
+        return 0.0
+    G = lanczos_tridiag(gamma, xi, U)
+    lam, V = np.linalg.eigh(G)              # columns of V are eigenvectors: S = V^T
+    first = V[0, :]                         # S_{u,1} for u = 1..U
+    return float(pnorm2 * np.sum(first * first * np.log(lam)))
+
+
+def logdet_estimate(gamma: np.ndarray, xi: np.ndarray, steps: np.ndarray, D: int) -> float:
+    """Eq. 11: nu = -(1/K) sum_k sum_u D * (S^{(k)}_{u,1})^2 log lambda^{(k)}_u, where D is
+    ||p_k||^2 for a Rademacher probe.  gamma, xi: [K, max_iter]; steps: [K]."""
+    K = gamma.shape[0]
+    tot = 0.0
+    for k in range(K):
+        tot += lanczos_log_quadrature(gamma[k], xi[k], int(steps[k]), float(D))
+    return -tot / K
+
+
+# --------------------------------------------------------------------------------------
+# E-steps
+# --------------------------------------------------------------------------------------
+
+def _task_arrays(Phi_list, y_list):
+    P = [np.asarray(p, dtype=np.float64) for p in Phi_list]
+    Y = [np.asarray(v, dtype=np.float64) for v in y_list]
+    return P, Y
+
+
+def exact_estep(Phi_list, y_list, alpha: np.ndarray, pi: np.ndarray, beta: float) -> dict:
+    """Eq. 3 evaluated exactly: Sigma_tc = (beta Phi^T Phi + diag alpha_c)^-1 by Cholesky
+    A = L L^T, mu = Sigma b0, diag Sigma from the columns of L^-1, log det Sigma = -2 sum log L_ii."""
+    P, Y = _task_arrays(Phi_list, y_list)
+    T, (C, D) = len(P), alpha.shape
+    mu = np.zeros((T, C, D))
+    sdiag = np.zeros((T, C, D))
+    logdet = np.zeros((T, C))
+    ell_tc = np.zeros((T, C))
+    consts = np.array([task_const(Y[t], beta) for t in range(T)])
+    for t in range(T):
+        G = beta * (P[t].T @ P[t])
+        b0 = rhs_mean(P[t], Y[t], beta)
+        for c in range(C):
+            A = G + np.diag(alpha[c])
+            L = np.linalg.cholesky(A)
+            Linv = solve_triangular(L, np.eye(D), lower=True)          # Sigma = Linv^T Linv
+            w = solve_triangular(L, b0, lower=True)
+            mu[t, c] = solve_triangular(L.T, w, lower=False)
+            sdiag[t, c] = np.einsum("ij,ij->j", Linv, Linv)
+            logdet[t, c] = -2.0 * np.sum(np.log(np.diag(L)))
+            ell_tc[t, c] = ell(logdet[t, c], alpha[c], b0, mu[t, c])
+    q = responsibilities(ell_tc, pi)
+    return dict(mu=mu, s=sdiag, logdet=logdet, ell=ell_tc, q=q,
+                loglik=log_likelihood(ell_tc, pi, consts))
+
+
+def cofem_estep(Phi_list, y_list, alpha: np.ndarray, pi: np.ndarray, beta: float, K: int,
+                seed: int, em_iter: int, tol: float, max_iter: int, probe_fn=None,
+                steps: np.ndarray = None, tasks=None, refine_tol: float = None,
+                refine_max: int = 8) -> dict:
+    """Alg. 2, inner loop (one E-step): for every (t, c) solve A mu = b0 and A x_k = p_k by CG
+    (Eq. 7, Alg. 1), s = (1/K) sum_k p_k * x_k (Eq. 4), the log-det estimate of Eq. 11 from the
+    CG coefficients of the probe systems, ell (Eq. 3) and the responsibilities (Eq. 3).
+
+    probe_fn(t, c) -> [K, D] overrides the Philox probes; steps [T, C, K+1] replays given CG
+    step counts; tasks gives the global task index of each entry of Phi_list (for the probe
+    counter) when the list is a subset.  With refine_tol set, mu and every x_k are refined
+    (``refine``) after the first CG solve, which alone supplies the Lanczos coefficients."""
+    P, Y = _task_arrays(Phi_list, y_list)
+    T, (C, D) = len(P), alpha.shape
+    tasks = list(range(T)) if tasks is None else list(tasks)
+    mu = np.zeros((T, C, D))
+    s = np.zeros((T, C, D))
+    nu = np.zeros((T, C))
+    ell_tc = np.zeros((T, C))
+    U = np.zeros((T, C, K + 1), dtype=np.int64)
+    gam = np.zeros((T, C, K + 1, max_iter))
+    xis = np.zeros((T, C, K + 1, max_iter))
+    rel = np.zeros((T, C, K + 1))
+    consts = np.array([task_const(Y[t], beta) for t in range(T)])
+    for t in range(T):
+        b0 = rhs_mean(P[t], Y[t], beta)
+        for c in range(C):
+            if probe_fn is None:
+                Pk = philox.probes(seed, em_iter, tasks[t], c, C, K, D)
+            else:
+                Pk = np.asarray(probe_fn(t, c), dtype=np.float64)
+            B = np.concatenate([b0[:, None], Pk.T], axis=1)              # [D, K+1]
+            op = lambda V, idx, t=t, c=c: apply_A(P[t], beta, alpha[c], V)
+            res = cg(op, B, tol, max_iter, None if steps is None else steps[t, c])
+            X = res.x
+            if refine_tol is not None:
+                X, _ = refine(op, B, X, tol, max_iter, refine_tol, refine_max)
+            mu[t, c] = X[:, 0]
+            s[t, c] = np.mean(Pk.T * X[:, 1:], axis=1)
+            nu[t, c] = logdet_estimate(res.gamma[1:], res.xi[1:], res.steps[1:], D)
+            ell_tc[t, c] = ell(nu[t, c], alpha[c], b0, mu[t, c])
+            U[t, c] = res.steps
+            gam[t, c] = res.gamma
+            xis[t, c] = res.xi
+            rel[t, c] = res.rel_resid
+    q = responsibilities(ell_tc, pi)
+    return dict(mu=mu, s=s, logdet=nu, ell=ell_tc, q=q, steps=U, gamma=gam, xi=xis,
+                rel_resid=rel, loglik=log_likelihood(ell_tc, pi, consts))
+
+
+# --------------------------------------------------------------------------------------
+# Alg. 2: the EM loop (exact or covariance-free E-step)
+# --------------------------------------------------------------------------------------
+
+def em(Phi_list, y_list, pi: np.ndarray, beta: float, n_iter: int, *, method: str = "cofem",
+       K: int = 16, seed: int = 0, tol: float = 1e-5, max_iter: int = 100,
+       alpha0: np.ndarray = None, em_iter_offset: int = 0, alpha_min: float = 1e-10,
+       alpha_max: float = 1e10, D: int = None, C: int = None, refine_tol: float = None,
+       refine_max: int = 8) -> dict:
+    """n_iter EM iterations from alpha0 (default: the Alg. 2 Uniform(0,1) draw).  Returns the
+    last E-step's outputs, the final alpha, the hard assignments argmax_c q_tc and the
+    reconstructions mu_{t, a_t}, plus the log-likelihood seen by every E-step."""
+    if alpha0 is None:
+        alpha = philox.alpha_init(seed, C, D)
+    else:
+        alpha = np.asarray(alpha0, dtype=np.float64).copy()
+    trace = []
+    alphas = [alpha.copy()]
+    est = None
+    for it in range(n_iter):
+        if method == "exact":
+            est = exact_estep(Phi_list, y_list, alpha, pi, beta)
+        else:
+            est = cofem_estep(Phi_list, y_list, alpha, pi, beta, K, seed, em_iter_offset + it,
+                              tol, max_iter, refine_tol=refine_tol, refine_max=refine_max)
+        trace.append(est["loglik"])
+        alpha = m_step(est["q"], est["mu"], est["s"], alpha, alpha_min, alpha_max)
+        alphas.append(alpha.copy())
+    assign = np.argmax(est["q"], axis=1)
+    recon = est["mu"][np.arange(len(assign)), assign]
+    return dict(last=est, alpha=alpha, alphas=alphas, assign=assign, recon=recon,
+                loglik_trace=np.array(trace))
