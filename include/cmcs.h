@@ -1,0 +1,172 @@
+/*
+ * cmcs.h -- C ABI of libcmcs.so: covariance-free EM (CoFEM) for clustered multi-task
+ * compressive sensing on one NVIDIA GB300 (sm_103a).
+ *
+ * Model (Lin & Ba, "An efficient algorithm for clustered multi-task compressive sensing",
+ * Sec. 2, Eq. 1): task t has measurements y_t = Phi_t z_t + noise (noise precision beta),
+ * z_t | a_t = c ~ N(0, diag(alpha_c)^-1), a_t ~ Categorical(pi).  The library runs the EM
+ * loop of Alg. 2 with the E-step of Sec. 3: for every (task t, cluster c) it solves
+ *     (beta Phi_t^T Phi_t + diag(alpha_c)) x = b                                  (Eq. 7)
+ * by conjugate gradient (Alg. 1) for b = beta Phi_t^T y_t (posterior mean mu_tc) and for K
+ * Rademacher probes (Eq. 4), estimates diag(Sigma_tc) (Eq. 4) and log det Sigma_tc by
+ * Lanczos quadrature over the CG coefficients (Eqs. 9-11), forms the responsibilities q_tc
+ * (Eq. 3) and updates alpha_c by Eq. 5.
+ *
+ * Conventions for every call:
+ *  - Array layouts are dense row-major with no padding: Phi is [sum_t N_t][D] (task t's
+ *    rows follow task t-1's), y is [sum_t N_t], per-(t,c) vectors are [T][C][D], per-(t,c)
+ *    scalars [T][C], alpha [C][D].
+ *  - A pointer argument is host memory when the accompanying `on_device` is 0 and CUDA device
+ *    memory of the context's device when it is 1.  The library never keeps a caller pointer
+ *    past the call that received it; it copies what it needs into memory it owns.
+ *  - All GPU work is ordered on the CUDA stream given to cmcs_create (0 = legacy default
+ *    stream).  Every call returns only after that work has completed, and reports device
+ *    errors through its status.
+ *  - Errors: a call that fails validation returns CMCS_ERR_INVALID_ARG and changes no state.
+ *    cmcs_last_error() returns a description of the most recent failure of that context.
+ *  - No call allocates or frees device memory except cmcs_create and cmcs_destroy.
+ */
+#ifndef CMCS_H
+#define CMCS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cmcs_ctx cmcs_ctx;
+
+typedef enum {
+  CMCS_OK = 0,
+  CMCS_ERR_INVALID_ARG = 1,   /* null pointer, bad size, bad enum, non-positive beta, ... */
+  CMCS_ERR_CUDA = 2,          /* a CUDA runtime call failed; see cmcs_last_error          */
+  CMCS_ERR_OOM = 3,           /* device allocation failed in cmcs_create                  */
+  CMCS_ERR_NUMERIC = 4,       /* NaN or Inf reached an output (e.g. NaN in y)             */
+  CMCS_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up                       */
+  CMCS_ERR_UNSUPPORTED = 6    /* a valid request this build does not implement            */
+} cmcs_status;
+
+typedef enum {
+  /* operator and CG in FP32 (SIMT FMA); refinement residual with compensated FP32 products
+     and sums (about twice FP32's precision) */
+  CMCS_FP32 = 0,
+  /* operator with Phi held in BF16 on the tcgen05 tensor cores (FP32 accumulation in TMEM);
+     CG vectors FP32; the refinement residual uses the FP32 Phi as in CMCS_FP32 */
+  CMCS_BF16_REFINE = 1
+} cmcs_precision;
+
+typedef struct {
+  int T;                  /* tasks, >= 1                                                  */
+  int C;                  /* clusters, >= 1                                               */
+  int D;                  /* signal dimension, >= 1                                       */
+  int K;                  /* Rademacher probes per (t, c), >= 1                           */
+  const int64_t *N;       /* host [T]: rows N_t of Phi_t, each >= 1                      */
+  double beta;            /* noise precision (known, Sec. 2), > 0                         */
+  const double *pi;       /* host [C]: cluster priors (known, Sec. 2), > 0, summing to 1  */
+  int cg_max_iter;        /* cap on CG steps per solve (U of Sec. 3), 1..512               */
+  double cg_tol;          /* stop a system once ||r_{u+1}|| <= cg_tol * ||b||, >= 0        */
+  uint64_t seed;          /* keys the Philox draws: alpha initialisation and probes       */
+  int precision;          /* cmcs_precision                                               */
+  int refine_max;         /* refinement sweeps after the first CG solve, 0..64            */
+  double refine_tol;      /* stop refining a system once ||delta|| <= refine_tol * ||x||  */
+  double alpha_min;       /* M-step clamp, > 0                                            */
+  double alpha_max;       /* M-step clamp, > alpha_min                                    */
+} cmcs_config;
+
+/* Summary of the most recent E-step and the EM state. */
+typedef struct {
+  int64_t em_iters_done;   /* M-steps applied since create (plus the offset of set_alpha) */
+  double loglik;           /* L(theta) = (1/T) sum_t log sum_c pi_c p(y_t|alpha_c) (Sec. 2)
+                              of the last E-step, with log det from the estimator of Eq. 11 */
+  int cg_steps_max;        /* largest CG step count U_i of the first solve                  */
+  double cg_steps_mean;    /* mean U_i over all T*C*(K+1) systems of the first solve        */
+  int64_t cg_capped;       /* systems of the first solve that stopped at cg_max_iter        */
+  int refine_sweeps_max;   /* largest number of refinement sweeps any system took           */
+  double refine_rel_max;   /* largest final ||delta|| / ||x|| over refined systems (0: none) */
+  double min_margin;       /* smallest gap q_{t,a_t} - max_{c != a_t} q_tc over tasks        */
+  int64_t operator_applies;/* batched operator applications (all systems) in the last E-step */
+} cmcs_summary;
+
+/* What cmcs_read copies out.  Element types and shapes: */
+typedef enum {
+  CMCS_OUT_MU = 0,       /* float  [T][C][D]  posterior means mu_tc (Eq. 3), refined       */
+  CMCS_OUT_S = 1,        /* float  [T][C][D]  diagonal estimates s_tc (Eq. 4)              */
+  CMCS_OUT_Q = 2,        /* double [T][C]     responsibilities q_tc (Eq. 3)                */
+  CMCS_OUT_LOGDET = 3,   /* double [T][C]     log det Sigma_tc estimate nu (Eq. 11)        */
+  CMCS_OUT_ELL = 4,      /* double [T][C]     ell_tc (Eq. 3)                               */
+  CMCS_OUT_ALPHA = 5,    /* float  [C][D]     current alpha_c (after the last M-step)      */
+  CMCS_OUT_ASSIGN = 6,   /* int32  [T]        a_t = argmax_c q_tc, lowest c on ties (Alg. 2)*/
+  CMCS_OUT_RECON = 7,    /* float  [T][D]     reconstructions mu_{t, a_t} (Alg. 2)         */
+  CMCS_OUT_STEPS = 8,    /* int32  [T][C][K+1] CG steps U of the first solve; index 0 is the
+                                              mean system, 1..K the probes                  */
+  CMCS_OUT_GAMMA = 9,    /* float  [T][C][K][cg_max_iter] CG step sizes gamma_u of the probe
+                                              systems (Alg. 1), zero past U               */
+  CMCS_OUT_XI = 10,      /* float  [T][C][K][cg_max_iter] CG coefficients xi_u, zero past U */
+  CMCS_OUT_B0 = 11,      /* float  [T][D]     beta Phi_t^T y_t (Eq. 7)                      */
+  CMCS_OUT_SWEEPS = 12   /* int32  [T][C][K+1] refinement sweeps taken per system           */
+} cmcs_output;
+
+/* Create a context: validates cfg, copies Phi and y into library-owned device memory (padded
+ * and, for CMCS_BF16_REFINE, also converted to BF16), computes b0_t = beta Phi_t^T y_t, and
+ * draws alpha_c ~ Uniform(0,1) (Alg. 2, first step) from Philox-4x32-10 keyed by cfg->seed.
+ * Phi: float [sum N_t][D]; y: float [sum N_t]; host or device per on_device.
+ * stream: a cudaStream_t (or NULL).  On success *out owns all its memory; free it with
+ * cmcs_destroy.  Returns CMCS_ERR_OOM if device memory runs out (nothing is leaked). */
+cmcs_status cmcs_create(const cmcs_config *cfg, const float *Phi, const float *y, int on_device,
+                        void *stream, cmcs_ctx **out);
+
+/* Replace alpha (float [C][D], every entry > 0) and set the EM iteration counter, which keys
+ * the probes of the next E-step (Alg. 2 draws fresh probes every iteration). */
+cmcs_status cmcs_set_alpha(cmcs_ctx *ctx, const float *alpha, int on_device, int64_t em_iter);
+
+/* One E-step (Eq. 3 via Sec. 3) with the current alpha: fills mu, s, logdet, ell, q, the
+ * assignments and the CG statistics.  alpha and the iteration counter are unchanged. */
+cmcs_status cmcs_estep(cmcs_ctx *ctx);
+
+/* n EM iterations of Alg. 2: each is an E-step followed by the M-step of Eq. 5 and an
+ * increment of the iteration counter.  After the call, mu/q/assign are those of the last
+ * E-step and alpha is the result of the last M-step. */
+cmcs_status cmcs_em_iter(cmcs_ctx *ctx, int n);
+
+/* Copy an output (see cmcs_output) into dst, host or device per on_device. */
+cmcs_status cmcs_read(const cmcs_ctx *ctx, int what, void *dst, int on_device);
+
+/* Scalar summary of the last E-step. */
+cmcs_status cmcs_result(const cmcs_ctx *ctx, cmcs_summary *out);
+
+/* Apply A_tc = beta Phi_t^T Phi_t + diag(alpha_c) (Eq. 7) to V, float [T][C*(K+1)][D] (vector
+ * j of task t uses cluster c = j / (K+1)), writing Z of the same shape.  accurate = 0 uses
+ * the E-step's batched operator (FP32 or BF16 per precision); accurate = 1 computes
+ * B - A V with compensated products and sums (the refinement residual) for B given in Z on
+ * entry.  V and Z are host or device per on_device.  The E-step's work buffers are reused,
+ * so results of a previous E-step other than alpha, b0 and the counter are invalidated. */
+cmcs_status cmcs_apply(cmcs_ctx *ctx, const float *V, float *Z, int on_device, int accurate);
+
+/* Write the probes p_{t,c,k} of EM iteration em_iter (Eq. 4, Alg. 2) as float +-1 into
+ * dst [T][C][K][D], host or device per on_device. */
+cmcs_status cmcs_probes(const cmcs_ctx *ctx, int64_t em_iter, float *dst, int on_device);
+
+/* Stand-alone Lanczos log quadrature (Eqs. 9-10): for each of nsys systems, build the
+ * U_i x U_i matrix of Eq. 9 from gamma[i*ld .. i*ld+U_i-1] and xi[i*ld .. i*ld+U_i-2]
+ * (float, device), eigendecompose it (implicit-shift QR in FP64, first eigenvector
+ * components only) and write out[i] = sum_u S_{u,1}^2 log lambda_u (double, device), i.e.
+ * Eq. 10 divided by ||p||^2.  steps: int32 [nsys] device, 0 <= U_i <= ld <= 512; U_i = 0
+ * gives 0.  status: int32 device scalar, set to nonzero if an eigen iteration cap was hit.
+ * stream: cudaStream_t or NULL. */
+cmcs_status cmcs_lanczos_quadrature(const float *gamma, const float *xi, const int32_t *steps,
+                                    int nsys, int ld, double *out, int32_t *status,
+                                    void *stream);
+
+/* Description of the last failure on ctx (or of the last failed cmcs_create when ctx is
+ * NULL).  Valid until the next call on the same context. */
+const char *cmcs_last_error(const cmcs_ctx *ctx);
+
+/* Release everything the context owns.  NULL is accepted. */
+void cmcs_destroy(cmcs_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CMCS_H */

@@ -1,0 +1,264 @@
+"""ctypes binding of libcmcs.so (include/cmcs.h): argument marshalling only.
+
+Every step of the E-step and M-step runs inside the library's CUDA kernels.  Host arrays are
+numpy; device arrays are torch CUDA tensors (PyTorch supplies device memory and streams).
+The library must be built (``paper_2310_00420_gb300.build.build()``); there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libcmcs.so")
+
+OK, ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_NUMERIC, ERR_TIMEOUT, ERR_UNSUPPORTED = range(7)
+STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "NUMERIC", 5: "TIMEOUT",
+                6: "UNSUPPORTED"}
+FP32, BF16_REFINE = 0, 1
+PRECISIONS = {"fp32": FP32, "bf16": BF16_REFINE, "bf16_refine": BF16_REFINE}
+
+(OUT_MU, OUT_S, OUT_Q, OUT_LOGDET, OUT_ELL, OUT_ALPHA, OUT_ASSIGN, OUT_RECON, OUT_STEPS,
+ OUT_GAMMA, OUT_XI, OUT_B0, OUT_SWEEPS) = range(13)
+
+# exported symbols, in the order include/cmcs.h declares them
+EXPORTS = ("cmcs_create", "cmcs_set_alpha", "cmcs_estep", "cmcs_em_iter", "cmcs_read",
+           "cmcs_result", "cmcs_apply", "cmcs_probes", "cmcs_lanczos_quadrature",
+           "cmcs_last_error", "cmcs_destroy")
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("T", ctypes.c_int), ("C", ctypes.c_int), ("D", ctypes.c_int), ("K", ctypes.c_int),
+                ("N", ctypes.POINTER(ctypes.c_int64)), ("beta", ctypes.c_double),
+                ("pi", ctypes.POINTER(ctypes.c_double)), ("cg_max_iter", ctypes.c_int),
+                ("cg_tol", ctypes.c_double), ("seed", ctypes.c_uint64), ("precision", ctypes.c_int),
+                ("refine_max", ctypes.c_int), ("refine_tol", ctypes.c_double),
+                ("alpha_min", ctypes.c_double), ("alpha_max", ctypes.c_double)]
+
+
+class Summary(ctypes.Structure):
+    _fields_ = [("em_iters_done", ctypes.c_int64), ("loglik", ctypes.c_double),
+                ("cg_steps_max", ctypes.c_int), ("cg_steps_mean", ctypes.c_double),
+                ("cg_capped", ctypes.c_int64), ("refine_sweeps_max", ctypes.c_int),
+                ("refine_rel_max", ctypes.c_double), ("min_margin", ctypes.c_double),
+                ("operator_applies", ctypes.c_int64)]
+
+
+class CmcsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"cmcs {STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib():
+    """Load libcmcs.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2310_00420_gb300.build.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i, i64, st = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_int
+    L.cmcs_create.argtypes = [ctypes.POINTER(Config), vp, vp, i, vp, ctypes.POINTER(vp)]
+    L.cmcs_set_alpha.argtypes = [vp, vp, i, i64]
+    L.cmcs_estep.argtypes = [vp]
+    L.cmcs_em_iter.argtypes = [vp, i]
+    L.cmcs_read.argtypes = [vp, i, vp, i]
+    L.cmcs_result.argtypes = [vp, ctypes.POINTER(Summary)]
+    L.cmcs_apply.argtypes = [vp, vp, vp, i, i]
+    L.cmcs_probes.argtypes = [vp, i64, vp, i]
+    L.cmcs_lanczos_quadrature.argtypes = [vp, vp, vp, i, i, vp, vp, vp]
+    L.cmcs_last_error.argtypes = [vp]
+    L.cmcs_last_error.restype = ctypes.c_char_p
+    L.cmcs_destroy.argtypes = [vp]
+    L.cmcs_destroy.restype = None
+    for name in EXPORTS:
+        if name not in ("cmcs_last_error", "cmcs_destroy"):
+            getattr(L, name).restype = st
+    _lib = L
+    return L
+
+
+def _check(status: int, handle=None):
+    if status != OK:
+        msg = lib().cmcs_last_error(handle).decode(errors="replace")
+        raise CmcsError(status, msg)
+
+
+def _is_torch(a) -> bool:
+    return type(a).__module__.startswith("torch")
+
+
+def _ptr(a):
+    """(pointer, on_device) of a contiguous numpy array or torch tensor."""
+    if _is_torch(a):
+        assert a.is_contiguous()
+        return ctypes.c_void_p(a.data_ptr()), (1 if a.is_cuda else 0)
+    assert a.flags["C_CONTIGUOUS"]
+    return ctypes.c_void_p(a.ctypes.data), 0
+
+
+def _stream_handle(stream):
+    if stream is not None:
+        return ctypes.c_void_p(int(stream))
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except Exception:  # pragma: no cover
+        pass
+    return ctypes.c_void_p(0)
+
+
+_OUT_META = {  # what: (dtype, shape function of (T, C, D, K, U))
+    OUT_MU: (np.float32, lambda T, C, D, K, U: (T, C, D)),
+    OUT_S: (np.float32, lambda T, C, D, K, U: (T, C, D)),
+    OUT_Q: (np.float64, lambda T, C, D, K, U: (T, C)),
+    OUT_LOGDET: (np.float64, lambda T, C, D, K, U: (T, C)),
+    OUT_ELL: (np.float64, lambda T, C, D, K, U: (T, C)),
+    OUT_ALPHA: (np.float32, lambda T, C, D, K, U: (C, D)),
+    OUT_ASSIGN: (np.int32, lambda T, C, D, K, U: (T,)),
+    OUT_RECON: (np.float32, lambda T, C, D, K, U: (T, D)),
+    OUT_STEPS: (np.int32, lambda T, C, D, K, U: (T, C, K + 1)),
+    OUT_GAMMA: (np.float32, lambda T, C, D, K, U: (T, C, K, U)),
+    OUT_XI: (np.float32, lambda T, C, D, K, U: (T, C, K, U)),
+    OUT_B0: (np.float32, lambda T, C, D, K, U: (T, D)),
+    OUT_SWEEPS: (np.int32, lambda T, C, D, K, U: (T, C, K + 1)),
+}
+
+
+class Context:
+    """One CoFEM problem resident on the GPU (cmcs_create ... cmcs_destroy)."""
+
+    def __init__(self, Phi, y, N, *, C: int, K: int, beta: float, pi=None, cg_max_iter: int = 100,
+                 cg_tol: float = 1e-5, seed: int = 0, precision="fp32", refine_max: int = 0,
+                 refine_tol: float = 1e-6, alpha_min: float = 1e-10, alpha_max: float = 1e10,
+                 stream=None):
+        N = np.ascontiguousarray(np.asarray(N, dtype=np.int64))
+        self.T, self.C, self.D, self.K = int(len(N)), int(C), int(Phi.shape[1]), int(K)
+        self.U = int(cg_max_iter)
+        pi = np.full(C, 1.0 / C) if pi is None else np.ascontiguousarray(np.asarray(pi, np.float64))
+        self._N, self._pi = N, pi                     # keep alive during create
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        cfg = Config(self.T, self.C, self.D, self.K,
+                     N.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), float(beta),
+                     pi.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(cg_max_iter),
+                     float(cg_tol), int(seed) & (2**64 - 1), prec, int(refine_max),
+                     float(refine_tol), float(alpha_min), float(alpha_max))
+        self.cfg = cfg
+        p_phi, dev1 = _ptr(Phi)
+        p_y, dev2 = _ptr(y)
+        if dev1 != dev2:
+            raise ValueError("Phi and y must both be host arrays or both device tensors")
+        self._stream = _stream_handle(stream)
+        h = ctypes.c_void_p()
+        _check(lib().cmcs_create(ctypes.byref(cfg), p_phi, p_y, dev1, self._stream, ctypes.byref(h)))
+        self.h = h
+
+    @classmethod
+    def from_workload(cls, wl, device: bool = True, **kw):
+        args = dict(C=wl.C, K=wl.K, beta=wl.beta, pi=wl.pi, cg_max_iter=wl.cg_max_iter,
+                    cg_tol=wl.cg_tol, seed=wl.seed)
+        args.update(kw)
+        Phi, y = wl.Phi, wl.y
+        if device:
+            import torch
+            Phi = torch.from_numpy(Phi).cuda()
+            y = torch.from_numpy(y).cuda()
+        return cls(Phi, y, wl.N, **args)
+
+    # ---- lifecycle ----
+    def close(self):
+        if getattr(self, "h", None):
+            lib().cmcs_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ---- calls ----
+    def estep(self):
+        _check(lib().cmcs_estep(self.h), self.h)
+
+    def em_iter(self, n: int = 1):
+        _check(lib().cmcs_em_iter(self.h, int(n)), self.h)
+
+    def set_alpha(self, alpha, em_iter: int = 0):
+        if not _is_torch(alpha):
+            alpha = np.ascontiguousarray(np.asarray(alpha, dtype=np.float32))
+        p, dev = _ptr(alpha)
+        _check(lib().cmcs_set_alpha(self.h, p, dev, int(em_iter)), self.h)
+
+    def read(self, what: int, out=None, device: bool = False):
+        dt, shp = _OUT_META[what]
+        shape = shp(self.T, self.C, self.D, self.K, self.U)
+        if out is None:
+            if device:
+                import torch
+                tdt = {np.float32: torch.float32, np.float64: torch.float64, np.int32: torch.int32}[dt]
+                out = torch.empty(shape, dtype=tdt, device="cuda")
+            else:
+                out = np.empty(shape, dtype=dt)
+        p, dev = _ptr(out)
+        _check(lib().cmcs_read(self.h, int(what), p, dev), self.h)
+        return out
+
+    def summary(self) -> dict:
+        s = Summary()
+        _check(lib().cmcs_result(self.h, ctypes.byref(s)), self.h)
+        return {f: getattr(s, f) for f, _ in Summary._fields_}
+
+    def apply(self, V, accurate: bool = False, B=None):
+        """A V (accurate=False) or B - A V with compensated arithmetic (accurate=True);
+        V (and B) are [T][C*(K+1)][D] float32, host numpy or device torch."""
+        if _is_torch(V):
+            import torch
+            Z = B.clone() if (accurate and B is not None) else torch.zeros_like(V)
+        else:
+            V = np.ascontiguousarray(V, dtype=np.float32)
+            Z = np.array(B, dtype=np.float32, copy=True) if (accurate and B is not None) else np.zeros_like(V)
+        pv, dev = _ptr(V)
+        pz, _ = _ptr(Z)
+        _check(lib().cmcs_apply(self.h, pv, pz, dev, 1 if accurate else 0), self.h)
+        return Z
+
+    def probes(self, em_iter: int, device: bool = False):
+        shape = (self.T, self.C, self.K, self.D)
+        if device:
+            import torch
+            out = torch.empty(shape, dtype=torch.float32, device="cuda")
+        else:
+            out = np.empty(shape, dtype=np.float32)
+        p, dev = _ptr(out)
+        _check(lib().cmcs_probes(self.h, int(em_iter), p, dev), self.h)
+        return out
+
+
+def lanczos_quadrature(gamma, xi, steps, stream=None):
+    """sum_u S_u1^2 log lambda_u of each U_i x U_i Lanczos matrix (Eqs. 9-10); gamma and xi are
+    [nsys][ld] float32 and steps [nsys] int32 CUDA tensors.  Returns (out float64, status int)."""
+    import torch
+    nsys, ld = gamma.shape
+    out = torch.empty(nsys, dtype=torch.float64, device=gamma.device)
+    status = torch.zeros(1, dtype=torch.int32, device=gamma.device)
+    _check(lib().cmcs_lanczos_quadrature(ctypes.c_void_p(gamma.data_ptr()),
+                                         ctypes.c_void_p(xi.data_ptr()),
+                                         ctypes.c_void_p(steps.data_ptr()), int(nsys), int(ld),
+                                         ctypes.c_void_p(out.data_ptr()),
+                                         ctypes.c_void_p(status.data_ptr()),
+                                         _stream_handle(stream)))
+    return out, int(status.item())

@@ -1,0 +1,536 @@
+// C ABI of libcmcs.so (declared in include/cmcs.h): context management and the host driver of
+// the E-step (Alg. 2, inner loop) and M-step (Eq. 5).
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+#include <utility>
+#include <vector>
+
+#include "cmcs_internal.cuh"
+
+using namespace cmcs;
+
+struct cmcs_ctx {
+  Ctx c;
+};
+
+namespace {
+
+thread_local char g_create_err[512] = "";
+
+void set_err(Ctx* c, const char* fmt, ...) {
+  char* dst = c ? c->err : g_create_err;
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(dst, 512, fmt, ap);
+  va_end(ap);
+}
+
+#define CK(call)                                                                    \
+  do {                                                                              \
+    cudaError_t _e = (call);                                                        \
+    if (_e != cudaSuccess) {                                                        \
+      set_err(c, "%s failed: %s", #call, cudaGetErrorString(_e));                   \
+      return _e == cudaErrorMemoryAllocation ? CMCS_ERR_OOM : CMCS_ERR_CUDA;         \
+    }                                                                               \
+  } while (0)
+
+template <typename Tp>
+cudaError_t dalloc(Tp** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(Tp));
+}
+
+void free_ctx(Ctx* c) {
+  if (!c) return;
+  void* ptrs[] = {c->phi, c->y, c->drow, c->tile_task, c->b0hi, c->b0lo, c->alpha,
+                  c->sumlogalpha, c->logpi, c->tconst, c->x, c->r, c->d, c->ad, c->xacc,
+                  c->w, c->wlo, c->part, c->rr, c->bb, c->steps, c->steps0, c->active,
+                  c->ractive, c->sweeps, c->rrel, c->task_active, c->counters, c->gam, c->xi,
+                  c->psteps, c->sest, c->quad, c->logdet, c->ell, c->q, c->assign, c->stats,
+                  c->dN};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (c->hcounters) cudaFreeHost(c->hcounters);
+  if (c->tc) tc_destroy(c);
+  free(c->hN);
+  free(c->hNp);
+  free(c->hrow);
+  free(c->hpi);
+}
+
+cudaMemcpyKind kind_in(int on_device) {
+  return on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+}
+cudaMemcpyKind kind_out(int on_device) {
+  return on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+}
+
+cmcs_status sync_check(Ctx* c) {
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_err(c, "CUDA error: %s", cudaGetErrorString(e));
+    return CMCS_ERR_CUDA;
+  }
+  return CMCS_OK;
+}
+
+cmcs_status read_counters(Ctx* c) {
+  CK(cudaMemcpyAsync(c->hcounters, c->counters, 4 * sizeof(int), cudaMemcpyDeviceToHost,
+                     c->stream));
+  return sync_check(c);
+}
+
+constexpr int kCheckEvery = 8;   // CG steps between host polls of the active-system count
+
+// Alg. 1 for every active system until all have stopped (or the step cap)
+cmcs_status run_cg(Ctx* c, int record) {
+  for (int u = 0; u < c->U; ++u) {
+    CK(launch_operator(c, c->d, c->ad, 1));
+    CK(launch_cg_update(c, record));
+    c->op_applies++;
+    if ((u + 1) % kCheckEvery == 0 && u + 1 < c->U) {
+      cmcs_status s = read_counters(c);
+      if (s != CMCS_OK) return s;
+      if (c->hcounters[0] == 0) break;
+    }
+  }
+  return CMCS_OK;
+}
+
+cmcs_status estep(Ctx* c) {
+  CK(cudaMemsetAsync(c->task_active, 0, sizeof(int) * c->T, c->stream));
+  CK(cudaMemsetAsync(c->counters, 0, sizeof(int) * 4, c->stream));
+  CK(cudaMemsetAsync(c->psteps, 0, sizeof(int) * (size_t)c->T * c->C * c->K, c->stream));
+  c->op_applies = 0;
+  // first solve: Alg. 1 from x = 0 on b0 and the probes, recording gamma and xi
+  CK(launch_cg_init(c, 0));
+  cmcs_status s = run_cg(c, 1);
+  if (s != CMCS_OK) return s;
+  CK(cudaMemcpyAsync(c->steps0, c->steps, sizeof(int) * c->S, cudaMemcpyDeviceToDevice, c->stream));
+  std::swap(c->x, c->xacc);
+  // refinement sweeps: residual with compensated products (FP64 combine), CG on it, add
+  for (int sw = 0; sw < c->refine_max; ++sw) {
+    CK(launch_residual(c, c->xacc, nullptr, c->r));
+    c->op_applies++;
+    CK(cudaMemsetAsync(c->task_active, 0, sizeof(int) * c->T, c->stream));
+    CK(cudaMemsetAsync(c->counters, 0, sizeof(int) * 2, c->stream));
+    CK(launch_cg_init(c, 1));
+    s = run_cg(c, 0);
+    if (s != CMCS_OK) return s;
+    CK(cudaMemsetAsync(c->counters + 1, 0, sizeof(int), c->stream));
+    CK(launch_refine_update(c));
+    s = read_counters(c);
+    if (s != CMCS_OK) return s;
+    if (c->hcounters[1] == 0) break;
+  }
+  CK(launch_sest(c));
+  CK(launch_quadrature_ctx(c));
+  CK(launch_ell_softmax(c));
+  s = read_counters(c);
+  if (s != CMCS_OK) return s;
+  if (c->hcounters[2] != 0) {
+    set_err(c, "non-finite value or eigen failure in the E-step (flags 0x%x)", c->hcounters[2]);
+    return CMCS_ERR_NUMERIC;
+  }
+  return CMCS_OK;
+}
+
+cmcs_status validate(const cmcs_config* cfg) {
+  if (!cfg) return CMCS_ERR_INVALID_ARG;
+  if (cfg->T < 1 || cfg->C < 1 || cfg->D < 1 || cfg->K < 1) return CMCS_ERR_INVALID_ARG;
+  if (!cfg->N || !cfg->pi) return CMCS_ERR_INVALID_ARG;
+  if (!(cfg->beta > 0.0) || !isfinite(cfg->beta)) return CMCS_ERR_INVALID_ARG;
+  if (cfg->cg_max_iter < 1 || cfg->cg_max_iter > 512) return CMCS_ERR_INVALID_ARG;
+  if (!(cfg->cg_tol >= 0.0)) return CMCS_ERR_INVALID_ARG;
+  if (cfg->precision != CMCS_FP32 && cfg->precision != CMCS_BF16_REFINE) return CMCS_ERR_INVALID_ARG;
+  if (cfg->refine_max < 0 || cfg->refine_max > 64) return CMCS_ERR_INVALID_ARG;
+  if (!(cfg->refine_tol >= 0.0)) return CMCS_ERR_INVALID_ARG;
+  if (!(cfg->alpha_min > 0.0) || !(cfg->alpha_max > cfg->alpha_min) || !isfinite(cfg->alpha_max))
+    return CMCS_ERR_INVALID_ARG;
+  double ps = 0.0;
+  for (int c = 0; c < cfg->C; ++c) {
+    if (!(cfg->pi[c] > 0.0)) return CMCS_ERR_INVALID_ARG;
+    ps += cfg->pi[c];
+  }
+  if (fabs(ps - 1.0) > 1e-6) return CMCS_ERR_INVALID_ARG;
+  for (int t = 0; t < cfg->T; ++t)
+    if (cfg->N[t] < 1 || cfg->N[t] > (1 << 24)) return CMCS_ERR_INVALID_ARG;
+  if ((int64_t)cfg->C * (cfg->K + 1) > 4096) return CMCS_ERR_INVALID_ARG;
+  return CMCS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+cmcs_status cmcs_create(const cmcs_config* cfg, const float* Phi, const float* y, int on_device,
+                        void* stream, cmcs_ctx** out) {
+  Ctx* c = nullptr;
+  if (!out) {
+    set_err(nullptr, "out is NULL");
+    return CMCS_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  if (validate(cfg) != CMCS_OK || !Phi || !y || (on_device != 0 && on_device != 1)) {
+    set_err(nullptr, "invalid configuration or null input");
+    return CMCS_ERR_INVALID_ARG;
+  }
+  cmcs_ctx* h = static_cast<cmcs_ctx*>(calloc(1, sizeof(cmcs_ctx)));
+  if (!h) {
+    set_err(nullptr, "host allocation failed");
+    return CMCS_ERR_OOM;
+  }
+  c = &h->c;
+  c->T = cfg->T;
+  c->C = cfg->C;
+  c->D = cfg->D;
+  c->K = cfg->K;
+  c->R = cfg->C * (cfg->K + 1);
+  c->S = cfg->T * c->R;
+  c->Dp = (int)round_up(cfg->D, kDAlign);
+  c->U = cfg->cg_max_iter;
+  c->beta = cfg->beta;
+  c->cg_tol = cfg->cg_tol;
+  c->refine_tol = cfg->refine_tol;
+  c->refine_max = cfg->refine_max;
+  c->alpha_min = cfg->alpha_min;
+  c->alpha_max = cfg->alpha_max;
+  c->precision = cfg->precision;
+  c->seed = cfg->seed;
+  c->em_iter = 0;
+  c->stream = static_cast<cudaStream_t>(stream);
+  c->hN = static_cast<int64_t*>(malloc(sizeof(int64_t) * c->T));
+  c->hNp = static_cast<int64_t*>(malloc(sizeof(int64_t) * c->T));
+  c->hrow = static_cast<int64_t*>(malloc(sizeof(int64_t) * (c->T + 1)));
+  c->hpi = static_cast<double*>(malloc(sizeof(double) * c->C));
+  if (!c->hN || !c->hNp || !c->hrow || !c->hpi) {
+    free_ctx(c);
+    free(h);
+    set_err(nullptr, "host allocation failed");
+    return CMCS_ERR_OOM;
+  }
+  c->hrow[0] = 0;
+  for (int t = 0; t < c->T; ++t) {
+    c->hN[t] = cfg->N[t];
+    c->hNp[t] = round_up(cfg->N[t], kNAlign);
+    c->hrow[t + 1] = c->hrow[t] + c->hNp[t];
+  }
+  for (int k = 0; k < c->C; ++k) c->hpi[k] = cfg->pi[k];
+  c->rows_total = c->hrow[c->T];
+
+  cmcs_status st = CMCS_OK;
+  auto fail = [&](cmcs_status s) {
+    char msg[512];
+    memcpy(msg, c->err, sizeof(msg));
+    free_ctx(c);
+    free(h);
+    snprintf(g_create_err, sizeof(g_create_err), "%s", msg);
+    return s;
+  };
+#define CKC(call)                                                                  \
+  do {                                                                             \
+    cudaError_t _e = (call);                                                       \
+    if (_e != cudaSuccess) {                                                       \
+      set_err(c, "%s failed: %s", #call, cudaGetErrorString(_e));                  \
+      return fail(_e == cudaErrorMemoryAllocation ? CMCS_ERR_OOM : CMCS_ERR_CUDA);  \
+    }                                                                              \
+  } while (0)
+
+  CKC(cudaGetDevice(&c->device));
+  CKC(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device));
+  const int64_t Dp = c->Dp, S = c->S, T = c->T, C = c->C, K = c->K;
+  const int64_t ntiles = c->rows_total / 128;
+  CKC(dalloc(&c->phi, (size_t)(c->rows_total * Dp)));
+  CKC(dalloc(&c->y, (size_t)c->rows_total));
+  CKC(dalloc(&c->drow, (size_t)(T + 1)));
+  CKC(dalloc(&c->dN, (size_t)T));
+  CKC(dalloc(&c->tile_task, (size_t)ntiles));
+  CKC(dalloc(&c->b0hi, (size_t)(T * Dp)));
+  CKC(dalloc(&c->b0lo, (size_t)(T * Dp)));
+  CKC(dalloc(&c->alpha, (size_t)(C * Dp)));
+  CKC(dalloc(&c->sumlogalpha, (size_t)C));
+  CKC(dalloc(&c->logpi, (size_t)C));
+  CKC(dalloc(&c->tconst, (size_t)T));
+  CKC(dalloc(&c->x, (size_t)(S * Dp)));
+  CKC(dalloc(&c->r, (size_t)(S * Dp)));
+  CKC(dalloc(&c->d, (size_t)(S * Dp)));
+  CKC(dalloc(&c->ad, (size_t)(S * Dp)));
+  CKC(dalloc(&c->xacc, (size_t)(S * Dp)));
+  CKC(dalloc(&c->w, (size_t)(c->R * c->rows_total)));
+  CKC(dalloc(&c->wlo, (size_t)(c->R * c->rows_total)));
+  CKC(dalloc(&c->part, (size_t)((Dp / 128) * S)));
+  CKC(dalloc(&c->rr, (size_t)S));
+  CKC(dalloc(&c->bb, (size_t)S));
+  CKC(dalloc(&c->steps, (size_t)S));
+  CKC(dalloc(&c->steps0, (size_t)S));
+  CKC(dalloc(&c->active, (size_t)S));
+  CKC(dalloc(&c->ractive, (size_t)S));
+  CKC(dalloc(&c->sweeps, (size_t)S));
+  CKC(dalloc(&c->rrel, (size_t)S));
+  CKC(dalloc(&c->task_active, (size_t)T));
+  CKC(dalloc(&c->counters, 4));
+  CKC(cudaMallocHost(reinterpret_cast<void**>(&c->hcounters), 4 * sizeof(int)));
+  CKC(dalloc(&c->gam, (size_t)(T * C * K * c->U)));
+  CKC(dalloc(&c->xi, (size_t)(T * C * K * c->U)));
+  CKC(dalloc(&c->psteps, (size_t)(T * C * K)));
+  CKC(dalloc(&c->sest, (size_t)(T * C * Dp)));
+  CKC(dalloc(&c->quad, (size_t)(T * C * K)));
+  CKC(dalloc(&c->logdet, (size_t)(T * C)));
+  CKC(dalloc(&c->ell, (size_t)(T * C)));
+  CKC(dalloc(&c->q, (size_t)(T * C)));
+  CKC(dalloc(&c->assign, (size_t)T));
+  CKC(dalloc(&c->stats, 4));
+
+  // zero everything that padding relies on
+  CKC(cudaMemsetAsync(c->phi, 0, sizeof(float) * c->rows_total * Dp, c->stream));
+  CKC(cudaMemsetAsync(c->y, 0, sizeof(float) * c->rows_total, c->stream));
+  for (void* p : {(void*)c->x, (void*)c->r, (void*)c->d, (void*)c->ad, (void*)c->xacc})
+    CKC(cudaMemsetAsync(p, 0, sizeof(float) * S * Dp, c->stream));
+  CKC(cudaMemsetAsync(c->sest, 0, sizeof(float) * T * C * Dp, c->stream));
+  CKC(cudaMemsetAsync(c->gam, 0, sizeof(float) * T * C * K * c->U, c->stream));
+  CKC(cudaMemsetAsync(c->xi, 0, sizeof(float) * T * C * K * c->U, c->stream));
+  CKC(cudaMemsetAsync(c->steps0, 0, sizeof(int) * S, c->stream));
+  CKC(cudaMemsetAsync(c->sweeps, 0, sizeof(int) * S, c->stream));
+  CKC(cudaMemsetAsync(c->rrel, 0, sizeof(float) * S, c->stream));
+  CKC(cudaMemsetAsync(c->q, 0, sizeof(double) * T * C, c->stream));
+  CKC(cudaMemsetAsync(c->stats, 0, sizeof(double) * 4, c->stream));
+
+  // Phi and y into the padded layout
+  const cudaMemcpyKind kin = kind_in(on_device);
+  int64_t src_row = 0;
+  for (int t = 0; t < c->T; ++t) {
+    CKC(cudaMemcpy2DAsync(c->phi + c->hrow[t] * Dp, sizeof(float) * Dp, Phi + src_row * c->D,
+                          sizeof(float) * c->D, sizeof(float) * c->D, (size_t)c->hN[t], kin,
+                          c->stream));
+    CKC(cudaMemcpyAsync(c->y + c->hrow[t], y + src_row, sizeof(float) * c->hN[t], kin, c->stream));
+    src_row += c->hN[t];
+  }
+  std::vector<int> ttask((size_t)ntiles);
+  for (int t = 0; t < c->T; ++t)
+    for (int64_t g = c->hrow[t] / 128; g < c->hrow[t + 1] / 128; ++g) ttask[(size_t)g] = t;
+  std::vector<double> lpi((size_t)C);
+  for (int k = 0; k < C; ++k) lpi[(size_t)k] = log(c->hpi[k]);
+  CKC(cudaMemcpyAsync(c->drow, c->hrow, sizeof(int64_t) * (T + 1), cudaMemcpyHostToDevice, c->stream));
+  CKC(cudaMemcpyAsync(c->dN, c->hN, sizeof(int64_t) * T, cudaMemcpyHostToDevice, c->stream));
+  CKC(cudaMemcpyAsync(c->tile_task, ttask.data(), sizeof(int) * ntiles, cudaMemcpyHostToDevice, c->stream));
+  CKC(cudaMemcpyAsync(c->logpi, lpi.data(), sizeof(double) * C, cudaMemcpyHostToDevice, c->stream));
+  CKC(launch_b0(c));
+  CKC(launch_alpha_init(c));
+  CKC(launch_sumlogalpha(c));
+  CKC(launch_tconst_dev(c, c->dN));
+  if (c->precision == CMCS_BF16_REFINE) {
+    if (tc_create(c) != 0) {
+      if (c->err[0] == 0) set_err(c, "BF16 tensor-core operator unavailable");
+      return fail(CMCS_ERR_UNSUPPORTED);
+    }
+  }
+  CKC(cudaStreamSynchronize(c->stream));
+  CKC(cudaGetLastError());
+#undef CKC
+  *out = h;
+  return st;
+}
+
+void cmcs_destroy(cmcs_ctx* h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->c.stream);
+  free_ctx(&h->c);
+  free(h);
+}
+
+const char* cmcs_last_error(const cmcs_ctx* h) { return h ? h->c.err : g_create_err; }
+
+cmcs_status cmcs_set_alpha(cmcs_ctx* h, const float* alpha, int on_device, int64_t em_iter) {
+  if (!h || !alpha || (on_device != 0 && on_device != 1) || em_iter < 0) return CMCS_ERR_INVALID_ARG;
+  Ctx* c = &h->c;
+  std::vector<float> tmp((size_t)c->C * c->D);
+  if (on_device) {
+    CK(cudaMemcpy(tmp.data(), alpha, sizeof(float) * tmp.size(), cudaMemcpyDeviceToHost));
+  } else {
+    memcpy(tmp.data(), alpha, sizeof(float) * tmp.size());
+  }
+  for (float v : tmp)
+    if (!(v > 0.f) || !isfinite(v)) {
+      set_err(c, "alpha must be positive and finite");
+      return CMCS_ERR_INVALID_ARG;
+    }
+  CK(cudaMemcpy2DAsync(c->alpha, sizeof(float) * c->Dp, tmp.data(), sizeof(float) * c->D,
+                       sizeof(float) * c->D, (size_t)c->C, cudaMemcpyHostToDevice, c->stream));
+  CK(launch_sumlogalpha(c));
+  c->em_iter = em_iter;
+  return sync_check(c);
+}
+
+cmcs_status cmcs_estep(cmcs_ctx* h) {
+  if (!h) return CMCS_ERR_INVALID_ARG;
+  Ctx* c = &h->c;
+  cmcs_status s = estep(c);
+  if (s != CMCS_OK) return s;
+  return sync_check(c);
+}
+
+cmcs_status cmcs_em_iter(cmcs_ctx* h, int n) {
+  if (!h || n < 0) return CMCS_ERR_INVALID_ARG;
+  Ctx* c = &h->c;
+  for (int i = 0; i < n; ++i) {
+    cmcs_status s = estep(c);
+    if (s != CMCS_OK) return s;
+    CK(launch_mstep(c));
+    CK(launch_sumlogalpha(c));
+    c->em_iter++;
+  }
+  return sync_check(c);
+}
+
+cmcs_status cmcs_read(const cmcs_ctx* hc, int what, void* dst, int on_device) {
+  if (!hc || !dst || (on_device != 0 && on_device != 1)) return CMCS_ERR_INVALID_ARG;
+  Ctx* c = const_cast<Ctx*>(&hc->c);
+  const cudaMemcpyKind k = kind_out(on_device);
+  const size_t D = c->D, Dp = c->Dp, T = c->T, C = c->C, K = c->K;
+  switch (what) {
+    case CMCS_OUT_MU:
+      CK(cudaMemcpy2DAsync(dst, sizeof(float) * D, c->xacc, sizeof(float) * Dp * (K + 1),
+                           sizeof(float) * D, T * C, k, c->stream));
+      break;
+    case CMCS_OUT_S:
+      CK(cudaMemcpy2DAsync(dst, sizeof(float) * D, c->sest, sizeof(float) * Dp, sizeof(float) * D,
+                           T * C, k, c->stream));
+      break;
+    case CMCS_OUT_Q:
+      CK(cudaMemcpyAsync(dst, c->q, sizeof(double) * T * C, k, c->stream));
+      break;
+    case CMCS_OUT_LOGDET:
+      CK(cudaMemcpyAsync(dst, c->logdet, sizeof(double) * T * C, k, c->stream));
+      break;
+    case CMCS_OUT_ELL:
+      CK(cudaMemcpyAsync(dst, c->ell, sizeof(double) * T * C, k, c->stream));
+      break;
+    case CMCS_OUT_ALPHA:
+      CK(cudaMemcpy2DAsync(dst, sizeof(float) * D, c->alpha, sizeof(float) * Dp, sizeof(float) * D,
+                           C, k, c->stream));
+      break;
+    case CMCS_OUT_ASSIGN:
+      CK(cudaMemcpyAsync(dst, c->assign, sizeof(int) * T, k, c->stream));
+      break;
+    case CMCS_OUT_RECON: {
+      std::vector<int> a(T);
+      CK(cudaMemcpyAsync(a.data(), c->assign, sizeof(int) * T, cudaMemcpyDeviceToHost, c->stream));
+      CK(cudaStreamSynchronize(c->stream));
+      for (size_t t = 0; t < T; ++t)
+        CK(cudaMemcpyAsync(static_cast<float*>(dst) + t * D,
+                           c->xacc + (t * c->R + (size_t)a[t] * (K + 1)) * Dp, sizeof(float) * D,
+                           k, c->stream));
+      break;
+    }
+    case CMCS_OUT_STEPS:
+      CK(cudaMemcpyAsync(dst, c->steps0, sizeof(int) * c->S, k, c->stream));
+      break;
+    case CMCS_OUT_GAMMA:
+      CK(cudaMemcpyAsync(dst, c->gam, sizeof(float) * T * C * K * c->U, k, c->stream));
+      break;
+    case CMCS_OUT_XI:
+      CK(cudaMemcpyAsync(dst, c->xi, sizeof(float) * T * C * K * c->U, k, c->stream));
+      break;
+    case CMCS_OUT_B0:
+      CK(cudaMemcpy2DAsync(dst, sizeof(float) * D, c->b0hi, sizeof(float) * Dp, sizeof(float) * D,
+                           T, k, c->stream));
+      break;
+    case CMCS_OUT_SWEEPS:
+      CK(cudaMemcpyAsync(dst, c->sweeps, sizeof(int) * c->S, k, c->stream));
+      break;
+    default:
+      set_err(c, "unknown output %d", what);
+      return CMCS_ERR_INVALID_ARG;
+  }
+  return sync_check(c);
+}
+
+cmcs_status cmcs_result(const cmcs_ctx* hc, cmcs_summary* out) {
+  if (!hc || !out) return CMCS_ERR_INVALID_ARG;
+  Ctx* c = const_cast<Ctx*>(&hc->c);
+  std::vector<int> st(c->S), sw(c->S);
+  std::vector<float> rel(c->S);
+  double stats[4];
+  CK(cudaMemcpyAsync(st.data(), c->steps0, sizeof(int) * c->S, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(sw.data(), c->sweeps, sizeof(int) * c->S, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(rel.data(), c->rrel, sizeof(float) * c->S, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(stats, c->stats, sizeof(double) * 4, cudaMemcpyDeviceToHost, c->stream));
+  cmcs_status s = sync_check(c);
+  if (s != CMCS_OK) return s;
+  memset(out, 0, sizeof(*out));
+  out->em_iters_done = c->em_iter;
+  out->loglik = stats[0];
+  out->min_margin = stats[1];
+  double sum = 0.0;
+  for (int i = 0; i < c->S; ++i) {
+    out->cg_steps_max = st[i] > out->cg_steps_max ? st[i] : out->cg_steps_max;
+    sum += st[i];
+    if (st[i] >= c->U) out->cg_capped++;
+    out->refine_sweeps_max = sw[i] > out->refine_sweeps_max ? sw[i] : out->refine_sweeps_max;
+    out->refine_rel_max = rel[i] > out->refine_rel_max ? rel[i] : out->refine_rel_max;
+  }
+  out->cg_steps_mean = sum / c->S;
+  out->operator_applies = c->op_applies;
+  return CMCS_OK;
+}
+
+cmcs_status cmcs_apply(cmcs_ctx* h, const float* V, float* Z, int on_device, int accurate) {
+  if (!h || !V || !Z || (on_device != 0 && on_device != 1) || (accurate != 0 && accurate != 1))
+    return CMCS_ERR_INVALID_ARG;
+  Ctx* c = &h->c;
+  const size_t D = c->D, Dp = c->Dp, S = c->S;
+  const cudaMemcpyKind kin = kind_in(on_device), kout = kind_out(on_device);
+  CK(cudaMemsetAsync(c->x, 0, sizeof(float) * S * Dp, c->stream));
+  CK(cudaMemcpy2DAsync(c->x, sizeof(float) * Dp, V, sizeof(float) * D, sizeof(float) * D, S, kin,
+                       c->stream));
+  if (!accurate) {
+    CK(launch_operator(c, c->x, c->ad, 0));
+  } else {
+    CK(cudaMemsetAsync(c->d, 0, sizeof(float) * S * Dp, c->stream));
+    CK(cudaMemcpy2DAsync(c->d, sizeof(float) * Dp, Z, sizeof(float) * D, sizeof(float) * D, S, kin,
+                         c->stream));
+    CK(launch_residual(c, c->x, c->d, c->ad));
+  }
+  CK(cudaMemcpy2DAsync(Z, sizeof(float) * D, c->ad, sizeof(float) * Dp, sizeof(float) * D, S, kout,
+                       c->stream));
+  return sync_check(c);
+}
+
+cmcs_status cmcs_probes(const cmcs_ctx* hc, int64_t em_iter, float* dst, int on_device) {
+  if (!hc || !dst || (on_device != 0 && on_device != 1) || em_iter < 0) return CMCS_ERR_INVALID_ARG;
+  Ctx* c = const_cast<Ctx*>(&hc->c);
+  const size_t n = (size_t)c->T * c->C * c->K * c->D;
+  if (on_device) {
+    CK(launch_probes_out(c, em_iter, dst));
+  } else {
+    CK(launch_probes_out(c, em_iter, c->ad));
+    CK(cudaMemcpyAsync(dst, c->ad, sizeof(float) * n, cudaMemcpyDeviceToHost, c->stream));
+  }
+  return sync_check(c);
+}
+
+cmcs_status cmcs_lanczos_quadrature(const float* gamma, const float* xi, const int32_t* steps,
+                                    int nsys, int ld, double* out, int32_t* status,
+                                    void* stream) {
+  if (!gamma || !xi || !steps || !out || !status || nsys < 0 || ld < 1 || ld > 512) {
+    set_err(nullptr, "invalid argument to cmcs_lanczos_quadrature");
+    return CMCS_ERR_INVALID_ARG;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = launch_quadrature(gamma, xi, steps, nsys, ld, out, status, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    set_err(nullptr, "CUDA error: %s", cudaGetErrorString(e));
+    return CMCS_ERR_CUDA;
+  }
+  return CMCS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,153 @@
+// Internal declarations shared by the translation units of libcmcs.so.
+//
+// Device memory layout (all owned by the context, sizes for the plain-scale workload
+// T=32, C=4, D=8192, N=2048, K=32 in brackets):
+//   D_pad  = D rounded up to 128; padded coordinates carry alpha = 1, zero Phi columns, zero
+//            right-hand sides and zero probes, so they never enter a Krylov space.
+//   Np_t   = N_t rounded up to 128; padded rows of Phi_t and y_t are zero (Phi^T Phi and
+//            Phi^T y are unchanged).
+//   phi    float [sum_t Np_t][D_pad]              Phi, row-major          [2 GiB]
+//   R      = C*(K+1) right-hand sides per task; system sys = t*R + j, j = c*(K+1) + k,
+//            k = 0 the posterior-mean system, k >= 1 the probe p_{t,c,k}.
+//   S      = T*R systems                                                   [4224]
+//   x, r, d, ad, xacc  float [S][D_pad]  CG state of Alg. 1 and the refined solution
+//   w, wlo float [sum_t R*Np_t]           Phi V (and its low part for the residual)
+//   b0hi, b0lo float [T][D_pad]           beta Phi^T y as an unevaluated sum hi + lo
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/cmcs.h"
+
+namespace cmcs {
+
+constexpr int kDAlign = 128;      // padding of D
+constexpr int kNAlign = 128;      // padding of N_t
+constexpr int kUpdThreads = 256;  // threads of the per-system CG kernels
+
+// ---- Philox-4x32-10 (Salmon et al., SC'11, Sec. 5) ------------------------------------
+struct U4 { uint32_t x, y, z, w; };
+
+__host__ __device__ inline U4 philox4x32_10(U4 c, uint32_t k0, uint32_t k1) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+  for (int i = 0; i < 10; ++i) {
+    uint64_t p0 = (uint64_t)M0 * c.x;
+    uint64_t p1 = (uint64_t)M1 * c.z;
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    c = U4{hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0};
+    k0 += W0;
+    k1 += W1;
+  }
+  return c;
+}
+
+__host__ __device__ inline uint32_t pick_word(const U4& w, int i) {
+  return i == 0 ? w.x : (i == 1 ? w.y : (i == 2 ? w.z : w.w));
+}
+
+// Probe counter: (d >> 7, k, t*C + c, (em_iter << 4) | 1); sign from bit d & 31 of word
+// (d >> 5) & 3; bit 0 -> +1.  k is 0-based (probe k+1 of the paper).
+constexpr uint32_t kTagProbe = 1u;
+constexpr uint32_t kTagAlpha = 2u;
+
+__device__ inline uint32_t probe_bits32(uint64_t seed, int64_t em_iter, int t, int c, int C,
+                                        int k, int d_base /* multiple of 32 */) {
+  U4 ctr{(uint32_t)(d_base >> 7), (uint32_t)k, (uint32_t)(t * C + c),
+         (uint32_t)(((uint64_t)em_iter << 4) | kTagProbe)};
+  U4 w = philox4x32_10(ctr, (uint32_t)seed, (uint32_t)(seed >> 32));
+  return pick_word(w, (d_base >> 5) & 3);
+}
+
+// ---- context --------------------------------------------------------------------------
+struct Ctx {
+  // configuration
+  int T, C, D, K, R, S, Dp, U;    // U = cg_max_iter
+  double beta, cg_tol, refine_tol, alpha_min, alpha_max;
+  int precision, refine_max;
+  uint64_t seed;
+  int64_t em_iter;
+  cudaStream_t stream;
+  int device;
+  int sm_count;
+
+  // host copies
+  int64_t* hN;       // [T]
+  int64_t* hNp;      // [T]
+  int64_t* hrow;     // [T+1] padded row offsets
+  double* hpi;       // [C]
+  int64_t rows_total;
+
+  // device buffers
+  float* phi;        // [rows_total][Dp]
+  float* y;          // [rows_total]
+  int64_t* drow;     // [T+1]
+  int64_t* dN;       // [T] unpadded N_t
+  int* tile_task;    // [rows_total / 128] task owning each 128-row tile of phi
+  int tn_plain, tn_ds; // operator tile widths (0: chosen from R)
+  float *b0hi, *b0lo;  // [T][Dp]
+  float* alpha;        // [C][Dp]
+  double* sumlogalpha; // [C]
+  double* logpi;       // [C]
+  double* tconst;      // [T]  (N_t log 2pi - N_t log beta + beta ||y_t||^2) / 2
+  float *x, *r, *d, *ad, *xacc;  // [S][Dp]
+  float *w, *wlo;      // [R * rows_total]
+  float* part;         // [Dp/128][S] partial d^T A d per 128-coordinate tile
+  float *rr, *bb;      // [S]
+  int* steps;          // [S] CG steps of the current solve
+  int* steps0;         // [S] CG steps of the first solve (Lanczos)
+  int* active;         // [S]
+  int* ractive;        // [S] still refining
+  int* sweeps;         // [S]
+  float* rrel;         // [S] last ||delta|| / ||x||
+  int* task_active;    // [T]
+  int* counters;       // [4]: 0 active systems, 1 refine-active systems, 2 status flags
+  int* hcounters;      // pinned host mirror [4]
+  float *gam, *xi;     // [T*C*K][U]
+  int* psteps;         // [T*C*K] CG steps of the probe systems' first solve
+  float* sest;         // [T][C][Dp]
+  double* quad;        // [T*C*K]
+  double *logdet, *ell, *q;  // [T][C]
+  int* assign;         // [T]
+  double* stats;       // [4]: 0 loglik, 1 min margin
+  int64_t op_applies;
+
+  // BF16 tensor-core operator (precision 1); null otherwise
+  void* tc;
+
+  char err[512];
+};
+
+// ---- kernels launched from the API unit -------------------------------------------------
+cudaError_t launch_b0(Ctx* c);
+cudaError_t launch_alpha_init(Ctx* c);
+cudaError_t launch_sumlogalpha(Ctx* c);
+cudaError_t launch_tconst_dev(Ctx* c, const int64_t* dN);
+cudaError_t launch_probes_out(const Ctx* c, int64_t em_iter, float* dst);
+// CG (kernels_cg.cu)
+cudaError_t launch_cg_init(Ctx* c, int mode /*0 first solve, 1 refinement*/);
+cudaError_t launch_cg_update(Ctx* c, int record);
+cudaError_t launch_refine_update(Ctx* c);
+cudaError_t launch_sest(Ctx* c);
+// operator (kernels_op.cu): AD = A D for all active tasks
+cudaError_t launch_operator(Ctx* c, const float* V, float* Z, int with_dots);
+// accurate residual: r = B - A xacc, B = b0 (k = 0) or the probe (k >= 1) when Bext == null
+cudaError_t launch_residual(Ctx* c, const float* X, const float* Bext, float* Rout);
+// E-step tail and M-step (kernels_estep.cu)
+cudaError_t launch_quadrature(const float* gam, const float* xi, const int* steps, int nsys,
+                              int ld, double* out, int* status, cudaStream_t st);
+cudaError_t launch_quadrature_ctx(Ctx* c);
+cudaError_t launch_ell_softmax(Ctx* c);
+cudaError_t launch_mstep(Ctx* c);
+
+// tensor-core operator hooks (kernels_tc.cu)
+int tc_create(Ctx* c);      // returns 0 on success
+void tc_destroy(Ctx* c);
+cudaError_t tc_operator(Ctx* c, const float* V, float* Z);
+
+inline int64_t round_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
+
+}  // namespace cmcs

@@ -1,0 +1,372 @@
+// Batched conjugate gradient (Alg. 1) over all S = T*C*(K+1) systems, the diagonal estimator
+// (Eq. 4) and the set-up kernels (b0 = beta Phi^T y, alpha ~ Uniform(0,1), probes).
+//
+// One CTA of 256 threads owns one system for the vector updates, so both inner products of a
+// CG step (d^T A d and r^T r) reduce inside the CTA: no grid-wide barrier or spin-wait exists.
+// d^T A d arrives as per-tile partials from the operator epilogue and is summed in a fixed
+// order; every reduction has a fixed tree order, so results are run-to-run deterministic.
+// Converged systems are masked (their CTA returns at once) and a task whose systems have all
+// converged is skipped by the operator.
+#include <math.h>
+
+#include "cmcs_internal.cuh"
+
+namespace cmcs {
+
+namespace {
+
+// fixed-order block sum over 256 threads (warp xor-tree, then warp 0 over the 8 warp sums)
+template <typename Tv>
+__device__ __forceinline__ Tv block_sum(Tv v, Tv* sh) {
+#pragma unroll
+  for (int m = 16; m > 0; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  Tv tot = 0;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) tot += sh[i];
+    sh[32] = tot;
+  }
+  __syncthreads();
+  return sh[32];
+}
+
+__device__ __forceinline__ float4 probe4(uint64_t seed, int64_t em, int t, int c, int C, int k0,
+                                         int d, int D) {
+  const uint32_t bits = probe_bits32(seed, em, t, c, C, k0, d & ~31);
+  const int sh = d & 31;
+  float v[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) v[e] = (d + e < D) ? (((bits >> (sh + e)) & 1u) ? -1.f : 1.f) : 0.f;
+  return make_float4(v[0], v[1], v[2], v[3]);
+}
+
+}  // namespace
+
+// ---- CG initialisation: x_1 = 0, r_1 = d_1 = b (Alg. 1, first line) ---------------------
+// mode 0: b = b0_t (k = 0) or the probe p_{t,c,k} (k >= 1); mode 1: b = the residual
+// already in r (refinement), systems no longer refining have r = 0.
+__global__ void __launch_bounds__(256)
+k_cg_init(int mode, float* __restrict__ x, float* __restrict__ r, float* __restrict__ d,
+          const float* __restrict__ b0hi, float* rr, float* bb, int* steps, int* active,
+          int* ractive, int* sweeps, float* rrel, int* task_active, int* counters, int R,
+          int K, int C, int Dp, int D, uint64_t seed, int64_t em_iter, int refine) {
+  __shared__ float sh[33];
+  const int64_t sys = blockIdx.x;
+  const int t = (int)(sys / R), j = (int)(sys % R), c = j / (K + 1), k = j % (K + 1);
+  float* xs = x + sys * Dp;
+  float* rs = r + sys * Dp;
+  float* ds = d + sys * Dp;
+  float acc = 0.f;
+  for (int i = threadIdx.x * 4; i < Dp; i += 256 * 4) {
+    float4 b;
+    if (mode == 0) {
+      b = (k == 0) ? *reinterpret_cast<const float4*>(b0hi + (int64_t)t * Dp + i)
+                   : probe4(seed, em_iter, t, c, C, k - 1, i, D);
+      *reinterpret_cast<float4*>(rs + i) = b;
+    } else {
+      b = *reinterpret_cast<const float4*>(rs + i);
+    }
+    *reinterpret_cast<float4*>(xs + i) = make_float4(0.f, 0.f, 0.f, 0.f);
+    *reinterpret_cast<float4*>(ds + i) = b;
+    acc = fmaf(b.x, b.x, acc);
+    acc = fmaf(b.y, b.y, acc);
+    acc = fmaf(b.z, b.z, acc);
+    acc = fmaf(b.w, b.w, acc);
+  }
+  const float rr0 = block_sum(acc, sh);
+  if (threadIdx.x == 0) {
+    rr[sys] = rr0;
+    bb[sys] = rr0;
+    steps[sys] = 0;
+    if (mode == 0) {
+      ractive[sys] = refine;
+      sweeps[sys] = 0;
+      rrel[sys] = 0.f;
+    }
+    const int on = (rr0 > 0.f) && (mode == 0 || ractive[sys] != 0);
+    active[sys] = on;
+    if (on) {
+      atomicAdd(&task_active[t], 1);
+      atomicAdd(&counters[0], 1);
+    }
+  }
+}
+
+// ---- one CG step after the operator has produced ad = A d (Alg. 1, loop body) ----------
+__global__ void __launch_bounds__(256)
+k_cg_update(float* __restrict__ x, float* __restrict__ r, float* __restrict__ d,
+            const float* __restrict__ ad, const float* __restrict__ part, int ndt, float* rr,
+            const float* bb, int* steps, int* active, int* task_active, int* counters,
+            float* gam, float* xih, int* psteps, int record, int R, int K, int C, int Dp, int S,
+            int U, float tol2) {
+  __shared__ float sh[33];
+  __shared__ float s_dad;
+  const int64_t sys = blockIdx.x;
+  if (active[sys] == 0) return;
+  const int t = (int)(sys / R), j = (int)(sys % R);
+  if (threadIdx.x < 32) {
+    float v = 0.f;
+    for (int q = threadIdx.x; q < ndt; q += 32) v += part[(int64_t)q * S + sys];
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
+    if (threadIdx.x == 0) s_dad = v;
+  }
+  __syncthreads();
+  const float dad = s_dad;
+  const float rr0 = rr[sys];
+  if (!(dad > 0.f) || !isfinite(dad)) {            // breakdown: stop this system
+    if (threadIdx.x == 0) {
+      active[sys] = 0;
+      atomicSub(&task_active[t], 1);
+      atomicSub(&counters[0], 1);
+      if (!isfinite(dad)) atomicOr(&counters[2], 1);
+    }
+    return;
+  }
+  const float g = rr0 / dad;                       // gamma_u
+  float* xs = x + sys * Dp;
+  float* rs = r + sys * Dp;
+  float* ds = d + sys * Dp;
+  const float* as = ad + sys * Dp;
+  float acc = 0.f;
+  for (int i = threadIdx.x * 4; i < Dp; i += 256 * 4) {
+    float4 xv = *reinterpret_cast<float4*>(xs + i);
+    float4 rv = *reinterpret_cast<float4*>(rs + i);
+    const float4 dv = *reinterpret_cast<const float4*>(ds + i);
+    const float4 av = *reinterpret_cast<const float4*>(as + i);
+    xv.x = fmaf(g, dv.x, xv.x); xv.y = fmaf(g, dv.y, xv.y);
+    xv.z = fmaf(g, dv.z, xv.z); xv.w = fmaf(g, dv.w, xv.w);
+    rv.x = fmaf(-g, av.x, rv.x); rv.y = fmaf(-g, av.y, rv.y);
+    rv.z = fmaf(-g, av.z, rv.z); rv.w = fmaf(-g, av.w, rv.w);
+    *reinterpret_cast<float4*>(xs + i) = xv;
+    *reinterpret_cast<float4*>(rs + i) = rv;
+    acc = fmaf(rv.x, rv.x, acc);
+    acc = fmaf(rv.y, rv.y, acc);
+    acc = fmaf(rv.z, rv.z, acc);
+    acc = fmaf(rv.w, rv.w, acc);
+  }
+  const float rr1 = block_sum(acc, sh);            // r_{u+1}^T r_{u+1}
+  const float xi = rr1 / rr0;                      // xi_u
+  for (int i = threadIdx.x * 4; i < Dp; i += 256 * 4) {
+    const float4 rv = *reinterpret_cast<const float4*>(rs + i);
+    float4 dv = *reinterpret_cast<float4*>(ds + i);
+    dv.x = fmaf(xi, dv.x, rv.x); dv.y = fmaf(xi, dv.y, rv.y);
+    dv.z = fmaf(xi, dv.z, rv.z); dv.w = fmaf(xi, dv.w, rv.w);
+    *reinterpret_cast<float4*>(ds + i) = dv;
+  }
+  if (threadIdx.x == 0) {
+    const int u = steps[sys];
+    const int c = j / (K + 1), k = j % (K + 1);
+    if (record && k > 0) {
+      const int64_t pidx = ((int64_t)t * C + c) * K + (k - 1);
+      gam[pidx * U + u] = g;
+      xih[pidx * U + u] = xi;
+      psteps[pidx] = u + 1;
+    }
+    steps[sys] = u + 1;
+    rr[sys] = rr1;
+    if (!isfinite(rr1)) atomicOr(&counters[2], 1);
+    const bool done = (rr1 <= tol2 * bb[sys]) || (rr1 == 0.f) || (u + 1 >= U) || !isfinite(rr1);
+    if (done) {
+      active[sys] = 0;
+      atomicSub(&task_active[t], 1);
+      atomicSub(&counters[0], 1);
+    }
+  }
+}
+
+// ---- refinement: xacc += delta; stop once ||delta|| <= refine_tol ||xacc|| -------------
+__global__ void __launch_bounds__(256)
+k_refine_update(float* __restrict__ xacc, const float* __restrict__ delta, int* ractive,
+                int* sweeps, float* rrel, int* counters, int Dp, float rtol) {
+  __shared__ float sh[33];
+  const int64_t sys = blockIdx.x;
+  if (ractive[sys] == 0) return;
+  float* xa = xacc + sys * Dp;
+  const float* de = delta + sys * Dp;
+  float a1 = 0.f, a2 = 0.f;
+  for (int i = threadIdx.x * 4; i < Dp; i += 256 * 4) {
+    float4 xv = *reinterpret_cast<float4*>(xa + i);
+    const float4 dv = *reinterpret_cast<const float4*>(de + i);
+    xv.x += dv.x; xv.y += dv.y; xv.z += dv.z; xv.w += dv.w;
+    *reinterpret_cast<float4*>(xa + i) = xv;
+    a1 += dv.x * dv.x + dv.y * dv.y + dv.z * dv.z + dv.w * dv.w;
+    a2 += xv.x * xv.x + xv.y * xv.y + xv.z * xv.z + xv.w * xv.w;
+  }
+  const float dn2 = block_sum(a1, sh);
+  const float xn2 = block_sum(a2, sh);
+  if (threadIdx.x == 0) {
+    sweeps[sys] += 1;
+    const float rel = xn2 > 0.f ? sqrtf(dn2 / xn2) : 0.f;
+    rrel[sys] = rel;
+    if (rel <= rtol || !(xn2 > 0.f)) {
+      ractive[sys] = 0;
+    } else {
+      atomicAdd(&counters[1], 1);
+    }
+  }
+}
+
+// ---- diagonal estimator s_tc = (1/K) sum_k p_k * x_k (Eq. 4) ----------------------------
+__global__ void __launch_bounds__(128)
+k_sest(const float* __restrict__ xacc, float* __restrict__ sest, int R, int K, int C, int Dp,
+       int D, uint64_t seed, int64_t em_iter) {
+  const int tc = blockIdx.y;
+  const int t = tc / C, c = tc % C;
+  const int i = (blockIdx.x * 128 + threadIdx.x) * 4;
+  if (i >= Dp) return;
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  const int64_t base = ((int64_t)t * R + (int64_t)c * (K + 1)) * Dp;
+  for (int k = 1; k <= K; ++k) {
+    const float4 p = probe4(seed, em_iter, t, c, C, k - 1, i, D);
+    const float4 xv = *reinterpret_cast<const float4*>(xacc + base + (int64_t)k * Dp + i);
+    acc.x = fmaf(p.x, xv.x, acc.x);
+    acc.y = fmaf(p.y, xv.y, acc.y);
+    acc.z = fmaf(p.z, xv.z, acc.z);
+    acc.w = fmaf(p.w, xv.w, acc.w);
+  }
+  const float inv = 1.0f / (float)K;
+  *reinterpret_cast<float4*>(sest + (int64_t)tc * Dp + i) =
+      make_float4(acc.x * inv, acc.y * inv, acc.z * inv, acc.w * inv);
+}
+
+// ---- b0_t = beta Phi_t^T y_t, kept as hi + lo (compensated sum, then FP64 scaling) ------
+__global__ void __launch_bounds__(128)
+k_b0(const float* __restrict__ phi, const float* __restrict__ y, const int64_t* drow,
+     float* b0hi, float* b0lo, int Dp, double beta) {
+  const int t = blockIdx.y;
+  const int d = blockIdx.x * 128 + threadIdx.x;
+  if (d >= Dp) return;
+  float hi = 0.f, lo = 0.f;
+  for (int64_t n = drow[t]; n < drow[t + 1]; ++n) {
+    const float a = phi[n * Dp + d], b = y[n];
+    const float p = __fmul_rn(a, b);
+    const float e = __fmaf_rn(a, b, -p);
+    const float s = __fadd_rn(hi, p);
+    const float bv = __fsub_rn(s, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bv)), __fsub_rn(p, bv));
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(err, e));
+  }
+  const double v = beta * ((double)hi + (double)lo);
+  const float vh = (float)v;
+  b0hi[(int64_t)t * Dp + d] = vh;
+  b0lo[(int64_t)t * Dp + d] = (float)(v - (double)vh);
+}
+
+// ---- alpha_c ~ Uniform(0,1) (Alg. 2, first step); padded coordinates get 1 ---------------
+__global__ void k_alpha_init(float* alpha, int Dp, int D, uint64_t seed) {
+  const int c = blockIdx.y;
+  const int d = blockIdx.x * 256 + threadIdx.x;
+  if (d >= Dp) return;
+  float v = 1.0f;
+  if (d < D) {
+    U4 ctr{(uint32_t)(d >> 2), (uint32_t)c, 0u, kTagAlpha};
+    const U4 w = philox4x32_10(ctr, (uint32_t)seed, (uint32_t)(seed >> 32));
+    const uint32_t word = pick_word(w, d & 3);
+    v = ((float)(word >> 9) + 0.5f) * 1.1920928955078125e-07f;   // 2^-23
+  }
+  alpha[(int64_t)c * Dp + d] = v;
+}
+
+// ---- sum_d log alpha_cd in FP64 (Eq. 3) ---------------------------------------------------
+__global__ void __launch_bounds__(256)
+k_sumlogalpha(const float* alpha, double* out, int Dp, int D) {
+  __shared__ double sh[33];
+  const int c = blockIdx.x;
+  double acc = 0.0;
+  for (int d = threadIdx.x; d < D; d += 256) acc += log((double)alpha[(int64_t)c * Dp + d]);
+  const double tot = block_sum(acc, sh);
+  if (threadIdx.x == 0) out[c] = tot;
+}
+
+// ---- per-task constant of log p(y_t | alpha_c) = ell/2 - const_t -------------------------
+__global__ void __launch_bounds__(256)
+k_tconst(const float* y, const int64_t* drow, const int64_t* Nt, double* out, double beta) {
+  __shared__ double sh[33];
+  const int t = blockIdx.x;
+  double acc = 0.0;
+  for (int64_t n = drow[t] + threadIdx.x; n < drow[t + 1]; n += 256) acc += (double)y[n] * (double)y[n];
+  const double yy = block_sum(acc, sh);
+  if (threadIdx.x == 0) {
+    const double N = (double)Nt[t];
+    out[t] = 0.5 * (N * 1.8378770664093453 - N * log(beta) + beta * yy);   // log(2 pi)
+  }
+}
+
+// ---- probes as +-1 floats [T][C][K][D] ----------------------------------------------------
+__global__ void k_probes_out(float* dst, int T, int C, int K, int D, uint64_t seed,
+                             int64_t em_iter) {
+  const int64_t tck = blockIdx.y;
+  const int k = (int)(tck % K);
+  const int c = (int)((tck / K) % C);
+  const int t = (int)(tck / ((int64_t)K * C));
+  const int d = blockIdx.x * 256 + threadIdx.x;
+  if (d >= D) return;
+  const uint32_t bits = probe_bits32(seed, em_iter, t, c, C, k, d & ~31);
+  dst[tck * D + d] = ((bits >> (d & 31)) & 1u) ? -1.f : 1.f;
+}
+
+// --------------------------------------------------------------------------------------
+cudaError_t launch_cg_init(Ctx* c, int mode) {
+  k_cg_init<<<c->S, 256, 0, c->stream>>>(mode, c->x, c->r, c->d, c->b0hi, c->rr, c->bb,
+                                         c->steps, c->active, c->ractive, c->sweeps, c->rrel,
+                                         c->task_active, c->counters, c->R, c->K, c->C, c->Dp,
+                                         c->D, c->seed, c->em_iter, c->refine_max > 0 ? 1 : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cg_update(Ctx* c, int record) {
+  const float tol2 = (float)(c->cg_tol * c->cg_tol);
+  k_cg_update<<<c->S, 256, 0, c->stream>>>(c->x, c->r, c->d, c->ad, c->part, c->Dp / 128,
+                                           c->rr, c->bb, c->steps, c->active, c->task_active,
+                                           c->counters, c->gam, c->xi, c->psteps, record, c->R,
+                                           c->K, c->C, c->Dp, c->S, c->U, tol2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_refine_update(Ctx* c) {
+  k_refine_update<<<c->S, 256, 0, c->stream>>>(c->xacc, c->x, c->ractive, c->sweeps, c->rrel,
+                                               c->counters, c->Dp, (float)c->refine_tol);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sest(Ctx* c) {
+  dim3 grid((c->Dp / 4 + 127) / 128, c->T * c->C);
+  k_sest<<<grid, 128, 0, c->stream>>>(c->xacc, c->sest, c->R, c->K, c->C, c->Dp, c->D, c->seed,
+                                      c->em_iter);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_b0(Ctx* c) {
+  dim3 grid(c->Dp / 128, c->T);
+  k_b0<<<grid, 128, 0, c->stream>>>(c->phi, c->y, c->drow, c->b0hi, c->b0lo, c->Dp, c->beta);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_alpha_init(Ctx* c) {
+  dim3 grid((c->Dp + 255) / 256, c->C);
+  k_alpha_init<<<grid, 256, 0, c->stream>>>(c->alpha, c->Dp, c->D, c->seed);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sumlogalpha(Ctx* c) {
+  k_sumlogalpha<<<c->C, 256, 0, c->stream>>>(c->alpha, c->sumlogalpha, c->Dp, c->D);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tconst_dev(Ctx* c, const int64_t* dN) {
+  k_tconst<<<c->T, 256, 0, c->stream>>>(c->y, c->drow, dN, c->tconst, c->beta);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_probes_out(const Ctx* c, int64_t em_iter, float* dst) {
+  dim3 grid((c->D + 255) / 256, (unsigned)((int64_t)c->T * c->C * c->K));
+  k_probes_out<<<grid, 256, 0, c->stream>>>(dst, c->T, c->C, c->K, c->D, c->seed, em_iter);
+  return cudaGetLastError();
+}
+
+}  // namespace cmcs

@@ -1,0 +1,246 @@
+// E-step tail and M-step: Lanczos log quadrature (Eqs. 9-11), ell (Eq. 3), responsibilities
+// by an FP64 log-sum-exp (Eq. 3), hard assignments (Alg. 2), and the alpha update (Eq. 5).
+#include <float.h>
+#include <math.h>
+
+#include "cmcs_internal.cuh"
+
+namespace cmcs {
+
+namespace {
+
+template <typename Tv>
+__device__ __forceinline__ Tv block_sum256(Tv v, Tv* sh) {
+#pragma unroll
+  for (int m = 16; m > 0; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    Tv tot = 0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) tot += sh[i];
+    sh[32] = tot;
+  }
+  __syncthreads();
+  return sh[32];
+}
+
+// Eigenvalues lambda_u and first eigenvector components S_{u,1} of the U x U Lanczos matrix
+// of Eq. 9, by implicit-shift symmetric QR steps with the Wilkinson shift on the trailing
+// unreduced block (Golub & Van Loan, "Matrix Computations", Sec. 8.3), accumulating only the
+// first row of the rotation product (the Golub-Welsch observation).  Returns
+// sum_u S_{u,1}^2 log lambda_u; sets *fail if the sweep cap is hit or an eigenvalue is <= 0.
+template <int UB>
+__device__ double lanczos_log_quad(const float* __restrict__ g, const float* __restrict__ xi,
+                                   int U, int* fail) {
+  double a[UB], b[UB], z[UB];
+  for (int i = 0; i < U; ++i) {
+    const double gi = (double)g[i];
+    a[i] = 1.0 / gi + (i > 0 ? (double)xi[i - 1] / (double)g[i - 1] : 0.0);
+    b[i] = (i + 1 < U) ? sqrt((double)xi[i]) / gi : 0.0;
+    z[i] = (i == 0) ? 1.0 : 0.0;
+  }
+  const double eps = DBL_EPSILON;
+  int m = U - 1;
+  int iters = 0;
+  const int max_iters = 60 * U + 60;
+  while (m > 0) {
+    if (fabs(b[m - 1]) <= eps * (fabs(a[m - 1]) + fabs(a[m]))) {
+      b[m - 1] = 0.0;
+      --m;
+      continue;
+    }
+    int l = m - 1;
+    while (l > 0 && fabs(b[l - 1]) > eps * (fabs(a[l - 1]) + fabs(a[l]))) --l;
+    if (l > 0) b[l - 1] = 0.0;
+    if (++iters > max_iters) {
+      *fail = 1;
+      break;
+    }
+    // Wilkinson shift: eigenvalue of the trailing 2x2 block closer to a[m]
+    const double dd = 0.5 * (a[m - 1] - a[m]);
+    const double bm = b[m - 1];
+    const double den = dd + copysign(hypot(dd, bm), dd);
+    const double mu = a[m] - bm * bm / den;
+    double x = a[l] - mu, y = b[l];
+    for (int k = l; k < m; ++k) {
+      const double r = hypot(x, y);
+      double c = 1.0, s = 0.0;
+      if (r > 0.0) {
+        c = x / r;
+        s = -y / r;
+      }
+      if (k > l) b[k - 1] = r;
+      const double ak = a[k], ak1 = a[k + 1], bk = b[k];
+      a[k] = c * c * ak - 2.0 * c * s * bk + s * s * ak1;
+      a[k + 1] = s * s * ak + 2.0 * c * s * bk + c * c * ak1;
+      b[k] = c * s * (ak - ak1) + (c * c - s * s) * bk;
+      if (k + 1 < m) {
+        const double bulge = -s * b[k + 1];
+        b[k + 1] = c * b[k + 1];
+        x = b[k];
+        y = bulge;
+      }
+      const double zk = z[k], zk1 = z[k + 1];
+      z[k] = c * zk - s * zk1;
+      z[k + 1] = s * zk + c * zk1;
+    }
+  }
+  double sum = 0.0;
+  for (int i = 0; i < U; ++i) {
+    if (!(a[i] > 0.0)) *fail = 1;
+    sum += z[i] * z[i] * log(a[i]);
+  }
+  return sum;
+}
+
+}  // namespace
+
+template <int UB>
+__global__ void __launch_bounds__(64)
+k_quad(const float* __restrict__ gam, const float* __restrict__ xi, const int* __restrict__ steps,
+       int nsys, int ld, double* out, int* status) {
+  const int i = blockIdx.x * 64 + threadIdx.x;
+  if (i >= nsys) return;
+  int U = steps[i];
+  if (U <= 0) {
+    out[i] = 0.0;
+    return;
+  }
+  if (U > UB || U > ld) {
+    atomicOr(status, 2);
+    out[i] = 0.0;
+    return;
+  }
+  int fail = 0;
+  out[i] = lanczos_log_quad<UB>(gam + (int64_t)i * ld, xi + (int64_t)i * ld, U, &fail);
+  if (fail) atomicOr(status, 1);
+}
+
+cudaError_t launch_quadrature(const float* gam, const float* xi, const int* steps, int nsys,
+                              int ld, double* out, int* status, cudaStream_t st) {
+  if (nsys <= 0) return cudaSuccess;
+  const int blocks = (nsys + 63) / 64;
+  if (ld <= 64) k_quad<64><<<blocks, 64, 0, st>>>(gam, xi, steps, nsys, ld, out, status);
+  else if (ld <= 128) k_quad<128><<<blocks, 64, 0, st>>>(gam, xi, steps, nsys, ld, out, status);
+  else if (ld <= 256) k_quad<256><<<blocks, 64, 0, st>>>(gam, xi, steps, nsys, ld, out, status);
+  else if (ld <= 512) k_quad<512><<<blocks, 64, 0, st>>>(gam, xi, steps, nsys, ld, out, status);
+  else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_quadrature_ctx(Ctx* c) {
+  return launch_quadrature(c->gam, c->xi, c->psteps, c->T * c->C * c->K, c->U, c->quad,
+                           &c->counters[2], c->stream);
+}
+
+// ---- ell_tc = nu + sum_d log alpha_cd + b0^T mu (Eq. 3), nu from Eq. 11 ------------------
+__global__ void __launch_bounds__(256)
+k_ell(const float* __restrict__ xacc, const float* __restrict__ b0hi,
+      const float* __restrict__ b0lo, const double* __restrict__ quad,
+      const double* __restrict__ sumlogalpha, double* logdet, double* ell, int R, int K, int C,
+      int Dp, int D) {
+  __shared__ double sh[33];
+  const int tc = blockIdx.x, t = tc / C, c = tc % C;
+  const float* mu = xacc + ((int64_t)t * R + (int64_t)c * (K + 1)) * Dp;
+  double acc = 0.0;
+  for (int d = threadIdx.x; d < D; d += 256)
+    acc += ((double)b0hi[(int64_t)t * Dp + d] + (double)b0lo[(int64_t)t * Dp + d]) * (double)mu[d];
+  const double b0mu = block_sum256(acc, sh);
+  if (threadIdx.x == 0) {
+    double qs = 0.0;
+    for (int k = 0; k < K; ++k) qs += quad[(int64_t)tc * K + k];
+    const double nu = -((double)D / (double)K) * qs;
+    logdet[tc] = nu;
+    ell[tc] = nu + sumlogalpha[c] + b0mu;
+  }
+}
+
+// ---- q_t = softmax_c(ell_tc / 2 + log pi_c), L(theta), a_t = argmax_c q_tc --------------
+__global__ void __launch_bounds__(256)
+k_softmax(const double* __restrict__ ell, const double* __restrict__ logpi,
+          const double* __restrict__ tconst, double* q, int* assign, double* stats, int* status,
+          int T, int C) {
+  __shared__ double sh[33];
+  __shared__ double smin[256];
+  double ll = 0.0, mn = 1.0;
+  for (int t = threadIdx.x; t < T; t += 256) {
+    double mx = -INFINITY;
+    int arg = 0;
+    for (int c = 0; c < C; ++c) {
+      const double z = 0.5 * ell[(int64_t)t * C + c] + logpi[c];
+      if (!isfinite(z)) atomicOr(status, 4);
+      if (z > mx) {
+        mx = z;
+        arg = c;
+      }
+    }
+    double se = 0.0;
+    for (int c = 0; c < C; ++c) se += exp(0.5 * ell[(int64_t)t * C + c] + logpi[c] - mx);
+    double best2 = 0.0;
+    for (int c = 0; c < C; ++c) {
+      const double qc = exp(0.5 * ell[(int64_t)t * C + c] + logpi[c] - mx) / se;
+      q[(int64_t)t * C + c] = qc;
+      if (c != arg && qc > best2) best2 = qc;
+    }
+    assign[t] = arg;
+    const double margin = q[(int64_t)t * C + arg] - best2;
+    mn = fmin(mn, margin);
+    ll += mx + log(se) - tconst[t];
+  }
+  const double tot = block_sum256(ll, sh);
+  smin[threadIdx.x] = mn;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 1.0;
+    for (int i = 0; i < 256; ++i) m = fmin(m, smin[i]);
+    stats[0] = tot / (double)T;
+    stats[1] = m;
+  }
+}
+
+cudaError_t launch_ell_softmax(Ctx* c) {
+  k_ell<<<c->T * c->C, 256, 0, c->stream>>>(c->xacc, c->b0hi, c->b0lo, c->quad, c->sumlogalpha,
+                                            c->logdet, c->ell, c->R, c->K, c->C, c->Dp, c->D);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_softmax<<<1, 256, 0, c->stream>>>(c->ell, c->logpi, c->tconst, c->q, c->assign, c->stats,
+                                      &c->counters[2], c->T, c->C);
+  return cudaGetLastError();
+}
+
+// ---- M-step, Eq. 5 with s for diag Sigma: alpha_cd = sum_t q_tc / sum_t q_tc (mu^2 + s) ---
+__global__ void __launch_bounds__(256)
+k_mstep(const float* __restrict__ xacc, const float* __restrict__ sest,
+        const double* __restrict__ q, float* alpha, int T, int C, int R, int K, int Dp, int D,
+        double amin, double amax) {
+  const int c = blockIdx.y;
+  const int d = blockIdx.x * 256 + threadIdx.x;
+  if (d >= Dp) return;
+  if (d >= D) {
+    alpha[(int64_t)c * Dp + d] = 1.0f;
+    return;
+  }
+  double num = 0.0, den = 0.0;
+  for (int t = 0; t < T; ++t) {
+    const double qt = q[(int64_t)t * C + c];
+    const double mu = (double)xacc[((int64_t)t * R + (int64_t)c * (K + 1)) * Dp + d];
+    const double s = (double)sest[((int64_t)t * C + c) * Dp + d];
+    num += qt;
+    den += qt * fmax(mu * mu + s, 0.0);
+  }
+  if (num < 1e-300) return;                        // empty cluster keeps its alpha
+  double a = (den <= num / amax) ? amax : num / den;
+  a = fmin(fmax(a, amin), amax);
+  alpha[(int64_t)c * Dp + d] = (float)a;
+}
+
+cudaError_t launch_mstep(Ctx* c) {
+  dim3 grid((c->Dp + 255) / 256, c->C);
+  k_mstep<<<grid, 256, 0, c->stream>>>(c->xacc, c->sest, c->q, c->alpha, c->T, c->C, c->R, c->K,
+                                       c->Dp, c->D, c->alpha_min, c->alpha_max);
+  return cudaGetLastError();
+}
+
+}  // namespace cmcs

@@ -1,0 +1,132 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads, exports every function
+include/cmcs.h declares, the binding's struct layouts match the header (checked by compiling
+a C probe against it), and argument validation fails cleanly before touching CUDA."""
+import ctypes
+import os
+import re
+import subprocess
+import tempfile
+
+import numpy as np
+import pytest
+
+from paper_2310_00420_gb300 import cmcs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "cmcs.h")
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not os.path.exists(cmcs.LIB_PATH):
+        from paper_2310_00420_gb300 import build
+        build.build()
+    return cmcs.lib()
+
+
+def _declared():
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:cmcs_status|void|const char \*)\s*(cmcs_\w+)\(", txt, re.M)))
+
+
+def test_header_declares_the_binding_exports():
+    assert _declared() == sorted(cmcs.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(L):
+    out = subprocess.run(["nm", "-D", "--defined-only", cmcs.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    syms = set(line.split()[-1] for line in out.splitlines() if line.strip())
+    for name in _declared():
+        assert name in syms, name
+        assert hasattr(L, name)
+
+
+def test_struct_layout_matches_header():
+    src = r"""
+#include <stdio.h>
+#include <stddef.h>
+#include "cmcs.h"
+#define O(s, f) printf(#s "." #f " %zu\n", offsetof(s, f))
+int main(void) {
+  printf("cmcs_config %zu\ncmcs_summary %zu\n", sizeof(cmcs_config), sizeof(cmcs_summary));
+  O(cmcs_config, N); O(cmcs_config, beta); O(cmcs_config, pi); O(cmcs_config, cg_max_iter);
+  O(cmcs_config, cg_tol); O(cmcs_config, seed); O(cmcs_config, precision);
+  O(cmcs_config, refine_max); O(cmcs_config, refine_tol); O(cmcs_config, alpha_min);
+  O(cmcs_config, alpha_max);
+  O(cmcs_summary, loglik); O(cmcs_summary, cg_steps_max); O(cmcs_summary, cg_steps_mean);
+  O(cmcs_summary, cg_capped); O(cmcs_summary, refine_sweeps_max);
+  O(cmcs_summary, refine_rel_max); O(cmcs_summary, min_margin);
+  O(cmcs_summary, operator_applies);
+  return 0;
+}
+"""
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "probe.c")
+        exe = os.path.join(d, "probe")
+        open(c, "w").write(src)
+        subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
+        lines = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = dict(l.rsplit(" ", 1) for l in lines if l.strip())
+    assert int(got["cmcs_config"]) == ctypes.sizeof(cmcs.Config)
+    assert int(got["cmcs_summary"]) == ctypes.sizeof(cmcs.Summary)
+    for key, val in got.items():
+        if "." in key:
+            s, f = key.split(".")
+            cls = cmcs.Config if s == "cmcs_config" else cmcs.Summary
+            assert getattr(cls, f).offset == int(val), key
+
+
+def _cfg(**kw):
+    N = np.array([64, 64], dtype=np.int64)
+    pi = np.array([0.5, 0.5])
+    base = dict(T=2, C=2, D=32, K=4, beta=1e4, cg_max_iter=50, cg_tol=1e-5, seed=0, precision=0,
+                refine_max=0, refine_tol=1e-6, alpha_min=1e-10, alpha_max=1e10)
+    base.update(kw)
+    cfg = cmcs.Config(base["T"], base["C"], base["D"], base["K"],
+                      N.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), base["beta"],
+                      pi.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), base["cg_max_iter"],
+                      base["cg_tol"], base["seed"], base["precision"], base["refine_max"],
+                      base["refine_tol"], base["alpha_min"], base["alpha_max"])
+    return cfg, (N, pi)
+
+
+@pytest.mark.parametrize("bad", [dict(T=0), dict(C=0), dict(D=0), dict(K=0), dict(beta=0.0),
+                                 dict(beta=-1.0), dict(cg_max_iter=0), dict(cg_max_iter=513),
+                                 dict(cg_tol=-1.0), dict(precision=7), dict(refine_max=-1),
+                                 dict(refine_max=65), dict(alpha_min=0.0),
+                                 dict(alpha_min=2.0, alpha_max=1.0)])
+def test_create_rejects_invalid_config_without_cuda(L, bad):
+    cfg, keep = _cfg(**bad)
+    phi = np.zeros((128, 32), np.float32)
+    y = np.zeros(128, np.float32)
+    h = ctypes.c_void_p()
+    st = L.cmcs_create(ctypes.byref(cfg), phi.ctypes.data, y.ctypes.data, 0, None, ctypes.byref(h))
+    assert st == cmcs.ERR_INVALID_ARG
+    assert not h.value
+    assert L.cmcs_last_error(None)
+
+
+def test_create_rejects_null_inputs_and_bad_pi(L):
+    cfg, keep = _cfg()
+    h = ctypes.c_void_p()
+    assert L.cmcs_create(ctypes.byref(cfg), None, None, 0, None, ctypes.byref(h)) == cmcs.ERR_INVALID_ARG
+    assert L.cmcs_create(None, None, None, 0, None, ctypes.byref(h)) == cmcs.ERR_INVALID_ARG
+    N, pi = keep
+    pi[:] = [0.7, 0.7]
+    phi = np.zeros((128, 32), np.float32)
+    y = np.zeros(128, np.float32)
+    assert L.cmcs_create(ctypes.byref(cfg), phi.ctypes.data, y.ctypes.data, 0, None,
+                         ctypes.byref(h)) == cmcs.ERR_INVALID_ARG
+
+
+def test_calls_on_null_context_are_rejected(L):
+    assert L.cmcs_estep(None) == cmcs.ERR_INVALID_ARG
+    assert L.cmcs_em_iter(None, 1) == cmcs.ERR_INVALID_ARG
+    assert L.cmcs_read(None, 0, None, 0) == cmcs.ERR_INVALID_ARG
+    assert L.cmcs_result(None, None) == cmcs.ERR_INVALID_ARG
+    assert L.cmcs_apply(None, None, None, 0, 0) == cmcs.ERR_INVALID_ARG
+    assert L.cmcs_set_alpha(None, None, 0, 0) == cmcs.ERR_INVALID_ARG
+    assert L.cmcs_probes(None, 0, None, 0) == cmcs.ERR_INVALID_ARG
+    assert L.cmcs_lanczos_quadrature(None, None, None, 1, 1, None, None, None) == cmcs.ERR_INVALID_ARG
+    L.cmcs_destroy(None)
