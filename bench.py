@@ -1,0 +1,322 @@
+#!/usr/bin/env python3
+"""CoFEM benchmark: EM iterations per second of covariance-free EM on one GB300.
+
+A step is one EM iteration of Alg. 2 (E-step over every task and cluster: batched CG on the
+posterior-mean system and K probe systems, refinement of the solutions, diagonal and
+log-det estimates, responsibilities; then the M-step) on the plain-scale workload
+(T=32, C=4, D=8192, N=2048, K=32 probes, CG tol 1e-5, at most 100 steps), synthetic seeded
+inputs, FP32 path with the solutions refined to the accuracy the parity tests check.
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on a bounded
+sample of the same workload instead.  Multi-GPU (torchrun): every rank runs an independent
+replica (its own seed); value is the replicas' total throughput (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "CoFEM EM iterations/s (plain-scale workload, one replica per GPU)"
+UNIT = "EM iters/s"
+FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="plain-scale")
+    ap.add_argument("--precision", default="fp32")
+    ap.add_argument("--refine-max", type=int, default=8)
+    ap.add_argument("--refine-tol", type=float, default=1e-5)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _workload(name: str, seed: int):
+    from paper_2310_00420_gb300 import synth
+    return synth.WORKLOADS[name](seed=seed)
+
+
+def _oracle_pair(wl, alpha, em_iter, t, c, refine_tol, refine_max):
+    """The FP64 oracle's E-step for one (task, cluster) pair: K + 1 CG solves + refinement."""
+    from oracle import cofem
+    P = [wl.phi(t).astype(np.float64)]
+    Y = [wl.yt(t).astype(np.float64)]
+    t0 = time.perf_counter()
+    o = cofem.cofem_estep(P, Y, np.asarray(alpha[c:c + 1], np.float64), np.array([1.0]), wl.beta,
+                          wl.K, wl.seed, em_iter, wl.cg_tol, wl.cg_max_iter, tasks=[t],
+                          clusters=[c], C_total=wl.C, refine_tol=refine_tol, refine_max=refine_max)
+    return o, time.perf_counter() - t0
+
+
+def _cpu_cores():
+    n = os.environ.get("OMP_NUM_THREADS") or os.environ.get("OPENBLAS_NUM_THREADS")
+    return int(n) if n else (os.cpu_count() or 1)
+
+
+def run_reference(a):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return
+    from oracle import philox
+    wl = _workload(a.workload, 0)
+    alpha = philox.alpha_init(wl.seed, wl.C, wl.D)
+    pairs = wl.T * wl.C
+    for i in range(a.warmup):
+        _oracle_pair(wl, alpha, i, i % wl.T, i % wl.C, a.refine_tol, a.refine_max)
+    times = []
+    for i in range(a.steps):
+        _, dt = _oracle_pair(wl, alpha, i, (7 * i) % wl.T, i % wl.C, a.refine_tol, a.refine_max)
+        times.append(dt)
+    per_iter = statistics.mean(times) * pairs            # extrapolated full EM iteration
+    value = 1.0 / per_iter
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": per_iter * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{wl.name} T={wl.T} C={wl.C} D={wl.D} N={int(wl.N[0])} "
+                                   f"K={wl.K} tol={wl.cg_tol} max_iter={wl.cg_max_iter}",
+                       "refine_tol": a.refine_tol, "refine_max": a.refine_max},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": _cpu_cores(), "kind": "oracle",
+                             "sample": f"one (task, cluster) pair per step ({wl.K + 1} FP64 CG "
+                                       f"solves + refinement), EM iteration extrapolated x{pairs}"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(a):
+    import torch
+    from paper_2310_00420_gb300 import cmcs
+
+    rank, world, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    wl = _workload(a.workload, rank)
+    kw = dict(C=wl.C, K=wl.K, beta=wl.beta, pi=wl.pi, cg_max_iter=wl.cg_max_iter, cg_tol=wl.cg_tol,
+              seed=wl.seed, precision=a.precision, refine_max=a.refine_max, refine_tol=a.refine_tol)
+    Phi_d = torch.from_numpy(wl.Phi).cuda()
+    y_d = torch.from_numpy(wl.y).cuda()
+    ctx = cmcs.Context(Phi_d, y_d, wl.N, **kw)
+    for _ in range(a.warmup):
+        ctx.em_iter(1)
+    ctx.profile(True)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    clocks = Clocks(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(a.steps):
+        ctx.em_iter(1)
+    e1.record()
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    prof = ctx.profile_read()
+    summ = ctx.summary()
+    ctx.profile(False)
+    ms_max = ms
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_max = float(t.item())
+    value = world * a.steps / (ms_max / 1e3)
+    systems = wl.T * wl.C * (wl.K + 1)
+
+    # operator roofline: algorithmic FLOPs / measured device time of the operator applications
+    peaks, src = _peaks()
+    op_tflops = prof["operator_flops"] / (prof["operator_ms"] * 1e-3) / 1e12 if prof["operator_ms"] else 0.0
+    op_gbs = prof["operator_bytes"] / (prof["operator_ms"] * 1e-3) / 1e9 if prof["operator_ms"] else 0.0
+    if a.precision == "fp32":
+        roof = {"bound": "alu", "achieved": op_tflops, "peak": FP32_ALU_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": op_tflops / FP32_ALU_PEAK_TFLOPS,
+                "traffic": None,
+                "kernel": "operator (k_pass1 + k_pass2, FP32 SIMT)",
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (derived)",
+                "per_launch_flops": prof["operator_flops"] / max(1, prof["operator_calls"]),
+                "per_launch_ms": prof["operator_ms"] / max(1, prof["operator_calls"]),
+                "hbm_gbs_achieved": op_gbs, "hbm_frac": op_gbs / peaks["hbm_gbs"]}
+    else:
+        pk = peaks["bf16_tflops_sustained"]
+        roof = {"bound": "tensor", "achieved": op_tflops, "peak": pk, "unit": "TFLOP/s",
+                "frac": op_tflops / pk, "traffic": None, "peak_source": src,
+                "hbm_gbs_achieved": op_gbs, "hbm_frac": op_gbs / peaks["hbm_gbs"]}
+
+    # error vs the FP64 oracle on one sampled (task, cluster) pair, and the CPU baseline
+    cpu = None
+    err = None
+    if rank == 0 and not a.no_cpu:
+        alpha = ctx.read(cmcs.OUT_ALPHA)
+        it = summ["em_iters_done"]
+        ctx.set_alpha(alpha, it)
+        ctx.estep()
+        mu_g = ctx.read(cmcs.OUT_MU)
+        s_g = ctx.read(cmcs.OUT_S)
+        t_s, c_s = 5, 2 % wl.C
+        o, dt = _oracle_pair(wl, alpha, it, t_s, c_s, 1e-12, 40)
+        rel = lambda g_, r_: float(np.linalg.norm(g_ - r_) / np.linalg.norm(r_))
+        err = {"pair": [t_s, c_s], "mu_rel": rel(mu_g[t_s, c_s], o["mu"][0, 0]),
+               "s_rel": rel(s_g[t_s, c_s], o["s"][0, 0])}
+        if world == 1:
+            _, dt_b = _oracle_pair(wl, alpha, it, t_s, c_s, a.refine_tol, a.refine_max)
+            cpu = {"value": 1.0 / (dt_b * wl.T * wl.C), "unit": UNIT, "cores": _cpu_cores(),
+                   "kind": "oracle",
+                   "sample": f"one (task, cluster) pair of the E-step ({wl.K + 1} FP64 CG solves "
+                             f"+ refinement to the same tolerance), {dt_b:.1f} s, EM iteration "
+                             f"extrapolated x{wl.T * wl.C} pairs"}
+
+    # end to end through the public API with host buffers: create from pinned host Phi and y
+    # (H2D inside), set alpha, one EM iteration, read q, alpha and the reconstructions (D2H)
+    e2e = None
+    if not a.no_e2e:
+        Phi_h = torch.from_numpy(wl.Phi).pin_memory()
+        y_h = torch.from_numpy(wl.y).pin_memory()
+        alpha_h = torch.from_numpy(ctx.read(cmcs.OUT_ALPHA)).pin_memory()
+        it = ctx.summary()["em_iters_done"]
+        outs = {"q": torch.empty((wl.T, wl.C), dtype=torch.float64).pin_memory(),
+                "alpha": torch.empty((wl.C, wl.D), dtype=torch.float32).pin_memory(),
+                "recon": torch.empty((wl.T, wl.D), dtype=torch.float32).pin_memory()}
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(a.steps):
+            c2 = cmcs.Context(Phi_h, y_h, wl.N, **kw)
+            c2.set_alpha(alpha_h, it)
+            c2.em_iter(1)
+            c2.read(cmcs.OUT_Q, out=outs["q"])
+            c2.read(cmcs.OUT_ALPHA, out=outs["alpha"])
+            c2.read(cmcs.OUT_RECON, out=outs["recon"])
+            c2.close()
+        torch.cuda.synchronize()
+        barrier()
+        dt = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([dt], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": world * a.steps / dt, "unit": UNIT,
+               "h2d_bytes_per_step": int(wl.Phi.nbytes + wl.y.nbytes + wl.C * wl.D * 4),
+               "d2h_bytes_per_step": int(sum(v.numel() * v.element_size() for v in outs.values()))}
+
+    ctx.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms_max / a.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32" if a.precision == "fp32" else "bf16+f32", "data": "synthetic",
+                "config": {"workload": f"{wl.name} T={wl.T} C={wl.C} D={wl.D} N={int(wl.N[0])} "
+                                       f"K={wl.K} tol={wl.cg_tol} max_iter={wl.cg_max_iter}",
+                           "precision": a.precision, "refine_max": a.refine_max,
+                           "refine_tol": a.refine_tol, "parallelism": f"{world} replicas",
+                           "l2": f"inputs larger than L2 (Phi {wl.Phi.nbytes / 1e9:.1f} GB)"},
+                "cg_solves_per_s": value * systems,
+                "cg_steps_mean": summ["cg_steps_mean"], "cg_capped": summ["cg_capped"],
+                "refine_sweeps_max": summ["refine_sweeps_max"],
+                "operator_applies_per_step": prof["operator_calls"] / a.steps,
+                "roofline": roof, "cpu_baseline": cpu, "err_vs_fp64": err, "e2e": e2e,
+                "clocks": clk, "gpu_launches": prof["kernel_launches"]}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    a = _args()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

@@ -159,6 +159,26 @@ cmcs_status cmcs_lanczos_quadrature(const float *gamma, const float *xi, const i
                                     int nsys, int ld, double *out, int32_t *status,
                                     void *stream);
 
+/* Operator profile accumulated since profiling was last enabled on a context. */
+typedef struct {
+  int64_t operator_calls;    /* batched operator applications (each: Phi pass + Phi^T pass) */
+  double operator_ms;        /* their summed device time, CUDA events on the context stream  */
+  double operator_flops;     /* algorithmic FLOPs: sum over applied tasks of 4 N_t D R        */
+  double operator_bytes;     /* algorithmic bytes: per applied task s_Phi N_t D (Phi read once,
+                                s_Phi = 4 for FP32, 2 for BF16) + 4 R (2 D + 2 N_t) (V, W, Z)  */
+  int64_t residual_calls;    /* compensated residual applications                            */
+  double residual_ms;        /* their summed device time                                     */
+  int64_t kernel_launches;   /* all kernels the library launched                             */
+} cmcs_profile_data;
+
+/* enable = 1 resets and starts the profile (events bracket every operator application, which
+ * adds a few microseconds per application); enable = 0 stops it.  Events are created here, not
+ * during the E-step; at most 8192 operator applications per E-step are timed. */
+cmcs_status cmcs_profile(cmcs_ctx *ctx, int enable);
+
+/* Read the profile (synchronises the context stream). */
+cmcs_status cmcs_profile_read(const cmcs_ctx *ctx, cmcs_profile_data *out);
+
 /* Description of the last failure on ctx (or of the last failed cmcs_create when ctx is
  * NULL).  Valid until the next call on the same context. */
 const char *cmcs_last_error(const cmcs_ctx *ctx);

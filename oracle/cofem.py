@@ -266,18 +266,21 @@ def exact_estep(Phi_list, y_list, alpha: np.ndarray, pi: np.ndarray, beta: float
 def cofem_estep(Phi_list, y_list, alpha: np.ndarray, pi: np.ndarray, beta: float, K: int,
                 seed: int, em_iter: int, tol: float, max_iter: int, probe_fn=None,
                 steps: np.ndarray = None, tasks=None, refine_tol: float = None,
-                refine_max: int = 8) -> dict:
+                refine_max: int = 8, clusters=None, C_total: int = None) -> dict:
     """Alg. 2, inner loop (one E-step): for every (t, c) solve A mu = b0 and A x_k = p_k by CG
     (Eq. 7, Alg. 1), s = (1/K) sum_k p_k * x_k (Eq. 4), the log-det estimate of Eq. 11 from the
     CG coefficients of the probe systems, ell (Eq. 3) and the responsibilities (Eq. 3).
 
     probe_fn(t, c) -> [K, D] overrides the Philox probes; steps [T, C, K+1] replays given CG
     step counts; tasks gives the global task index of each entry of Phi_list (for the probe
-    counter) when the list is a subset.  With refine_tol set, mu and every x_k are refined
+    counter) when the list is a subset; likewise clusters gives the global index of each row
+    of alpha and C_total the full cluster count (bounded samples).  With refine_tol set, mu and every x_k are refined
     (``refine``) after the first CG solve, which alone supplies the Lanczos coefficients."""
     P, Y = _task_arrays(Phi_list, y_list)
     T, (C, D) = len(P), alpha.shape
     tasks = list(range(T)) if tasks is None else list(tasks)
+    clusters = list(range(C)) if clusters is None else list(clusters)
+    C_total = C if C_total is None else int(C_total)
     mu = np.zeros((T, C, D))
     s = np.zeros((T, C, D))
     nu = np.zeros((T, C))
@@ -291,7 +294,7 @@ def cofem_estep(Phi_list, y_list, alpha: np.ndarray, pi: np.ndarray, beta: float
         b0 = rhs_mean(P[t], Y[t], beta)
         for c in range(C):
             if probe_fn is None:
-                Pk = philox.probes(seed, em_iter, tasks[t], c, C, K, D)
+                Pk = philox.probes(seed, em_iter, tasks[t], clusters[c], C_total, K, D)
             else:
                 Pk = np.asarray(probe_fn(t, c), dtype=np.float64)
             B = np.concatenate([b0[:, None], Pk.T], axis=1)              # [D, K+1]

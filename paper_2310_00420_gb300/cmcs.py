@@ -26,7 +26,7 @@ PRECISIONS = {"fp32": FP32, "bf16": BF16_REFINE, "bf16_refine": BF16_REFINE}
 # exported symbols, in the order include/cmcs.h declares them
 EXPORTS = ("cmcs_create", "cmcs_set_alpha", "cmcs_estep", "cmcs_em_iter", "cmcs_read",
            "cmcs_result", "cmcs_apply", "cmcs_probes", "cmcs_lanczos_quadrature",
-           "cmcs_last_error", "cmcs_destroy")
+           "cmcs_profile", "cmcs_profile_read", "cmcs_last_error", "cmcs_destroy")
 
 
 class Config(ctypes.Structure):
@@ -44,6 +44,13 @@ class Summary(ctypes.Structure):
                 ("cg_capped", ctypes.c_int64), ("refine_sweeps_max", ctypes.c_int),
                 ("refine_rel_max", ctypes.c_double), ("min_margin", ctypes.c_double),
                 ("operator_applies", ctypes.c_int64)]
+
+
+class ProfileData(ctypes.Structure):
+    _fields_ = [("operator_calls", ctypes.c_int64), ("operator_ms", ctypes.c_double),
+                ("operator_flops", ctypes.c_double), ("operator_bytes", ctypes.c_double),
+                ("residual_calls", ctypes.c_int64), ("residual_ms", ctypes.c_double),
+                ("kernel_launches", ctypes.c_int64)]
 
 
 class CmcsError(RuntimeError):
@@ -73,6 +80,8 @@ def lib():
     L.cmcs_apply.argtypes = [vp, vp, vp, i, i]
     L.cmcs_probes.argtypes = [vp, i64, vp, i]
     L.cmcs_lanczos_quadrature.argtypes = [vp, vp, vp, i, i, vp, vp, vp]
+    L.cmcs_profile.argtypes = [vp, i]
+    L.cmcs_profile_read.argtypes = [vp, ctypes.POINTER(ProfileData)]
     L.cmcs_last_error.argtypes = [vp]
     L.cmcs_last_error.restype = ctypes.c_char_p
     L.cmcs_destroy.argtypes = [vp]
@@ -221,6 +230,14 @@ class Context:
         s = Summary()
         _check(lib().cmcs_result(self.h, ctypes.byref(s)), self.h)
         return {f: getattr(s, f) for f, _ in Summary._fields_}
+
+    def profile(self, enable: bool = True):
+        _check(lib().cmcs_profile(self.h, 1 if enable else 0), self.h)
+
+    def profile_read(self) -> dict:
+        p = ProfileData()
+        _check(lib().cmcs_profile_read(self.h, ctypes.byref(p)), self.h)
+        return {f: getattr(p, f) for f, _ in ProfileData._fields_}
 
     def apply(self, V, accurate: bool = False, B=None):
         """A V (accurate=False) or B - A V with compensated arithmetic (accurate=True);

@@ -53,9 +53,15 @@ void free_ctx(Ctx* c) {
                   c->w, c->wlo, c->part, c->rr, c->bb, c->steps, c->steps0, c->active,
                   c->ractive, c->sweeps, c->rrel, c->task_active, c->counters, c->gam, c->xi,
                   c->psteps, c->sest, c->quad, c->logdet, c->ell, c->q, c->assign, c->stats,
-                  c->dN};
+                  c->dN, c->opcount};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  if (c->prof_ev) {
+    for (int i = 0; i < 2 * kProfEvents; ++i) cudaEventDestroy(c->prof_ev[i]);
+    cudaEventDestroy(c->res_ev[0]);
+    cudaEventDestroy(c->res_ev[1]);
+    free(c->prof_ev);
+  }
   if (c->hcounters) cudaFreeHost(c->hcounters);
   if (c->tc) tc_destroy(c);
   free(c->hN);
@@ -89,10 +95,33 @@ cmcs_status read_counters(Ctx* c) {
 
 constexpr int kCheckEvery = 8;   // CG steps between host polls of the active-system count
 
+// operator application, bracketed by profiling events when enabled
+cudaError_t timed_operator(Ctx* c) {
+  const bool ev = c->prof_on && c->prof_nev < kProfEvents;
+  if (ev) cudaEventRecord(c->prof_ev[2 * c->prof_nev], c->stream);
+  cudaError_t e = launch_operator(c, c->d, c->ad, 1);
+  if (ev) {
+    cudaEventRecord(c->prof_ev[2 * c->prof_nev + 1], c->stream);
+    c->prof_nev++;
+  }
+  if (c->prof_on) c->prof_calls++;
+  return e;
+}
+
+// fold the recorded event pairs into the profile (the stream must have been synchronised)
+void fold_events(Ctx* c) {
+  for (int i = 0; i < c->prof_nev; ++i) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->prof_ev[2 * i], c->prof_ev[2 * i + 1]) == cudaSuccess)
+      c->prof_ms += ms;
+  }
+  c->prof_nev = 0;
+}
+
 // Alg. 1 for every active system until all have stopped (or the step cap)
 cmcs_status run_cg(Ctx* c, int record) {
   for (int u = 0; u < c->U; ++u) {
-    CK(launch_operator(c, c->d, c->ad, 1));
+    CK(timed_operator(c));
     CK(launch_cg_update(c, record));
     c->op_applies++;
     if ((u + 1) % kCheckEvery == 0 && u + 1 < c->U) {
@@ -117,7 +146,12 @@ cmcs_status estep(Ctx* c) {
   std::swap(c->x, c->xacc);
   // refinement sweeps: residual with compensated products (FP64 combine), CG on it, add
   for (int sw = 0; sw < c->refine_max; ++sw) {
+    if (c->prof_on) cudaEventRecord(c->res_ev[0], c->stream);
     CK(launch_residual(c, c->xacc, nullptr, c->r));
+    if (c->prof_on) {
+      cudaEventRecord(c->res_ev[1], c->stream);
+      c->res_calls++;
+    }
     c->op_applies++;
     CK(cudaMemsetAsync(c->task_active, 0, sizeof(int) * c->T, c->stream));
     CK(cudaMemsetAsync(c->counters, 0, sizeof(int) * 2, c->stream));
@@ -128,6 +162,10 @@ cmcs_status estep(Ctx* c) {
     CK(launch_refine_update(c));
     s = read_counters(c);
     if (s != CMCS_OK) return s;
+    if (c->prof_on) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, c->res_ev[0], c->res_ev[1]) == cudaSuccess) c->res_ms += ms;
+    }
     if (c->hcounters[1] == 0) break;
   }
   CK(launch_sest(c));
@@ -135,6 +173,7 @@ cmcs_status estep(Ctx* c) {
   CK(launch_ell_softmax(c));
   s = read_counters(c);
   if (s != CMCS_OK) return s;
+  fold_events(c);
   if (c->hcounters[2] != 0) {
     set_err(c, "non-finite value or eigen failure in the E-step (flags 0x%x)", c->hcounters[2]);
     return CMCS_ERR_NUMERIC;
@@ -287,6 +326,8 @@ cmcs_status cmcs_create(const cmcs_config* cfg, const float* Phi, const float* y
   CKC(dalloc(&c->q, (size_t)(T * C)));
   CKC(dalloc(&c->assign, (size_t)T));
   CKC(dalloc(&c->stats, 4));
+  CKC(dalloc(&c->opcount, (size_t)T));
+  CKC(cudaMemsetAsync(c->opcount, 0, sizeof(int64_t) * T, c->stream));
 
   // zero everything that padding relies on
   CKC(cudaMemsetAsync(c->phi, 0, sizeof(float) * c->rows_total * Dp, c->stream));
@@ -346,6 +387,51 @@ void cmcs_destroy(cmcs_ctx* h) {
 }
 
 const char* cmcs_last_error(const cmcs_ctx* h) { return h ? h->c.err : g_create_err; }
+
+cmcs_status cmcs_profile(cmcs_ctx* h, int enable) {
+  if (!h || (enable != 0 && enable != 1)) return CMCS_ERR_INVALID_ARG;
+  Ctx* c = &h->c;
+  if (enable) {
+    if (!c->prof_ev) {
+      c->prof_ev = static_cast<cudaEvent_t*>(calloc(2 * kProfEvents, sizeof(cudaEvent_t)));
+      if (!c->prof_ev) return CMCS_ERR_OOM;
+      for (int i = 0; i < 2 * kProfEvents; ++i) CK(cudaEventCreate(&c->prof_ev[i]));
+      CK(cudaEventCreate(&c->res_ev[0]));
+      CK(cudaEventCreate(&c->res_ev[1]));
+    }
+    CK(cudaMemsetAsync(c->opcount, 0, sizeof(int64_t) * c->T, c->stream));
+    c->prof_nev = 0;
+    c->prof_calls = c->res_calls = c->launches = 0;
+    c->prof_ms = c->res_ms = 0.0;
+  }
+  c->prof_on = enable;
+  return sync_check(c);
+}
+
+cmcs_status cmcs_profile_read(const cmcs_ctx* hc, cmcs_profile_data* out) {
+  if (!hc || !out) return CMCS_ERR_INVALID_ARG;
+  Ctx* c = const_cast<Ctx*>(&hc->c);
+  std::vector<int64_t> cnt(c->T);
+  CK(cudaMemcpyAsync(cnt.data(), c->opcount, sizeof(int64_t) * c->T, cudaMemcpyDeviceToHost, c->stream));
+  cmcs_status s = sync_check(c);
+  if (s != CMCS_OK) return s;
+  fold_events(c);
+  const double sphi = c->precision == CMCS_BF16_REFINE ? 2.0 : 4.0;
+  double fl = 0.0, by = 0.0;
+  for (int t = 0; t < c->T; ++t) {
+    const double n = (double)c->hN[t], D = (double)c->D, R = (double)c->R;
+    fl += (double)cnt[t] * 4.0 * n * D * R;
+    by += (double)cnt[t] * (sphi * n * D + 4.0 * R * (2.0 * D + 2.0 * n));
+  }
+  out->operator_calls = c->prof_calls;
+  out->operator_ms = c->prof_ms;
+  out->operator_flops = fl;
+  out->operator_bytes = by;
+  out->residual_calls = c->res_calls;
+  out->residual_ms = c->res_ms;
+  out->kernel_launches = c->launches;
+  return CMCS_OK;
+}
 
 cmcs_status cmcs_set_alpha(cmcs_ctx* h, const float* alpha, int on_device, int64_t em_iter) {
   if (!h || !alpha || (on_device != 0 && on_device != 1) || em_iter < 0) return CMCS_ERR_INVALID_ARG;

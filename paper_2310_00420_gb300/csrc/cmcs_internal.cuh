@@ -25,6 +25,7 @@ namespace cmcs {
 constexpr int kDAlign = 128;      // padding of D
 constexpr int kNAlign = 128;      // padding of N_t
 constexpr int kUpdThreads = 256;  // threads of the per-system CG kernels
+constexpr int kProfEvents = 8192; // timed operator applications per E-step
 
 // ---- Philox-4x32-10 (Salmon et al., SC'11, Sec. 5) ------------------------------------
 struct U4 { uint32_t x, y, z, w; };
@@ -114,6 +115,16 @@ struct Ctx {
   int* assign;         // [T]
   double* stats;       // [4]: 0 loglik, 1 min margin
   int64_t op_applies;
+
+  // profiling (cmcs_profile): events around operator applications, per-task application
+  // counts (device), launch counter (host)
+  int prof_on;
+  int prof_nev;                  // events recorded in the current E-step (pairs)
+  cudaEvent_t* prof_ev;          // [2 * kProfEvents]
+  int64_t* opcount;              // [T] device: operator applications per task
+  int64_t prof_calls, res_calls, launches;
+  double prof_ms, res_ms;
+  cudaEvent_t res_ev[2];
 
   // BF16 tensor-core operator (precision 1); null otherwise
   void* tc;

@@ -312,6 +312,7 @@ __global__ void k_probes_out(float* dst, int T, int C, int K, int D, uint64_t se
 
 // --------------------------------------------------------------------------------------
 cudaError_t launch_cg_init(Ctx* c, int mode) {
+  c->launches += 1;
   k_cg_init<<<c->S, 256, 0, c->stream>>>(mode, c->x, c->r, c->d, c->b0hi, c->rr, c->bb,
                                          c->steps, c->active, c->ractive, c->sweeps, c->rrel,
                                          c->task_active, c->counters, c->R, c->K, c->C, c->Dp,
@@ -320,6 +321,7 @@ cudaError_t launch_cg_init(Ctx* c, int mode) {
 }
 
 cudaError_t launch_cg_update(Ctx* c, int record) {
+  c->launches += 1;
   const float tol2 = (float)(c->cg_tol * c->cg_tol);
   k_cg_update<<<c->S, 256, 0, c->stream>>>(c->x, c->r, c->d, c->ad, c->part, c->Dp / 128,
                                            c->rr, c->bb, c->steps, c->active, c->task_active,
@@ -329,12 +331,14 @@ cudaError_t launch_cg_update(Ctx* c, int record) {
 }
 
 cudaError_t launch_refine_update(Ctx* c) {
+  c->launches += 1;
   k_refine_update<<<c->S, 256, 0, c->stream>>>(c->xacc, c->x, c->ractive, c->sweeps, c->rrel,
                                                c->counters, c->Dp, (float)c->refine_tol);
   return cudaGetLastError();
 }
 
 cudaError_t launch_sest(Ctx* c) {
+  c->launches += 1;
   dim3 grid((c->Dp / 4 + 127) / 128, c->T * c->C);
   k_sest<<<grid, 128, 0, c->stream>>>(c->xacc, c->sest, c->R, c->K, c->C, c->Dp, c->D, c->seed,
                                       c->em_iter);
@@ -342,23 +346,27 @@ cudaError_t launch_sest(Ctx* c) {
 }
 
 cudaError_t launch_b0(Ctx* c) {
+  c->launches += 1;
   dim3 grid(c->Dp / 128, c->T);
   k_b0<<<grid, 128, 0, c->stream>>>(c->phi, c->y, c->drow, c->b0hi, c->b0lo, c->Dp, c->beta);
   return cudaGetLastError();
 }
 
 cudaError_t launch_alpha_init(Ctx* c) {
+  c->launches += 1;
   dim3 grid((c->Dp + 255) / 256, c->C);
   k_alpha_init<<<grid, 256, 0, c->stream>>>(c->alpha, c->Dp, c->D, c->seed);
   return cudaGetLastError();
 }
 
 cudaError_t launch_sumlogalpha(Ctx* c) {
+  c->launches += 1;
   k_sumlogalpha<<<c->C, 256, 0, c->stream>>>(c->alpha, c->sumlogalpha, c->Dp, c->D);
   return cudaGetLastError();
 }
 
 cudaError_t launch_tconst_dev(Ctx* c, const int64_t* dN) {
+  c->launches += 1;
   k_tconst<<<c->T, 256, 0, c->stream>>>(c->y, c->drow, dN, c->tconst, c->beta);
   return cudaGetLastError();
 }

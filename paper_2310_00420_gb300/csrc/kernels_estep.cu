@@ -131,6 +131,7 @@ cudaError_t launch_quadrature(const float* gam, const float* xi, const int* step
 }
 
 cudaError_t launch_quadrature_ctx(Ctx* c) {
+  c->launches += 1;
   return launch_quadrature(c->gam, c->xi, c->psteps, c->T * c->C * c->K, c->U, c->quad,
                            &c->counters[2], c->stream);
 }
@@ -201,6 +202,7 @@ k_softmax(const double* __restrict__ ell, const double* __restrict__ logpi,
 }
 
 cudaError_t launch_ell_softmax(Ctx* c) {
+  c->launches += 2;
   k_ell<<<c->T * c->C, 256, 0, c->stream>>>(c->xacc, c->b0hi, c->b0lo, c->quad, c->sumlogalpha,
                                             c->logdet, c->ell, c->R, c->K, c->C, c->Dp, c->D);
   cudaError_t e = cudaGetLastError();
@@ -237,6 +239,7 @@ k_mstep(const float* __restrict__ xacc, const float* __restrict__ sest,
 }
 
 cudaError_t launch_mstep(Ctx* c) {
+  c->launches += 1;
   dim3 grid((c->Dp + 255) / 256, c->C);
   k_mstep<<<grid, 256, 0, c->stream>>>(c->xacc, c->sest, c->q, c->alpha, c->T, c->C, c->R, c->K,
                                        c->Dp, c->D, c->alpha_min, c->alpha_max);

@@ -171,6 +171,7 @@ struct P2Args {
   const int* ractive;    // DS: systems still refining (null: all)
   const int64_t* drow;
   const int* task_active;
+  unsigned long long* opcount;  // [T] applications per task (plain pass only, may be null)
   int R, K, C, Dp, D, S;
   float beta_f;
   double beta_d;
@@ -191,6 +192,8 @@ __global__ void __launch_bounds__(256) k_pass2(P2Args p) {
   const int dt = blockIdx.y;
   const int d0 = dt * 128;
   const int j0 = blockIdx.x * BN;
+  if (!DS && p.opcount != nullptr && blockIdx.x == 0 && dt == 0 && threadIdx.x == 0)
+    atomicAdd(&p.opcount[t], 1ull);
   const int64_t rbeg = p.drow[t];
   const int64_t Np = p.drow[t + 1] - rbeg;
   const float* Ag = p.phi + rbeg * p.Dp + d0;
@@ -424,6 +427,8 @@ cudaError_t launch_operator(Ctx* c, const float* V, float* Z, int with_dots) {
   a.Z = Z;
   a.part = with_dots ? c->part : nullptr;
   a.task_active = mask;
+  a.opcount = c->prof_on ? reinterpret_cast<unsigned long long*>(c->opcount) : nullptr;
+  c->launches += 2;
   return pass2<false>(c, tn, a);
 }
 
@@ -436,6 +441,7 @@ cudaError_t launch_residual(Ctx* c, const float* X, const float* Bext, float* Ro
   a.Z = Rout;
   a.Bext = Bext;
   a.ractive = Bext ? nullptr : c->ractive;
+  c->launches += 2;
   return pass2<true>(c, tn, a);
 }
 

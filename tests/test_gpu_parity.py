@@ -84,10 +84,14 @@ def test_residual_is_compensated(small):
     for t in range(small.T):
         for j in range(R):
             c = j // (small.K + 1)
-            ref = B[t, j].astype(np.float64) - cofem.apply_A(P[t], small.beta, alpha[c],
-                                                             X[t, j].astype(np.float64))
+            x = X[t, j].astype(np.float64)
+            ref = B[t, j].astype(np.float64) - cofem.apply_A(P[t], small.beta, alpha[c], x)
+            # magnitude of the summed terms: |B| + beta |Phi|^T |Phi| |x| + alpha |x|
+            scale = np.linalg.norm(np.abs(B[t, j]) + cofem.apply_A(np.abs(P[t]), small.beta,
+                                                                    alpha[c], np.abs(x)))
             err = np.linalg.norm(Rg[t, j] - ref)
-            assert err <= 2e-7 * np.linalg.norm(ref) + 1e-13 * np.linalg.norm(B[t, j]), (t, j)
+            # compensated sums: ~2^-44 of the terms; a plain FP32 residual errs by ~1e-7 * scale
+            assert err <= 2e-7 * np.linalg.norm(ref) + 1e-11 * scale, (t, j, err, scale)
 
 
 def test_quadrature_matches_oracle_on_same_coefficients(small):
@@ -103,8 +107,12 @@ def test_quadrature_matches_oracle_on_same_coefficients(small):
                 r = cofem.cg(lambda V, idx: cofem.apply_A(P[t], small.beta, alpha[c], V), Pk.T,
                              0.0, U)
                 for k in range(6):
-                    rows_g.append(r.gamma[k].astype(np.float32))
-                    rows_x.append(r.xi[k].astype(np.float32))
+                    gk = np.zeros(100, np.float32)
+                    xk = np.zeros(100, np.float32)
+                    gk[:U] = r.gamma[k][:U]
+                    xk[:U] = r.xi[k][:U]
+                    rows_g.append(gk)
+                    rows_x.append(xk)
                     steps.append(int(r.steps[k]))
     g = np.stack(rows_g)
     x = np.stack(rows_x)
@@ -119,6 +127,25 @@ def test_quadrature_matches_oracle_on_same_coefficients(small):
         ref = float(np.sum(V[0] ** 2 * np.log(lam)))
         scale = float(np.sum(V[0] ** 2 * np.abs(np.log(lam)))) + 1.0
         assert abs(out[i] - ref) <= 1e-9 * scale, (i, out[i], ref)
+
+
+FREE_Q_TOL = 1e-3   # free-running FP32-vs-FP64 Lanczos: log det differs by ~1e-6 relative
+
+
+def replay_q(wl, g, o, alpha32):
+    """Responsibilities the oracle computes from the GPU's own CG coefficients (replay of the
+    Lanczos coefficients, Eqs. 9-11) and the oracle's refined means: q, ell, nu."""
+    T, C = wl.T, wl.C
+    nu = np.zeros((T, C))
+    ell = np.zeros((T, C))
+    for t in range(T):
+        b0 = cofem.rhs_mean(wl.phi(t).astype(np.float64), wl.yt(t).astype(np.float64), wl.beta)
+        for c in range(C):
+            nu[t, c] = cofem.logdet_estimate(g["gamma"][t, c].astype(np.float64),
+                                             g["xi"][t, c].astype(np.float64),
+                                             g["steps"][t, c, 1:], wl.D)
+            ell[t, c] = cofem.ell(nu[t, c], alpha32[c].astype(np.float64), b0, o["mu"][t, c])
+    return cofem.responsibilities(ell, wl.pi), ell, nu
 
 
 def _estep_pair(wl, alpha32, em_iter, refine_tol_gpu=1e-6):
@@ -141,18 +168,14 @@ def test_estep_parity_plain_small(small):
     g, o = _estep_pair(small, alpha, em_iter=2)
     assert rel_err_rows(g["mu"], o["mu"]).max() <= REL_TOL
     assert rel_err_rows(g["s"], o["s"]).max() <= REL_TOL
-    # log det: the oracle's quadrature on the GPU's own CG coefficients (replay) ...
-    for t in range(small.T):
-        for c in range(small.C):
-            nu = cofem.logdet_estimate(g["gamma"][t, c].astype(np.float64),
-                                       g["xi"][t, c].astype(np.float64), g["steps"][t, c, 1:], small.D)
-            assert abs(g["logdet"][t, c] - nu) <= 1e-9 * abs(nu)
-            b0 = cofem.rhs_mean(small.phi(t).astype(np.float64), small.yt(t).astype(np.float64), small.beta)
-            ell = cofem.ell(nu, alpha[c].astype(np.float64), b0, o["mu"][t, c])
-            assert abs(g["ell"][t, c] - ell) <= 1e-6 * abs(ell)
-    # ... and the free-running FP32 vs FP64 CG estimates stay within 1e-4 relative
+    # log det, ell, q: the oracle's quadrature on the GPU's own CG coefficients (replay) ...
+    q_rep, ell_rep, nu_rep = replay_q(small, g, o, alpha)
+    assert np.max(np.abs(g["logdet"] - nu_rep) / np.abs(nu_rep)) <= 1e-9
+    assert np.max(np.abs(g["ell"] - ell_rep) / np.abs(ell_rep)) <= 1e-6
+    assert np.max(np.abs(g["q"] - q_rep)) <= Q_TOL
+    # ... and the free-running FP32 vs FP64 CG estimates
     assert np.max(np.abs(g["logdet"] - o["logdet"]) / np.abs(o["logdet"])) <= 1e-4
-    assert np.max(np.abs(g["q"] - o["q"])) <= Q_TOL
+    assert np.max(np.abs(g["q"] - o["q"])) <= FREE_Q_TOL
     assert np.array_equal(g["assign"], np.argmax(o["q"], axis=1))
 
 
@@ -181,7 +204,7 @@ def test_em_parity_plain_small(small):
                  tol=small.cg_tol, max_iter=small.cg_max_iter, C=small.C, D=small.D,
                  refine_tol=1e-12, refine_max=40)
     assert np.array_equal(asg, o["assign"])
-    assert np.max(np.abs(q_g - o["last"]["q"])) <= Q_TOL
+    assert np.max(np.abs(q_g - o["last"]["q"])) <= FREE_Q_TOL
     assert rel_err_rows(a_g, o["alpha"]).max() <= REL_TOL
     assert rel_err_rows(recon, o["recon"]).max() <= REL_TOL
 
@@ -196,7 +219,9 @@ def test_ragged_and_degenerate_shapes(shape):
     g, o = _estep_pair(wl, alpha, em_iter=1)
     assert rel_err_rows(g["mu"], o["mu"]).max() <= REL_TOL
     assert rel_err_rows(g["s"], o["s"]).max() <= REL_TOL
-    assert np.max(np.abs(g["q"] - o["q"])) <= Q_TOL
+    q_rep, _, _ = replay_q(wl, g, o, alpha)
+    assert np.max(np.abs(g["q"] - q_rep)) <= Q_TOL
+    assert np.max(np.abs(g["q"] - o["q"])) <= FREE_Q_TOL
     with make_ctx(wl) as ctx:
         P = ctx.probes(1)
     for t in range(wl.T):

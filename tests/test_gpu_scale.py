@@ -1,0 +1,79 @@
+"""Parity at the benchmark's full size and launch configuration (plain-scale workload:
+T=32, C=4, D=8192, N=2048, K=32; FP32 path, refine_max 8, refine_tol 1e-5), on outputs the
+oracle can compute one (task, cluster) pair at a time, plus properties that hold at any size."""
+import numpy as np
+import pytest
+
+from oracle import cofem
+from paper_2310_00420_gb300 import cmcs, synth
+
+from gpu_helpers import make_ctx, rel_err_rows
+
+pytestmark = pytest.mark.gpu
+
+BENCH = dict(refine_max=8, refine_tol=1e-5)
+
+
+@pytest.fixture(scope="module")
+def scale():
+    wl = synth.plain_scale()
+    with make_ctx(wl, **BENCH) as ctx:
+        ctx.em_iter(2)                                 # move away from the initial draw
+        alpha = ctx.read(cmcs.OUT_ALPHA)
+        it = ctx.summary()["em_iters_done"]
+        ctx.estep()
+        out = {k: ctx.read(v) for k, v in dict(mu=cmcs.OUT_MU, s=cmcs.OUT_S, q=cmcs.OUT_Q,
+                                                logdet=cmcs.OUT_LOGDET, ell=cmcs.OUT_ELL,
+                                                steps=cmcs.OUT_STEPS, gamma=cmcs.OUT_GAMMA,
+                                                xi=cmcs.OUT_XI, assign=cmcs.OUT_ASSIGN).items()}
+        out["summary"] = ctx.summary()
+        ctx.set_alpha(alpha, it)
+        ctx.em_iter(1)
+        out["alpha_next"] = ctx.read(cmcs.OUT_ALPHA)
+        out["mu2"] = ctx.read(cmcs.OUT_MU)
+    return wl, alpha, it, out
+
+
+@pytest.mark.parametrize("pair", [(0, 0), (19, 3)])
+def test_sampled_pairs_match_oracle(scale, pair):
+    wl, alpha, it, g = scale
+    t, c = pair
+    o = cofem.cofem_estep([wl.phi(t).astype(np.float64)], [wl.yt(t).astype(np.float64)],
+                          alpha[c:c + 1].astype(np.float64), np.array([1.0]), wl.beta, wl.K,
+                          wl.seed, it, wl.cg_tol, wl.cg_max_iter, tasks=[t], clusters=[c],
+                          C_total=wl.C, refine_tol=1e-12, refine_max=40)
+    assert rel_err_rows(g["mu"][t, c], o["mu"][0, 0]) <= 1e-4
+    assert rel_err_rows(g["s"][t, c], o["s"][0, 0]) <= 1e-4
+    # log-det estimate: the oracle's quadrature on the GPU's coefficients (replay)
+    nu = cofem.logdet_estimate(g["gamma"][t, c].astype(np.float64), g["xi"][t, c].astype(np.float64),
+                               g["steps"][t, c, 1:], wl.D)
+    assert abs(g["logdet"][t, c] - nu) <= 1e-9 * abs(nu)
+    b0 = cofem.rhs_mean(wl.phi(t).astype(np.float64), wl.yt(t).astype(np.float64), wl.beta)
+    ell = cofem.ell(nu, alpha[c].astype(np.float64), b0, o["mu"][0, 0])
+    assert abs(g["ell"][t, c] - ell) <= 1e-6 * abs(ell)
+    # free-running FP32 vs FP64 Lanczos estimate
+    assert abs(g["logdet"][t, c] - o["logdet"][0, 0]) <= 1e-4 * abs(o["logdet"][0, 0])
+
+
+def test_softmax_and_assignments_follow_ell(scale):
+    wl, alpha, it, g = scale
+    q = cofem.responsibilities(g["ell"], wl.pi)
+    assert np.max(np.abs(q - g["q"])) <= 1e-12
+    assert np.array_equal(g["assign"], np.argmax(g["q"], axis=1))
+    np.testing.assert_allclose(g["q"].sum(axis=1), 1.0, atol=1e-12)
+
+
+def test_mstep_at_scale(scale):
+    wl, alpha, it, g = scale
+    ref = cofem.m_step(g["q"], g["mu"].astype(np.float64), g["s"].astype(np.float64),
+                       alpha.astype(np.float64))
+    np.testing.assert_allclose(g["alpha_next"], ref, rtol=2e-7)
+    # the repeated E-step from the same state is bit-identical
+    assert np.array_equal(g["mu2"], g["mu"])
+
+
+def test_lanczos_first_entry_identity_at_scale(scale):
+    """||p||^2 / gamma_1 = p^T A p > 0 and every recorded step count is within the cap."""
+    wl, alpha, it, g = scale
+    assert g["steps"].min() >= 1 and g["steps"].max() <= wl.cg_max_iter
+    assert np.all(g["gamma"][..., 0] > 0)
