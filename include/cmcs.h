@@ -87,6 +87,8 @@ typedef struct {
   double refine_rel_max;   /* largest final ||delta|| / ||x|| over refined systems (0: none) */
   double min_margin;       /* smallest gap q_{t,a_t} - max_{c != a_t} q_tc over tasks        */
   int64_t operator_applies;/* batched operator applications (all systems) in the last E-step */
+  double resid_rel_max;    /* largest ||b - A x|| / ||b|| of the returned solutions, from the
+                              compensated residual after refinement (0 when refine_max = 0)  */
 } cmcs_summary;
 
 /* What cmcs_read copies out.  Element types and shapes: */
@@ -105,7 +107,9 @@ typedef enum {
                                               systems (Alg. 1), zero past U               */
   CMCS_OUT_XI = 10,      /* float  [T][C][K][cg_max_iter] CG coefficients xi_u, zero past U */
   CMCS_OUT_B0 = 11,      /* float  [T][D]     beta Phi_t^T y_t (Eq. 7)                      */
-  CMCS_OUT_SWEEPS = 12   /* int32  [T][C][K+1] refinement sweeps taken per system           */
+  CMCS_OUT_SWEEPS = 12,  /* int32  [T][C][K+1] refinement sweeps taken per system           */
+  CMCS_OUT_RESID = 13    /* float  [T][C][K+1] ||b - A x|| / ||b|| of the returned solutions
+                                              (0 when refine_max = 0)                     */
 } cmcs_output;
 
 /* Create a context: validates cfg, copies Phi and y into library-owned device memory (padded
@@ -122,7 +126,10 @@ cmcs_status cmcs_create(const cmcs_config *cfg, const float *Phi, const float *y
 cmcs_status cmcs_set_alpha(cmcs_ctx *ctx, const float *alpha, int on_device, int64_t em_iter);
 
 /* One E-step (Eq. 3 via Sec. 3) with the current alpha: fills mu, s, logdet, ell, q, the
- * assignments and the CG statistics.  alpha and the iteration counter are unchanged. */
+ * assignments and the CG statistics.  alpha and the iteration counter are unchanged.
+ * With refine_max > 0 the data term beta y^T Phi mu of ell (= b0^T A^-1 b0) is evaluated as
+ * b0^T mu + mu^T (b0 - A mu) with the compensated residual, so its error is quadratic in the
+ * error of mu. */
 cmcs_status cmcs_estep(cmcs_ctx *ctx);
 
 /* n EM iterations of Alg. 2: each is an E-step followed by the M-step of Eq. 5 and an

@@ -21,7 +21,7 @@ FP32, BF16_REFINE = 0, 1
 PRECISIONS = {"fp32": FP32, "bf16": BF16_REFINE, "bf16_refine": BF16_REFINE}
 
 (OUT_MU, OUT_S, OUT_Q, OUT_LOGDET, OUT_ELL, OUT_ALPHA, OUT_ASSIGN, OUT_RECON, OUT_STEPS,
- OUT_GAMMA, OUT_XI, OUT_B0, OUT_SWEEPS) = range(13)
+ OUT_GAMMA, OUT_XI, OUT_B0, OUT_SWEEPS, OUT_RESID) = range(14)
 
 # exported symbols, in the order include/cmcs.h declares them
 EXPORTS = ("cmcs_create", "cmcs_set_alpha", "cmcs_estep", "cmcs_em_iter", "cmcs_read",
@@ -43,7 +43,7 @@ class Summary(ctypes.Structure):
                 ("cg_steps_max", ctypes.c_int), ("cg_steps_mean", ctypes.c_double),
                 ("cg_capped", ctypes.c_int64), ("refine_sweeps_max", ctypes.c_int),
                 ("refine_rel_max", ctypes.c_double), ("min_margin", ctypes.c_double),
-                ("operator_applies", ctypes.c_int64)]
+                ("operator_applies", ctypes.c_int64), ("resid_rel_max", ctypes.c_double)]
 
 
 class ProfileData(ctypes.Structure):
@@ -138,6 +138,7 @@ _OUT_META = {  # what: (dtype, shape function of (T, C, D, K, U))
     OUT_XI: (np.float32, lambda T, C, D, K, U: (T, C, K, U)),
     OUT_B0: (np.float32, lambda T, C, D, K, U: (T, D)),
     OUT_SWEEPS: (np.int32, lambda T, C, D, K, U: (T, C, K + 1)),
+    OUT_RESID: (np.float32, lambda T, C, D, K, U: (T, C, K + 1)),
 }
 
 

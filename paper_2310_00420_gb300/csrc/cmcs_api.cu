@@ -51,7 +51,7 @@ void free_ctx(Ctx* c) {
   void* ptrs[] = {c->phi, c->y, c->drow, c->tile_task, c->b0hi, c->b0lo, c->alpha,
                   c->sumlogalpha, c->logpi, c->tconst, c->x, c->r, c->d, c->ad, c->xacc,
                   c->w, c->wlo, c->part, c->rr, c->bb, c->steps, c->steps0, c->active,
-                  c->ractive, c->sweeps, c->rrel, c->task_active, c->counters, c->gam, c->xi,
+                  c->ractive, c->sweeps, c->rrel, c->rres, c->task_active, c->counters, c->gam, c->xi,
                   c->psteps, c->sest, c->quad, c->logdet, c->ell, c->q, c->assign, c->stats,
                   c->dN, c->opcount};
   for (void* p : ptrs)
@@ -168,9 +168,18 @@ cmcs_status estep(Ctx* c) {
     }
     if (c->hcounters[1] == 0) break;
   }
+  const float* rmu = nullptr;
+  if (c->refine_max > 0) {
+    // residual of the returned solutions: verified accuracy and the correction of ell
+    CK(launch_residual(c, c->xacc, nullptr, c->r, 1));
+    CK(launch_resid_norm(c));
+    rmu = c->r;
+  } else {
+    CK(cudaMemsetAsync(c->rres, 0, sizeof(float) * c->S, c->stream));
+  }
   CK(launch_sest(c));
   CK(launch_quadrature_ctx(c));
-  CK(launch_ell_softmax(c));
+  CK(launch_ell_softmax(c, rmu));
   s = read_counters(c);
   if (s != CMCS_OK) return s;
   fold_events(c);
@@ -313,6 +322,8 @@ cmcs_status cmcs_create(const cmcs_config* cfg, const float* Phi, const float* y
   CKC(dalloc(&c->ractive, (size_t)S));
   CKC(dalloc(&c->sweeps, (size_t)S));
   CKC(dalloc(&c->rrel, (size_t)S));
+  CKC(dalloc(&c->rres, (size_t)S));
+  CKC(cudaMemsetAsync(c->rres, 0, sizeof(float) * S, c->stream));
   CKC(dalloc(&c->task_active, (size_t)T));
   CKC(dalloc(&c->counters, 4));
   CKC(cudaMallocHost(reinterpret_cast<void**>(&c->hcounters), 4 * sizeof(int)));
@@ -531,6 +542,9 @@ cmcs_status cmcs_read(const cmcs_ctx* hc, int what, void* dst, int on_device) {
     case CMCS_OUT_SWEEPS:
       CK(cudaMemcpyAsync(dst, c->sweeps, sizeof(int) * c->S, k, c->stream));
       break;
+    case CMCS_OUT_RESID:
+      CK(cudaMemcpyAsync(dst, c->rres, sizeof(float) * c->S, k, c->stream));
+      break;
     default:
       set_err(c, "unknown output %d", what);
       return CMCS_ERR_INVALID_ARG;
@@ -542,8 +556,9 @@ cmcs_status cmcs_result(const cmcs_ctx* hc, cmcs_summary* out) {
   if (!hc || !out) return CMCS_ERR_INVALID_ARG;
   Ctx* c = const_cast<Ctx*>(&hc->c);
   std::vector<int> st(c->S), sw(c->S);
-  std::vector<float> rel(c->S);
+  std::vector<float> rel(c->S), res(c->S);
   double stats[4];
+  CK(cudaMemcpyAsync(res.data(), c->rres, sizeof(float) * c->S, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaMemcpyAsync(st.data(), c->steps0, sizeof(int) * c->S, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaMemcpyAsync(sw.data(), c->sweeps, sizeof(int) * c->S, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaMemcpyAsync(rel.data(), c->rrel, sizeof(float) * c->S, cudaMemcpyDeviceToHost, c->stream));
@@ -561,6 +576,7 @@ cmcs_status cmcs_result(const cmcs_ctx* hc, cmcs_summary* out) {
     if (st[i] >= c->U) out->cg_capped++;
     out->refine_sweeps_max = sw[i] > out->refine_sweeps_max ? sw[i] : out->refine_sweeps_max;
     out->refine_rel_max = rel[i] > out->refine_rel_max ? rel[i] : out->refine_rel_max;
+    out->resid_rel_max = res[i] > out->resid_rel_max ? res[i] : out->resid_rel_max;
   }
   out->cg_steps_mean = sum / c->S;
   out->operator_applies = c->op_applies;

@@ -104,6 +104,7 @@ struct Ctx {
   int* ractive;        // [S] still refining
   int* sweeps;         // [S]
   float* rrel;         // [S] last ||delta|| / ||x||
+  float* rres;         // [S] ||b - A x|| / ||b|| of the returned solution
   int* task_active;    // [T]
   int* counters;       // [4]: 0 active systems, 1 refine-active systems, 2 status flags
   int* hcounters;      // pinned host mirror [4]
@@ -146,12 +147,14 @@ cudaError_t launch_sest(Ctx* c);
 // operator (kernels_op.cu): AD = A D for all active tasks
 cudaError_t launch_operator(Ctx* c, const float* V, float* Z, int with_dots);
 // accurate residual: r = B - A xacc, B = b0 (k = 0) or the probe (k >= 1) when Bext == null
-cudaError_t launch_residual(Ctx* c, const float* X, const float* Bext, float* Rout);
+cudaError_t launch_residual(Ctx* c, const float* X, const float* Bext, float* Rout,
+                            int all_systems = 0);
+cudaError_t launch_resid_norm(Ctx* c);
 // E-step tail and M-step (kernels_estep.cu)
 cudaError_t launch_quadrature(const float* gam, const float* xi, const int* steps, int nsys,
                               int ld, double* out, int* status, cudaStream_t st);
 cudaError_t launch_quadrature_ctx(Ctx* c);
-cudaError_t launch_ell_softmax(Ctx* c);
+cudaError_t launch_ell_softmax(Ctx* c, const float* rmu /* residuals for the correction, or null */);
 cudaError_t launch_mstep(Ctx* c);
 
 // tensor-core operator hooks (kernels_tc.cu)

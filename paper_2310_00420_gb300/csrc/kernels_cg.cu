@@ -210,6 +210,35 @@ k_refine_update(float* __restrict__ xacc, const float* __restrict__ delta, int* 
   }
 }
 
+// ---- ||b - A x|| / ||b|| per system from the residual in r ----------------------------
+__global__ void __launch_bounds__(256)
+k_resid_norm(const float* __restrict__ r, const float* __restrict__ b0hi,
+             const float* __restrict__ b0lo, float* rres, int R, int K, int Dp, int D) {
+  __shared__ double sh[33];
+  const int64_t sys = blockIdx.x;
+  const int t = (int)(sys / R), j = (int)(sys % R), k = j % (K + 1);
+  const float* rs = r + sys * Dp;
+  double a1 = 0.0, a2 = 0.0;
+  for (int d = threadIdx.x; d < D; d += 256) {
+    const double rv = (double)rs[d];
+    a1 += rv * rv;
+    if (k == 0) {
+      const double bv = (double)b0hi[(int64_t)t * Dp + d] + (double)b0lo[(int64_t)t * Dp + d];
+      a2 += bv * bv;
+    }
+  }
+  const double rr = block_sum(a1, sh);
+  const double bb = (k == 0) ? block_sum(a2, sh) : (double)D;
+  if (threadIdx.x == 0) rres[sys] = bb > 0.0 ? (float)sqrt(rr / bb) : 0.f;
+}
+
+cudaError_t launch_resid_norm(Ctx* c) {
+  c->launches += 1;
+  k_resid_norm<<<c->S, 256, 0, c->stream>>>(c->r, c->b0hi, c->b0lo, c->rres, c->R, c->K, c->Dp,
+                                            c->D);
+  return cudaGetLastError();
+}
+
 // ---- diagonal estimator s_tc = (1/K) sum_k p_k * x_k (Eq. 4) ----------------------------
 __global__ void __launch_bounds__(128)
 k_sest(const float* __restrict__ xacc, float* __restrict__ sest, int R, int K, int C, int Dp,

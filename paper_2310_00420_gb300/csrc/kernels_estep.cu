@@ -140,14 +140,18 @@ cudaError_t launch_quadrature_ctx(Ctx* c) {
 __global__ void __launch_bounds__(256)
 k_ell(const float* __restrict__ xacc, const float* __restrict__ b0hi,
       const float* __restrict__ b0lo, const double* __restrict__ quad,
-      const double* __restrict__ sumlogalpha, double* logdet, double* ell, int R, int K, int C,
-      int Dp, int D) {
+      const double* __restrict__ sumlogalpha, const float* __restrict__ rmu, double* logdet,
+      double* ell, int R, int K, int C, int Dp, int D) {
   __shared__ double sh[33];
   const int tc = blockIdx.x, t = tc / C, c = tc % C;
-  const float* mu = xacc + ((int64_t)t * R + (int64_t)c * (K + 1)) * Dp;
+  const int64_t off = ((int64_t)t * R + (int64_t)c * (K + 1)) * Dp;
+  const float* mu = xacc + off;
   double acc = 0.0;
-  for (int d = threadIdx.x; d < D; d += 256)
-    acc += ((double)b0hi[(int64_t)t * Dp + d] + (double)b0lo[(int64_t)t * Dp + d]) * (double)mu[d];
+  for (int d = threadIdx.x; d < D; d += 256) {
+    const double m = (double)mu[d];
+    acc += ((double)b0hi[(int64_t)t * Dp + d] + (double)b0lo[(int64_t)t * Dp + d]) * m;
+    if (rmu != nullptr) acc += m * (double)rmu[off + d];    // + mu^T (b0 - A mu)
+  }
   const double b0mu = block_sum256(acc, sh);
   if (threadIdx.x == 0) {
     double qs = 0.0;
@@ -201,10 +205,10 @@ k_softmax(const double* __restrict__ ell, const double* __restrict__ logpi,
   }
 }
 
-cudaError_t launch_ell_softmax(Ctx* c) {
+cudaError_t launch_ell_softmax(Ctx* c, const float* rmu) {
   c->launches += 2;
   k_ell<<<c->T * c->C, 256, 0, c->stream>>>(c->xacc, c->b0hi, c->b0lo, c->quad, c->sumlogalpha,
-                                            c->logdet, c->ell, c->R, c->K, c->C, c->Dp, c->D);
+                                            rmu, c->logdet, c->ell, c->R, c->K, c->C, c->Dp, c->D);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_softmax<<<1, 256, 0, c->stream>>>(c->ell, c->logpi, c->tconst, c->q, c->assign, c->stats,

@@ -432,7 +432,8 @@ cudaError_t launch_operator(Ctx* c, const float* V, float* Z, int with_dots) {
   return pass2<false>(c, tn, a);
 }
 
-cudaError_t launch_residual(Ctx* c, const float* X, const float* Bext, float* Rout) {
+cudaError_t launch_residual(Ctx* c, const float* X, const float* Bext, float* Rout,
+                            int all_systems) {
   const int tn = c->tn_ds > 0 ? c->tn_ds : pick_tn(c->R, 4);
   cudaError_t e = pass1<true>(c, tn, X, c->w, c->wlo, nullptr);
   if (e != cudaSuccess) return e;
@@ -440,7 +441,7 @@ cudaError_t launch_residual(Ctx* c, const float* X, const float* Bext, float* Ro
   a.V = X;
   a.Z = Rout;
   a.Bext = Bext;
-  a.ractive = Bext ? nullptr : c->ractive;
+  a.ractive = (Bext || all_systems) ? nullptr : c->ractive;
   c->launches += 2;
   return pass2<true>(c, tn, a);
 }
