@@ -40,6 +40,8 @@ def _args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="plain-scale")
+    ap.add_argument("--tasks", type=int, default=0,
+                    help="keep only the first TASKS tasks of the workload (profiling slices)")
     ap.add_argument("--precision", default="fp32")
     ap.add_argument("--refine-max", type=int, default=8)
     ap.add_argument("--refine-tol", type=float, default=1e-5)
@@ -114,9 +116,12 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def _workload(name: str, seed: int):
+def _workload(name: str, seed: int, tasks: int = 0):
     from paper_2310_00420_gb300 import synth
-    return synth.WORKLOADS[name](seed=seed)
+    wl = synth.WORKLOADS[name](seed=seed)
+    if tasks and tasks < wl.T:
+        wl = wl.subset(range(tasks))
+    return wl
 
 
 def _oracle_pair(wl, alpha, em_iter, t, c, refine_tol, refine_max):
@@ -141,7 +146,7 @@ def run_reference(a):
     if rank != 0:
         return
     from oracle import philox
-    wl = _workload(a.workload, 0)
+    wl = _workload(a.workload, 0, a.tasks)
     alpha = philox.alpha_init(wl.seed, wl.C, wl.D)
     pairs = wl.T * wl.C
     for i in range(a.warmup):
@@ -175,7 +180,7 @@ def run_ours(a):
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
-    wl = _workload(a.workload, rank)
+    wl = _workload(a.workload, rank, a.tasks)
     kw = dict(C=wl.C, K=wl.K, beta=wl.beta, pi=wl.pi, cg_max_iter=wl.cg_max_iter, cg_tol=wl.cg_tol,
               seed=wl.seed, precision=a.precision, refine_max=a.refine_max, refine_tol=a.refine_tol)
     Phi_d = torch.from_numpy(wl.Phi).cuda()
