@@ -186,8 +186,24 @@ cmcs_status cmcs_profile(cmcs_ctx *ctx, int enable);
 /* Read the profile (synchronises the context stream). */
 cmcs_status cmcs_profile_read(const cmcs_ctx *ctx, cmcs_profile_data *out);
 
-/* Description of the last failure on ctx (or of the last failed cmcs_create when ctx is
- * NULL).  Valid until the next call on the same context. */
+/* Operator without device allocation: Z = beta Phi^T (Phi V) + diag(alpha) V for m vectors
+ * of one task.  The paper has no counterpart; this entry point exists for callers that cannot
+ * call cudaMalloc while they run (their device memory is owned by their own pool allocator,
+ * or they cannot afford cudaMalloc's implicit synchronisation).  It allocates nothing and calls
+ * no allocating routine: the intermediate Phi V is kept in a fixed 16 MiB device array inside
+ * the library, so m * N must not exceed 4,194,304 (larger requests return
+ * CMCS_ERR_INVALID_ARG with a message for cmcs_last_error(NULL)).
+ * Phi: float [N][D] row-major, alpha: float [D], V and Z: float [m][D]; all device pointers on
+ * the current device; beta > 0.  stream: cudaStream_t or NULL; the call returns after the work
+ * has completed.  Every call shares that one array (per device), which keeps the previous
+ * call's contents; calls whose GPU work overlaps (other host threads, other streams) race on it.
+ * The first call on each device looks up the array's device address with that device current;
+ * make that first call before capturing a stream into a CUDA graph. */
+cmcs_status cmcs_apply_noalloc(const float *Phi, int N, int D, const float *alpha, double beta,
+                               const float *V, int m, float *Z, void *stream);
+
+/* Description of the last failure on ctx (or, when ctx is NULL, of the last failed
+ * cmcs_create or context-free call).  Valid until the next call on the same context. */
 const char *cmcs_last_error(const cmcs_ctx *ctx);
 
 /* Release everything the context owns.  NULL is accepted. */

@@ -26,7 +26,8 @@ PRECISIONS = {"fp32": FP32, "bf16": BF16_REFINE, "bf16_refine": BF16_REFINE}
 # exported symbols, in the order include/cmcs.h declares them
 EXPORTS = ("cmcs_create", "cmcs_set_alpha", "cmcs_estep", "cmcs_em_iter", "cmcs_read",
            "cmcs_result", "cmcs_apply", "cmcs_probes", "cmcs_lanczos_quadrature",
-           "cmcs_profile", "cmcs_profile_read", "cmcs_last_error", "cmcs_destroy")
+           "cmcs_profile", "cmcs_profile_read", "cmcs_apply_noalloc", "cmcs_last_error",
+           "cmcs_destroy")
 
 
 class Config(ctypes.Structure):
@@ -82,6 +83,7 @@ def lib():
     L.cmcs_lanczos_quadrature.argtypes = [vp, vp, vp, i, i, vp, vp, vp]
     L.cmcs_profile.argtypes = [vp, i]
     L.cmcs_profile_read.argtypes = [vp, ctypes.POINTER(ProfileData)]
+    L.cmcs_apply_noalloc.argtypes = [vp, i, i, vp, ctypes.c_double, vp, i, vp, vp]
     L.cmcs_last_error.argtypes = [vp]
     L.cmcs_last_error.restype = ctypes.c_char_p
     L.cmcs_destroy.argtypes = [vp]
@@ -264,6 +266,21 @@ class Context:
         p, dev = _ptr(out)
         _check(lib().cmcs_probes(self.h, int(em_iter), p, dev), self.h)
         return out
+
+
+def apply_noalloc(Phi, alpha, beta: float, V, Z=None, stream=None):
+    """Z = beta Phi^T (Phi V) + alpha * V for one task without any device allocation inside
+    the library (Phi [N][D], alpha [D], V [m][D]: float32 CUDA tensors)."""
+    import torch
+    N, D = Phi.shape
+    m = V.shape[0]
+    if Z is None:
+        Z = torch.empty_like(V)
+    _check(lib().cmcs_apply_noalloc(ctypes.c_void_p(Phi.data_ptr()), int(N), int(D),
+                                    ctypes.c_void_p(alpha.data_ptr()), float(beta),
+                                    ctypes.c_void_p(V.data_ptr()), int(m),
+                                    ctypes.c_void_p(Z.data_ptr()), _stream_handle(stream)))
+    return Z
 
 
 def lanczos_quadrature(gamma, xi, steps, stream=None):

@@ -216,6 +216,11 @@ cmcs_status validate(const cmcs_config* cfg) {
 
 }  // namespace
 
+namespace cmcs {
+// error text reported by cmcs_last_error(NULL) for calls that have no context
+void set_global_error(const char* msg) { snprintf(g_create_err, sizeof(g_create_err), "%s", msg); }
+}  // namespace cmcs
+
 extern "C" {
 
 cmcs_status cmcs_create(const cmcs_config* cfg, const float* Phi, const float* y, int on_device,
