@@ -53,8 +53,12 @@ typedef enum {
      and sums (about twice FP32's precision) */
   CMCS_FP32 = 0,
   /* operator with Phi held in BF16 on the tcgen05 tensor cores (FP32 accumulation in TMEM);
-     CG vectors FP32; the refinement residual uses the FP32 Phi as in CMCS_FP32 */
-  CMCS_BF16_REFINE = 1
+     CG vectors FP32 (entering the MMA as BF16 hi + lo pairs); the refinement residual uses the
+     FP32 Phi as in CMCS_FP32 */
+  CMCS_BF16_REFINE = 1,
+  /* operator on the tensor cores with Phi and the vectors both split into BF16 hi + lo pairs
+     (three MMAs per step: about 16 significant bits per product, FP32 accumulation) */
+  CMCS_BF16X3 = 2
 } cmcs_precision;
 
 typedef struct {

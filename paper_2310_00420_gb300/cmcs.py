@@ -17,8 +17,8 @@ LIB_PATH = os.path.join(HERE, "_build", "libcmcs.so")
 OK, ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_NUMERIC, ERR_TIMEOUT, ERR_UNSUPPORTED = range(7)
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "NUMERIC", 5: "TIMEOUT",
                 6: "UNSUPPORTED"}
-FP32, BF16_REFINE = 0, 1
-PRECISIONS = {"fp32": FP32, "bf16": BF16_REFINE, "bf16_refine": BF16_REFINE}
+FP32, BF16_REFINE, BF16X3 = 0, 1, 2
+PRECISIONS = {"fp32": FP32, "bf16": BF16_REFINE, "bf16_refine": BF16_REFINE, "bf16x3": BF16X3}
 
 (OUT_MU, OUT_S, OUT_Q, OUT_LOGDET, OUT_ELL, OUT_ALPHA, OUT_ASSIGN, OUT_RECON, OUT_STEPS,
  OUT_GAMMA, OUT_XI, OUT_B0, OUT_SWEEPS, OUT_RESID) = range(14)

@@ -197,7 +197,9 @@ cmcs_status validate(const cmcs_config* cfg) {
   if (!(cfg->beta > 0.0) || !isfinite(cfg->beta)) return CMCS_ERR_INVALID_ARG;
   if (cfg->cg_max_iter < 1 || cfg->cg_max_iter > 512) return CMCS_ERR_INVALID_ARG;
   if (!(cfg->cg_tol >= 0.0)) return CMCS_ERR_INVALID_ARG;
-  if (cfg->precision != CMCS_FP32 && cfg->precision != CMCS_BF16_REFINE) return CMCS_ERR_INVALID_ARG;
+  if (cfg->precision != CMCS_FP32 && cfg->precision != CMCS_BF16_REFINE &&
+      cfg->precision != CMCS_BF16X3)
+    return CMCS_ERR_INVALID_ARG;
   if (cfg->refine_max < 0 || cfg->refine_max > 64) return CMCS_ERR_INVALID_ARG;
   if (!(cfg->refine_tol >= 0.0)) return CMCS_ERR_INVALID_ARG;
   if (!(cfg->alpha_min > 0.0) || !(cfg->alpha_max > cfg->alpha_min) || !isfinite(cfg->alpha_max))
@@ -382,7 +384,7 @@ cmcs_status cmcs_create(const cmcs_config* cfg, const float* Phi, const float* y
   CKC(launch_alpha_init(c));
   CKC(launch_sumlogalpha(c));
   CKC(launch_tconst_dev(c, c->dN));
-  if (c->precision == CMCS_BF16_REFINE) {
+  if (c->precision == CMCS_BF16_REFINE || c->precision == CMCS_BF16X3) {
     if (tc_create(c) != 0) {
       if (c->err[0] == 0) set_err(c, "BF16 tensor-core operator unavailable");
       return fail(CMCS_ERR_UNSUPPORTED);
@@ -598,6 +600,7 @@ cmcs_status cmcs_apply(cmcs_ctx* h, const float* V, float* Z, int on_device, int
   CK(cudaMemcpy2DAsync(c->x, sizeof(float) * Dp, V, sizeof(float) * D, sizeof(float) * D, S, kin,
                        c->stream));
   if (!accurate) {
+    if (c->tc != nullptr) CK(tc_split_vectors(c, c->x));
     CK(launch_operator(c, c->x, c->ad, 0));
   } else {
     CK(cudaMemsetAsync(c->d, 0, sizeof(float) * S * Dp, c->stream));

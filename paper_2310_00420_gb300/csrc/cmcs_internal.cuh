@@ -127,8 +127,9 @@ struct Ctx {
   double prof_ms, res_ms;
   cudaEvent_t res_ev[2];
 
-  // BF16 tensor-core operator (precision 1); null otherwise
+  // tensor-core operator (precision 1 and 2); null otherwise
   void* tc;
+  void *dhi, *dlo;     // [S][Dp] BF16 hi and lo parts of the CG direction d (tensor-core path)
 
   char err[512];
 };
@@ -160,7 +161,8 @@ cudaError_t launch_mstep(Ctx* c);
 // tensor-core operator hooks (kernels_tc.cu)
 int tc_create(Ctx* c);      // returns 0 on success
 void tc_destroy(Ctx* c);
-cudaError_t tc_operator(Ctx* c, const float* V, float* Z);
+cudaError_t tc_operator(Ctx* c, const float* V, float* Z, int with_dots);
+cudaError_t tc_split_vectors(Ctx* c, const float* V);   // V -> dhi, dlo
 
 inline int64_t round_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
 

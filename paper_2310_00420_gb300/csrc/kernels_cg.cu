@@ -7,6 +7,7 @@
 // order; every reduction has a fixed tree order, so results are run-to-run deterministic.
 // Converged systems are masked (their CTA returns at once) and a task whose systems have all
 // converged is skipped by the operator.
+#include <cuda_bf16.h>
 #include <math.h>
 
 #include "cmcs_internal.cuh"
@@ -43,6 +44,20 @@ __device__ __forceinline__ float4 probe4(uint64_t seed, int64_t em, int t, int c
   return make_float4(v[0], v[1], v[2], v[3]);
 }
 
+// BF16 pair split x = hi + lo of four values, written for the tensor-core operator
+__device__ __forceinline__ void store_split4(__nv_bfloat16* hi, __nv_bfloat16* lo, int64_t i,
+                                             float4 v) {
+  const float x[4] = {v.x, v.y, v.z, v.w};
+  __nv_bfloat16 h[4], l[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    h[e] = __float2bfloat16_rn(x[e]);
+    l[e] = __float2bfloat16_rn(x[e] - __bfloat162float(h[e]));
+  }
+  *reinterpret_cast<uint2*>(hi + i) = *reinterpret_cast<const uint2*>(h);
+  *reinterpret_cast<uint2*>(lo + i) = *reinterpret_cast<const uint2*>(l);
+}
+
 }  // namespace
 
 // ---- CG initialisation: x_1 = 0, r_1 = d_1 = b (Alg. 1, first line) ---------------------
@@ -52,7 +67,8 @@ __global__ void __launch_bounds__(256)
 k_cg_init(int mode, float* __restrict__ x, float* __restrict__ r, float* __restrict__ d,
           const float* __restrict__ b0hi, float* rr, float* bb, int* steps, int* active,
           int* ractive, int* sweeps, float* rrel, int* task_active, int* counters, int R,
-          int K, int C, int Dp, int D, uint64_t seed, int64_t em_iter, int refine) {
+          int K, int C, int Dp, int D, uint64_t seed, int64_t em_iter, int refine,
+          __nv_bfloat16* dhi, __nv_bfloat16* dlo) {
   __shared__ float sh[33];
   const int64_t sys = blockIdx.x;
   const int t = (int)(sys / R), j = (int)(sys % R), c = j / (K + 1), k = j % (K + 1);
@@ -71,6 +87,7 @@ k_cg_init(int mode, float* __restrict__ x, float* __restrict__ r, float* __restr
     }
     *reinterpret_cast<float4*>(xs + i) = make_float4(0.f, 0.f, 0.f, 0.f);
     *reinterpret_cast<float4*>(ds + i) = b;
+    if (dhi != nullptr) store_split4(dhi, dlo, sys * Dp + i, b);
     acc = fmaf(b.x, b.x, acc);
     acc = fmaf(b.y, b.y, acc);
     acc = fmaf(b.z, b.z, acc);
@@ -101,7 +118,7 @@ k_cg_update(float* __restrict__ x, float* __restrict__ r, float* __restrict__ d,
             const float* __restrict__ ad, const float* __restrict__ part, int ndt, float* rr,
             const float* bb, int* steps, int* active, int* task_active, int* counters,
             float* gam, float* xih, int* psteps, int record, int R, int K, int C, int Dp, int S,
-            int U, float tol2) {
+            int U, float tol2, __nv_bfloat16* dhi, __nv_bfloat16* dlo) {
   __shared__ float sh[33];
   __shared__ float s_dad;
   const int64_t sys = blockIdx.x;
@@ -156,6 +173,7 @@ k_cg_update(float* __restrict__ x, float* __restrict__ r, float* __restrict__ d,
     dv.x = fmaf(xi, dv.x, rv.x); dv.y = fmaf(xi, dv.y, rv.y);
     dv.z = fmaf(xi, dv.z, rv.z); dv.w = fmaf(xi, dv.w, rv.w);
     *reinterpret_cast<float4*>(ds + i) = dv;
+    if (dhi != nullptr) store_split4(dhi, dlo, sys * Dp + i, dv);
   }
   if (threadIdx.x == 0) {
     const int u = steps[sys];
@@ -345,7 +363,9 @@ cudaError_t launch_cg_init(Ctx* c, int mode) {
   k_cg_init<<<c->S, 256, 0, c->stream>>>(mode, c->x, c->r, c->d, c->b0hi, c->rr, c->bb,
                                          c->steps, c->active, c->ractive, c->sweeps, c->rrel,
                                          c->task_active, c->counters, c->R, c->K, c->C, c->Dp,
-                                         c->D, c->seed, c->em_iter, c->refine_max > 0 ? 1 : 0);
+                                         c->D, c->seed, c->em_iter, c->refine_max > 0 ? 1 : 0,
+                                         static_cast<__nv_bfloat16*>(c->dhi),
+                                         static_cast<__nv_bfloat16*>(c->dlo));
   return cudaGetLastError();
 }
 
@@ -355,7 +375,9 @@ cudaError_t launch_cg_update(Ctx* c, int record) {
   k_cg_update<<<c->S, 256, 0, c->stream>>>(c->x, c->r, c->d, c->ad, c->part, c->Dp / 128,
                                            c->rr, c->bb, c->steps, c->active, c->task_active,
                                            c->counters, c->gam, c->xi, c->psteps, record, c->R,
-                                           c->K, c->C, c->Dp, c->S, c->U, tol2);
+                                           c->K, c->C, c->Dp, c->S, c->U, tol2,
+                                           static_cast<__nv_bfloat16*>(c->dhi),
+                                           static_cast<__nv_bfloat16*>(c->dlo));
   return cudaGetLastError();
 }
 

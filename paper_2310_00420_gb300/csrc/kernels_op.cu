@@ -411,13 +411,7 @@ P2Args base_args(Ctx* c) {
 }  // namespace
 
 cudaError_t launch_operator(Ctx* c, const float* V, float* Z, int with_dots) {
-  if (c->precision == CMCS_BF16_REFINE && c->tc != nullptr) {
-    cudaError_t e = tc_operator(c, V, Z);
-    if (e != cudaSuccess) return e;
-    // the tensor-core path writes W and Z; dots come from the shared epilogue below when
-    // requested, so nothing else to do here
-    return cudaSuccess;
-  }
+  if (c->tc != nullptr) return tc_operator(c, V, Z, with_dots);
   const int* mask = with_dots ? c->task_active : nullptr;
   const int tn = c->tn_plain > 0 ? c->tn_plain : pick_tn(c->R, 9);
   cudaError_t e = pass1<false>(c, tn, V, c->w, nullptr, mask);

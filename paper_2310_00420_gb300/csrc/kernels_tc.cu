@@ -1,17 +1,538 @@
-// BF16 tensor-core operator (tcgen05 + TMA) for CMCS_BF16_REFINE.
+// Tensor-core operator for CMCS_BF16_REFINE and CMCS_BF16X3 (tcgen05 MMA, TMA, TMEM; sm_103a).
+//
+// Same two passes as the FP32 operator (Eq. 7 applied to all R = C*(K+1) right-hand sides of a
+// task), each a K-major BF16 GEMM with FP32 accumulation in tensor memory:
+//   pass 1: W[j][n] = sum_d Phi[n][d] V[j][d]          A = Phi  [rows][D_pad], B = V [S][D_pad]
+//   pass 2: Z[j][d] = beta sum_n PhiT[d][n] W[j][n] + alpha_c[d] V[j][d]
+//                                                       A = PhiT [D_pad][rows], B = W [R][rows]
+// FP32 operands enter as unevaluated BF16 pairs x = x_hi + x_lo.  BF16_REFINE multiplies the
+// BF16-rounded Phi by (V_hi + V_lo) (two MMAs per k-step); BF16X3 also splits Phi and adds
+// Phi_lo V_hi (three MMAs), about 16 significant bits per product.
+//
+// One CTA (4 warps) owns one 128-row output tile and all R columns (up to 512 TMEM columns).
+// Warp 0 lane 0 streams A and B tiles with TMA (128-byte swizzle) through a ring of shared-memory
+// stages; warp 1 lane 0 issues tcgen05.mma from shared-memory descriptors into TMEM; then all
+// four warps drain TMEM (tcgen05.ld, 32 rows each) in the epilogue.  Every mbarrier wait is
+// bounded: on expiry the kernel records CMCS status bit 8, stops issuing, waits (bounded) for its
+// copies in flight and still frees its TMEM.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
 #include <stdio.h>
+#include <stdlib.h>
 
 #include "cmcs_internal.cuh"
 
 namespace cmcs {
 
-int tc_create(Ctx* c) {
-  snprintf(c->err, sizeof(c->err), "the BF16 tensor-core operator is not built yet");
-  return 1;
+namespace {
+
+constexpr int kBM = 128;                   // rows of an output tile (MMA M)
+constexpr int kBK = 64;                    // K per stage: one 128-byte row of BF16
+constexpr int kTcThreads = 128;
+constexpr uint32_t kWaitLimit = 1u << 24;  // try_wait polls before a wait is declared stuck
+constexpr int kSmemBudget = 225 * 1024;
+
+struct TcArgs {
+  const int* tile_task;
+  const int64_t* drow;
+  const int* task_active;
+  int R, K, C, Dp, D, S;
+  int64_t rows_total;
+  int Rpad, BR, nbox, stages, stage_bytes;
+  uint32_t tmem_cols;
+  __nv_bfloat16* w_hi;    // pass 1 output, [R][rows_total]
+  __nv_bfloat16* w_lo;
+  const float* V;         // pass 2 epilogue: the FP32 vectors A is applied to, [S][D_pad]
+  float* Z;               // pass 2 output A V, [S][D_pad]
+  float* part;            // [D_pad/128][S] partial v^T A v, or null
+  const float* alpha;     // [C][D_pad]
+  float beta;
+  unsigned long long* opcount;
+  int* status;
+};
+
+// ---- PTX wrappers ---------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (uint32_t i = 0; i < kWaitLimit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tm, int x, int y,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
+               "r"(ncols) : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+// shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row groups 1024 B apart
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);   // start address
+  d |= (uint64_t)1 << 16;                     // leading byte offset (unused for this layout)
+  d |= (uint64_t)(1024 >> 4) << 32;           // stride byte offset
+  d |= (uint64_t)1 << 46;                     // descriptor version
+  d |= (uint64_t)2 << 61;                     // 128-byte swizzle
+  return d;
+}
+// instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both K-major
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15},"
+      " [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-void tc_destroy(Ctx* c) { c->tc = nullptr; }
+}  // namespace
 
-cudaError_t tc_operator(Ctx*, const float*, float*) { return cudaErrorNotSupported; }
+// ---- the GEMM kernel ---------------------------------------------------------------------
+template <int PASS, int NA, int NB>
+__global__ void __launch_bounds__(kTcThreads, 1)
+k_tc(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMap tA1,
+     const __grid_constant__ CUtensorMap tB0, const __grid_constant__ CUtensorMap tB1,
+     const TcArgs p) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                             ~static_cast<uintptr_t>(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)p.stages * p.stage_bytes);
+  uint64_t* empty = full + p.stages;
+  uint64_t* done = empty + p.stages;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  float* red = reinterpret_cast<float*>(tmem_slot + 4);          // [4][Rpad] (pass 2)
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  int t, a_row, b_row, kx, nk, dtile = 0;
+  if (PASS == 1) {
+    const int g = blockIdx.x;
+    t = p.tile_task[g];
+    a_row = g * kBM;
+    b_row = t * p.R;
+    kx = 0;
+    nk = p.Dp / kBK;
+  } else {
+    dtile = blockIdx.x;
+    t = blockIdx.y;
+    a_row = dtile * kBM;
+    b_row = 0;
+    kx = (int)p.drow[t];
+    nk = (int)((p.drow[t + 1] - p.drow[t]) / kBK);
+  }
+  if (p.task_active != nullptr && p.task_active[t] == 0) return;   // whole CTA, before set-up
+  if (PASS == 2 && p.opcount != nullptr && dtile == 0 && threadIdx.x == 0)
+    atomicAdd(&p.opcount[t], 1ull);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < p.stages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == 0) tmem_alloc(tmem_slot, p.tmem_cols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t a_bytes = kBM * kBK * 2;                  // 16 KiB per A operand
+  const uint32_t b_bytes = (uint32_t)p.Rpad * kBK * 2;     // per B operand
+  int issued = 0;                                          // stages the producer issued
+
+  if (warp == 0 && lane == 0) {
+    // ---- TMA producer
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % p.stages;
+      if (kb >= p.stages && !mbar_wait(&empty[s], ((kb / p.stages) - 1) & 1)) {
+        *abort_flag = 1;
+        atomicOr(p.status, 8);
+        break;
+      }
+      if (*abort_flag) break;
+      uint8_t* st = smem + (size_t)s * p.stage_bytes;
+      mbar_expect_tx(&full[s], (uint32_t)p.stage_bytes);
+      tma_load_2d(st, &tA0, kx + kb * kBK, a_row, &full[s]);
+      if (NA == 2) tma_load_2d(st + a_bytes, &tA1, kx + kb * kBK, a_row, &full[s]);
+      uint8_t* bst = st + NA * a_bytes;
+      for (int bx = 0; bx < p.nbox; ++bx) {
+        tma_load_2d(bst + bx * p.BR * 128, &tB0, kx + kb * kBK, b_row + bx * p.BR, &full[s]);
+        if (NB == 2)
+          tma_load_2d(bst + b_bytes + bx * p.BR * 128, &tB1, kx + kb * kBK, b_row + bx * p.BR, &full[s]);
+      }
+      issued = kb + 1;
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer
+    const uint32_t idesc = idesc_bf16(kBM, p.BR);
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % p.stages;
+      if (!mbar_wait(&full[s], (kb / p.stages) & 1)) {
+        *abort_flag = 1;
+        atomicOr(p.status, 8);
+        break;
+      }
+      tc_fence_after();
+      const uint32_t st = smem_u32(smem + (size_t)s * p.stage_bytes);
+#pragma unroll
+      for (int kk = 0; kk < kBK / 16; ++kk) {
+        const uint64_t a0 = smem_desc(st + kk * 32);
+        const uint64_t a1 = smem_desc(st + a_bytes + kk * 32);
+        for (int bx = 0; bx < p.nbox; ++bx) {
+          const uint32_t bo = st + NA * a_bytes + bx * p.BR * 128 + kk * 32;
+          const uint32_t dt = tmem + (uint32_t)(bx * p.BR);
+          mma_bf16(dt, a0, smem_desc(bo), idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+          if (NB == 2) mma_bf16(dt, a0, smem_desc(bo + b_bytes), idesc, 1u);
+          if (NA == 2) mma_bf16(dt, a1, smem_desc(bo), idesc, 1u);
+        }
+      }
+      mma_commit(&empty[s]);
+    }
+    mma_commit(done);    // arrives once every MMA issued above has completed
+  }
+  __syncwarp();
+
+  // ---- epilogue (all four warps; warp w reads TMEM lanes 32w .. 32w+31)
+  const bool ok = mbar_wait(done, 0);
+  tc_fence_after();
+  if (!ok) {
+    *abort_flag = 1;
+    if (lane == 0) atomicOr(p.status, 8);
+  }
+  __syncthreads();
+  const bool run = !*abort_flag;
+  const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
+  if (PASS == 1) {
+    if (run) {
+      const int64_t n = (int64_t)a_row + 32 * warp + lane;    // global row of Phi
+      for (int c0 = 0; c0 < p.Rpad; c0 += 16) {
+        float v[16];
+        tmem_ld16(trow + c0, v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int j = c0 + i;
+          if (j < p.R) {
+            const __nv_bfloat16 hi = __float2bfloat16_rn(v[i]);
+            const __nv_bfloat16 lo = __float2bfloat16_rn(v[i] - __bfloat162float(hi));
+            p.w_hi[(int64_t)j * p.rows_total + n] = hi;
+            p.w_lo[(int64_t)j * p.rows_total + n] = lo;
+          }
+        }
+      }
+    }
+  } else {
+    const int d = a_row + 32 * warp + lane;                   // coordinate of this row
+    if (run) {
+      for (int c0 = 0; c0 < p.Rpad; c0 += 16) {
+        float v[16];
+        tmem_ld16(trow + c0, v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int j = c0 + i;
+          float dot = 0.f;
+          if (j < p.R) {
+            const int64_t sys = (int64_t)t * p.R + j;
+            const int c = j / (p.K + 1);
+            const float vv = p.V[sys * p.Dp + d];
+            const float ad = fmaf(p.beta, v[i], p.alpha[(int64_t)c * p.Dp + d] * vv);
+            p.Z[sys * p.Dp + d] = ad;
+            dot = vv * ad;
+          }
+#pragma unroll
+          for (int m = 16; m > 0; m >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, m);
+          if (lane == 0 && j < p.Rpad) red[warp * p.Rpad + j] = dot;
+        }
+      }
+    }
+    __syncthreads();
+    if (run && p.part != nullptr) {
+      for (int j = threadIdx.x; j < p.R; j += kTcThreads)
+        p.part[(int64_t)dtile * p.S + (int64_t)t * p.R + j] =
+            ((red[j] + red[p.Rpad + j]) + red[2 * p.Rpad + j]) + red[3 * p.Rpad + j];
+    }
+  }
+
+  // ---- teardown: no copy may still be landing in shared memory when the CTA exits
+  if (*abort_flag && warp == 0 && lane == 0) {
+    for (int kb = issued - 1; kb >= 0 && kb >= issued - p.stages; --kb)
+      mbar_wait(&full[kb % p.stages], (kb / p.stages) & 1);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, p.tmem_cols);
+}
+
+// ---- set-up kernels ----------------------------------------------------------------------
+// x = hi + lo with hi = bf16(x), lo = bf16(x - hi)
+__global__ void k_split_bf16(const float* __restrict__ src, __nv_bfloat16* __restrict__ hi,
+                             __nv_bfloat16* __restrict__ lo, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float x = src[i];
+    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+    hi[i] = h;
+    if (lo) lo[i] = __float2bfloat16_rn(x - __bfloat162float(h));
+  }
+}
+
+// PhiT[d][n] = Phi[n][d] split into BF16 pairs, 32 x 32 tiles through shared memory
+__global__ void k_transpose_split(const float* __restrict__ phi, __nv_bfloat16* __restrict__ thi,
+                                  __nv_bfloat16* __restrict__ tlo, int64_t rows, int Dp) {
+  __shared__ float tile[32][33];
+  const int64_t n0 = (int64_t)blockIdx.y * 32;
+  const int d0 = blockIdx.x * 32;
+  for (int r = threadIdx.y; r < 32; r += 8) tile[r][threadIdx.x] = phi[(n0 + r) * Dp + d0 + threadIdx.x];
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const float x = tile[threadIdx.x][r];
+    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+    const int64_t o = (int64_t)(d0 + r) * rows + n0 + threadIdx.x;
+    thi[o] = h;
+    if (tlo) tlo[o] = __float2bfloat16_rn(x - __bfloat162float(h));
+  }
+}
+
+// ---- host side ---------------------------------------------------------------------------
+namespace {
+
+struct TcState {
+  int NA, NB;
+  int Rpad, BR, nbox, stages, stage_bytes, smem_bytes;
+  uint32_t tmem_cols;
+  __nv_bfloat16 *phi_hi, *phi_lo, *phit_hi, *phit_lo, *w_hi, *w_lo;
+  CUtensorMap tm_phi[2], tm_phit[2], tm_d[2], tm_w[2];
+};
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// 2-D BF16 tensor [outer][inner] (inner contiguous), box [box_rows][64], 128-byte swizzle
+bool encode_2d(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer, uint32_t box_rows) {
+  auto fn = get_encode();
+  if (!fn || base == nullptr) return false;
+  cuuint64_t dims[2] = {inner, outer};
+  cuuint64_t strides[1] = {inner * 2};
+  cuuint32_t box[2] = {(cuuint32_t)kBK, box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box,
+                  estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+template <int PASS, int NA, int NB>
+cudaError_t set_smem_attr(int bytes) {
+  return cudaFuncSetAttribute(k_tc<PASS, NA, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+TcArgs base_args(Ctx* c, TcState* s) {
+  TcArgs a{};
+  a.tile_task = c->tile_task;
+  a.drow = c->drow;
+  a.R = c->R;
+  a.K = c->K;
+  a.C = c->C;
+  a.Dp = c->Dp;
+  a.D = c->D;
+  a.S = c->S;
+  a.rows_total = c->rows_total;
+  a.Rpad = s->Rpad;
+  a.BR = s->BR;
+  a.nbox = s->nbox;
+  a.stages = s->stages;
+  a.stage_bytes = s->stage_bytes;
+  a.tmem_cols = s->tmem_cols;
+  a.w_hi = s->w_hi;
+  a.w_lo = s->w_lo;
+  a.alpha = c->alpha;
+  a.beta = (float)c->beta;
+  a.status = &c->counters[2];
+  return a;
+}
+
+template <int NA, int NB>
+cudaError_t run_passes(Ctx* c, TcState* s, const float* V, float* Z, int with_dots) {
+  TcArgs a = base_args(c, s);
+  a.task_active = with_dots ? c->task_active : nullptr;
+  a.opcount = c->prof_on ? reinterpret_cast<unsigned long long*>(c->opcount) : nullptr;
+  a.V = V;
+  a.Z = Z;
+  a.part = with_dots ? c->part : nullptr;
+  k_tc<1, NA, NB><<<(unsigned)(c->rows_total / kBM), kTcThreads, s->smem_bytes, c->stream>>>(
+      s->tm_phi[0], s->tm_phi[NA - 1], s->tm_d[0], s->tm_d[NB - 1], a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  dim3 g2(c->Dp / kBM, c->T);
+  k_tc<2, NA, NB><<<g2, kTcThreads, s->smem_bytes, c->stream>>>(s->tm_phit[0], s->tm_phit[NA - 1],
+                                                                s->tm_w[0], s->tm_w[NB - 1], a);
+  c->launches += 2;
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int tc_create(Ctx* c) {
+  TcState* s = static_cast<TcState*>(calloc(1, sizeof(TcState)));
+  if (!s) return 1;
+  c->tc = s;
+  s->NA = c->precision == CMCS_BF16X3 ? 2 : 1;
+  s->NB = 2;
+  s->nbox = (c->R + 255) / 256;
+  s->BR = (int)round_up((c->R + s->nbox - 1) / s->nbox, 16);
+  s->Rpad = s->BR * s->nbox;
+  if (s->Rpad > 512) {
+    snprintf(c->err, sizeof(c->err), "tensor-core operator supports C*(K+1) <= 512 (got %d)", c->R);
+    return 1;
+  }
+  s->tmem_cols = 32;
+  while ((int)s->tmem_cols < s->Rpad) s->tmem_cols <<= 1;
+  s->stage_bytes = s->NA * kBM * kBK * 2 + s->NB * s->Rpad * kBK * 2;
+  const int extra = 1024 + 2 * 8 * 8 + 8 + 16 + 4 * s->Rpad * 4 + 64;
+  s->stages = (kSmemBudget - extra) / s->stage_bytes;
+  if (s->stages > 6) s->stages = 6;
+  if (s->stages < 2) {
+    snprintf(c->err, sizeof(c->err), "tensor-core operator: stage of %d bytes does not fit", s->stage_bytes);
+    return 1;
+  }
+  s->smem_bytes = s->stages * s->stage_bytes + 1024 + (2 * s->stages + 1) * 8 + 16 + 4 * s->Rpad * 4 + 64;
+
+  const int64_t rows = c->rows_total, Dp = c->Dp, S = c->S, R = c->R;
+  auto alloc = [&](__nv_bfloat16** p, int64_t n) {
+    return cudaMalloc(reinterpret_cast<void**>(p), sizeof(__nv_bfloat16) * (size_t)n) == cudaSuccess;
+  };
+  bool okm = alloc(&s->phi_hi, rows * Dp) && alloc(&s->phit_hi, rows * Dp) &&
+             alloc(reinterpret_cast<__nv_bfloat16**>(&c->dhi), S * Dp) &&
+             alloc(reinterpret_cast<__nv_bfloat16**>(&c->dlo), S * Dp) && alloc(&s->w_hi, R * rows) &&
+             alloc(&s->w_lo, R * rows);
+  if (okm && s->NA == 2) okm = alloc(&s->phi_lo, rows * Dp) && alloc(&s->phit_lo, rows * Dp);
+  if (!okm) {
+    snprintf(c->err, sizeof(c->err), "tensor-core operator: device allocation failed");
+    return 1;
+  }
+  k_split_bf16<<<4096, 256, 0, c->stream>>>(c->phi, s->phi_hi, s->phi_lo, rows * Dp);
+  k_transpose_split<<<dim3(Dp / 32, (unsigned)(rows / 32)), dim3(32, 8), 0, c->stream>>>(
+      c->phi, s->phit_hi, s->phit_lo, rows, (int)Dp);
+  cudaMemsetAsync(c->dhi, 0, sizeof(__nv_bfloat16) * S * Dp, c->stream);
+  cudaMemsetAsync(c->dlo, 0, sizeof(__nv_bfloat16) * S * Dp, c->stream);
+  bool ok = encode_2d(&s->tm_phi[0], s->phi_hi, Dp, rows, kBM) &&
+            encode_2d(&s->tm_phit[0], s->phit_hi, rows, Dp, kBM) &&
+            encode_2d(&s->tm_d[0], c->dhi, Dp, S, s->BR) && encode_2d(&s->tm_d[1], c->dlo, Dp, S, s->BR) &&
+            encode_2d(&s->tm_w[0], s->w_hi, rows, R, s->BR) && encode_2d(&s->tm_w[1], s->w_lo, rows, R, s->BR);
+  if (ok && s->NA == 2)
+    ok = encode_2d(&s->tm_phi[1], s->phi_lo, Dp, rows, kBM) &&
+         encode_2d(&s->tm_phit[1], s->phit_lo, rows, Dp, kBM);
+  if (!ok) {
+    snprintf(c->err, sizeof(c->err), "tensor-core operator: tensor map encoding failed");
+    return 1;
+  }
+  cudaError_t e = s->NA == 2 ? set_smem_attr<1, 2, 2>(s->smem_bytes) : set_smem_attr<1, 1, 2>(s->smem_bytes);
+  if (e == cudaSuccess)
+    e = s->NA == 2 ? set_smem_attr<2, 2, 2>(s->smem_bytes) : set_smem_attr<2, 1, 2>(s->smem_bytes);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    snprintf(c->err, sizeof(c->err), "tensor-core operator set-up: %s", cudaGetErrorString(e));
+    return 1;
+  }
+  c->launches += 2;
+  return 0;
+}
+
+void tc_destroy(Ctx* c) {
+  TcState* s = static_cast<TcState*>(c->tc);
+  if (!s) return;
+  void* ptrs[] = {s->phi_hi, s->phi_lo, s->phit_hi, s->phit_lo, s->w_hi, s->w_lo, c->dhi, c->dlo};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  c->dhi = c->dlo = nullptr;
+  free(s);
+  c->tc = nullptr;
+}
+
+cudaError_t tc_split_vectors(Ctx* c, const float* V) {
+  k_split_bf16<<<4096, 256, 0, c->stream>>>(V, static_cast<__nv_bfloat16*>(c->dhi),
+                                            static_cast<__nv_bfloat16*>(c->dlo), (int64_t)c->S * c->Dp);
+  c->launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t tc_operator(Ctx* c, const float* V, float* Z, int with_dots) {
+  TcState* s = static_cast<TcState*>(c->tc);
+  if (!s) return cudaErrorNotSupported;
+  return s->NA == 2 ? run_passes<2, 2>(c, s, V, Z, with_dots) : run_passes<1, 2>(c, s, V, Z, with_dots);
+}
 
 }  // namespace cmcs

@@ -93,7 +93,7 @@ def _cfg(**kw):
 
 @pytest.mark.parametrize("bad", [dict(T=0), dict(C=0), dict(D=0), dict(K=0), dict(beta=0.0),
                                  dict(beta=-1.0), dict(cg_max_iter=0), dict(cg_max_iter=513),
-                                 dict(cg_tol=-1.0), dict(precision=7), dict(refine_max=-1),
+                                 dict(cg_tol=-1.0), dict(precision=7), dict(precision=-1), dict(refine_max=-1),
                                  dict(refine_max=65), dict(alpha_min=0.0),
                                  dict(alpha_min=2.0, alpha_max=1.0)])
 def test_create_rejects_invalid_config_without_cuda(L, bad):

@@ -1,0 +1,83 @@
+"""Tensor-core operator (tcgen05) parity: the BF16-split operator against the FP64 oracle, and
+the E-step on it (with refinement) against the oracle.
+
+Bounds: BF16X3 keeps ~16 significant bits per product (Phi and the vectors each split into two
+BF16 parts, the lo*lo term dropped), so a normwise operator error of 1e-4 is ~6 units of 2^-16;
+BF16_REFINE rounds Phi itself to 8 bits (2^-9 relative per entry), bound 1e-2.  After
+refinement the E-step meets the path's tolerances: 1e-4 (BF16X3, the FP32 bar) and 1e-3 (BF16
+with refinement), responsibilities 1e-4 in coefficient replay."""
+import numpy as np
+import pytest
+
+from oracle import cofem
+from paper_2310_00420_gb300 import cmcs, synth
+
+from gpu_helpers import make_ctx, rel_err_rows, task_lists
+from test_gpu_parity import replay_q
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def small():
+    return synth.plain_small()
+
+
+@pytest.mark.parametrize("precision,bound", [("bf16x3", 1e-4), ("bf16", 1e-2)])
+def test_tc_operator_matches_oracle(small, precision, bound):
+    P, Y = task_lists(small)
+    R = small.C * (small.K + 1)
+    rng = np.random.default_rng(21)
+    V = rng.standard_normal((small.T, R, small.D)).astype(np.float32)
+    with make_ctx(small, precision=precision) as ctx:
+        alpha = ctx.read(cmcs.OUT_ALPHA).astype(np.float64)
+        Z = ctx.apply(V)
+        Z2 = ctx.apply(V)
+    assert np.array_equal(Z, Z2)                       # deterministic
+    errs = []
+    for t in range(small.T):
+        for j in range(R):
+            c = j // (small.K + 1)
+            ref = cofem.apply_A(P[t], small.beta, alpha[c], V[t, j].astype(np.float64))
+            errs.append(rel_err_rows(Z[t, j], ref))
+    assert max(errs) < bound, max(errs)
+
+
+@pytest.mark.parametrize("shape", [dict(T=3, C=3, D=200, N=(37, 150), K=5),
+                                   dict(T=2, C=4, D=384, N=(1, 300), K=70)])
+def test_tc_operator_ragged(shape):
+    """Uneven N_t, D not a multiple of 128, and R = C(K+1) = 284 > 256 (two TMEM column blocks)."""
+    wl = synth.make_workload("ragged", shape["T"], shape["C"], shape["D"], shape["N"], nnz=5,
+                             sigma=0.01, K=shape["K"], seed=9)
+    P, Y = task_lists(wl)
+    R = wl.C * (wl.K + 1)
+    V = np.random.default_rng(22).standard_normal((wl.T, R, wl.D)).astype(np.float32)
+    with make_ctx(wl, precision="bf16x3") as ctx:
+        alpha = ctx.read(cmcs.OUT_ALPHA).astype(np.float64)
+        Z = ctx.apply(V)
+    for t in range(wl.T):
+        for j in range(R):
+            c = j // (wl.K + 1)
+            ref = cofem.apply_A(P[t], wl.beta, alpha[c], V[t, j].astype(np.float64))
+            assert rel_err_rows(Z[t, j], ref) < 1e-4, (t, j)
+
+
+@pytest.mark.parametrize("precision,tol", [("bf16x3", 1e-4), ("bf16", 1e-3)])
+def test_tc_estep_parity(small, precision, tol):
+    P, Y = task_lists(small)
+    alpha = synth.uniform_alpha(small.C, small.D, seed=3)
+    with make_ctx(small, precision=precision, refine_max=16, refine_tol=1e-6) as ctx:
+        ctx.set_alpha(alpha, 2)
+        ctx.estep()
+        g = {k: ctx.read(v) for k, v in dict(mu=cmcs.OUT_MU, s=cmcs.OUT_S, q=cmcs.OUT_Q,
+                                              logdet=cmcs.OUT_LOGDET, ell=cmcs.OUT_ELL,
+                                              steps=cmcs.OUT_STEPS, gamma=cmcs.OUT_GAMMA,
+                                              xi=cmcs.OUT_XI, assign=cmcs.OUT_ASSIGN).items()}
+    o = cofem.cofem_estep(P, Y, alpha.astype(np.float64), small.pi, small.beta, small.K,
+                          small.seed, 2, small.cg_tol, small.cg_max_iter, refine_tol=1e-12,
+                          refine_max=40)
+    assert rel_err_rows(g["mu"], o["mu"]).max() <= tol
+    assert rel_err_rows(g["s"], o["s"]).max() <= tol
+    q_rep, _, _ = replay_q(small, g, o, alpha)
+    assert np.max(np.abs(g["q"] - q_rep)) <= 1e-4
+    assert np.array_equal(g["assign"], np.argmax(o["q"], axis=1))
