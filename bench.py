@@ -232,10 +232,27 @@ def run_ours(a):
                 "per_launch_ms": prof["operator_ms"] / max(1, prof["operator_calls"]),
                 "hbm_gbs_achieved": op_gbs, "hbm_frac": op_gbs / peaks["hbm_gbs"]}
     else:
-        pk = peaks["bf16_tflops_sustained"]
-        roof = {"bound": "tensor", "achieved": op_tflops, "peak": pk, "unit": "TFLOP/s",
-                "frac": op_tflops / pk, "traffic": None, "peak_source": src,
-                "hbm_gbs_achieved": op_gbs, "hbm_frac": op_gbs / peaks["hbm_gbs"]}
+        # tensor-core operator: bound by whichever of its algorithmic FLOPs at the measured BF16
+        # peak and its algorithmic bytes at the measured HBM bandwidth takes longer
+        pk_t = peaks["bf16_tflops_sustained"]
+        pk_b = peaks["hbm_gbs"]
+        t_flop = prof["operator_flops"] / (pk_t * 1e12)
+        t_byte = prof["operator_bytes"] / (pk_b * 1e9)
+        per = max(1, prof["operator_calls"])
+        common = {"kernel": "operator (k_tc<1> + k_tc<2>, tcgen05 BF16 split)",
+                  "per_launch_flops": prof["operator_flops"] / per,
+                  "per_launch_bytes": prof["operator_bytes"] / per,
+                  "per_launch_ms": prof["operator_ms"] / per, "traffic": None,
+                  "peak_source": f"MEASURED_PEAKS.json ({src}): HBM {pk_b} GB/s, "
+                                 f"BF16 sustained {pk_t} TFLOP/s",
+                  "tflops_achieved": op_tflops, "tensor_frac": op_tflops / pk_t}
+        if t_byte >= t_flop:
+            roof = {"bound": "hbm", "achieved": op_gbs, "peak": pk_b, "unit": "GB/s",
+                    "frac": op_gbs / pk_b, **common}
+        else:
+            roof = {"bound": "tensor", "achieved": op_tflops, "peak": pk_t, "unit": "TFLOP/s",
+                    "frac": op_tflops / pk_t, **common}
+        roof["hbm_gbs_achieved"] = op_gbs
 
     # error vs the FP64 oracle on one sampled (task, cluster) pair, and the CPU baseline
     cpu = None
@@ -298,7 +315,8 @@ def run_ours(a):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms_max / a.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f32" if a.precision == "fp32" else "bf16+f32", "data": "synthetic",
+                "dtype": {"fp32": "f32", "bf16": "bf16+f32", "bf16x3": "bf16x2+f32"}[a.precision],
+                "data": "synthetic",
                 "config": {"workload": f"{wl.name} T={wl.T} C={wl.C} D={wl.D} N={int(wl.N[0])} "
                                        f"K={wl.K} tol={wl.cg_tol} max_iter={wl.cg_max_iter}",
                            "precision": a.precision, "refine_max": a.refine_max,
@@ -307,6 +325,9 @@ def run_ours(a):
                 "cg_solves_per_s": value * systems,
                 "cg_steps_mean": summ["cg_steps_mean"], "cg_capped": summ["cg_capped"],
                 "refine_sweeps_max": summ["refine_sweeps_max"],
+                "refine_diverged": summ["refine_diverged"], "resid_rel_max": summ["resid_rel_max"],
+                "operator_share": prof["operator_ms"] / ms if ms else None,
+                "residual_ms_per_step": prof["residual_ms"] / a.steps,
                 "operator_applies_per_step": prof["operator_calls"] / a.steps,
                 "roofline": roof, "cpu_baseline": cpu, "err_vs_fp64": err, "e2e": e2e,
                 "clocks": clk, "gpu_launches": prof["kernel_launches"]}

@@ -93,6 +93,8 @@ typedef struct {
   int64_t operator_applies;/* batched operator applications (all systems) in the last E-step */
   double resid_rel_max;    /* largest ||b - A x|| / ||b|| of the returned solutions, from the
                               compensated residual after refinement (0 when refine_max = 0)  */
+  int64_t refine_diverged; /* systems whose refinement stopped because a correction grew (the
+                              inner solves did not contract); their last correction is undone */
 } cmcs_summary;
 
 /* What cmcs_read copies out.  Element types and shapes: */

@@ -44,7 +44,8 @@ class Summary(ctypes.Structure):
                 ("cg_steps_max", ctypes.c_int), ("cg_steps_mean", ctypes.c_double),
                 ("cg_capped", ctypes.c_int64), ("refine_sweeps_max", ctypes.c_int),
                 ("refine_rel_max", ctypes.c_double), ("min_margin", ctypes.c_double),
-                ("operator_applies", ctypes.c_int64), ("resid_rel_max", ctypes.c_double)]
+                ("operator_applies", ctypes.c_int64), ("resid_rel_max", ctypes.c_double),
+                ("refine_diverged", ctypes.c_int64)]
 
 
 class ProfileData(ctypes.Structure):

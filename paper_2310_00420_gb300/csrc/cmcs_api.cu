@@ -182,6 +182,7 @@ cmcs_status estep(Ctx* c) {
   CK(launch_ell_softmax(c, rmu));
   s = read_counters(c);
   if (s != CMCS_OK) return s;
+  c->last_diverged = c->hcounters[3];
   fold_events(c);
   if (c->hcounters[2] != 0) {
     set_err(c, "non-finite value or eigen failure in the E-step (flags 0x%x)", c->hcounters[2]);
@@ -587,6 +588,7 @@ cmcs_status cmcs_result(const cmcs_ctx* hc, cmcs_summary* out) {
   }
   out->cg_steps_mean = sum / c->S;
   out->operator_applies = c->op_applies;
+  out->refine_diverged = c->last_diverged;
   return CMCS_OK;
 }
 

@@ -106,7 +106,9 @@ struct Ctx {
   float* rrel;         // [S] last ||delta|| / ||x||
   float* rres;         // [S] ||b - A x|| / ||b|| of the returned solution
   int* task_active;    // [T]
-  int* counters;       // [4]: 0 active systems, 1 refine-active systems, 2 status flags
+  int* counters;       // [4]: 0 active systems, 1 refine-active systems, 2 status flags,
+                       //      3 systems whose refinement diverged (reverted) in this E-step
+  int last_diverged;   // host copy of counters[3] after the last E-step
   int* hcounters;      // pinned host mirror [4]
   float *gam, *xi;     // [T*C*K][U]
   int* psteps;         // [T*C*K] CG steps of the probe systems' first solve

@@ -216,14 +216,35 @@ k_refine_update(float* __restrict__ xacc, const float* __restrict__ delta, int* 
   }
   const float dn2 = block_sum(a1, sh);
   const float xn2 = block_sum(a2, sh);
+  __shared__ int s_revert;
   if (threadIdx.x == 0) {
-    sweeps[sys] += 1;
+    const int sw = sweeps[sys] + 1;
+    sweeps[sys] = sw;
     const float rel = xn2 > 0.f ? sqrtf(dn2 / xn2) : 0.f;
-    rrel[sys] = rel;
-    if (rel <= rtol || !(xn2 > 0.f)) {
+    const float prev = rrel[sys];
+    // a correction larger than the previous one means the inner solves no longer contract:
+    // undo it, stop refining this system and count it
+    const int diverged = (sw > 1 && rel > prev) || !isfinite(rel);
+    s_revert = diverged;
+    if (diverged) {
       ractive[sys] = 0;
+      atomicAdd(&counters[3], 1);
     } else {
-      atomicAdd(&counters[1], 1);
+      rrel[sys] = rel;
+      if (rel <= rtol || !(xn2 > 0.f)) {
+        ractive[sys] = 0;
+      } else {
+        atomicAdd(&counters[1], 1);
+      }
+    }
+  }
+  __syncthreads();
+  if (s_revert) {
+    for (int i = threadIdx.x * 4; i < Dp; i += 256 * 4) {
+      float4 xv = *reinterpret_cast<float4*>(xa + i);
+      const float4 dv = *reinterpret_cast<const float4*>(de + i);
+      xv.x -= dv.x; xv.y -= dv.y; xv.z -= dv.z; xv.w -= dv.w;
+      *reinterpret_cast<float4*>(xa + i) = xv;
     }
   }
 }

@@ -58,6 +58,7 @@ int main(void) {
   O(cmcs_summary, cg_capped); O(cmcs_summary, refine_sweeps_max);
   O(cmcs_summary, refine_rel_max); O(cmcs_summary, min_margin);
   O(cmcs_summary, operator_applies); O(cmcs_summary, resid_rel_max);
+  O(cmcs_summary, refine_diverged);
   return 0;
 }
 """

@@ -62,7 +62,22 @@ def test_tc_operator_ragged(shape):
             assert rel_err_rows(Z[t, j], ref) < 1e-4, (t, j)
 
 
-@pytest.mark.parametrize("precision,tol", [("bf16x3", 1e-4), ("bf16", 1e-3)])
+def test_bf16_phi_refinement_divergence_is_detected(small):
+    """Rounding Phi itself to BF16 moves the small eigenvalues of A by about
+    beta ||Phi - bf16(Phi)||^2 ~ 1 here, more than the smallest alpha, so refinement from
+    BF16-Phi inner solves does not contract.  The library must notice, undo the growing
+    corrections and report the systems, not return a blown-up solution silently."""
+    alpha = synth.uniform_alpha(small.C, small.D, seed=3)
+    with make_ctx(small, precision="bf16", refine_max=16, refine_tol=1e-6) as ctx:
+        ctx.set_alpha(alpha, 2)
+        ctx.estep()
+        summ = ctx.summary()
+        mu = ctx.read(cmcs.OUT_MU)
+    assert summ["refine_diverged"] > 0
+    assert np.all(np.isfinite(mu))
+
+
+@pytest.mark.parametrize("precision,tol", [("bf16x3", 1e-4)])
 def test_tc_estep_parity(small, precision, tol):
     P, Y = task_lists(small)
     alpha = synth.uniform_alpha(small.C, small.D, seed=3)
