@@ -9,12 +9,13 @@
 // BF16-rounded Phi by (V_hi + V_lo) (two MMAs per k-step); BF16X3 also splits Phi and adds
 // Phi_lo V_hi (three MMAs), about 16 significant bits per product.
 //
-// One CTA (4 warps) owns one 128-row output tile and all R columns (up to 512 TMEM columns).
-// Warp 0 lane 0 streams A and B tiles with TMA (128-byte swizzle) through a ring of shared-memory
-// stages; warp 1 lane 0 issues tcgen05.mma from shared-memory descriptors into TMEM; then all
-// four warps drain TMEM (tcgen05.ld, 32 rows each) in the epilogue.  Every mbarrier wait is
-// bounded: on expiry the kernel records CMCS status bit 8, stops issuing, waits (bounded) for its
-// copies in flight and still frees its TMEM.
+// Persistent kernel, one CTA (6 warps) per SM, looping over 128-row output tiles (each with all
+// R columns, up to 512 TMEM columns).  Warp 0 lane 0 streams A and B tiles with TMA (128-byte
+// swizzle) through a ring of shared-memory stages; warp 1 lane 0 issues tcgen05.mma from
+// shared-memory descriptors into one of two TMEM accumulators; warps 2-5 drain the other
+// accumulator (tcgen05.ld, 32 rows each), so a tile's epilogue overlaps the next tile's
+// mainloop.  Every mbarrier wait is bounded: on expiry the kernel records status bit 8, stops
+// issuing, waits (bounded) for its copies and MMAs in flight and still frees its TMEM.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -29,8 +30,9 @@ namespace {
 
 constexpr int kBM = 128;                   // rows of an output tile (MMA M)
 constexpr int kBK = 64;                    // K per stage: one 128-byte row of BF16
-constexpr int kTcThreads = 128;
-constexpr uint32_t kWaitLimit = 1u << 24;  // try_wait polls before a wait is declared stuck
+constexpr int kEpiWarps = 4;               // warps 2..5 drain TMEM
+constexpr int kTcThreads = 64 + 32 * kEpiWarps;
+constexpr uint64_t kWaitNs = 2000000000ull; // wall time before an mbarrier wait is declared stuck
 constexpr int kSmemBudget = 225 * 1024;
 
 struct TcArgs {
@@ -40,7 +42,9 @@ struct TcArgs {
   int R, K, C, Dp, D, S;
   int64_t rows_total;
   int Rpad, BR, nbox, stages, stage_bytes;
-  uint32_t tmem_cols;
+  int ntiles, nbuf;
+  uint32_t tmem_cols;     // columns of one accumulator buffer
+  uint32_t tmem_alloc;    // columns allocated (nbuf buffers)
   __nv_bfloat16* w_hi;    // pass 1 output, [R][rows_total]
   __nv_bfloat16* w_lo;
   const float* V;         // pass 2 epilogue: the FP32 vectors A is applied to, [S][D_pad]
@@ -77,10 +81,19 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// bounded wait: false once kWaitNs of wall time has passed without the phase completing
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (uint32_t i = 0; i < kWaitLimit; ++i)
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (uint32_t i = 1;; ++i) {
     if (mbar_try_wait(bar, parity)) return true;
-  return false;
+    if ((i & 255u) == 0 && global_ns() - t0 > kWaitNs) return false;
+  }
 }
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tm, int x, int y,
                                             uint64_t* bar) {
@@ -149,7 +162,75 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 
 }  // namespace
 
-// ---- the GEMM kernel ---------------------------------------------------------------------
+// ---- the GEMM kernel (persistent, two TMEM accumulators) --------------------------------
+struct TileInfo {
+  int t, a_row, b_row, kx, nk, dtile;
+};
+
+template <int PASS>
+__device__ __forceinline__ bool tile_info(const TcArgs& p, int tile, TileInfo& ti) {
+  if (PASS == 1) {
+    ti.t = p.tile_task[tile];
+    ti.a_row = tile * kBM;
+    ti.b_row = ti.t * p.R;
+    ti.kx = 0;
+    ti.nk = p.Dp / kBK;
+    ti.dtile = 0;
+  } else {
+    const int ndt = p.Dp / kBM;
+    ti.t = tile / ndt;
+    ti.dtile = tile - ti.t * ndt;
+    ti.a_row = ti.dtile * kBM;
+    ti.b_row = 0;
+    ti.kx = (int)p.drow[ti.t];
+    ti.nk = (int)((p.drow[ti.t + 1] - p.drow[ti.t]) / kBK);
+  }
+  return p.task_active == nullptr || p.task_active[ti.t] != 0;
+}
+
+// Sum each of 16 per-lane values over the 32 lanes of a warp with 16 shuffles: every step
+// hands half of the remaining values to the partner lane.  The lane with bit 0 clear returns
+// the total of value index ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2
+// + ((lane >> 1) & 1).
+__device__ __forceinline__ float warp_reduce16(float* v, int lane) {
+#pragma unroll
+  for (int w = 8, off = 16; w >= 1; w >>= 1, off >>= 1) {
+    const bool up = (lane & off) != 0;
+#pragma unroll
+    for (int i = 0; i < w; ++i) {
+      const float send = up ? v[i] : v[i + w];
+      const float keep = up ? v[i + w] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+    }
+  }
+  return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
+__device__ __forceinline__ int reduce16_index(int lane) {
+  return ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void epi_bar() {   // the four epilogue warps only
+  asm volatile("bar.sync 1, 128;" ::: "memory");
+}
+// barrier of the four epilogue warps that also returns whether any of them passed true, so
+// every epilogue thread takes the same branch
+__device__ __forceinline__ bool epi_bar_any(bool pred) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 q, %1, 0;\n\t"
+      "bar.red.or.pred p, 1, 128, q;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(r)
+      : "r"((uint32_t)pred)
+      : "memory");
+  return r != 0;
+}
+
 template <int PASS, int NA, int NB>
 __global__ void __launch_bounds__(kTcThreads, 1)
 k_tc(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMap tA1,
@@ -160,170 +241,196 @@ k_tc(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMa
                                              ~static_cast<uintptr_t>(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)p.stages * p.stage_bytes);
   uint64_t* empty = full + p.stages;
-  uint64_t* done = empty + p.stages;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  uint64_t* tfull = empty + p.stages;        // [2] accumulator ready for the epilogue
+  uint64_t* tempty = tfull + 2;              // [2] accumulator drained
+  uint64_t* mdone = tempty + 2;              // every MMA issued has completed
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mdone + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   float* red = reinterpret_cast<float*>(tmem_slot + 4);          // [4][Rpad] (pass 2)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-
-  int t, a_row, b_row, kx, nk, dtile = 0;
-  if (PASS == 1) {
-    const int g = blockIdx.x;
-    t = p.tile_task[g];
-    a_row = g * kBM;
-    b_row = t * p.R;
-    kx = 0;
-    nk = p.Dp / kBK;
-  } else {
-    dtile = blockIdx.x;
-    t = blockIdx.y;
-    a_row = dtile * kBM;
-    b_row = 0;
-    kx = (int)p.drow[t];
-    nk = (int)((p.drow[t + 1] - p.drow[t]) / kBK);
-  }
-  if (p.task_active != nullptr && p.task_active[t] == 0) return;   // whole CTA, before set-up
-  if (PASS == 2 && p.opcount != nullptr && dtile == 0 && threadIdx.x == 0)
-    atomicAdd(&p.opcount[t], 1ull);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < p.stages; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(done, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 32 * kEpiWarps);
+    }
+    mbar_init(mdone, 1);
     *abort_flag = 0;
     fence_mbar_init();
   }
-  if (warp == 0) tmem_alloc(tmem_slot, p.tmem_cols);
+  if (warp == 0) tmem_alloc(tmem_slot, p.tmem_alloc);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   const uint32_t a_bytes = kBM * kBK * 2;                  // 16 KiB per A operand
   const uint32_t b_bytes = (uint32_t)p.Rpad * kBK * 2;     // per B operand
-  int issued = 0;                                          // stages the producer issued
+  uint32_t issued = 0;                                      // k-blocks the producer issued
 
-  if (warp == 0 && lane == 0) {
+  if (warp == 0) {
     // ---- TMA producer
-    for (int kb = 0; kb < nk; ++kb) {
-      const int s = kb % p.stages;
-      if (kb >= p.stages && !mbar_wait(&empty[s], ((kb / p.stages) - 1) & 1)) {
-        *abort_flag = 1;
-        atomicOr(p.status, 8);
-        break;
-      }
-      if (*abort_flag) break;
-      uint8_t* st = smem + (size_t)s * p.stage_bytes;
-      mbar_expect_tx(&full[s], (uint32_t)p.stage_bytes);
-      tma_load_2d(st, &tA0, kx + kb * kBK, a_row, &full[s]);
-      if (NA == 2) tma_load_2d(st + a_bytes, &tA1, kx + kb * kBK, a_row, &full[s]);
-      uint8_t* bst = st + NA * a_bytes;
-      for (int bx = 0; bx < p.nbox; ++bx) {
-        tma_load_2d(bst + bx * p.BR * 128, &tB0, kx + kb * kBK, b_row + bx * p.BR, &full[s]);
-        if (NB == 2)
-          tma_load_2d(bst + b_bytes + bx * p.BR * 128, &tB1, kx + kb * kBK, b_row + bx * p.BR, &full[s]);
-      }
-      issued = kb + 1;
-    }
-  } else if (warp == 1 && lane == 0) {
-    // ---- MMA issuer
-    const uint32_t idesc = idesc_bf16(kBM, p.BR);
-    for (int kb = 0; kb < nk; ++kb) {
-      const int s = kb % p.stages;
-      if (!mbar_wait(&full[s], (kb / p.stages) & 1)) {
-        *abort_flag = 1;
-        atomicOr(p.status, 8);
-        break;
-      }
-      tc_fence_after();
-      const uint32_t st = smem_u32(smem + (size_t)s * p.stage_bytes);
-#pragma unroll
-      for (int kk = 0; kk < kBK / 16; ++kk) {
-        const uint64_t a0 = smem_desc(st + kk * 32);
-        const uint64_t a1 = smem_desc(st + a_bytes + kk * 32);
-        for (int bx = 0; bx < p.nbox; ++bx) {
-          const uint32_t bo = st + NA * a_bytes + bx * p.BR * 128 + kk * 32;
-          const uint32_t dt = tmem + (uint32_t)(bx * p.BR);
-          mma_bf16(dt, a0, smem_desc(bo), idesc, (kb > 0 || kk > 0) ? 1u : 0u);
-          if (NB == 2) mma_bf16(dt, a0, smem_desc(bo + b_bytes), idesc, 1u);
-          if (NA == 2) mma_bf16(dt, a1, smem_desc(bo), idesc, 1u);
-        }
-      }
-      mma_commit(&empty[s]);
-    }
-    mma_commit(done);    // arrives once every MMA issued above has completed
-  }
-  __syncwarp();
-
-  // ---- epilogue (all four warps; warp w reads TMEM lanes 32w .. 32w+31)
-  const bool ok = mbar_wait(done, 0);
-  tc_fence_after();
-  if (!ok) {
-    *abort_flag = 1;
-    if (lane == 0) atomicOr(p.status, 8);
-  }
-  __syncthreads();
-  const bool run = !*abort_flag;
-  const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
-  if (PASS == 1) {
-    if (run) {
-      const int64_t n = (int64_t)a_row + 32 * warp + lane;    // global row of Phi
-      for (int c0 = 0; c0 < p.Rpad; c0 += 16) {
-        float v[16];
-        tmem_ld16(trow + c0, v);
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const int j = c0 + i;
-          if (j < p.R) {
-            const __nv_bfloat16 hi = __float2bfloat16_rn(v[i]);
-            const __nv_bfloat16 lo = __float2bfloat16_rn(v[i] - __bfloat162float(hi));
-            p.w_hi[(int64_t)j * p.rows_total + n] = hi;
-            p.w_lo[(int64_t)j * p.rows_total + n] = lo;
+    if (lane == 0) {
+      uint32_t it = 0;
+      for (int tile = blockIdx.x; tile < p.ntiles && !*abort_flag; tile += gridDim.x) {
+        TileInfo ti;
+        if (!tile_info<PASS>(p, tile, ti)) continue;
+        for (int kb = 0; kb < ti.nk; ++kb, ++it) {
+          const int s = (int)(it % p.stages);
+          if (it >= (uint32_t)p.stages && !mbar_wait(&empty[s], ((it / p.stages) - 1) & 1)) {
+            *abort_flag = 1;
+            atomicOr(p.status, 8);
+            break;
           }
+          if (*abort_flag) break;
+          uint8_t* st = smem + (size_t)s * p.stage_bytes;
+          mbar_expect_tx(&full[s], (uint32_t)p.stage_bytes);
+          tma_load_2d(st, &tA0, ti.kx + kb * kBK, ti.a_row, &full[s]);
+          if (NA == 2) tma_load_2d(st + a_bytes, &tA1, ti.kx + kb * kBK, ti.a_row, &full[s]);
+          uint8_t* bst = st + NA * a_bytes;
+          for (int bx = 0; bx < p.nbox; ++bx) {
+            tma_load_2d(bst + bx * p.BR * 128, &tB0, ti.kx + kb * kBK, ti.b_row + bx * p.BR, &full[s]);
+            if (NB == 2)
+              tma_load_2d(bst + b_bytes + bx * p.BR * 128, &tB1, ti.kx + kb * kBK,
+                          ti.b_row + bx * p.BR, &full[s]);
+          }
+          issued = it + 1;
         }
       }
+    }
+  } else if (warp == 1) {
+    // ---- MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16(kBM, p.BR);
+      uint32_t it = 0, lt = 0;
+      for (int tile = blockIdx.x; tile < p.ntiles && !*abort_flag; tile += gridDim.x) {
+        TileInfo ti;
+        if (!tile_info<PASS>(p, tile, ti)) continue;
+        const int b = (int)(lt % p.nbuf);
+        if (lt >= (uint32_t)p.nbuf && !mbar_wait(&tempty[b], ((lt / p.nbuf) - 1) & 1)) {
+          *abort_flag = 1;
+          atomicOr(p.status, 8);
+          break;
+        }
+        tc_fence_after();
+        const uint32_t dbase = tmem + (uint32_t)b * p.tmem_cols;
+        bool stop = false;
+        for (int kb = 0; kb < ti.nk; ++kb, ++it) {
+          const int s = (int)(it % p.stages);
+          if (!mbar_wait(&full[s], (it / p.stages) & 1)) {
+            *abort_flag = 1;
+            atomicOr(p.status, 8);
+            stop = true;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t st = smem_u32(smem + (size_t)s * p.stage_bytes);
+#pragma unroll
+          for (int kk = 0; kk < kBK / 16; ++kk) {
+            const uint64_t a0 = smem_desc(st + kk * 32);
+            const uint64_t a1 = smem_desc(st + a_bytes + kk * 32);
+            for (int bx = 0; bx < p.nbox; ++bx) {
+              const uint32_t bo = st + NA * a_bytes + bx * p.BR * 128 + kk * 32;
+              const uint32_t dt = dbase + (uint32_t)(bx * p.BR);
+              mma_bf16(dt, a0, smem_desc(bo), idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+              if (NB == 2) mma_bf16(dt, a0, smem_desc(bo + b_bytes), idesc, 1u);
+              if (NA == 2) mma_bf16(dt, a1, smem_desc(bo), idesc, 1u);
+            }
+          }
+          mma_commit(&empty[s]);
+        }
+        if (stop) break;
+        mma_commit(&tfull[b]);
+        ++lt;
+      }
+      mma_commit(mdone);
+      if (!mbar_wait(mdone, 0)) atomicOr(p.status, 8);
     }
   } else {
-    const int d = a_row + 32 * warp + lane;                   // coordinate of this row
-    if (run) {
-      for (int c0 = 0; c0 < p.Rpad; c0 += 16) {
-        float v[16];
-        tmem_ld16(trow + c0, v);
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const int j = c0 + i;
-          float dot = 0.f;
-          if (j < p.R) {
-            const int64_t sys = (int64_t)t * p.R + j;
-            const int c = j / (p.K + 1);
-            const float vv = p.V[sys * p.Dp + d];
-            const float ad = fmaf(p.beta, v[i], p.alpha[(int64_t)c * p.Dp + d] * vv);
-            p.Z[sys * p.Dp + d] = ad;
-            dot = vv * ad;
-          }
-#pragma unroll
-          for (int m = 16; m > 0; m >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, m);
-          if (lane == 0 && j < p.Rpad) red[warp * p.Rpad + j] = dot;
-        }
+    // ---- epilogue: warp w may read TMEM lanes 32 (w % 4) .. 32 (w % 4) + 31
+    const int lg = warp & 3;
+    const int etid = threadIdx.x - 64;                 // 0..127 among the epilogue warps
+    uint32_t lt = 0;
+    for (int tile = blockIdx.x; tile < p.ntiles; tile += gridDim.x) {
+      TileInfo ti;
+      if (!tile_info<PASS>(p, tile, ti)) continue;
+      const int b = (int)(lt % p.nbuf);
+      const bool ok = mbar_wait(&tfull[b], (lt / p.nbuf) & 1);
+      if (!ok) {
+        *abort_flag = 1;
+        if (lane == 0) atomicOr(p.status, 8);
       }
-    }
-    __syncthreads();
-    if (run && p.part != nullptr) {
-      for (int j = threadIdx.x; j < p.R; j += kTcThreads)
-        p.part[(int64_t)dtile * p.S + (int64_t)t * p.R + j] =
-            ((red[j] + red[p.Rpad + j]) + red[2 * p.Rpad + j]) + red[3 * p.Rpad + j];
+      if (epi_bar_any(!ok || *abort_flag)) break;   // uniform across the epilogue warps
+      tc_fence_after();
+      const uint32_t trow = tmem + (uint32_t)b * p.tmem_cols + ((uint32_t)(32 * lg) << 16);
+      if (PASS == 1) {
+        const int64_t n = (int64_t)ti.a_row + 32 * lg + lane;     // global row of Phi
+        for (int c0 = 0; c0 < p.Rpad; c0 += 16) {
+          float v[16];
+          tmem_ld16(trow + c0, v);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const int j = c0 + i;
+            if (j < p.R) {
+              const __nv_bfloat16 hi = __float2bfloat16_rn(v[i]);
+              const __nv_bfloat16 lo = __float2bfloat16_rn(v[i] - __bfloat162float(hi));
+              p.w_hi[(int64_t)j * p.rows_total + n] = hi;
+              p.w_lo[(int64_t)j * p.rows_total + n] = lo;
+            }
+          }
+        }
+      } else {
+        const int d = ti.a_row + 32 * lg + lane;
+        if (p.opcount != nullptr && ti.dtile == 0 && etid == 0) atomicAdd(&p.opcount[ti.t], 1ull);
+        for (int c0 = 0; c0 < p.Rpad; c0 += 16) {
+          float vv[16], aa[16];
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const int j = c0 + i;
+            const int jj = j < p.R ? j : 0;
+            const int64_t sys = (int64_t)ti.t * p.R + jj;
+            vv[i] = j < p.R ? __ldg(p.V + sys * p.Dp + d) : 0.f;
+            aa[i] = j < p.R ? __ldg(p.alpha + (int64_t)(jj / (p.K + 1)) * p.Dp + d) : 0.f;
+          }
+          float acc[16], dot[16];
+          tmem_ld16(trow + c0, acc);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const int j = c0 + i;
+            const float ad = fmaf(p.beta, acc[i], aa[i] * vv[i]);
+            if (j < p.R) p.Z[((int64_t)ti.t * p.R + j) * p.Dp + d] = ad;
+            dot[i] = vv[i] * ad;
+          }
+          const float tot = warp_reduce16(dot, lane);
+          if ((lane & 1) == 0) red[lg * p.Rpad + c0 + reduce16_index(lane)] = tot;
+        }
+        epi_bar();
+        if (p.part != nullptr) {
+          for (int j = etid; j < p.R; j += 128)
+            p.part[(int64_t)ti.dtile * p.S + (int64_t)ti.t * p.R + j] =
+                ((red[j] + red[p.Rpad + j]) + red[2 * p.Rpad + j]) + red[3 * p.Rpad + j];
+        }
+        epi_bar();
+      }
+      tc_fence_before();
+      mbar_arrive(&tempty[b]);
+      ++lt;
     }
   }
 
   // ---- teardown: no copy may still be landing in shared memory when the CTA exits
+  __syncwarp();
   if (*abort_flag && warp == 0 && lane == 0) {
-    for (int kb = issued - 1; kb >= 0 && kb >= issued - p.stages; --kb)
-      mbar_wait(&full[kb % p.stages], (kb / p.stages) & 1);
+    for (uint32_t k = issued; k > 0 && k + p.stages > issued; --k)
+      mbar_wait(&full[(k - 1) % p.stages], ((k - 1) / p.stages) & 1);
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) tmem_dealloc(tmem, p.tmem_cols);
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(tmem, p.tmem_alloc);
 }
 
 // ---- set-up kernels ----------------------------------------------------------------------
@@ -361,8 +468,8 @@ namespace {
 
 struct TcState {
   int NA, NB;
-  int Rpad, BR, nbox, stages, stage_bytes, smem_bytes;
-  uint32_t tmem_cols;
+  int Rpad, BR, nbox, stages, stage_bytes, smem_bytes, nbuf;
+  uint32_t tmem_cols, tmem_alloc;
   __nv_bfloat16 *phi_hi, *phi_lo, *phit_hi, *phit_lo, *w_hi, *w_lo;
   CUtensorMap tm_phi[2], tm_phit[2], tm_d[2], tm_w[2];
 };
@@ -416,6 +523,8 @@ TcArgs base_args(Ctx* c, TcState* s) {
   a.stages = s->stages;
   a.stage_bytes = s->stage_bytes;
   a.tmem_cols = s->tmem_cols;
+  a.tmem_alloc = s->tmem_alloc;
+  a.nbuf = s->nbuf;
   a.w_hi = s->w_hi;
   a.w_lo = s->w_lo;
   a.alpha = c->alpha;
@@ -432,13 +541,15 @@ cudaError_t run_passes(Ctx* c, TcState* s, const float* V, float* Z, int with_do
   a.V = V;
   a.Z = Z;
   a.part = with_dots ? c->part : nullptr;
-  k_tc<1, NA, NB><<<(unsigned)(c->rows_total / kBM), kTcThreads, s->smem_bytes, c->stream>>>(
+  const int sms = c->sm_count > 0 ? c->sm_count : 1;
+  a.ntiles = (int)(c->rows_total / kBM);
+  k_tc<1, NA, NB><<<a.ntiles < sms ? a.ntiles : sms, kTcThreads, s->smem_bytes, c->stream>>>(
       s->tm_phi[0], s->tm_phi[NA - 1], s->tm_d[0], s->tm_d[NB - 1], a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  dim3 g2(c->Dp / kBM, c->T);
-  k_tc<2, NA, NB><<<g2, kTcThreads, s->smem_bytes, c->stream>>>(s->tm_phit[0], s->tm_phit[NA - 1],
-                                                                s->tm_w[0], s->tm_w[NB - 1], a);
+  a.ntiles = c->T * (c->Dp / kBM);
+  k_tc<2, NA, NB><<<a.ntiles < sms ? a.ntiles : sms, kTcThreads, s->smem_bytes, c->stream>>>(
+      s->tm_phit[0], s->tm_phit[NA - 1], s->tm_w[0], s->tm_w[NB - 1], a);
   c->launches += 2;
   return cudaGetLastError();
 }
@@ -460,15 +571,17 @@ int tc_create(Ctx* c) {
   }
   s->tmem_cols = 32;
   while ((int)s->tmem_cols < s->Rpad) s->tmem_cols <<= 1;
+  s->nbuf = 2 * s->tmem_cols <= 512 ? 2 : 1;     // double-buffer the accumulator when it fits
+  s->tmem_alloc = s->tmem_cols * (uint32_t)s->nbuf;
   s->stage_bytes = s->NA * kBM * kBK * 2 + s->NB * s->Rpad * kBK * 2;
-  const int extra = 1024 + 2 * 8 * 8 + 8 + 16 + 4 * s->Rpad * 4 + 64;
+  const int extra = 1024 + (2 * 6 + 5) * 8 + 16 + 4 * s->Rpad * 4 + 64;
   s->stages = (kSmemBudget - extra) / s->stage_bytes;
   if (s->stages > 6) s->stages = 6;
   if (s->stages < 2) {
     snprintf(c->err, sizeof(c->err), "tensor-core operator: stage of %d bytes does not fit", s->stage_bytes);
     return 1;
   }
-  s->smem_bytes = s->stages * s->stage_bytes + 1024 + (2 * s->stages + 1) * 8 + 16 + 4 * s->Rpad * 4 + 64;
+  s->smem_bytes = s->stages * s->stage_bytes + 1024 + (2 * s->stages + 5) * 8 + 16 + 4 * s->Rpad * 4 + 64;
 
   const int64_t rows = c->rows_total, Dp = c->Dp, S = c->S, R = c->R;
   auto alloc = [&](__nv_bfloat16** p, int64_t n) {
