@@ -91,7 +91,7 @@ typedef struct {
   double refine_rel_max;   /* largest final ||delta|| / ||x|| over refined systems (0: none) */
   double min_margin;       /* smallest gap q_{t,a_t} - max_{c != a_t} q_tc over tasks        */
   int64_t operator_applies;/* batched operator applications (all systems) in the last E-step */
-  double resid_rel_max;    /* largest ||b - A x|| / ||b|| of the returned solutions, from the
+  double resid_rel_max;    /* largest ||b0 - A mu|| / ||b0|| of the returned means, from the
                               compensated residual after refinement (0 when refine_max = 0)  */
   int64_t refine_diverged; /* systems whose refinement stopped because a correction grew (the
                               inner solves did not contract); their last correction is undone */
@@ -114,8 +114,8 @@ typedef enum {
   CMCS_OUT_XI = 10,      /* float  [T][C][K][cg_max_iter] CG coefficients xi_u, zero past U */
   CMCS_OUT_B0 = 11,      /* float  [T][D]     beta Phi_t^T y_t (Eq. 7)                      */
   CMCS_OUT_SWEEPS = 12,  /* int32  [T][C][K+1] refinement sweeps taken per system           */
-  CMCS_OUT_RESID = 13    /* float  [T][C][K+1] ||b - A x|| / ||b|| of the returned solutions
-                                              (0 when refine_max = 0)                     */
+  CMCS_OUT_RESID = 13    /* float  [T][C][K+1] ||b - A x|| / ||b|| of the returned means
+                                              (index 0; other entries and refine_max = 0: 0) */
 } cmcs_output;
 
 /* Create a context: validates cfg, copies Phi and y into library-owned device memory (padded

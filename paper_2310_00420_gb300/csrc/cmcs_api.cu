@@ -170,8 +170,9 @@ cmcs_status estep(Ctx* c) {
   }
   const float* rmu = nullptr;
   if (c->refine_max > 0) {
-    // residual of the returned solutions: verified accuracy and the correction of ell
-    CK(launch_residual(c, c->xacc, nullptr, c->r, 1));
+    // residual of the returned means: verified accuracy and the correction of ell
+    CK(cudaMemsetAsync(c->rres, 0, sizeof(float) * c->S, c->stream));
+    CK(launch_residual(c, c->xacc, nullptr, c->r, 1, 1));
     CK(launch_resid_norm(c));
     rmu = c->r;
   } else {

@@ -151,7 +151,7 @@ cudaError_t launch_sest(Ctx* c);
 cudaError_t launch_operator(Ctx* c, const float* V, float* Z, int with_dots);
 // accurate residual: r = B - A xacc, B = b0 (k = 0) or the probe (k >= 1) when Bext == null
 cudaError_t launch_residual(Ctx* c, const float* X, const float* Bext, float* Rout,
-                            int all_systems = 0);
+                            int all_systems = 0, int means_only = 0);
 cudaError_t launch_resid_norm(Ctx* c);
 // E-step tail and M-step (kernels_estep.cu)
 cudaError_t launch_quadrature(const float* gam, const float* xi, const int* steps, int nsys,

@@ -113,6 +113,9 @@ k_cg_init(int mode, float* __restrict__ x, float* __restrict__ r, float* __restr
 }
 
 // ---- one CG step after the operator has produced ad = A d (Alg. 1, loop body) ----------
+// NV > 0: each thread keeps its NV float4s of r_{u+1} and d_u in registers between the two
+// phases (D_pad <= 1024 NV); NV = 0: generic loop that re-reads them.
+template <int NV>
 __global__ void __launch_bounds__(256)
 k_cg_update(float* __restrict__ x, float* __restrict__ r, float* __restrict__ d,
             const float* __restrict__ ad, const float* __restrict__ part, int ndt, float* rr,
@@ -149,7 +152,8 @@ k_cg_update(float* __restrict__ x, float* __restrict__ r, float* __restrict__ d,
   float* ds = d + sys * Dp;
   const float* as = ad + sys * Dp;
   float acc = 0.f;
-  for (int i = threadIdx.x * 4; i < Dp; i += 256 * 4) {
+  float4 rk[NV > 0 ? NV : 1], dk[NV > 0 ? NV : 1];
+  auto step1 = [&](int i, float4& ro, float4& dout) {
     float4 xv = *reinterpret_cast<float4*>(xs + i);
     float4 rv = *reinterpret_cast<float4*>(rs + i);
     const float4 dv = *reinterpret_cast<const float4*>(ds + i);
@@ -164,16 +168,35 @@ k_cg_update(float* __restrict__ x, float* __restrict__ r, float* __restrict__ d,
     acc = fmaf(rv.y, rv.y, acc);
     acc = fmaf(rv.z, rv.z, acc);
     acc = fmaf(rv.w, rv.w, acc);
+    ro = rv;
+    dout = dv;
+  };
+  if constexpr (NV > 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      const int i = (threadIdx.x + 256 * q) * 4;
+      if (i < Dp) step1(i, rk[q], dk[q]);
+    }
+  } else {
+    for (int i = threadIdx.x * 4; i < Dp; i += 256 * 4) step1(i, rk[0], dk[0]);
   }
   const float rr1 = block_sum(acc, sh);            // r_{u+1}^T r_{u+1}
   const float xi = rr1 / rr0;                      // xi_u
-  for (int i = threadIdx.x * 4; i < Dp; i += 256 * 4) {
-    const float4 rv = *reinterpret_cast<const float4*>(rs + i);
-    float4 dv = *reinterpret_cast<float4*>(ds + i);
+  auto step2 = [&](int i, float4 rv, float4 dv) {
     dv.x = fmaf(xi, dv.x, rv.x); dv.y = fmaf(xi, dv.y, rv.y);
     dv.z = fmaf(xi, dv.z, rv.z); dv.w = fmaf(xi, dv.w, rv.w);
     *reinterpret_cast<float4*>(ds + i) = dv;
     if (dhi != nullptr) store_split4(dhi, dlo, sys * Dp + i, dv);
+  };
+  if constexpr (NV > 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      const int i = (threadIdx.x + 256 * q) * 4;
+      if (i < Dp) step2(i, rk[q], dk[q]);
+    }
+  } else {
+    for (int i = threadIdx.x * 4; i < Dp; i += 256 * 4)
+      step2(i, *reinterpret_cast<const float4*>(rs + i), *reinterpret_cast<const float4*>(ds + i));
   }
   if (threadIdx.x == 0) {
     const int u = steps[sys];
@@ -256,6 +279,7 @@ k_resid_norm(const float* __restrict__ r, const float* __restrict__ b0hi,
   __shared__ double sh[33];
   const int64_t sys = blockIdx.x;
   const int t = (int)(sys / R), j = (int)(sys % R), k = j % (K + 1);
+  if (k != 0) return;                  // the final residual is formed for the mean systems
   const float* rs = r + sys * Dp;
   double a1 = 0.0, a2 = 0.0;
   for (int d = threadIdx.x; d < D; d += 256) {
@@ -267,7 +291,7 @@ k_resid_norm(const float* __restrict__ r, const float* __restrict__ b0hi,
     }
   }
   const double rr = block_sum(a1, sh);
-  const double bb = (k == 0) ? block_sum(a2, sh) : (double)D;
+  const double bb = block_sum(a2, sh);
   if (threadIdx.x == 0) rres[sys] = bb > 0.0 ? (float)sqrt(rr / bb) : 0.f;
 }
 
@@ -393,12 +417,21 @@ cudaError_t launch_cg_init(Ctx* c, int mode) {
 cudaError_t launch_cg_update(Ctx* c, int record) {
   c->launches += 1;
   const float tol2 = (float)(c->cg_tol * c->cg_tol);
-  k_cg_update<<<c->S, 256, 0, c->stream>>>(c->x, c->r, c->d, c->ad, c->part, c->Dp / 128,
-                                           c->rr, c->bb, c->steps, c->active, c->task_active,
-                                           c->counters, c->gam, c->xi, c->psteps, record, c->R,
-                                           c->K, c->C, c->Dp, c->S, c->U, tol2,
-                                           static_cast<__nv_bfloat16*>(c->dhi),
-                                           static_cast<__nv_bfloat16*>(c->dlo));
+  const int nv = (c->Dp + 1023) / 1024;
+#define UPD(NV)                                                                                  \
+  k_cg_update<NV><<<c->S, 256, 0, c->stream>>>(c->x, c->r, c->d, c->ad, c->part, c->Dp / 128,   \
+                                               c->rr, c->bb, c->steps, c->active,              \
+                                               c->task_active, c->counters, c->gam, c->xi,     \
+                                               c->psteps, record, c->R, c->K, c->C, c->Dp, c->S, \
+                                               c->U, tol2, static_cast<__nv_bfloat16*>(c->dhi), \
+                                               static_cast<__nv_bfloat16*>(c->dlo))
+  if (nv <= 1) UPD(1);
+  else if (nv <= 2) UPD(2);
+  else if (nv <= 4) UPD(4);
+  else if (nv <= 8) UPD(8);
+  else if (nv <= 16) UPD(16);
+  else UPD(0);
+#undef UPD
   return cudaGetLastError();
 }
 

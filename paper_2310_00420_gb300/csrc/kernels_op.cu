@@ -54,7 +54,10 @@ template <int TN, bool DS>
 __global__ void __launch_bounds__(256)
 k_pass1(const float* __restrict__ phi, const float* __restrict__ V, float* __restrict__ W,
         float* __restrict__ Wlo, const int64_t* __restrict__ drow,
-        const int* __restrict__ tile_task, const int* __restrict__ task_active, int R, int Dp) {
+        const int* __restrict__ tile_task, const int* __restrict__ task_active, int R, int Dp,
+        int Rc, int jstride) {
+  // columns j' = 0 .. Rc-1 of the tile are systems j = j' * jstride of the task (all R
+  // systems when Rc = R, jstride = 1; the mean systems only when Rc = C, jstride = K + 1)
   constexpr int BN = 16 * TN;
   constexpr int NB = (BN * 4 + 255) / 256;
   __shared__ __align__(16) float As[2][16][132];
@@ -88,8 +91,8 @@ k_pass1(const float* __restrict__ phi, const float* __restrict__ V, float* __res
     for (int q = 0; q < NB; ++q) {
       const int idx = tid + 256 * q, row = idx >> 2, c4 = idx & 3, j = j0 + row;
       rb[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (idx < BN * 4 && j < R)
-        rb[q] = *reinterpret_cast<const float4*>(Vg + (int64_t)j * Dp + k0 + c4 * 4);
+      if (idx < BN * 4 && j < Rc)
+        rb[q] = *reinterpret_cast<const float4*>(Vg + (int64_t)j * jstride * Dp + k0 + c4 * 4);
     }
   };
   auto store = [&](int buf) {
@@ -137,12 +140,12 @@ k_pass1(const float* __restrict__ phi, const float* __restrict__ V, float* __res
     __syncthreads();
   }
 
-  float* Wt = W + rbeg * R;
-  float* Wlt = DS ? Wlo + rbeg * R : nullptr;
+  float* Wt = W + rbeg * Rc;
+  float* Wlt = DS ? Wlo + rbeg * Rc : nullptr;
 #pragma unroll
   for (int jj = 0; jj < TN; ++jj) {
     const int j = j0 + ty + 16 * jj;
-    if (j >= R) continue;
+    if (j >= Rc) continue;
     float* wr = Wt + (int64_t)j * Np + nl0;
     *reinterpret_cast<float4*>(wr + tx * 4) = make_float4(hi[0][jj], hi[1][jj], hi[2][jj], hi[3][jj]);
     *reinterpret_cast<float4*>(wr + 64 + tx * 4) = make_float4(hi[4][jj], hi[5][jj], hi[6][jj], hi[7][jj]);
@@ -173,6 +176,7 @@ struct P2Args {
   const int* task_active;
   unsigned long long* opcount;  // [T] applications per task (plain pass only, may be null)
   int R, K, C, Dp, D, S;
+  int Rc, jstride;        // columns processed: systems j = j' * jstride, j' < Rc
   float beta_f;
   double beta_d;
   uint64_t seed;
@@ -197,8 +201,8 @@ __global__ void __launch_bounds__(256) k_pass2(P2Args p) {
   const int64_t rbeg = p.drow[t];
   const int64_t Np = p.drow[t + 1] - rbeg;
   const float* Ag = p.phi + rbeg * p.Dp + d0;
-  const float* Wt = p.W + rbeg * p.R;
-  const float* Wlt = DS ? p.Wlo + rbeg * p.R : nullptr;
+  const float* Wt = p.W + rbeg * p.Rc;
+  const float* Wlt = DS ? p.Wlo + rbeg * p.Rc : nullptr;
 
   float hi[8][TN], lo[8][TN];
 #pragma unroll
@@ -218,7 +222,7 @@ __global__ void __launch_bounds__(256) k_pass2(P2Args p) {
       const int idx = tid + 256 * q, row = idx >> 2, c4 = idx & 3, j = j0 + row;
       rb[q] = make_float4(0.f, 0.f, 0.f, 0.f);
       if constexpr (DS) rl[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (idx < BN * 4 && j < p.R) {
+      if (idx < BN * 4 && j < p.Rc) {
         rb[q] = *reinterpret_cast<const float4*>(Wt + (int64_t)j * Np + n0 + c4 * 4);
         if constexpr (DS) rl[q] = *reinterpret_cast<const float4*>(Wlt + (int64_t)j * Np + n0 + c4 * 4);
       }
@@ -278,8 +282,9 @@ __global__ void __launch_bounds__(256) k_pass2(P2Args p) {
   // epilogue
 #pragma unroll
   for (int jj = 0; jj < TN; ++jj) {
-    const int j = j0 + ty + 16 * jj;
-    const bool valid = j < p.R;
+    const int jc = j0 + ty + 16 * jj;
+    const bool valid = jc < p.Rc;
+    const int j = jc * p.jstride;
     const int64_t sys = (int64_t)t * p.R + j;
     const int c = j / (p.K + 1);
     const int k = j - c * (p.K + 1);
@@ -354,13 +359,14 @@ int pick_tn(int R, int max_tn) {
 }
 
 template <bool DS>
-cudaError_t pass1(Ctx* c, int tn, const float* V, float* W, float* Wlo, const int* mask) {
+cudaError_t pass1(Ctx* c, int tn, const float* V, float* W, float* Wlo, const int* mask, int Rc,
+                  int jstride) {
   const int bn = 16 * tn;
-  dim3 grid((c->R + bn - 1) / bn, (unsigned)(c->rows_total / 128));
+  dim3 grid((Rc + bn - 1) / bn, (unsigned)(c->rows_total / 128));
 #define P1CASE(TN)                                                                          \
   case TN:                                                                                  \
     k_pass1<TN, DS><<<grid, 256, 0, c->stream>>>(c->phi, V, W, Wlo, c->drow, c->tile_task, \
-                                                 mask, c->R, c->Dp);                        \
+                                                 mask, c->R, c->Dp, Rc, jstride);           \
     break;
   switch (tn) {
     P1CASE(1) P1CASE(2) P1CASE(3) P1CASE(4) P1CASE(6) P1CASE(8) P1CASE(9)
@@ -373,7 +379,7 @@ cudaError_t pass1(Ctx* c, int tn, const float* V, float* W, float* Wlo, const in
 template <bool DS>
 cudaError_t pass2(Ctx* c, int tn, const P2Args& a) {
   const int bn = 16 * tn;
-  dim3 grid((c->R + bn - 1) / bn, c->Dp / 128, c->T);
+  dim3 grid((a.Rc + bn - 1) / bn, c->Dp / 128, c->T);
 #define P2CASE(TN)                                          \
   case TN:                                                  \
     k_pass2<TN, DS><<<grid, 256, 0, c->stream>>>(a);        \
@@ -405,6 +411,8 @@ P2Args base_args(Ctx* c) {
   a.beta_d = c->beta;
   a.seed = c->seed;
   a.em_iter = c->em_iter;
+  a.Rc = c->R;
+  a.jstride = 1;
   return a;
 }
 
@@ -414,7 +422,7 @@ cudaError_t launch_operator(Ctx* c, const float* V, float* Z, int with_dots) {
   if (c->tc != nullptr) return tc_operator(c, V, Z, with_dots);
   const int* mask = with_dots ? c->task_active : nullptr;
   const int tn = c->tn_plain > 0 ? c->tn_plain : pick_tn(c->R, 9);
-  cudaError_t e = pass1<false>(c, tn, V, c->w, nullptr, mask);
+  cudaError_t e = pass1<false>(c, tn, V, c->w, nullptr, mask, c->R, 1);
   if (e != cudaSuccess) return e;
   P2Args a = base_args(c);
   a.V = V;
@@ -427,11 +435,15 @@ cudaError_t launch_operator(Ctx* c, const float* V, float* Z, int with_dots) {
 }
 
 cudaError_t launch_residual(Ctx* c, const float* X, const float* Bext, float* Rout,
-                            int all_systems) {
-  const int tn = c->tn_ds > 0 ? c->tn_ds : pick_tn(c->R, 4);
-  cudaError_t e = pass1<true>(c, tn, X, c->w, c->wlo, nullptr);
+                            int all_systems, int means_only) {
+  const int Rc = means_only ? c->C : c->R;
+  const int js = means_only ? c->K + 1 : 1;
+  const int tn = c->tn_ds > 0 ? c->tn_ds : pick_tn(Rc, 4);
+  cudaError_t e = pass1<true>(c, tn, X, c->w, c->wlo, nullptr, Rc, js);
   if (e != cudaSuccess) return e;
   P2Args a = base_args(c);
+  a.Rc = Rc;
+  a.jstride = js;
   a.V = X;
   a.Z = Rout;
   a.Bext = Bext;
