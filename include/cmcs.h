@@ -143,6 +143,27 @@ cmcs_status cmcs_estep(cmcs_ctx *ctx);
  * E-step and alpha is the result of the last M-step. */
 cmcs_status cmcs_em_iter(cmcs_ctx *ctx, int n);
 
+/* Replace Phi and y (same shapes as at create; host or device per on_device) and recompute
+ * b0 = beta Phi^T y.  alpha, the iteration counter and the settings are kept; outputs of earlier
+ * E-steps are stale until the next cmcs_estep. */
+cmcs_status cmcs_set_data(cmcs_ctx *ctx, const float *Phi, const float *y, int on_device);
+
+/* Reverse-mode derivative of the posterior means of the last E-step.  The paper has no adjoint;
+ * this follows from Eq. 3 by differentiating mu_tc = A_tc^-1 (beta Phi_t^T y_t) with
+ * A_tc = beta Phi_t^T Phi_t + diag(alpha_c).  Given g = dL/dmu (float [T][C][D]) it solves the
+ * adjoint systems A_tc lambda_tc = g_tc with the same symmetric operator (CG of Alg. 1 with the
+ * context's tol and step cap, then compensated refinement as in the E-step; nothing from the
+ * forward CG is stored) and writes
+ *   dy     float [sum N_t]     = beta sum_c Phi_t lambda_tc
+ *   dalpha float [C][D]        = - sum_t lambda_tc * mu_tc
+ *   dPhi   float [sum N_t][D]  = beta sum_c ((y_t - Phi_t mu_tc) lambda_tc^T - (Phi_t lambda_tc) mu_tc^T)
+ * (dPhi may be NULL).  Responsibilities, s and the log-det estimate are treated as constants.
+ * All pointers host or device per on_device.  The E-step's work buffers and refinement
+ * statistics (CMCS_OUT_SWEEPS, refine fields of cmcs_summary) are overwritten; mu, s, q and
+ * alpha are not. */
+cmcs_status cmcs_adjoint(cmcs_ctx *ctx, const float *g, float *dy, float *dalpha, float *dPhi,
+                         int on_device);
+
 /* Copy an output (see cmcs_output) into dst, host or device per on_device. */
 cmcs_status cmcs_read(const cmcs_ctx *ctx, int what, void *dst, int on_device);
 

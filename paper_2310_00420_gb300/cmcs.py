@@ -26,8 +26,8 @@ PRECISIONS = {"fp32": FP32, "bf16": BF16_REFINE, "bf16_refine": BF16_REFINE, "bf
 # exported symbols, in the order include/cmcs.h declares them
 EXPORTS = ("cmcs_create", "cmcs_set_alpha", "cmcs_estep", "cmcs_em_iter", "cmcs_read",
            "cmcs_result", "cmcs_apply", "cmcs_probes", "cmcs_lanczos_quadrature",
-           "cmcs_profile", "cmcs_profile_read", "cmcs_apply_noalloc", "cmcs_last_error",
-           "cmcs_destroy")
+           "cmcs_profile", "cmcs_profile_read", "cmcs_apply_noalloc", "cmcs_set_data",
+           "cmcs_adjoint", "cmcs_last_error", "cmcs_destroy")
 
 
 class Config(ctypes.Structure):
@@ -85,6 +85,8 @@ def lib():
     L.cmcs_profile.argtypes = [vp, i]
     L.cmcs_profile_read.argtypes = [vp, ctypes.POINTER(ProfileData)]
     L.cmcs_apply_noalloc.argtypes = [vp, i, i, vp, ctypes.c_double, vp, i, vp, vp]
+    L.cmcs_set_data.argtypes = [vp, vp, vp, i]
+    L.cmcs_adjoint.argtypes = [vp, vp, vp, vp, vp, i]
     L.cmcs_last_error.argtypes = [vp]
     L.cmcs_last_error.restype = ctypes.c_char_p
     L.cmcs_destroy.argtypes = [vp]
@@ -234,6 +236,32 @@ class Context:
         s = Summary()
         _check(lib().cmcs_result(self.h, ctypes.byref(s)), self.h)
         return {f: getattr(s, f) for f, _ in Summary._fields_}
+
+    def set_data(self, Phi, y):
+        p_phi, dev1 = _ptr(Phi)
+        p_y, dev2 = _ptr(y)
+        if dev1 != dev2:
+            raise ValueError("Phi and y must both be host arrays or both device tensors")
+        _check(lib().cmcs_set_data(self.h, p_phi, p_y, dev1), self.h)
+
+    def adjoint(self, g, with_phi: bool = True):
+        """(dy, dalpha, dPhi) for g = dL/dmu [T][C][D] (float32; numpy or CUDA tensor)."""
+        n_rows = int(self._N.sum())
+        if _is_torch(g):
+            import torch
+            dev = g.device
+            dy = torch.empty(n_rows, dtype=torch.float32, device=dev)
+            da = torch.empty((self.C, self.D), dtype=torch.float32, device=dev)
+            dP = torch.empty((n_rows, self.D), dtype=torch.float32, device=dev) if with_phi else None
+        else:
+            g = np.ascontiguousarray(g, dtype=np.float32)
+            dy = np.empty(n_rows, np.float32)
+            da = np.empty((self.C, self.D), np.float32)
+            dP = np.empty((n_rows, self.D), np.float32) if with_phi else None
+        pg, dev = _ptr(g)
+        _check(lib().cmcs_adjoint(self.h, pg, _ptr(dy)[0], _ptr(da)[0],
+                                  _ptr(dP)[0] if dP is not None else None, dev), self.h)
+        return dy, da, dP
 
     def profile(self, enable: bool = True):
         _check(lib().cmcs_profile(self.h, 1 if enable else 0), self.h)

@@ -53,7 +53,8 @@ void free_ctx(Ctx* c) {
                   c->w, c->wlo, c->part, c->rr, c->bb, c->steps, c->steps0, c->active,
                   c->ractive, c->sweeps, c->rrel, c->rres, c->task_active, c->counters, c->gam, c->xi,
                   c->psteps, c->sest, c->quad, c->logdet, c->ell, c->q, c->assign, c->stats,
-                  c->dN, c->opcount};
+                  c->dN, c->opcount, c->dorow, c->adj_g, c->adj_x, c->adj_wl, c->adj_wm,
+                  c->adj_dy, c->adj_da};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->prof_ev) {
@@ -68,6 +69,7 @@ void free_ctx(Ctx* c) {
   free(c->hNp);
   free(c->hrow);
   free(c->hpi);
+  free(c->horow);
 }
 
 cudaMemcpyKind kind_in(int on_device) {
@@ -133,6 +135,36 @@ cmcs_status run_cg(Ctx* c, int record) {
   return CMCS_OK;
 }
 
+// Iterative refinement of the solutions in xacc: each sweep forms the residual B - A xacc with
+// compensated products (B = b0 and the probes, or Bext), solves for the correction with
+// Alg. 1 and adds it; a system stops once its correction is small or stops shrinking.
+cmcs_status refine_sweeps(Ctx* c, const float* Bext) {
+  for (int sw = 0; sw < c->refine_max; ++sw) {
+    if (c->prof_on) cudaEventRecord(c->res_ev[0], c->stream);
+    CK(launch_residual(c, c->xacc, Bext, c->r));
+    if (c->prof_on) {
+      cudaEventRecord(c->res_ev[1], c->stream);
+      c->res_calls++;
+    }
+    c->op_applies++;
+    CK(cudaMemsetAsync(c->task_active, 0, sizeof(int) * c->T, c->stream));
+    CK(cudaMemsetAsync(c->counters, 0, sizeof(int) * 2, c->stream));
+    CK(launch_cg_init(c, 1));
+    cmcs_status s = run_cg(c, 0);
+    if (s != CMCS_OK) return s;
+    CK(cudaMemsetAsync(c->counters + 1, 0, sizeof(int), c->stream));
+    CK(launch_refine_update(c));
+    s = read_counters(c);
+    if (s != CMCS_OK) return s;
+    if (c->prof_on) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, c->res_ev[0], c->res_ev[1]) == cudaSuccess) c->res_ms += ms;
+    }
+    if (c->hcounters[1] == 0) break;
+  }
+  return CMCS_OK;
+}
+
 cmcs_status estep(Ctx* c) {
   CK(cudaMemsetAsync(c->task_active, 0, sizeof(int) * c->T, c->stream));
   CK(cudaMemsetAsync(c->counters, 0, sizeof(int) * 4, c->stream));
@@ -145,29 +177,8 @@ cmcs_status estep(Ctx* c) {
   CK(cudaMemcpyAsync(c->steps0, c->steps, sizeof(int) * c->S, cudaMemcpyDeviceToDevice, c->stream));
   std::swap(c->x, c->xacc);
   // refinement sweeps: residual with compensated products (FP64 combine), CG on it, add
-  for (int sw = 0; sw < c->refine_max; ++sw) {
-    if (c->prof_on) cudaEventRecord(c->res_ev[0], c->stream);
-    CK(launch_residual(c, c->xacc, nullptr, c->r));
-    if (c->prof_on) {
-      cudaEventRecord(c->res_ev[1], c->stream);
-      c->res_calls++;
-    }
-    c->op_applies++;
-    CK(cudaMemsetAsync(c->task_active, 0, sizeof(int) * c->T, c->stream));
-    CK(cudaMemsetAsync(c->counters, 0, sizeof(int) * 2, c->stream));
-    CK(launch_cg_init(c, 1));
-    s = run_cg(c, 0);
-    if (s != CMCS_OK) return s;
-    CK(cudaMemsetAsync(c->counters + 1, 0, sizeof(int), c->stream));
-    CK(launch_refine_update(c));
-    s = read_counters(c);
-    if (s != CMCS_OK) return s;
-    if (c->prof_on) {
-      float ms = 0.f;
-      if (cudaEventElapsedTime(&ms, c->res_ev[0], c->res_ev[1]) == cudaSuccess) c->res_ms += ms;
-    }
-    if (c->hcounters[1] == 0) break;
-  }
+  s = refine_sweeps(c, nullptr);
+  if (s != CMCS_OK) return s;
   const float* rmu = nullptr;
   if (c->refine_max > 0) {
     // residual of the returned means: verified accuracy and the correction of ell
@@ -273,8 +284,17 @@ cmcs_status cmcs_create(const cmcs_config* cfg, const float* Phi, const float* y
     set_err(nullptr, "host allocation failed");
     return CMCS_ERR_OOM;
   }
+  c->horow = static_cast<int64_t*>(malloc(sizeof(int64_t) * (c->T + 1)));
+  if (!c->horow) {
+    free_ctx(c);
+    free(h);
+    set_err(nullptr, "host allocation failed");
+    return CMCS_ERR_OOM;
+  }
   c->hrow[0] = 0;
+  c->horow[0] = 0;
   for (int t = 0; t < c->T; ++t) {
+    c->horow[t + 1] = c->horow[t] + cfg->N[t];
     c->hN[t] = cfg->N[t];
     c->hNp[t] = round_up(cfg->N[t], kNAlign);
     c->hrow[t + 1] = c->hrow[t] + c->hNp[t];
@@ -347,6 +367,13 @@ cmcs_status cmcs_create(const cmcs_config* cfg, const float* Phi, const float* y
   CKC(dalloc(&c->assign, (size_t)T));
   CKC(dalloc(&c->stats, 4));
   CKC(dalloc(&c->opcount, (size_t)T));
+  CKC(dalloc(&c->dorow, (size_t)(T + 1)));
+  CKC(dalloc(&c->adj_g, (size_t)(T * C * Dp)));
+  CKC(dalloc(&c->adj_x, (size_t)(T * C * Dp)));
+  CKC(dalloc(&c->adj_wl, (size_t)(C * c->rows_total)));
+  CKC(dalloc(&c->adj_wm, (size_t)(C * c->rows_total)));
+  CKC(dalloc(&c->adj_dy, (size_t)c->hrow[c->T]));
+  CKC(dalloc(&c->adj_da, (size_t)(C * Dp)));
   CKC(cudaMemsetAsync(c->opcount, 0, sizeof(int64_t) * T, c->stream));
 
   // zero everything that padding relies on
@@ -380,6 +407,7 @@ cmcs_status cmcs_create(const cmcs_config* cfg, const float* Phi, const float* y
   for (int k = 0; k < C; ++k) lpi[(size_t)k] = log(c->hpi[k]);
   CKC(cudaMemcpyAsync(c->drow, c->hrow, sizeof(int64_t) * (T + 1), cudaMemcpyHostToDevice, c->stream));
   CKC(cudaMemcpyAsync(c->dN, c->hN, sizeof(int64_t) * T, cudaMemcpyHostToDevice, c->stream));
+  CKC(cudaMemcpyAsync(c->dorow, c->horow, sizeof(int64_t) * (T + 1), cudaMemcpyHostToDevice, c->stream));
   CKC(cudaMemcpyAsync(c->tile_task, ttask.data(), sizeof(int) * ntiles, cudaMemcpyHostToDevice, c->stream));
   CKC(cudaMemcpyAsync(c->logpi, lpi.data(), sizeof(double) * C, cudaMemcpyHostToDevice, c->stream));
   CKC(launch_b0(c));
@@ -472,6 +500,86 @@ cmcs_status cmcs_set_alpha(cmcs_ctx* h, const float* alpha, int on_device, int64
   CK(launch_sumlogalpha(c));
   c->em_iter = em_iter;
   return sync_check(c);
+}
+
+cmcs_status cmcs_set_data(cmcs_ctx* h, const float* Phi, const float* y, int on_device) {
+  if (!h || !Phi || !y || (on_device != 0 && on_device != 1)) return CMCS_ERR_INVALID_ARG;
+  Ctx* c = &h->c;
+  const cudaMemcpyKind kin = kind_in(on_device);
+  int64_t src_row = 0;
+  for (int t = 0; t < c->T; ++t) {
+    CK(cudaMemcpy2DAsync(c->phi + c->hrow[t] * c->Dp, sizeof(float) * c->Dp, Phi + src_row * c->D,
+                         sizeof(float) * c->D, sizeof(float) * c->D, (size_t)c->hN[t], kin, c->stream));
+    CK(cudaMemcpyAsync(c->y + c->hrow[t], y + src_row, sizeof(float) * c->hN[t], kin, c->stream));
+    src_row += c->hN[t];
+  }
+  CK(launch_b0(c));
+  CK(launch_tconst_dev(c, c->dN));
+  if (c->tc != nullptr) CK(tc_refresh(c));
+  return sync_check(c);
+}
+
+cmcs_status cmcs_adjoint(cmcs_ctx* h, const float* g, float* dy, float* dalpha, float* dPhi,
+                         int on_device) {
+  if (!h || !g || !dy || !dalpha || (on_device != 0 && on_device != 1)) return CMCS_ERR_INVALID_ARG;
+  Ctx* c = &h->c;
+  const size_t D = c->D, Dp = c->Dp, T = c->T, C = c->C;
+  // the adjoint systems A_tc lambda_tc = g_tc as a narrow problem: R = C columns per task, K = 0,
+  // FP32 operator and compensated refinement; its solution goes to adj_x, not to the means
+  const int64_t launches0 = c->launches;
+  Ctx a = *c;
+  a.R = c->C;
+  a.K = 0;
+  a.S = c->T * c->C;
+  a.tc = nullptr;
+  a.dhi = a.dlo = nullptr;
+  a.prof_on = 0;
+  a.xacc = c->adj_x;
+  a.tn_plain = a.tn_ds = 0;
+  CK(cudaMemsetAsync(c->adj_g, 0, sizeof(float) * T * C * Dp, c->stream));
+  CK(cudaMemcpy2DAsync(c->adj_g, sizeof(float) * Dp, g, sizeof(float) * D, sizeof(float) * D, T * C,
+                       kind_in(on_device), c->stream));
+  CK(cudaMemcpyAsync(a.r, c->adj_g, sizeof(float) * T * C * Dp, cudaMemcpyDeviceToDevice, c->stream));
+  CK(cudaMemsetAsync(c->task_active, 0, sizeof(int) * T, c->stream));
+  CK(cudaMemsetAsync(c->counters, 0, sizeof(int) * 4, c->stream));
+  CK(launch_cg_init(&a, 2));
+  cmcs_status s = run_cg(&a, 0);
+  if (s != CMCS_OK) return s;
+  CK(cudaMemcpyAsync(a.xacc, a.x, sizeof(float) * T * C * Dp, cudaMemcpyDeviceToDevice, c->stream));
+  s = refine_sweeps(&a, c->adj_g);
+  if (s != CMCS_OK) return s;
+  // gradients
+  CK(launch_phi_v(&a, c->adj_x, c->adj_wl, (int)C, 1));             // Phi lambda
+  CK(launch_phi_v(c, c->xacc, c->adj_wm, (int)C, c->K + 1));         // Phi mu
+  CK(launch_adj_dy(c, c->adj_wl, c->adj_dy));
+  CK(launch_adj_dalpha(c, c->adj_x, c->adj_da));
+  const cudaMemcpyKind kout = kind_out(on_device);
+  CK(cudaMemcpyAsync(dy, c->adj_dy, sizeof(float) * c->horow[c->T], kout, c->stream));
+  CK(cudaMemcpy2DAsync(dalpha, sizeof(float) * D, c->adj_da, sizeof(float) * Dp, sizeof(float) * D,
+                       C, kout, c->stream));
+  if (dPhi != nullptr) {
+    if (on_device) {
+      CK(launch_adj_dphi(c, c->adj_x, c->adj_wl, c->adj_wm, dPhi, 0, c->T, 0));
+    } else {
+      for (int t = 0; t < c->T; ++t) {          // stage one task at a time in the work buffer ad
+        if ((size_t)c->hN[t] * D > (size_t)c->S * Dp) {
+          set_err(c, "cmcs_adjoint: host dPhi staging does not fit; pass device memory");
+          return CMCS_ERR_UNSUPPORTED;
+        }
+        CK(launch_adj_dphi(c, c->adj_x, c->adj_wl, c->adj_wm, c->ad, t, t + 1, c->horow[t]));
+        CK(cudaMemcpyAsync(dPhi + c->horow[t] * D, c->ad, sizeof(float) * c->hN[t] * D,
+                           cudaMemcpyDeviceToHost, c->stream));
+      }
+    }
+  }
+  c->launches += a.launches - launches0;
+  s = read_counters(c);
+  if (s != CMCS_OK) return s;
+  if (c->hcounters[2] != 0) {
+    set_err(c, "non-finite value in the adjoint solve (flags 0x%x)", c->hcounters[2]);
+    return CMCS_ERR_NUMERIC;
+  }
+  return CMCS_OK;
 }
 
 cmcs_status cmcs_estep(cmcs_ctx* h) {

@@ -87,6 +87,11 @@ struct Ctx {
   float* y;          // [rows_total]
   int64_t* drow;     // [T+1]
   int64_t* dN;       // [T] unpadded N_t
+  int64_t* dorow;    // [T+1] unpadded row offsets (caller's layout)
+  int64_t* horow;    // host copy
+  // adjoint work buffers: right-hand side and solution [T*C][Dp], Phi lambda and Phi mu
+  // [C * rows_total], dy [sum N_t], dalpha [C][Dp]
+  float *adj_g, *adj_x, *adj_wl, *adj_wm, *adj_dy, *adj_da;
   int* tile_task;    // [rows_total / 128] task owning each 128-row tile of phi
   int tn_plain, tn_ds; // operator tile widths (0: chosen from R)
   float *b0hi, *b0lo;  // [T][Dp]
@@ -153,6 +158,13 @@ cudaError_t launch_operator(Ctx* c, const float* V, float* Z, int with_dots);
 cudaError_t launch_residual(Ctx* c, const float* X, const float* Bext, float* Rout,
                             int all_systems = 0, int means_only = 0);
 cudaError_t launch_resid_norm(Ctx* c);
+// W[t][j'][n] = (Phi_t V_{t, j' * jstride})[n] for j' < Rc (FP32 SIMT pass 1 only)
+cudaError_t launch_phi_v(Ctx* c, const float* V, float* W, int Rc, int jstride);
+// adjoint gradients (adjoint.cu)
+cudaError_t launch_adj_dy(Ctx* c, const float* Wl, float* dy);
+cudaError_t launch_adj_dalpha(Ctx* c, const float* lam, float* dalpha);
+cudaError_t launch_adj_dphi(Ctx* c, const float* lam, const float* Wl, const float* Wm, float* out,
+                            int t0, int t1, int64_t out_row_base);
 // E-step tail and M-step (kernels_estep.cu)
 cudaError_t launch_quadrature(const float* gam, const float* xi, const int* steps, int nsys,
                               int ld, double* out, int* status, cudaStream_t st);
@@ -165,6 +177,7 @@ int tc_create(Ctx* c);      // returns 0 on success
 void tc_destroy(Ctx* c);
 cudaError_t tc_operator(Ctx* c, const float* V, float* Z, int with_dots);
 cudaError_t tc_split_vectors(Ctx* c, const float* V);   // V -> dhi, dlo
+cudaError_t tc_refresh(Ctx* c);                         // recompute the BF16 copies of Phi
 
 inline int64_t round_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
 

@@ -62,7 +62,8 @@ __device__ __forceinline__ void store_split4(__nv_bfloat16* hi, __nv_bfloat16* l
 
 // ---- CG initialisation: x_1 = 0, r_1 = d_1 = b (Alg. 1, first line) ---------------------
 // mode 0: b = b0_t (k = 0) or the probe p_{t,c,k} (k >= 1); mode 1: b = the residual
-// already in r (refinement), systems no longer refining have r = 0.
+// already in r (refinement), systems no longer refining have r = 0; mode 2: b = a given
+// right-hand side already in r (first solve of the adjoint system).
 __global__ void __launch_bounds__(256)
 k_cg_init(int mode, float* __restrict__ x, float* __restrict__ r, float* __restrict__ d,
           const float* __restrict__ b0hi, float* rr, float* bb, int* steps, int* active,
@@ -98,12 +99,12 @@ k_cg_init(int mode, float* __restrict__ x, float* __restrict__ r, float* __restr
     rr[sys] = rr0;
     bb[sys] = rr0;
     steps[sys] = 0;
-    if (mode == 0) {
+    if (mode != 1) {
       ractive[sys] = refine;
       sweeps[sys] = 0;
       rrel[sys] = 0.f;
     }
-    const int on = (rr0 > 0.f) && (mode == 0 || ractive[sys] != 0);
+    const int on = (rr0 > 0.f) && (mode != 1 || ractive[sys] != 0);
     active[sys] = on;
     if (on) {
       atomicAdd(&task_active[t], 1);

@@ -434,6 +434,11 @@ cudaError_t launch_operator(Ctx* c, const float* V, float* Z, int with_dots) {
   return pass2<false>(c, tn, a);
 }
 
+cudaError_t launch_phi_v(Ctx* c, const float* V, float* W, int Rc, int jstride) {
+  c->launches += 1;
+  return pass1<false>(c, pick_tn(Rc, 9), V, W, nullptr, nullptr, Rc, jstride);
+}
+
 cudaError_t launch_residual(Ctx* c, const float* X, const float* Bext, float* Rout,
                             int all_systems, int means_only) {
   const int Rc = means_only ? c->C : c->R;

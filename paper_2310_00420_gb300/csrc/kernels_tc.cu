@@ -635,6 +635,17 @@ void tc_destroy(Ctx* c) {
   c->tc = nullptr;
 }
 
+cudaError_t tc_refresh(Ctx* c) {
+  TcState* s = static_cast<TcState*>(c->tc);
+  if (!s) return cudaSuccess;
+  const int64_t rows = c->rows_total, Dp = c->Dp;
+  k_split_bf16<<<4096, 256, 0, c->stream>>>(c->phi, s->phi_hi, s->phi_lo, rows * Dp);
+  k_transpose_split<<<dim3(Dp / 32, (unsigned)(rows / 32)), dim3(32, 8), 0, c->stream>>>(
+      c->phi, s->phit_hi, s->phit_lo, rows, (int)Dp);
+  c->launches += 2;
+  return cudaGetLastError();
+}
+
 cudaError_t tc_split_vectors(Ctx* c, const float* V) {
   k_split_bf16<<<4096, 256, 0, c->stream>>>(V, static_cast<__nv_bfloat16*>(c->dhi),
                                             static_cast<__nv_bfloat16*>(c->dlo), (int64_t)c->S * c->Dp);
