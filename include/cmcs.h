@@ -19,9 +19,10 @@
  *  - A pointer argument is host memory when the accompanying `on_device` is 0 and CUDA device
  *    memory of the context's device when it is 1.  The library never keeps a caller pointer
  *    past the call that received it; it copies what it needs into memory it owns.
- *  - All GPU work is ordered on the CUDA stream given to cmcs_create (0 = legacy default
- *    stream).  Every call returns only after that work has completed, and reports device
- *    errors through its status.
+ *  - All GPU work is ordered on the CUDA stream given to cmcs_create.  For NULL (the legacy
+ *    default stream) the context creates a blocking stream of its own, which orders itself
+ *    with the legacy stream and, unlike it, can be captured into CUDA graphs.  Every call
+ *    returns only after its work has completed, and reports device errors through its status.
  *  - Errors: a call that fails validation returns CMCS_ERR_INVALID_ARG and changes no state.
  *    cmcs_last_error() returns a description of the most recent failure of that context.
  *  - No call allocates or frees device memory except cmcs_create and cmcs_destroy.
@@ -77,6 +78,11 @@ typedef struct {
   double refine_tol;      /* stop refining a system once ||delta|| <= refine_tol * ||x||  */
   double alpha_min;       /* M-step clamp, > 0                                            */
   double alpha_max;       /* M-step clamp, > alpha_min                                    */
+  int schedule;           /* 0: every task in one operator launch per pass (default);
+                             1: one launch per task (the per-task loop, for comparison)   */
+  int graphs;             /* 1: capture chunks of CG steps in CUDA graphs and replay them  */
+  int autotune;           /* 1: at create, time the operator variants (SIMT tile width or
+                             tensor-core pipeline depth) and keep the fastest              */
 } cmcs_config;
 
 /* Summary of the most recent E-step and the EM state. */
@@ -95,6 +101,8 @@ typedef struct {
                               compensated residual after refinement (0 when refine_max = 0)  */
   int64_t refine_diverged; /* systems whose refinement stopped because a correction grew (the
                               inner solves did not contract); their last correction is undone */
+  int operator_variant;    /* operator variant in use: SIMT tile width (columns per thread)
+                              or tensor-core pipeline stages                                */
 } cmcs_summary;
 
 /* What cmcs_read copies out.  Element types and shapes: */

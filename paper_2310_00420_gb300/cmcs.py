@@ -36,7 +36,8 @@ class Config(ctypes.Structure):
                 ("pi", ctypes.POINTER(ctypes.c_double)), ("cg_max_iter", ctypes.c_int),
                 ("cg_tol", ctypes.c_double), ("seed", ctypes.c_uint64), ("precision", ctypes.c_int),
                 ("refine_max", ctypes.c_int), ("refine_tol", ctypes.c_double),
-                ("alpha_min", ctypes.c_double), ("alpha_max", ctypes.c_double)]
+                ("alpha_min", ctypes.c_double), ("alpha_max", ctypes.c_double),
+                ("schedule", ctypes.c_int), ("graphs", ctypes.c_int), ("autotune", ctypes.c_int)]
 
 
 class Summary(ctypes.Structure):
@@ -45,7 +46,7 @@ class Summary(ctypes.Structure):
                 ("cg_capped", ctypes.c_int64), ("refine_sweeps_max", ctypes.c_int),
                 ("refine_rel_max", ctypes.c_double), ("min_margin", ctypes.c_double),
                 ("operator_applies", ctypes.c_int64), ("resid_rel_max", ctypes.c_double),
-                ("refine_diverged", ctypes.c_int64)]
+                ("refine_diverged", ctypes.c_int64), ("operator_variant", ctypes.c_int)]
 
 
 class ProfileData(ctypes.Structure):
@@ -153,6 +154,7 @@ class Context:
     def __init__(self, Phi, y, N, *, C: int, K: int, beta: float, pi=None, cg_max_iter: int = 100,
                  cg_tol: float = 1e-5, seed: int = 0, precision="fp32", refine_max: int = 0,
                  refine_tol: float = 1e-6, alpha_min: float = 1e-10, alpha_max: float = 1e10,
+                 schedule: str = "batched", graphs: bool = True, autotune: bool = False,
                  stream=None):
         N = np.ascontiguousarray(np.asarray(N, dtype=np.int64))
         self.T, self.C, self.D, self.K = int(len(N)), int(C), int(Phi.shape[1]), int(K)
@@ -164,7 +166,9 @@ class Context:
                      N.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), float(beta),
                      pi.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(cg_max_iter),
                      float(cg_tol), int(seed) & (2**64 - 1), prec, int(refine_max),
-                     float(refine_tol), float(alpha_min), float(alpha_max))
+                     float(refine_tol), float(alpha_min), float(alpha_max),
+                     {"batched": 0, "per_task": 1}[schedule], 1 if graphs else 0,
+                     1 if autotune else 0)
         self.cfg = cfg
         p_phi, dev1 = _ptr(Phi)
         p_y, dev2 = _ptr(y)

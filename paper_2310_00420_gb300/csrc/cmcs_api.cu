@@ -64,6 +64,10 @@ void free_ctx(Ctx* c) {
     free(c->prof_ev);
   }
   if (c->hcounters) cudaFreeHost(c->hcounters);
+  for (int r = 0; r < 2; ++r)
+    for (int q = 0; q < 2; ++q)
+      if (c->graph[r][q]) cudaGraphExecDestroy(c->graph[r][q]);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   if (c->tc) tc_destroy(c);
   free(c->hN);
   free(c->hNp);
@@ -96,8 +100,10 @@ cmcs_status read_counters(Ctx* c) {
 }
 
 constexpr int kCheckEvery = 8;   // CG steps between host polls of the active-system count
+static_assert(kCheckEvery <= kProfEvents, "events of one chunk");
 
-// operator application, bracketed by profiling events when enabled
+// operator application, bracketed by profiling events when enabled (pair prof_nev of the
+// current chunk of CG steps)
 cudaError_t timed_operator(Ctx* c) {
   const bool ev = c->prof_on && c->prof_nev < kProfEvents;
   if (ev) cudaEventRecord(c->prof_ev[2 * c->prof_nev], c->stream);
@@ -120,17 +126,68 @@ void fold_events(Ctx* c) {
   c->prof_nev = 0;
 }
 
-// Alg. 1 for every active system until all have stopped (or the step cap)
-cmcs_status run_cg(Ctx* c, int record) {
-  for (int u = 0; u < c->U; ++u) {
+// n CG steps (operator + update) launched directly
+cmcs_status cg_steps_direct(Ctx* c, int record, int n) {
+  for (int i = 0; i < n; ++i) {
     CK(timed_operator(c));
     CK(launch_cg_update(c, record));
     c->op_applies++;
-    if ((u + 1) % kCheckEvery == 0 && u + 1 < c->U) {
-      cmcs_status s = read_counters(c);
+  }
+  return CMCS_OK;
+}
+
+// the graph replaying kCheckEvery CG steps, captured on first use
+cudaGraphExec_t chunk_graph(Ctx* c, int record) {
+  cudaGraphExec_t& g = c->graph[record][c->prof_on];
+  if (g != nullptr) return g;
+  const int64_t l0 = c->launches, a0 = c->op_applies, p0 = c->prof_calls;
+  cudaGraph_t graph = nullptr;
+  if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return nullptr;
+  c->prof_nev = 0;
+  cmcs_status s = cg_steps_direct(c, record, kCheckEvery);
+  cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+  c->graph_launches = c->launches - l0;
+  c->launches = l0;
+  c->op_applies = a0;
+  c->prof_calls = p0;
+  c->prof_nev = 0;
+  if (s != CMCS_OK || e != cudaSuccess || graph == nullptr) {
+    cudaGetLastError();
+    if (graph) cudaGraphDestroy(graph);
+    return nullptr;
+  }
+  e = cudaGraphInstantiate(&g, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    g = nullptr;
+  }
+  return g;
+}
+
+// Alg. 1 for every active system until all have stopped (or the step cap), in chunks of
+// kCheckEvery steps between host polls of the number of active systems
+cmcs_status run_cg(Ctx* c, int record) {
+  for (int u = 0; u < c->U; u += kCheckEvery) {
+    const int n = c->U - u < kCheckEvery ? c->U - u : kCheckEvery;
+    cudaGraphExec_t g = (c->use_graphs && n == kCheckEvery) ? chunk_graph(c, record) : nullptr;
+    if (g != nullptr) {
+      CK(cudaGraphLaunch(g, c->stream));
+      c->launches += c->graph_launches;
+      c->op_applies += n;
+      if (c->prof_on) {
+        c->prof_calls += n;
+        c->prof_nev = n;
+      }
+    } else {
+      c->prof_nev = 0;
+      cmcs_status s = cg_steps_direct(c, record, n);
       if (s != CMCS_OK) return s;
-      if (c->hcounters[0] == 0) break;
     }
+    cmcs_status s = read_counters(c);
+    if (s != CMCS_OK) return s;
+    fold_events(c);
+    if (c->hcounters[0] == 0) break;
   }
   return CMCS_OK;
 }
@@ -175,7 +232,9 @@ cmcs_status estep(Ctx* c) {
   cmcs_status s = run_cg(c, 1);
   if (s != CMCS_OK) return s;
   CK(cudaMemcpyAsync(c->steps0, c->steps, sizeof(int) * c->S, cudaMemcpyDeviceToDevice, c->stream));
-  std::swap(c->x, c->xacc);
+  // the solution moves to xacc by copy, so captured graphs keep valid buffer addresses
+  CK(cudaMemcpyAsync(c->xacc, c->x, sizeof(float) * (size_t)c->S * c->Dp, cudaMemcpyDeviceToDevice,
+                     c->stream));
   // refinement sweeps: residual with compensated products (FP64 combine), CG on it, add
   s = refine_sweeps(c, nullptr);
   if (s != CMCS_OK) return s;
@@ -203,6 +262,48 @@ cmcs_status estep(Ctx* c) {
   return CMCS_OK;
 }
 
+// time one operator application of every variant (after one warm-up) on the context's own
+// buffers and keep the fastest: SIMT tile width TN, or tensor-core pipeline depth
+cmcs_status autotune(Ctx* c) {
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  std::vector<int> cands;
+  if (c->tc) {
+    for (int st = 2; st <= tc_max_stages(c); ++st) cands.push_back(st);
+  } else {
+    for (int tn : {3, 4, 6, 8, 9}) cands.push_back(tn);
+  }
+  float best = 1e30f;
+  int best_v = cands.empty() ? 0 : cands.back();
+  for (int v : cands) {
+    if (c->tc) tc_set_stages(c, v);
+    else c->tn_plain = v;
+    cudaError_t e = launch_operator(c, c->d, c->ad, 0);
+    cudaEventRecord(e0, c->stream);
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = launch_operator(c, c->d, c->ad, 0);
+    cudaEventRecord(e1, c->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      set_err(c, "autotune: %s", cudaGetErrorString(e));
+      return CMCS_ERR_CUDA;
+    }
+    if (ms < best) {
+      best = ms;
+      best_v = v;
+    }
+  }
+  if (c->tc) tc_set_stages(c, best_v);
+  else c->tn_plain = best_v;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return CMCS_OK;
+}
+
 cmcs_status validate(const cmcs_config* cfg) {
   if (!cfg) return CMCS_ERR_INVALID_ARG;
   if (cfg->T < 1 || cfg->C < 1 || cfg->D < 1 || cfg->K < 1) return CMCS_ERR_INVALID_ARG;
@@ -226,6 +327,9 @@ cmcs_status validate(const cmcs_config* cfg) {
   for (int t = 0; t < cfg->T; ++t)
     if (cfg->N[t] < 1 || cfg->N[t] > (1 << 24)) return CMCS_ERR_INVALID_ARG;
   if ((int64_t)cfg->C * (cfg->K + 1) > 4096) return CMCS_ERR_INVALID_ARG;
+  if (cfg->schedule != 0 && cfg->schedule != 1) return CMCS_ERR_INVALID_ARG;
+  if (cfg->graphs != 0 && cfg->graphs != 1) return CMCS_ERR_INVALID_ARG;
+  if (cfg->autotune != 0 && cfg->autotune != 1) return CMCS_ERR_INVALID_ARG;
   return CMCS_OK;
 }
 
@@ -274,6 +378,8 @@ cmcs_status cmcs_create(const cmcs_config* cfg, const float* Phi, const float* y
   c->seed = cfg->seed;
   c->em_iter = 0;
   c->stream = static_cast<cudaStream_t>(stream);
+  c->per_task = cfg->schedule;
+  c->use_graphs = cfg->graphs;
   c->hN = static_cast<int64_t*>(malloc(sizeof(int64_t) * c->T));
   c->hNp = static_cast<int64_t*>(malloc(sizeof(int64_t) * c->T));
   c->hrow = static_cast<int64_t*>(malloc(sizeof(int64_t) * (c->T + 1)));
@@ -321,6 +427,11 @@ cmcs_status cmcs_create(const cmcs_config* cfg, const float* Phi, const float* y
   } while (0)
 
   CKC(cudaGetDevice(&c->device));
+  if (c->stream == nullptr) {
+    // a blocking stream of our own: ordered with the legacy stream, and capturable
+    CKC(cudaStreamCreate(&c->stream));
+    c->own_stream = 1;
+  }
   CKC(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device));
   const int64_t Dp = c->Dp, S = c->S, T = c->T, C = c->C, K = c->K;
   const int64_t ntiles = c->rows_total / 128;
@@ -422,9 +533,14 @@ cmcs_status cmcs_create(const cmcs_config* cfg, const float* Phi, const float* y
   }
   CKC(cudaStreamSynchronize(c->stream));
   CKC(cudaGetLastError());
+  if (cfg->autotune) {
+    st = autotune(c);
+    if (st != CMCS_OK) return fail(st);
+  }
+  c->tuned = c->tc ? tc_set_stages(c, 0) : (c->tn_plain > 0 ? c->tn_plain : pick_tn(c->R, 9));
 #undef CKC
   *out = h;
-  return st;
+  return CMCS_OK;
 }
 
 void cmcs_destroy(cmcs_ctx* h) {
@@ -536,6 +652,7 @@ cmcs_status cmcs_adjoint(cmcs_ctx* h, const float* g, float* dy, float* dalpha, 
   a.prof_on = 0;
   a.xacc = c->adj_x;
   a.tn_plain = a.tn_ds = 0;
+  a.use_graphs = 0;
   CK(cudaMemsetAsync(c->adj_g, 0, sizeof(float) * T * C * Dp, c->stream));
   CK(cudaMemcpy2DAsync(c->adj_g, sizeof(float) * Dp, g, sizeof(float) * D, sizeof(float) * D, T * C,
                        kind_in(on_device), c->stream));
@@ -698,6 +815,7 @@ cmcs_status cmcs_result(const cmcs_ctx* hc, cmcs_summary* out) {
   out->cg_steps_mean = sum / c->S;
   out->operator_applies = c->op_applies;
   out->refine_diverged = c->last_diverged;
+  out->operator_variant = c->tuned;
   return CMCS_OK;
 }
 

@@ -72,6 +72,10 @@ struct Ctx {
   uint64_t seed;
   int64_t em_iter;
   cudaStream_t stream;
+  int own_stream;      // the context created its stream (caller passed NULL)
+  // captured CG chunks: [record][profiling]
+  cudaGraphExec_t graph[2][2];
+  int64_t graph_launches;  // kernels in one captured chunk
   int device;
   int sm_count;
 
@@ -94,6 +98,9 @@ struct Ctx {
   float *adj_g, *adj_x, *adj_wl, *adj_wm, *adj_dy, *adj_da;
   int* tile_task;    // [rows_total / 128] task owning each 128-row tile of phi
   int tn_plain, tn_ds; // operator tile widths (0: chosen from R)
+  int per_task;        // 1: launch the operator once per task (comparison schedule)
+  int use_graphs;      // 1: replay the CG step chunks from captured CUDA graphs
+  int tuned;           // operator variant the autotuner chose (TN or pipeline stages), 0: none
   float *b0hi, *b0lo;  // [T][Dp]
   float* alpha;        // [C][Dp]
   double* sumlogalpha; // [C]
@@ -180,5 +187,8 @@ cudaError_t tc_split_vectors(Ctx* c, const float* V);   // V -> dhi, dlo
 cudaError_t tc_refresh(Ctx* c);                         // recompute the BF16 copies of Phi
 
 inline int64_t round_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
+int pick_tn(int R, int max_tn);
+int tc_set_stages(Ctx* c, int stages);   // returns the stages in force (0: not a TC context)
+int tc_max_stages(Ctx* c);
 
 }  // namespace cmcs

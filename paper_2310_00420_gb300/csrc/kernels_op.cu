@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(256)
 k_pass1(const float* __restrict__ phi, const float* __restrict__ V, float* __restrict__ W,
         float* __restrict__ Wlo, const int64_t* __restrict__ drow,
         const int* __restrict__ tile_task, const int* __restrict__ task_active, int R, int Dp,
-        int Rc, int jstride) {
+        int Rc, int jstride, int g0) {
   // columns j' = 0 .. Rc-1 of the tile are systems j = j' * jstride of the task (all R
   // systems when Rc = R, jstride = 1; the mean systems only when Rc = C, jstride = K + 1)
   constexpr int BN = 16 * TN;
@@ -63,7 +63,7 @@ k_pass1(const float* __restrict__ phi, const float* __restrict__ V, float* __res
   __shared__ __align__(16) float As[2][16][132];
   __shared__ __align__(16) float Bs[2][16][BN + 4];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  const int g = blockIdx.y;
+  const int g = g0 + blockIdx.y;
   const int t = tile_task[g];
   if (task_active != nullptr && task_active[t] == 0) return;
   const int64_t row0 = (int64_t)g * 128;
@@ -177,6 +177,7 @@ struct P2Args {
   unsigned long long* opcount;  // [T] applications per task (plain pass only, may be null)
   int R, K, C, Dp, D, S;
   int Rc, jstride;        // columns processed: systems j = j' * jstride, j' < Rc
+  int t0;                 // first task (grid z covers tasks t0 ..)
   float beta_f;
   double beta_d;
   uint64_t seed;
@@ -191,7 +192,7 @@ __global__ void __launch_bounds__(256) k_pass2(P2Args p) {
   __shared__ __align__(16) float Bs[2][16][BN + 4];
   __shared__ __align__(16) float Bl[DS ? 2 : 1][16][DS ? BN + 4 : 1];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  const int t = blockIdx.z;
+  const int t = p.t0 + blockIdx.z;
   if (p.task_active != nullptr && p.task_active[t] == 0) return;
   const int dt = blockIdx.y;
   const int d0 = dt * 128;
@@ -342,6 +343,8 @@ namespace {
 
 // tile width TN (columns per thread) from the supported set minimising padded R, then
 // preferring wider tiles (fewer re-reads of Phi)
+}  // namespace
+
 int pick_tn(int R, int max_tn) {
   static const int cands[] = {9, 8, 6, 4, 3, 2, 1};
   int best = 1;
@@ -358,15 +361,18 @@ int pick_tn(int R, int max_tn) {
   return best;
 }
 
+namespace {
+
 template <bool DS>
 cudaError_t pass1(Ctx* c, int tn, const float* V, float* W, float* Wlo, const int* mask, int Rc,
-                  int jstride) {
+                  int jstride, int g0 = 0, int ng = -1) {
   const int bn = 16 * tn;
-  dim3 grid((Rc + bn - 1) / bn, (unsigned)(c->rows_total / 128));
+  if (ng < 0) ng = (int)(c->rows_total / 128);
+  dim3 grid((Rc + bn - 1) / bn, (unsigned)ng);
 #define P1CASE(TN)                                                                          \
   case TN:                                                                                  \
     k_pass1<TN, DS><<<grid, 256, 0, c->stream>>>(c->phi, V, W, Wlo, c->drow, c->tile_task, \
-                                                 mask, c->R, c->Dp, Rc, jstride);           \
+                                                 mask, c->R, c->Dp, Rc, jstride, g0);       \
     break;
   switch (tn) {
     P1CASE(1) P1CASE(2) P1CASE(3) P1CASE(4) P1CASE(6) P1CASE(8) P1CASE(9)
@@ -377,9 +383,9 @@ cudaError_t pass1(Ctx* c, int tn, const float* V, float* W, float* Wlo, const in
 }
 
 template <bool DS>
-cudaError_t pass2(Ctx* c, int tn, const P2Args& a) {
+cudaError_t pass2(Ctx* c, int tn, const P2Args& a, int nt = -1) {
   const int bn = 16 * tn;
-  dim3 grid((a.Rc + bn - 1) / bn, c->Dp / 128, c->T);
+  dim3 grid((a.Rc + bn - 1) / bn, c->Dp / 128, nt < 0 ? c->T : nt);
 #define P2CASE(TN)                                          \
   case TN:                                                  \
     k_pass2<TN, DS><<<grid, 256, 0, c->stream>>>(a);        \
@@ -413,6 +419,7 @@ P2Args base_args(Ctx* c) {
   a.em_iter = c->em_iter;
   a.Rc = c->R;
   a.jstride = 1;
+  a.t0 = 0;
   return a;
 }
 
@@ -422,14 +429,27 @@ cudaError_t launch_operator(Ctx* c, const float* V, float* Z, int with_dots) {
   if (c->tc != nullptr) return tc_operator(c, V, Z, with_dots);
   const int* mask = with_dots ? c->task_active : nullptr;
   const int tn = c->tn_plain > 0 ? c->tn_plain : pick_tn(c->R, 9);
-  cudaError_t e = pass1<false>(c, tn, V, c->w, nullptr, mask, c->R, 1);
-  if (e != cudaSuccess) return e;
   P2Args a = base_args(c);
   a.V = V;
   a.Z = Z;
   a.part = with_dots ? c->part : nullptr;
   a.task_active = mask;
   a.opcount = c->prof_on ? reinterpret_cast<unsigned long long*>(c->opcount) : nullptr;
+  if (c->per_task) {
+    // comparison schedule: one pair of launches per task
+    for (int t = 0; t < c->T; ++t) {
+      cudaError_t e = pass1<false>(c, tn, V, c->w, nullptr, mask, c->R, 1,
+                                   (int)(c->hrow[t] / 128), (int)((c->hrow[t + 1] - c->hrow[t]) / 128));
+      if (e != cudaSuccess) return e;
+      a.t0 = t;
+      e = pass2<false>(c, tn, a, 1);
+      if (e != cudaSuccess) return e;
+      c->launches += 2;
+    }
+    return cudaSuccess;
+  }
+  cudaError_t e = pass1<false>(c, tn, V, c->w, nullptr, mask, c->R, 1);
+  if (e != cudaSuccess) return e;
   c->launches += 2;
   return pass2<false>(c, tn, a);
 }

@@ -43,6 +43,7 @@ struct TcArgs {
   int64_t rows_total;
   int Rpad, BR, nbox, stages, stage_bytes;
   int ntiles, nbuf;
+  int tile_lo;            // tiles tile_lo .. ntiles-1 (a single task's range when per task)
   uint32_t tmem_cols;     // columns of one accumulator buffer
   uint32_t tmem_alloc;    // columns allocated (nbuf buffers)
   __nv_bfloat16* w_hi;    // pass 1 output, [R][rows_total]
@@ -275,7 +276,7 @@ k_tc(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMa
     // ---- TMA producer
     if (lane == 0) {
       uint32_t it = 0;
-      for (int tile = blockIdx.x; tile < p.ntiles && !*abort_flag; tile += gridDim.x) {
+      for (int tile = p.tile_lo + blockIdx.x; tile < p.ntiles && !*abort_flag; tile += gridDim.x) {
         TileInfo ti;
         if (!tile_info<PASS>(p, tile, ti)) continue;
         for (int kb = 0; kb < ti.nk; ++kb, ++it) {
@@ -306,7 +307,7 @@ k_tc(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMa
     if (lane == 0) {
       const uint32_t idesc = idesc_bf16(kBM, p.BR);
       uint32_t it = 0, lt = 0;
-      for (int tile = blockIdx.x; tile < p.ntiles && !*abort_flag; tile += gridDim.x) {
+      for (int tile = p.tile_lo + blockIdx.x; tile < p.ntiles && !*abort_flag; tile += gridDim.x) {
         TileInfo ti;
         if (!tile_info<PASS>(p, tile, ti)) continue;
         const int b = (int)(lt % p.nbuf);
@@ -354,7 +355,7 @@ k_tc(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMa
     const int lg = warp & 3;
     const int etid = threadIdx.x - 64;                 // 0..127 among the epilogue warps
     uint32_t lt = 0;
-    for (int tile = blockIdx.x; tile < p.ntiles; tile += gridDim.x) {
+    for (int tile = p.tile_lo + blockIdx.x; tile < p.ntiles; tile += gridDim.x) {
       TileInfo ti;
       if (!tile_info<PASS>(p, tile, ti)) continue;
       const int b = (int)(lt % p.nbuf);
@@ -542,16 +543,27 @@ cudaError_t run_passes(Ctx* c, TcState* s, const float* V, float* Z, int with_do
   a.Z = Z;
   a.part = with_dots ? c->part : nullptr;
   const int sms = c->sm_count > 0 ? c->sm_count : 1;
-  a.ntiles = (int)(c->rows_total / kBM);
-  k_tc<1, NA, NB><<<a.ntiles < sms ? a.ntiles : sms, kTcThreads, s->smem_bytes, c->stream>>>(
-      s->tm_phi[0], s->tm_phi[NA - 1], s->tm_d[0], s->tm_d[NB - 1], a);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  a.ntiles = c->T * (c->Dp / kBM);
-  k_tc<2, NA, NB><<<a.ntiles < sms ? a.ntiles : sms, kTcThreads, s->smem_bytes, c->stream>>>(
-      s->tm_phit[0], s->tm_phit[NA - 1], s->tm_w[0], s->tm_w[NB - 1], a);
-  c->launches += 2;
-  return cudaGetLastError();
+  const int ndt = c->Dp / kBM;
+  const int nloop = c->per_task ? c->T : 1;
+  for (int t = 0; t < nloop; ++t) {
+    // all tasks in one persistent launch per pass, or (comparison schedule) one per task
+    a.tile_lo = c->per_task ? (int)(c->hrow[t] / kBM) : 0;
+    a.ntiles = c->per_task ? (int)(c->hrow[t + 1] / kBM) : (int)(c->rows_total / kBM);
+    int n = a.ntiles - a.tile_lo;
+    k_tc<1, NA, NB><<<n < sms ? n : sms, kTcThreads, s->smem_bytes, c->stream>>>(
+        s->tm_phi[0], s->tm_phi[NA - 1], s->tm_d[0], s->tm_d[NB - 1], a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    a.tile_lo = c->per_task ? t * ndt : 0;
+    a.ntiles = c->per_task ? (t + 1) * ndt : c->T * ndt;
+    n = a.ntiles - a.tile_lo;
+    k_tc<2, NA, NB><<<n < sms ? n : sms, kTcThreads, s->smem_bytes, c->stream>>>(
+        s->tm_phit[0], s->tm_phit[NA - 1], s->tm_w[0], s->tm_w[NB - 1], a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    c->launches += 2;
+  }
+  return cudaSuccess;
 }
 
 }  // namespace
@@ -633,6 +645,24 @@ void tc_destroy(Ctx* c) {
   c->dhi = c->dlo = nullptr;
   free(s);
   c->tc = nullptr;
+}
+
+int tc_max_stages(Ctx* c) {
+  TcState* s = static_cast<TcState*>(c->tc);
+  if (!s) return 0;
+  const int extra = 1024 + (2 * 6 + 5) * 8 + 16 + 4 * s->Rpad * 4 + 64;
+  int m = (kSmemBudget - extra) / s->stage_bytes;
+  return m > 6 ? 6 : m;
+}
+
+int tc_set_stages(Ctx* c, int stages) {
+  TcState* s = static_cast<TcState*>(c->tc);
+  if (!s) return 0;
+  if (stages >= 2 && stages <= tc_max_stages(c)) {
+    s->stages = stages;
+    s->smem_bytes = s->stages * s->stage_bytes + 1024 + (2 * s->stages + 5) * 8 + 16 + 4 * s->Rpad * 4 + 64;
+  }
+  return s->stages;
 }
 
 cudaError_t tc_refresh(Ctx* c) {

@@ -53,12 +53,13 @@ int main(void) {
   O(cmcs_config, N); O(cmcs_config, beta); O(cmcs_config, pi); O(cmcs_config, cg_max_iter);
   O(cmcs_config, cg_tol); O(cmcs_config, seed); O(cmcs_config, precision);
   O(cmcs_config, refine_max); O(cmcs_config, refine_tol); O(cmcs_config, alpha_min);
-  O(cmcs_config, alpha_max);
+  O(cmcs_config, alpha_max); O(cmcs_config, schedule); O(cmcs_config, graphs);
+  O(cmcs_config, autotune);
   O(cmcs_summary, loglik); O(cmcs_summary, cg_steps_max); O(cmcs_summary, cg_steps_mean);
   O(cmcs_summary, cg_capped); O(cmcs_summary, refine_sweeps_max);
   O(cmcs_summary, refine_rel_max); O(cmcs_summary, min_margin);
   O(cmcs_summary, operator_applies); O(cmcs_summary, resid_rel_max);
-  O(cmcs_summary, refine_diverged);
+  O(cmcs_summary, refine_diverged); O(cmcs_summary, operator_variant);
   return 0;
 }
 """
@@ -88,7 +89,7 @@ def _cfg(**kw):
                       N.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), base["beta"],
                       pi.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), base["cg_max_iter"],
                       base["cg_tol"], base["seed"], base["precision"], base["refine_max"],
-                      base["refine_tol"], base["alpha_min"], base["alpha_max"])
+                      base["refine_tol"], base["alpha_min"], base["alpha_max"], 0, 0, 0)
     return cfg, (N, pi)
 
 
