@@ -5,7 +5,9 @@ A step is one EM iteration of Alg. 2 (E-step over every task and cluster: batche
 posterior-mean system and K probe systems, refinement of the solutions, diagonal and
 log-det estimates, responsibilities; then the M-step) on the plain-scale workload
 (T=32, C=4, D=8192, N=2048, K=32 probes, CG tol 1e-5, at most 100 steps), synthetic seeded
-inputs, FP32 path with the solutions refined to the accuracy the parity tests check.
+inputs, solutions refined to the accuracy the parity tests check.  The default path keeps Phi
+as a BF16 pair on the tcgen05 tensor cores (FP32-class products, FP32 accumulation); the
+plain FP32 SIMT form is timed beside it on the same workload ("fp32_form").
 
 Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on a bounded
 sample of the same workload instead.  Multi-GPU (torchrun): every rank runs an independent
@@ -42,7 +44,14 @@ def _args():
     ap.add_argument("--workload", default="plain-scale")
     ap.add_argument("--tasks", type=int, default=0,
                     help="keep only the first TASKS tasks of the workload (profiling slices)")
-    ap.add_argument("--precision", default="fp32")
+    ap.add_argument("--precision", default="bf16x3",
+                    help="bf16x3 (tensor cores, Phi as a BF16 pair) or fp32 (SIMT FP32)")
+    ap.add_argument("--no-fp32-form", action="store_true",
+                    help="skip timing the plain FP32 form beside the tensor-core path")
+    ap.add_argument("--schedule", default="batched", choices=["batched", "per_task"])
+    ap.add_argument("--compare-schedule", action="store_true",
+                    help="also time the per-task launch loop on the same workload")
+    ap.add_argument("--no-graphs", action="store_true")
     ap.add_argument("--refine-max", type=int, default=8)
     ap.add_argument("--refine-tol", type=float, default=1e-5)
     ap.add_argument("--no-e2e", action="store_true")
@@ -182,7 +191,8 @@ def run_ours(a):
     torch.cuda.set_device(local)
     wl = _workload(a.workload, rank, a.tasks)
     kw = dict(C=wl.C, K=wl.K, beta=wl.beta, pi=wl.pi, cg_max_iter=wl.cg_max_iter, cg_tol=wl.cg_tol,
-              seed=wl.seed, precision=a.precision, refine_max=a.refine_max, refine_tol=a.refine_tol)
+              seed=wl.seed, precision=a.precision, refine_max=a.refine_max, refine_tol=a.refine_tol,
+              schedule=a.schedule, graphs=not a.no_graphs)
     Phi_d = torch.from_numpy(wl.Phi).cuda()
     y_d = torch.from_numpy(wl.y).cuda()
     ctx = cmcs.Context(Phi_d, y_d, wl.N, **kw)
@@ -311,6 +321,36 @@ def run_ours(a):
                "d2h_bytes_per_step": int(sum(v.numel() * v.element_size() for v in outs.values()))}
 
     ctx.close()
+
+    def timed_leg(**over):
+        """EM iterations/s of another form on the same workload (same warm-up and steps)."""
+        kw2 = dict(kw)
+        kw2.update(over)
+        c3 = cmcs.Context(Phi_d, y_d, wl.N, **kw2)
+        for _ in range(a.warmup):
+            c3.em_iter(1)
+        c3.profile(True)
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record()
+        for _ in range(a.steps):
+            c3.em_iter(1)
+        f1.record()
+        torch.cuda.synchronize()
+        ms3 = f0.elapsed_time(f1)
+        pr = c3.profile_read()
+        c3.close()
+        return {"value": a.steps / (ms3 / 1e3), "unit": UNIT, "ms_per_step": ms3 / a.steps,
+                "operator_ms_per_application": pr["operator_ms"] / max(1, pr["operator_calls"]),
+                "operator_tflops": pr["operator_flops"] / (pr["operator_ms"] * 1e-3) / 1e12
+                if pr["operator_ms"] else None, **{k: v for k, v in over.items()}}
+
+    fp32_form = None
+    if a.precision != "fp32" and not a.no_fp32_form:
+        fp32_form = timed_leg(precision="fp32")
+    per_task = None
+    if a.compare_schedule:
+        per_task = timed_leg(schedule="per_task")
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms_max / a.steps,
@@ -330,7 +370,8 @@ def run_ours(a):
                 "residual_ms_per_step": prof["residual_ms"] / a.steps,
                 "operator_applies_per_step": prof["operator_calls"] / a.steps,
                 "roofline": roof, "cpu_baseline": cpu, "err_vs_fp64": err, "e2e": e2e,
-                "clocks": clk, "gpu_launches": prof["kernel_launches"]}
+                "clocks": clk, "gpu_launches": prof["kernel_launches"],
+                "fp32_form": fp32_form, "per_task_schedule": per_task}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -106,10 +106,11 @@ static_assert(kCheckEvery <= kProfEvents, "events of one chunk");
 // current chunk of CG steps)
 cudaError_t timed_operator(Ctx* c) {
   const bool ev = c->prof_on && c->prof_nev < kProfEvents;
-  if (ev) cudaEventRecord(c->prof_ev[2 * c->prof_nev], c->stream);
+  // external records, so that inside a captured graph they become event-record nodes
+  if (ev) cudaEventRecordWithFlags(c->prof_ev[2 * c->prof_nev], c->stream, cudaEventRecordExternal);
   cudaError_t e = launch_operator(c, c->d, c->ad, 1);
   if (ev) {
-    cudaEventRecord(c->prof_ev[2 * c->prof_nev + 1], c->stream);
+    cudaEventRecordWithFlags(c->prof_ev[2 * c->prof_nev + 1], c->stream, cudaEventRecordExternal);
     c->prof_nev++;
   }
   if (c->prof_on) c->prof_calls++;
@@ -122,6 +123,8 @@ void fold_events(Ctx* c) {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, c->prof_ev[2 * i], c->prof_ev[2 * i + 1]) == cudaSuccess)
       c->prof_ms += ms;
+    else
+      cudaGetLastError();     // a missing timing must not surface as a failure of the E-step
   }
   c->prof_nev = 0;
 }
@@ -216,6 +219,7 @@ cmcs_status refine_sweeps(Ctx* c, const float* Bext) {
     if (c->prof_on) {
       float ms = 0.f;
       if (cudaEventElapsedTime(&ms, c->res_ev[0], c->res_ev[1]) == cudaSuccess) c->res_ms += ms;
+      else cudaGetLastError();
     }
     if (c->hcounters[1] == 0) break;
   }
