@@ -106,11 +106,15 @@ static_assert(kCheckEvery <= kProfEvents, "events of one chunk");
 // current chunk of CG steps)
 cudaError_t timed_operator(Ctx* c) {
   const bool ev = c->prof_on && c->prof_nev < kProfEvents;
-  // external records, so that inside a captured graph they become event-record nodes
-  if (ev) cudaEventRecordWithFlags(c->prof_ev[2 * c->prof_nev], c->stream, cudaEventRecordExternal);
-  cudaError_t e = launch_operator(c, c->d, c->ad, 1);
+  // while capturing, external records become event-record nodes of the graph
+  const unsigned flags = c->capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
   if (ev) {
-    cudaEventRecordWithFlags(c->prof_ev[2 * c->prof_nev + 1], c->stream, cudaEventRecordExternal);
+    cudaError_t er = cudaEventRecordWithFlags(c->prof_ev[2 * c->prof_nev], c->stream, flags);
+    if (er != cudaSuccess) return er;
+  }
+  cudaError_t e = launch_operator(c, c->d, c->ad, 1);
+  if (ev && e == cudaSuccess) {
+    e = cudaEventRecordWithFlags(c->prof_ev[2 * c->prof_nev + 1], c->stream, flags);
     c->prof_nev++;
   }
   if (c->prof_on) c->prof_calls++;
@@ -142,12 +146,14 @@ cmcs_status cg_steps_direct(Ctx* c, int record, int n) {
 // the graph replaying kCheckEvery CG steps, captured on first use
 cudaGraphExec_t chunk_graph(Ctx* c, int record) {
   cudaGraphExec_t& g = c->graph[record][c->prof_on];
-  if (g != nullptr) return g;
+  if (g != nullptr || c->graph_failed[record][c->prof_on]) return g;
   const int64_t l0 = c->launches, a0 = c->op_applies, p0 = c->prof_calls;
   cudaGraph_t graph = nullptr;
   if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return nullptr;
   c->prof_nev = 0;
+  c->capturing = 1;
   cmcs_status s = cg_steps_direct(c, record, kCheckEvery);
+  c->capturing = 0;
   cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
   c->graph_launches = c->launches - l0;
   c->launches = l0;
@@ -157,6 +163,8 @@ cudaGraphExec_t chunk_graph(Ctx* c, int record) {
   if (s != CMCS_OK || e != cudaSuccess || graph == nullptr) {
     cudaGetLastError();
     if (graph) cudaGraphDestroy(graph);
+    c->graph_failed[record][c->prof_on] = 1;    // run this variant with direct launches
+    c->err[0] = 0;
     return nullptr;
   }
   e = cudaGraphInstantiate(&g, graph, 0);
@@ -164,6 +172,7 @@ cudaGraphExec_t chunk_graph(Ctx* c, int record) {
   if (e != cudaSuccess) {
     cudaGetLastError();
     g = nullptr;
+    c->graph_failed[record][c->prof_on] = 1;
   }
   return g;
 }

@@ -76,6 +76,8 @@ struct Ctx {
   // captured CG chunks: [record][profiling]
   cudaGraphExec_t graph[2][2];
   int64_t graph_launches;  // kernels in one captured chunk
+  int graph_failed[2][2];  // capture of that variant failed: use direct launches
+  int capturing;           // a chunk is being captured
   int device;
   int sm_count;
 

@@ -72,3 +72,17 @@ def test_batching_workload_sampled_parity(batching):
         nu = cofem.logdet_estimate(g["gamma"][t, c].astype(np.float64),
                                    g["xi"][t, c].astype(np.float64), g["steps"][t, c, 1:], wl.D)
         assert abs(g["logdet"][t, c] - nu) <= 1e-9 * abs(nu)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+def test_profiling_with_graphs(ragged, precision):
+    """Operator timing with captured graphs: events become graph nodes; results unchanged."""
+    base = _run(ragged, precision=precision, graphs=False)
+    with make_ctx(ragged, refine_max=6, refine_tol=1e-6, precision=precision, graphs=True) as ctx:
+        ctx.profile(True)
+        ctx.em_iter(2)
+        prof = ctx.profile_read()
+        mu = ctx.read(cmcs.OUT_MU)
+    assert np.array_equal(mu, base["mu"])
+    assert prof["operator_calls"] > 0 and prof["operator_ms"] > 0
+    assert prof["operator_flops"] > 0 and prof["kernel_launches"] > prof["operator_calls"]
