@@ -125,6 +125,19 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def aggregate(ms_local: float, steps: int, world: int, device: str = "cuda"):
+    """Whole-job throughput over ranks: the slowest rank's time, every rank's steps.
+    Returns (value in steps/s, max ms over ranks)."""
+    ms_max = ms_local
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    return world * steps / (ms_max / 1e3), ms_max
+
+
 def _workload(name: str, seed: int, tasks: int = 0):
     from paper_2310_00420_gb300 import synth
     wl = synth.WORKLOADS[name](seed=seed)
@@ -220,12 +233,7 @@ def run_ours(a):
     prof = ctx.profile_read()
     summ = ctx.summary()
     ctx.profile(False)
-    ms_max = ms
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_max = float(t.item())
-    value = world * a.steps / (ms_max / 1e3)
+    value, ms_max = aggregate(ms, a.steps, world)
     systems = wl.T * wl.C * (wl.K + 1)
 
     # operator roofline: algorithmic FLOPs / measured device time of the operator applications
@@ -311,12 +319,8 @@ def run_ours(a):
             c2.close()
         torch.cuda.synchronize()
         barrier()
-        dt = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([dt], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            dt = float(t.item())
-        e2e = {"value": world * a.steps / dt, "unit": UNIT,
+        e2e_value, _ = aggregate((time.perf_counter() - t0) * 1e3, a.steps, world)
+        e2e = {"value": e2e_value, "unit": UNIT,
                "h2d_bytes_per_step": int(wl.Phi.nbytes + wl.y.nbytes + wl.C * wl.D * 4),
                "d2h_bytes_per_step": int(sum(v.numel() * v.element_size() for v in outs.values()))}
 

@@ -68,6 +68,9 @@ void free_ctx(Ctx* c) {
     for (int q = 0; q < 2; ++q)
       if (c->graph[r][q]) cudaGraphExecDestroy(c->graph[r][q]);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  if (c->side) cudaStreamDestroy(c->side);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
   if (c->tc) tc_destroy(c);
   free(c->hN);
   free(c->hNp);
@@ -245,6 +248,12 @@ cmcs_status estep(Ctx* c) {
   cmcs_status s = run_cg(c, 1);
   if (s != CMCS_OK) return s;
   CK(cudaMemcpyAsync(c->steps0, c->steps, sizeof(int) * c->S, cudaMemcpyDeviceToDevice, c->stream));
+  // the Lanczos coefficients are final: their eigen step (Eqs. 9-11) runs on the side stream,
+  // overlapping the refinement sweeps
+  CK(cudaEventRecord(c->ev_fork, c->stream));
+  CK(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+  CK(launch_quadrature_ctx(c, c->side));
+  CK(cudaEventRecord(c->ev_join, c->side));
   // the solution moves to xacc by copy, so captured graphs keep valid buffer addresses
   CK(cudaMemcpyAsync(c->xacc, c->x, sizeof(float) * (size_t)c->S * c->Dp, cudaMemcpyDeviceToDevice,
                      c->stream));
@@ -262,7 +271,7 @@ cmcs_status estep(Ctx* c) {
     CK(cudaMemsetAsync(c->rres, 0, sizeof(float) * c->S, c->stream));
   }
   CK(launch_sest(c));
-  CK(launch_quadrature_ctx(c));
+  CK(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
   CK(launch_ell_softmax(c, rmu));
   s = read_counters(c);
   if (s != CMCS_OK) return s;
@@ -445,6 +454,9 @@ cmcs_status cmcs_create(const cmcs_config* cfg, const float* Phi, const float* y
     CKC(cudaStreamCreate(&c->stream));
     c->own_stream = 1;
   }
+  CKC(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+  CKC(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+  CKC(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
   CKC(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device));
   const int64_t Dp = c->Dp, S = c->S, T = c->T, C = c->C, K = c->K;
   const int64_t ntiles = c->rows_total / 128;

@@ -73,6 +73,8 @@ struct Ctx {
   int64_t em_iter;
   cudaStream_t stream;
   int own_stream;      // the context created its stream (caller passed NULL)
+  cudaStream_t side;   // runs the Lanczos eigen step while refinement proceeds on stream
+  cudaEvent_t ev_fork, ev_join;
   // captured CG chunks: [record][profiling]
   cudaGraphExec_t graph[2][2];
   int64_t graph_launches;  // kernels in one captured chunk
@@ -177,7 +179,7 @@ cudaError_t launch_adj_dphi(Ctx* c, const float* lam, const float* Wl, const flo
 // E-step tail and M-step (kernels_estep.cu)
 cudaError_t launch_quadrature(const float* gam, const float* xi, const int* steps, int nsys,
                               int ld, double* out, int* status, cudaStream_t st);
-cudaError_t launch_quadrature_ctx(Ctx* c);
+cudaError_t launch_quadrature_ctx(Ctx* c, cudaStream_t st);
 cudaError_t launch_ell_softmax(Ctx* c, const float* rmu /* residuals for the correction, or null */);
 cudaError_t launch_mstep(Ctx* c);
 

@@ -61,11 +61,13 @@ __device__ double lanczos_log_quad(const float* __restrict__ g, const float* __r
     // Wilkinson shift: eigenvalue of the trailing 2x2 block closer to a[m]
     const double dd = 0.5 * (a[m - 1] - a[m]);
     const double bm = b[m - 1];
-    const double den = dd + copysign(hypot(dd, bm), dd);
+    // entries of these matrices lie within about 1e-12 .. 1e12, far from overflow, so the
+    // plain square root replaces the (slower) scaled hypot
+    const double den = dd + copysign(sqrt(dd * dd + bm * bm), dd);
     const double mu = a[m] - bm * bm / den;
     double x = a[l] - mu, y = b[l];
     for (int k = l; k < m; ++k) {
-      const double r = hypot(x, y);
+      const double r = sqrt(x * x + y * y);
       double c = 1.0, s = 0.0;
       if (r > 0.0) {
         c = x / r;
@@ -97,11 +99,13 @@ __device__ double lanczos_log_quad(const float* __restrict__ g, const float* __r
 
 }  // namespace
 
+constexpr int kQuadThreads = 32;   // one serial eigen solve per thread: spread over all SMs
+
 template <int UB>
-__global__ void __launch_bounds__(64)
+__global__ void __launch_bounds__(kQuadThreads)
 k_quad(const float* __restrict__ gam, const float* __restrict__ xi, const int* __restrict__ steps,
        int nsys, int ld, double* out, int* status) {
-  const int i = blockIdx.x * 64 + threadIdx.x;
+  const int i = blockIdx.x * kQuadThreads + threadIdx.x;
   if (i >= nsys) return;
   int U = steps[i];
   if (U <= 0) {
@@ -121,19 +125,20 @@ k_quad(const float* __restrict__ gam, const float* __restrict__ xi, const int* _
 cudaError_t launch_quadrature(const float* gam, const float* xi, const int* steps, int nsys,
                               int ld, double* out, int* status, cudaStream_t st) {
   if (nsys <= 0) return cudaSuccess;
-  const int blocks = (nsys + 63) / 64;
-  if (ld <= 64) k_quad<64><<<blocks, 64, 0, st>>>(gam, xi, steps, nsys, ld, out, status);
-  else if (ld <= 128) k_quad<128><<<blocks, 64, 0, st>>>(gam, xi, steps, nsys, ld, out, status);
-  else if (ld <= 256) k_quad<256><<<blocks, 64, 0, st>>>(gam, xi, steps, nsys, ld, out, status);
-  else if (ld <= 512) k_quad<512><<<blocks, 64, 0, st>>>(gam, xi, steps, nsys, ld, out, status);
+  const int blocks = (nsys + kQuadThreads - 1) / kQuadThreads;
+  const int nt = kQuadThreads;
+  if (ld <= 64) k_quad<64><<<blocks, nt, 0, st>>>(gam, xi, steps, nsys, ld, out, status);
+  else if (ld <= 128) k_quad<128><<<blocks, nt, 0, st>>>(gam, xi, steps, nsys, ld, out, status);
+  else if (ld <= 256) k_quad<256><<<blocks, nt, 0, st>>>(gam, xi, steps, nsys, ld, out, status);
+  else if (ld <= 512) k_quad<512><<<blocks, nt, 0, st>>>(gam, xi, steps, nsys, ld, out, status);
   else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 
-cudaError_t launch_quadrature_ctx(Ctx* c) {
+cudaError_t launch_quadrature_ctx(Ctx* c, cudaStream_t st) {
   c->launches += 1;
   return launch_quadrature(c->gam, c->xi, c->psteps, c->T * c->C * c->K, c->U, c->quad,
-                           &c->counters[2], c->stream);
+                           &c->counters[2], st);
 }
 
 // ---- ell_tc = nu + sum_d log alpha_cd + b0^T mu (Eq. 3), nu from Eq. 11 ------------------

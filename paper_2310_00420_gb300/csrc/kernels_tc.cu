@@ -9,8 +9,8 @@
 // BF16-rounded Phi by (V_hi + V_lo) (two MMAs per k-step); BF16X3 also splits Phi and adds
 // Phi_lo V_hi (three MMAs), about 16 significant bits per product.
 //
-// Persistent kernel, one CTA (6 warps) per SM, looping over 128-row output tiles (each with all
-// R columns, up to 512 TMEM columns).  Warp 0 lane 0 streams A and B tiles with TMA (128-byte
+// Persistent kernel, one CTA (6 warps) per SM, looping over output tiles of 128 rows by up to
+// 256 columns (R wider than 256 is split into column tiles).  Warp 0 lane 0 streams A and B tiles with TMA (128-byte
 // swizzle) through a ring of shared-memory stages; warp 1 lane 0 issues tcgen05.mma from
 // shared-memory descriptors into one of two TMEM accumulators; warps 2-5 drain the other
 // accumulator (tcgen05.ld, 32 rows each), so a tile's epilogue overlaps the next tile's
@@ -44,6 +44,7 @@ struct TcArgs {
   int Rpad, BR, nbox, stages, stage_bytes;
   int ntiles, nbuf;
   int tile_lo;            // tiles tile_lo .. ntiles-1 (a single task's range when per task)
+  int ncol;               // column tiles per row tile (Rpad columns each)
   uint32_t tmem_cols;     // columns of one accumulator buffer
   uint32_t tmem_alloc;    // columns allocated (nbuf buffers)
   __nv_bfloat16* w_hi;    // pass 1 output, [R][rows_total]
@@ -165,11 +166,15 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 
 // ---- the GEMM kernel (persistent, two TMEM accumulators) --------------------------------
 struct TileInfo {
-  int t, a_row, b_row, kx, nk, dtile;
+  int t, a_row, b_row, kx, nk, dtile, col0;
 };
 
+// tile = row_tile * ncol + column_tile: the column tiles of one row tile run on neighbouring
+// CTAs at the same time, so the second read of the A tile is served by L2
 template <int PASS>
-__device__ __forceinline__ bool tile_info(const TcArgs& p, int tile, TileInfo& ti) {
+__device__ __forceinline__ bool tile_info(const TcArgs& p, int tile_in, TileInfo& ti) {
+  const int tile = tile_in / p.ncol;
+  ti.col0 = (tile_in - tile * p.ncol) * p.Rpad;
   if (PASS == 1) {
     ti.t = p.tile_task[tile];
     ti.a_row = tile * kBM;
@@ -293,10 +298,9 @@ k_tc(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMa
           if (NA == 2) tma_load_2d(st + a_bytes, &tA1, ti.kx + kb * kBK, ti.a_row, &full[s]);
           uint8_t* bst = st + NA * a_bytes;
           for (int bx = 0; bx < p.nbox; ++bx) {
-            tma_load_2d(bst + bx * p.BR * 128, &tB0, ti.kx + kb * kBK, ti.b_row + bx * p.BR, &full[s]);
-            if (NB == 2)
-              tma_load_2d(bst + b_bytes + bx * p.BR * 128, &tB1, ti.kx + kb * kBK,
-                          ti.b_row + bx * p.BR, &full[s]);
+            const int brow = ti.b_row + ti.col0 + bx * p.BR;
+            tma_load_2d(bst + bx * p.BR * 128, &tB0, ti.kx + kb * kBK, brow, &full[s]);
+            if (NB == 2) tma_load_2d(bst + b_bytes + bx * p.BR * 128, &tB1, ti.kx + kb * kBK, brow, &full[s]);
           }
           issued = it + 1;
         }
@@ -374,7 +378,7 @@ k_tc(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMa
           tmem_ld16(trow + c0, v);
 #pragma unroll
           for (int i = 0; i < 16; ++i) {
-            const int j = c0 + i;
+            const int j = ti.col0 + c0 + i;
             if (j < p.R) {
               const __nv_bfloat16 hi = __float2bfloat16_rn(v[i]);
               const __nv_bfloat16 lo = __float2bfloat16_rn(v[i] - __bfloat162float(hi));
@@ -385,12 +389,13 @@ k_tc(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMa
         }
       } else {
         const int d = ti.a_row + 32 * lg + lane;
-        if (p.opcount != nullptr && ti.dtile == 0 && etid == 0) atomicAdd(&p.opcount[ti.t], 1ull);
+        if (p.opcount != nullptr && ti.dtile == 0 && ti.col0 == 0 && etid == 0)
+          atomicAdd(&p.opcount[ti.t], 1ull);
         for (int c0 = 0; c0 < p.Rpad; c0 += 16) {
           float vv[16], aa[16];
 #pragma unroll
           for (int i = 0; i < 16; ++i) {
-            const int j = c0 + i;
+            const int j = ti.col0 + c0 + i;
             const int jj = j < p.R ? j : 0;
             const int64_t sys = (int64_t)ti.t * p.R + jj;
             vv[i] = j < p.R ? __ldg(p.V + sys * p.Dp + d) : 0.f;
@@ -400,7 +405,7 @@ k_tc(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMa
           tmem_ld16(trow + c0, acc);
 #pragma unroll
           for (int i = 0; i < 16; ++i) {
-            const int j = c0 + i;
+            const int j = ti.col0 + c0 + i;
             const float ad = fmaf(p.beta, acc[i], aa[i] * vv[i]);
             if (j < p.R) p.Z[((int64_t)ti.t * p.R + j) * p.Dp + d] = ad;
             dot[i] = vv[i] * ad;
@@ -410,9 +415,9 @@ k_tc(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMa
         }
         epi_bar();
         if (p.part != nullptr) {
-          for (int j = etid; j < p.R; j += 128)
-            p.part[(int64_t)ti.dtile * p.S + (int64_t)ti.t * p.R + j] =
-                ((red[j] + red[p.Rpad + j]) + red[2 * p.Rpad + j]) + red[3 * p.Rpad + j];
+          for (int jl = etid; jl < p.Rpad && ti.col0 + jl < p.R; jl += 128)
+            p.part[(int64_t)ti.dtile * p.S + (int64_t)ti.t * p.R + ti.col0 + jl] =
+                ((red[jl] + red[p.Rpad + jl]) + red[2 * p.Rpad + jl]) + red[3 * p.Rpad + jl];
         }
         epi_bar();
       }
@@ -469,7 +474,7 @@ namespace {
 
 struct TcState {
   int NA, NB;
-  int Rpad, BR, nbox, stages, stage_bytes, smem_bytes, nbuf;
+  int Rpad, BR, nbox, stages, stage_bytes, smem_bytes, nbuf, ncol;
   uint32_t tmem_cols, tmem_alloc;
   __nv_bfloat16 *phi_hi, *phi_lo, *phit_hi, *phit_lo, *w_hi, *w_lo;
   CUtensorMap tm_phi[2], tm_phit[2], tm_d[2], tm_w[2];
@@ -526,6 +531,7 @@ TcArgs base_args(Ctx* c, TcState* s) {
   a.tmem_cols = s->tmem_cols;
   a.tmem_alloc = s->tmem_alloc;
   a.nbuf = s->nbuf;
+  a.ncol = s->ncol;
   a.w_hi = s->w_hi;
   a.w_lo = s->w_lo;
   a.alpha = c->alpha;
@@ -547,15 +553,15 @@ cudaError_t run_passes(Ctx* c, TcState* s, const float* V, float* Z, int with_do
   const int nloop = c->per_task ? c->T : 1;
   for (int t = 0; t < nloop; ++t) {
     // all tasks in one persistent launch per pass, or (comparison schedule) one per task
-    a.tile_lo = c->per_task ? (int)(c->hrow[t] / kBM) : 0;
-    a.ntiles = c->per_task ? (int)(c->hrow[t + 1] / kBM) : (int)(c->rows_total / kBM);
+    a.tile_lo = (c->per_task ? (int)(c->hrow[t] / kBM) : 0) * s->ncol;
+    a.ntiles = (c->per_task ? (int)(c->hrow[t + 1] / kBM) : (int)(c->rows_total / kBM)) * s->ncol;
     int n = a.ntiles - a.tile_lo;
     k_tc<1, NA, NB><<<n < sms ? n : sms, kTcThreads, s->smem_bytes, c->stream>>>(
         s->tm_phi[0], s->tm_phi[NA - 1], s->tm_d[0], s->tm_d[NB - 1], a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    a.tile_lo = c->per_task ? t * ndt : 0;
-    a.ntiles = c->per_task ? (t + 1) * ndt : c->T * ndt;
+    a.tile_lo = (c->per_task ? t * ndt : 0) * s->ncol;
+    a.ntiles = (c->per_task ? (t + 1) * ndt : c->T * ndt) * s->ncol;
     n = a.ntiles - a.tile_lo;
     k_tc<2, NA, NB><<<n < sms ? n : sms, kTcThreads, s->smem_bytes, c->stream>>>(
         s->tm_phit[0], s->tm_phit[NA - 1], s->tm_w[0], s->tm_w[NB - 1], a);
@@ -574,13 +580,11 @@ int tc_create(Ctx* c) {
   c->tc = s;
   s->NA = c->precision == CMCS_BF16X3 ? 2 : 1;
   s->NB = 2;
-  s->nbox = (c->R + 255) / 256;
-  s->BR = (int)round_up((c->R + s->nbox - 1) / s->nbox, 16);
-  s->Rpad = s->BR * s->nbox;
-  if (s->Rpad > 512) {
-    snprintf(c->err, sizeof(c->err), "tensor-core operator supports C*(K+1) <= 512 (got %d)", c->R);
-    return 1;
-  }
+  // columns: tiles of at most 256 (one MMA width), so two accumulators always fit in TMEM
+  s->ncol = (c->R + 255) / 256;
+  s->nbox = 1;
+  s->BR = (int)round_up((c->R + s->ncol - 1) / s->ncol, 16);
+  s->Rpad = s->BR;
   s->tmem_cols = 32;
   while ((int)s->tmem_cols < s->Rpad) s->tmem_cols <<= 1;
   s->nbuf = 2 * s->tmem_cols <= 512 ? 2 : 1;     // double-buffer the accumulator when it fits

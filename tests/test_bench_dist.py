@@ -1,0 +1,47 @@
+"""The multi-rank path of bench.py on CPU: two gloo ranks, each an independent replica with its
+own step time; the reported throughput uses the slowest rank's time and all ranks' steps."""
+import os
+import socket
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _worker(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    value, ms_max = bench.aggregate(1000.0 * (rank + 1), steps=3, world=world, device="cpu")
+    out[rank] = (value, ms_max)
+    dist.destroy_process_group()
+
+
+def test_two_rank_aggregation():
+    world = 2
+    port = _free_port()
+    with mp.Manager() as m:
+        out = m.dict()
+        mp.spawn(_worker, args=(world, port, out), nprocs=world, join=True)
+        res = dict(out)
+    for rank in range(world):
+        value, ms_max = res[rank]
+        assert ms_max == 2000.0                      # slowest rank
+        assert abs(value - world * 3 / 2.0) < 1e-12  # 6 steps in 2 s
+
+
+def test_single_rank_aggregation():
+    import bench
+    value, ms_max = bench.aggregate(500.0, steps=4, world=1, device="cpu")
+    assert ms_max == 500.0 and value == 8.0
