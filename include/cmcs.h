@@ -201,6 +201,13 @@ cmcs_status cmcs_lanczos_quadrature(const float *gamma, const float *xi, const i
                                     int nsys, int ld, double *out, int32_t *status,
                                     void *stream);
 
+/* Test hook for failure detection (tensor-core precisions only).  With enable = 1 every
+ * operator launch makes its MMA warp wait on a barrier that nothing arrives at; the wait gives
+ * up after its 2-second wall-time limit, the kernel takes its abort path (stops issuing, waits
+ * for its copies and MMAs in flight, frees its tensor memory) and the E-step returns
+ * CMCS_ERR_TIMEOUT.  enable = 0 restores normal operation; the context stays usable. */
+cmcs_status cmcs_test_stall(cmcs_ctx *ctx, int enable);
+
 /* Operator profile accumulated since profiling was last enabled on a context. */
 typedef struct {
   int64_t operator_calls;    /* batched operator applications (each: Phi pass + Phi^T pass) */

@@ -27,7 +27,7 @@ PRECISIONS = {"fp32": FP32, "bf16": BF16_REFINE, "bf16_refine": BF16_REFINE, "bf
 EXPORTS = ("cmcs_create", "cmcs_set_alpha", "cmcs_estep", "cmcs_em_iter", "cmcs_read",
            "cmcs_result", "cmcs_apply", "cmcs_probes", "cmcs_lanczos_quadrature",
            "cmcs_profile", "cmcs_profile_read", "cmcs_apply_noalloc", "cmcs_set_data",
-           "cmcs_adjoint", "cmcs_last_error", "cmcs_destroy")
+           "cmcs_adjoint", "cmcs_test_stall", "cmcs_last_error", "cmcs_destroy")
 
 
 class Config(ctypes.Structure):
@@ -88,6 +88,7 @@ def lib():
     L.cmcs_apply_noalloc.argtypes = [vp, i, i, vp, ctypes.c_double, vp, i, vp, vp]
     L.cmcs_set_data.argtypes = [vp, vp, vp, i]
     L.cmcs_adjoint.argtypes = [vp, vp, vp, vp, vp, i]
+    L.cmcs_test_stall.argtypes = [vp, i]
     L.cmcs_last_error.argtypes = [vp]
     L.cmcs_last_error.restype = ctypes.c_char_p
     L.cmcs_destroy.argtypes = [vp]
@@ -266,6 +267,9 @@ class Context:
         _check(lib().cmcs_adjoint(self.h, pg, _ptr(dy)[0], _ptr(da)[0],
                                   _ptr(dP)[0] if dP is not None else None, dev), self.h)
         return dy, da, dP
+
+    def test_stall(self, enable: bool):
+        _check(lib().cmcs_test_stall(self.h, 1 if enable else 0), self.h)
 
     def profile(self, enable: bool = True):
         _check(lib().cmcs_profile(self.h, 1 if enable else 0), self.h)

@@ -53,7 +53,7 @@ void free_ctx(Ctx* c) {
                   c->w, c->wlo, c->part, c->rr, c->bb, c->steps, c->steps0, c->active,
                   c->ractive, c->sweeps, c->rrel, c->rres, c->task_active, c->counters, c->gam, c->xi,
                   c->psteps, c->sest, c->quad, c->logdet, c->ell, c->q, c->assign, c->stats,
-                  c->dN, c->opcount, c->dorow, c->adj_g, c->adj_x, c->adj_wl, c->adj_wm,
+                  c->dN, c->opcount, c->dorow, c->stall_flag, c->adj_g, c->adj_x, c->adj_wl, c->adj_wm,
                   c->adj_dy, c->adj_da};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -202,6 +202,10 @@ cmcs_status run_cg(Ctx* c, int record) {
     cmcs_status s = read_counters(c);
     if (s != CMCS_OK) return s;
     fold_events(c);
+    if (c->hcounters[2] & 8) {
+      set_err(c, "a bounded device-side wait expired in the tensor-core operator");
+      return CMCS_ERR_TIMEOUT;
+    }
     if (c->hcounters[0] == 0) break;
   }
   return CMCS_OK;
@@ -504,6 +508,8 @@ cmcs_status cmcs_create(const cmcs_config* cfg, const float* Phi, const float* y
   CKC(dalloc(&c->stats, 4));
   CKC(dalloc(&c->opcount, (size_t)T));
   CKC(dalloc(&c->dorow, (size_t)(T + 1)));
+  CKC(dalloc(&c->stall_flag, 1));
+  CKC(cudaMemsetAsync(c->stall_flag, 0, sizeof(int), c->stream));
   CKC(dalloc(&c->adj_g, (size_t)(T * C * Dp)));
   CKC(dalloc(&c->adj_x, (size_t)(T * C * Dp)));
   CKC(dalloc(&c->adj_wl, (size_t)(C * c->rows_total)));
@@ -576,6 +582,17 @@ void cmcs_destroy(cmcs_ctx* h) {
 }
 
 const char* cmcs_last_error(const cmcs_ctx* h) { return h ? h->c.err : g_create_err; }
+
+cmcs_status cmcs_test_stall(cmcs_ctx* h, int enable) {
+  if (!h || (enable != 0 && enable != 1)) return CMCS_ERR_INVALID_ARG;
+  Ctx* c = &h->c;
+  if (c->tc == nullptr) {
+    set_err(c, "cmcs_test_stall: only the tensor-core operator has device-side waits");
+    return CMCS_ERR_UNSUPPORTED;
+  }
+  CK(cudaMemcpyAsync(c->stall_flag, &enable, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  return sync_check(c);
+}
 
 cmcs_status cmcs_profile(cmcs_ctx* h, int enable) {
   if (!h || (enable != 0 && enable != 1)) return CMCS_ERR_INVALID_ARG;

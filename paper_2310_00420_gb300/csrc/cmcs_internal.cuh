@@ -80,6 +80,7 @@ struct Ctx {
   int64_t graph_launches;  // kernels in one captured chunk
   int graph_failed[2][2];  // capture of that variant failed: use direct launches
   int capturing;           // a chunk is being captured
+  int* stall_flag;         // device int, test hook of the bounded-wait path (cmcs_test_stall)
   int device;
   int sm_count;
 

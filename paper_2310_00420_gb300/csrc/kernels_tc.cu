@@ -56,6 +56,7 @@ struct TcArgs {
   float beta;
   unsigned long long* opcount;
   int* status;
+  const int* stall;       // test hook: nonzero makes the MMA warp wait on a barrier nothing arrives at
 };
 
 // ---- PTX wrappers ---------------------------------------------------------------------
@@ -250,10 +251,13 @@ k_tc(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMa
   uint64_t* tfull = empty + p.stages;        // [2] accumulator ready for the epilogue
   uint64_t* tempty = tfull + 2;              // [2] accumulator drained
   uint64_t* mdone = tempty + 2;              // every MMA issued has completed
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mdone + 1);
+  uint64_t* never = mdone + 1;               // test hook: no thread ever arrives here
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(never + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   float* red = reinterpret_cast<float*>(tmem_slot + 4);          // [4][Rpad] (pass 2)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // once a wait has expired in this E-step, later launches do nothing (the host reports it)
+  if (*reinterpret_cast<volatile int*>(p.status) & 8) return;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < p.stages; ++s) {
@@ -265,6 +269,7 @@ k_tc(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMa
       mbar_init(&tempty[b], 32 * kEpiWarps);
     }
     mbar_init(mdone, 1);
+    mbar_init(never, 1);
     *abort_flag = 0;
     fence_mbar_init();
   }
@@ -311,6 +316,10 @@ k_tc(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMa
     if (lane == 0) {
       const uint32_t idesc = idesc_bf16(kBM, p.BR);
       uint32_t it = 0, lt = 0;
+      if (p.stall != nullptr && *p.stall != 0 && !mbar_wait(never, 0)) {
+        *abort_flag = 1;               // the bounded wait expired: take the abort path
+        atomicOr(p.status, 8);
+      }
       for (int tile = p.tile_lo + blockIdx.x; tile < p.ntiles && !*abort_flag; tile += gridDim.x) {
         TileInfo ti;
         if (!tile_info<PASS>(p, tile, ti)) continue;
@@ -537,6 +546,7 @@ TcArgs base_args(Ctx* c, TcState* s) {
   a.alpha = c->alpha;
   a.beta = (float)c->beta;
   a.status = &c->counters[2];
+  a.stall = c->stall_flag;
   return a;
 }
 
@@ -597,7 +607,7 @@ int tc_create(Ctx* c) {
     snprintf(c->err, sizeof(c->err), "tensor-core operator: stage of %d bytes does not fit", s->stage_bytes);
     return 1;
   }
-  s->smem_bytes = s->stages * s->stage_bytes + 1024 + (2 * s->stages + 5) * 8 + 16 + 4 * s->Rpad * 4 + 64;
+  s->smem_bytes = s->stages * s->stage_bytes + 1024 + (2 * s->stages + 6) * 8 + 16 + 4 * s->Rpad * 4 + 64;
 
   const int64_t rows = c->rows_total, Dp = c->Dp, S = c->S, R = c->R;
   auto alloc = [&](__nv_bfloat16** p, int64_t n) {
@@ -664,7 +674,7 @@ int tc_set_stages(Ctx* c, int stages) {
   if (!s) return 0;
   if (stages >= 2 && stages <= tc_max_stages(c)) {
     s->stages = stages;
-    s->smem_bytes = s->stages * s->stage_bytes + 1024 + (2 * s->stages + 5) * 8 + 16 + 4 * s->Rpad * 4 + 64;
+    s->smem_bytes = s->stages * s->stage_bytes + 1024 + (2 * s->stages + 6) * 8 + 16 + 4 * s->Rpad * 4 + 64;
   }
   return s->stages;
 }
