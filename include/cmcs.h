@@ -46,7 +46,7 @@ typedef enum {
   CMCS_ERR_OOM = 3,           /* device allocation failed in cmcs_create                  */
   CMCS_ERR_NUMERIC = 4,       /* NaN or Inf reached an output (e.g. NaN in y)             */
   CMCS_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up                       */
-  CMCS_ERR_UNSUPPORTED = 6    /* a valid request this build does not implement            */
+  CMCS_ERR_UNSUPPORTED = 6    /* a valid request the library does not implement          */
 } cmcs_status;
 
 typedef enum {
