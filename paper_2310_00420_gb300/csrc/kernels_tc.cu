@@ -57,6 +57,7 @@ struct TcArgs {
   unsigned long long* opcount;
   int* status;
   const int* stall;       // test hook: nonzero makes the MMA warp wait on a barrier nothing arrives at
+  uint32_t mn_lbo, mn_sbo; // MN-major A descriptor strides (pass 2 reading Phi directly)
 };
 
 // ---- PTX wrappers ---------------------------------------------------------------------
@@ -129,6 +130,18 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
   d |= (uint64_t)(1024 >> 4) << 32;           // stride byte offset
   d |= (uint64_t)1 << 46;                     // descriptor version
   d |= (uint64_t)2 << 61;                     // 128-byte swizzle
+  return d;
+}
+// shared-memory matrix descriptor: MN-major operand, 128-byte swizzle.  Rows of 128 bytes hold
+// 64 consecutive M (or N) elements for one k; lbo = bytes between 64-element M chunks,
+// sbo = bytes between groups of 8 k rows
+__device__ __forceinline__ uint64_t smem_desc_mn(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
   return d;
 }
 // instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both K-major
@@ -299,8 +312,18 @@ k_tc(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMa
           if (*abort_flag) break;
           uint8_t* st = smem + (size_t)s * p.stage_bytes;
           mbar_expect_tx(&full[s], (uint32_t)p.stage_bytes);
-          tma_load_2d(st, &tA0, ti.kx + kb * kBK, ti.a_row, &full[s]);
-          if (NA == 2) tma_load_2d(st + a_bytes, &tA1, ti.kx + kb * kBK, ti.a_row, &full[s]);
+          if (PASS == 3) {
+            // Phi itself (rows n = kx + kb*64 .., columns d = a_row ..): two 64-column boxes
+            tma_load_2d(st, &tA0, ti.a_row, ti.kx + kb * kBK, &full[s]);
+            tma_load_2d(st + a_bytes / 2, &tA0, ti.a_row + 64, ti.kx + kb * kBK, &full[s]);
+            if (NA == 2) {
+              tma_load_2d(st + a_bytes, &tA1, ti.a_row, ti.kx + kb * kBK, &full[s]);
+              tma_load_2d(st + a_bytes + a_bytes / 2, &tA1, ti.a_row + 64, ti.kx + kb * kBK, &full[s]);
+            }
+          } else {
+            tma_load_2d(st, &tA0, ti.kx + kb * kBK, ti.a_row, &full[s]);
+            if (NA == 2) tma_load_2d(st + a_bytes, &tA1, ti.kx + kb * kBK, ti.a_row, &full[s]);
+          }
           uint8_t* bst = st + NA * a_bytes;
           for (int bx = 0; bx < p.nbox; ++bx) {
             const int brow = ti.b_row + ti.col0 + bx * p.BR;
@@ -314,7 +337,8 @@ k_tc(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMa
   } else if (warp == 1) {
     // ---- MMA issuer
     if (lane == 0) {
-      const uint32_t idesc = idesc_bf16(kBM, p.BR);
+      // PASS 3: A is MN-major (transpose bit 15 of the instruction descriptor)
+      const uint32_t idesc = idesc_bf16(kBM, p.BR) | (PASS == 3 ? (1u << 15) : 0u);
       uint32_t it = 0, lt = 0;
       if (p.stall != nullptr && *p.stall != 0 && !mbar_wait(never, 0)) {
         *abort_flag = 1;               // the bounded wait expired: take the abort path
@@ -344,8 +368,11 @@ k_tc(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMa
           const uint32_t st = smem_u32(smem + (size_t)s * p.stage_bytes);
 #pragma unroll
           for (int kk = 0; kk < kBK / 16; ++kk) {
-            const uint64_t a0 = smem_desc(st + kk * 32);
-            const uint64_t a1 = smem_desc(st + a_bytes + kk * 32);
+            // K-major: the next 16 k are 32 bytes along the swizzled row; MN-major: 16 rows down
+            const uint64_t a0 = PASS == 3 ? smem_desc_mn(st + kk * 2048, p.mn_lbo, p.mn_sbo)
+                                          : smem_desc(st + kk * 32);
+            const uint64_t a1 = PASS == 3 ? smem_desc_mn(st + a_bytes + kk * 2048, p.mn_lbo, p.mn_sbo)
+                                          : smem_desc(st + a_bytes + kk * 32);
             for (int bx = 0; bx < p.nbox; ++bx) {
               const uint32_t bo = st + NA * a_bytes + bx * p.BR * 128 + kk * 32;
               const uint32_t dt = dbase + (uint32_t)(bx * p.BR);
@@ -486,7 +513,9 @@ struct TcState {
   int Rpad, BR, nbox, stages, stage_bytes, smem_bytes, nbuf, ncol;
   uint32_t tmem_cols, tmem_alloc;
   __nv_bfloat16 *phi_hi, *phi_lo, *phit_hi, *phit_lo, *w_hi, *w_lo;
-  CUtensorMap tm_phi[2], tm_phit[2], tm_d[2], tm_w[2];
+  CUtensorMap tm_phi[2], tm_phit[2], tm_d[2], tm_w[2], tm_phimn[2];
+  int mn;                     // pass 2 reads Phi as an MN-major operand (no transposed copy)
+  uint32_t mn_lbo, mn_sbo;
 };
 
 PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
@@ -541,6 +570,8 @@ TcArgs base_args(Ctx* c, TcState* s) {
   a.tmem_alloc = s->tmem_alloc;
   a.nbuf = s->nbuf;
   a.ncol = s->ncol;
+  a.mn_lbo = s->mn_lbo;
+  a.mn_sbo = s->mn_sbo;
   a.w_hi = s->w_hi;
   a.w_lo = s->w_lo;
   a.alpha = c->alpha;
@@ -573,8 +604,12 @@ cudaError_t run_passes(Ctx* c, TcState* s, const float* V, float* Z, int with_do
     a.tile_lo = (c->per_task ? t * ndt : 0) * s->ncol;
     a.ntiles = (c->per_task ? (t + 1) * ndt : c->T * ndt) * s->ncol;
     n = a.ntiles - a.tile_lo;
-    k_tc<2, NA, NB><<<n < sms ? n : sms, kTcThreads, s->smem_bytes, c->stream>>>(
-        s->tm_phit[0], s->tm_phit[NA - 1], s->tm_w[0], s->tm_w[NB - 1], a);
+    if (s->mn)
+      k_tc<3, NA, NB><<<n < sms ? n : sms, kTcThreads, s->smem_bytes, c->stream>>>(
+          s->tm_phimn[0], s->tm_phimn[NA - 1], s->tm_w[0], s->tm_w[NB - 1], a);
+    else
+      k_tc<2, NA, NB><<<n < sms ? n : sms, kTcThreads, s->smem_bytes, c->stream>>>(
+          s->tm_phit[0], s->tm_phit[NA - 1], s->tm_w[0], s->tm_w[NB - 1], a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     c->launches += 2;
@@ -634,6 +669,15 @@ int tc_create(Ctx* c) {
   if (ok && s->NA == 2)
     ok = encode_2d(&s->tm_phi[1], s->phi_lo, Dp, rows, kBM) &&
          encode_2d(&s->tm_phit[1], s->phit_lo, rows, Dp, kBM);
+  if (ok) ok = encode_2d(&s->tm_phimn[0], s->phi_hi, Dp, rows, 64);
+  if (ok && s->NA == 2) ok = encode_2d(&s->tm_phimn[1], s->phi_lo, Dp, rows, 64);
+  {
+    const char* mv = getenv("CMCS_TC_MN");
+    s->mn = mv ? atoi(mv) : 0;
+    s->mn_lbo = s->mn == 2 ? 1024 : 8192;
+    s->mn_sbo = s->mn == 2 ? 8192 : 1024;
+    if (s->mn) s->mn = 1;
+  }
   if (!ok) {
     snprintf(c->err, sizeof(c->err), "tensor-core operator: tensor map encoding failed");
     return 1;
@@ -641,6 +685,8 @@ int tc_create(Ctx* c) {
   cudaError_t e = s->NA == 2 ? set_smem_attr<1, 2, 2>(s->smem_bytes) : set_smem_attr<1, 1, 2>(s->smem_bytes);
   if (e == cudaSuccess)
     e = s->NA == 2 ? set_smem_attr<2, 2, 2>(s->smem_bytes) : set_smem_attr<2, 1, 2>(s->smem_bytes);
+  if (e == cudaSuccess)
+    e = s->NA == 2 ? set_smem_attr<3, 2, 2>(s->smem_bytes) : set_smem_attr<3, 1, 2>(s->smem_bytes);
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) {
     snprintf(c->err, sizeof(c->err), "tensor-core operator set-up: %s", cudaGetErrorString(e));
