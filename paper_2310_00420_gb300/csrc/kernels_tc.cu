@@ -22,6 +22,9 @@
 #include <stdio.h>
 #include <stdlib.h>
 
+#include <new>
+#include <vector>
+
 #include "cmcs_internal.cuh"
 
 namespace cmcs {
@@ -58,6 +61,16 @@ struct TcArgs {
   int* status;
   const int* stall;       // test hook: nonzero makes the MMA warp wait on a barrier nothing arrives at
   uint32_t mn_lbo, mn_sbo; // MN-major A descriptor strides (pass 2 reading Phi directly)
+  const int* tile_code;    // fused launches: per tile (local << 2) | (pass - 1)
+  const int* tile_task2;   // fused launches: task of each tile
+  int* p1done;             // fused launches: finished pass-1 tiles per task (zeroed per launch)
+  const int* n1;           // fused launches: pass-1 tiles per task
+};
+
+// all tensor maps of the operator: a[pass-1][hi/lo] (pass 2 reads Phi MN-major), b[pass-1][hi/lo]
+struct TcMaps {
+  CUtensorMap a[2][2];
+  CUtensorMap b[2][2];
 };
 
 // ---- PTX wrappers ---------------------------------------------------------------------
@@ -180,26 +193,39 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 
 // ---- the GEMM kernel (persistent, two TMEM accumulators) --------------------------------
 struct TileInfo {
+  int pass;                       // 1: W = Phi V;  2: Z = beta Phi^T W + alpha V
   int t, a_row, b_row, kx, nk, dtile, col0;
 };
 
-// tile = row_tile * ncol + column_tile: the column tiles of one row tile run on neighbouring
-// CTAs at the same time, so the second read of the A tile is served by L2
+// Tile decoding.  Single-pass launches (PASS 1, 2 or 3; 3 is pass 2 reading Phi MN-major):
+// tile = row_tile * ncol + column_tile, so the column tiles of one row tile run on
+// neighbouring CTAs at the same time and the second read of the A tile is served by L2.
+// Fused launches (PASS 0): tile_code[tile] = (local << 2) | (pass - 1) with tasks in order,
+// each task's pass-1 tiles before its pass-2 tiles; task = tile_task2[tile].
 template <int PASS>
 __device__ __forceinline__ bool tile_info(const TcArgs& p, int tile_in, TileInfo& ti) {
-  const int tile = tile_in / p.ncol;
-  ti.col0 = (tile_in - tile * p.ncol) * p.Rpad;
-  if (PASS == 1) {
-    ti.t = p.tile_task[tile];
-    ti.a_row = tile * kBM;
+  int pass = PASS == 1 ? 1 : 2, local = tile_in;
+  if (PASS == 0) {
+    const int code = p.tile_code[tile_in];
+    pass = (code & 3) + 1;
+    local = code >> 2;
+  }
+  ti.pass = pass;
+  const int tile = local / p.ncol;
+  ti.col0 = (local - tile * p.ncol) * p.Rpad;
+  if (pass == 1) {
+    // row tiles are numbered within the whole Phi (fused: within the task, offset below)
+    const int g = PASS == 0 ? (int)(p.drow[p.tile_task2[tile_in]] / kBM) + tile : tile;
+    ti.t = p.tile_task[g];
+    ti.a_row = g * kBM;
     ti.b_row = ti.t * p.R;
     ti.kx = 0;
     ti.nk = p.Dp / kBK;
     ti.dtile = 0;
   } else {
     const int ndt = p.Dp / kBM;
-    ti.t = tile / ndt;
-    ti.dtile = tile - ti.t * ndt;
+    ti.t = PASS == 0 ? p.tile_task2[tile_in] : tile / ndt;
+    ti.dtile = PASS == 0 ? tile : tile - ti.t * ndt;
     ti.a_row = ti.dtile * kBM;
     ti.b_row = 0;
     ti.kx = (int)p.drow[ti.t];
@@ -208,10 +234,25 @@ __device__ __forceinline__ bool tile_info(const TcArgs& p, int tile_in, TileInfo
   return p.task_active == nullptr || p.task_active[ti.t] != 0;
 }
 
-// Sum each of 16 per-lane values over the 32 lanes of a warp with 16 shuffles: every step
-// hands half of the remaining values to the partner lane.  The lane with bit 0 clear returns
-// the total of value index ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2
-// + ((lane >> 1) & 1).
+// release / acquire of the per-task count of finished pass-1 tiles (fused launches); W is
+// written with generic stores and read by TMA (async proxy), hence the proxy fences
+__device__ __forceinline__ void signal_pass1_done(int* cnt) {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+  __threadfence();
+  atomicAdd(cnt, 1);
+}
+__device__ __forceinline__ bool wait_pass1_done(const int* cnt, int want) {
+  const volatile int* v = cnt;
+  if (*v < want) {
+    const uint64_t t0 = global_ns();
+    for (uint32_t i = 1; *v < want; ++i)
+      if ((i & 255u) == 0 && global_ns() - t0 > kWaitNs) return false;
+  }
+  __threadfence();
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+  return true;
+}
+
 __device__ __forceinline__ float warp_reduce16(float* v, int lane) {
 #pragma unroll
   for (int w = 8, off = 16; w >= 1; w >>= 1, off >>= 1) {
@@ -253,9 +294,7 @@ __device__ __forceinline__ bool epi_bar_any(bool pred) {
 
 template <int PASS, int NA, int NB>
 __global__ void __launch_bounds__(kTcThreads, 1)
-k_tc(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMap tA1,
-     const __grid_constant__ CUtensorMap tB0, const __grid_constant__ CUtensorMap tB1,
-     const TcArgs p) {
+k_tc(const __grid_constant__ TcMaps maps, const TcArgs p) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~static_cast<uintptr_t>(1023));
@@ -299,37 +338,48 @@ k_tc(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMa
     // ---- TMA producer
     if (lane == 0) {
       uint32_t it = 0;
-      for (int tile = p.tile_lo + blockIdx.x; tile < p.ntiles && !*abort_flag; tile += gridDim.x) {
+      bool stop = false;
+      for (int tile = p.tile_lo + blockIdx.x; tile < p.ntiles && !stop && !*abort_flag;
+           tile += gridDim.x) {
         TileInfo ti;
         if (!tile_info<PASS>(p, tile, ti)) continue;
+        const bool a_mn = PASS == 3 || (PASS == 0 && ti.pass == 2);
+        const int pi = ti.pass - 1;
+        if (PASS == 0 && ti.pass == 2 && !wait_pass1_done(&p.p1done[ti.t], p.n1[ti.t])) {
+          *abort_flag = 1;                 // W of this task never completed
+          atomicOr(p.status, 8);
+          break;
+        }
         for (int kb = 0; kb < ti.nk; ++kb, ++it) {
           const int s = (int)(it % p.stages);
           if (it >= (uint32_t)p.stages && !mbar_wait(&empty[s], ((it / p.stages) - 1) & 1)) {
             *abort_flag = 1;
             atomicOr(p.status, 8);
+            stop = true;
             break;
           }
-          if (*abort_flag) break;
+          if (*abort_flag) {
+            stop = true;
+            break;
+          }
           uint8_t* st = smem + (size_t)s * p.stage_bytes;
           mbar_expect_tx(&full[s], (uint32_t)p.stage_bytes);
-          if (PASS == 3) {
-            // Phi itself (rows n = kx + kb*64 .., columns d = a_row ..): two 64-column boxes
-            tma_load_2d(st, &tA0, ti.a_row, ti.kx + kb * kBK, &full[s]);
-            tma_load_2d(st + a_bytes / 2, &tA0, ti.a_row + 64, ti.kx + kb * kBK, &full[s]);
-            if (NA == 2) {
-              tma_load_2d(st + a_bytes, &tA1, ti.a_row, ti.kx + kb * kBK, &full[s]);
-              tma_load_2d(st + a_bytes + a_bytes / 2, &tA1, ti.a_row + 64, ti.kx + kb * kBK, &full[s]);
+          const int kcol = ti.kx + kb * kBK;
+#pragma unroll
+          for (int h = 0; h < NA; ++h) {
+            uint8_t* ad = st + h * a_bytes;
+            if (a_mn) {
+              // Phi itself (rows n = kcol .., columns d = a_row ..): two 64-column boxes
+              tma_load_2d(ad, &maps.a[1][h], ti.a_row, kcol, &full[s]);
+              tma_load_2d(ad + a_bytes / 2, &maps.a[1][h], ti.a_row + 64, kcol, &full[s]);
+            } else {
+              tma_load_2d(ad, &maps.a[pi][h], kcol, ti.a_row, &full[s]);
             }
-          } else {
-            tma_load_2d(st, &tA0, ti.kx + kb * kBK, ti.a_row, &full[s]);
-            if (NA == 2) tma_load_2d(st + a_bytes, &tA1, ti.kx + kb * kBK, ti.a_row, &full[s]);
           }
           uint8_t* bst = st + NA * a_bytes;
-          for (int bx = 0; bx < p.nbox; ++bx) {
-            const int brow = ti.b_row + ti.col0 + bx * p.BR;
-            tma_load_2d(bst + bx * p.BR * 128, &tB0, ti.kx + kb * kBK, brow, &full[s]);
-            if (NB == 2) tma_load_2d(bst + b_bytes + bx * p.BR * 128, &tB1, ti.kx + kb * kBK, brow, &full[s]);
-          }
+          const int brow = ti.b_row + ti.col0;
+          tma_load_2d(bst, &maps.b[pi][0], kcol, brow, &full[s]);
+          if (NB == 2) tma_load_2d(bst + b_bytes, &maps.b[pi][1], kcol, brow, &full[s]);
           issued = it + 1;
         }
       }
@@ -337,8 +387,8 @@ k_tc(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMa
   } else if (warp == 1) {
     // ---- MMA issuer
     if (lane == 0) {
-      // PASS 3: A is MN-major (transpose bit 15 of the instruction descriptor)
-      const uint32_t idesc = idesc_bf16(kBM, p.BR) | (PASS == 3 ? (1u << 15) : 0u);
+      const uint32_t idesc_k = idesc_bf16(kBM, p.BR);
+      const uint32_t idesc_mn = idesc_k | (1u << 15);      // A transposed (MN-major)
       uint32_t it = 0, lt = 0;
       if (p.stall != nullptr && *p.stall != 0 && !mbar_wait(never, 0)) {
         *abort_flag = 1;               // the bounded wait expired: take the abort path
@@ -347,6 +397,8 @@ k_tc(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMa
       for (int tile = p.tile_lo + blockIdx.x; tile < p.ntiles && !*abort_flag; tile += gridDim.x) {
         TileInfo ti;
         if (!tile_info<PASS>(p, tile, ti)) continue;
+        const bool a_mn = PASS == 3 || (PASS == 0 && ti.pass == 2);
+        const uint32_t idesc = a_mn ? idesc_mn : idesc_k;
         const int b = (int)(lt % p.nbuf);
         if (lt >= (uint32_t)p.nbuf && !mbar_wait(&tempty[b], ((lt / p.nbuf) - 1) & 1)) {
           *abort_flag = 1;
@@ -354,7 +406,7 @@ k_tc(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMa
           break;
         }
         tc_fence_after();
-        const uint32_t dbase = tmem + (uint32_t)b * p.tmem_cols;
+        const uint32_t dt = tmem + (uint32_t)b * p.tmem_cols;
         bool stop = false;
         for (int kb = 0; kb < ti.nk; ++kb, ++it) {
           const int s = (int)(it % p.stages);
@@ -369,17 +421,14 @@ k_tc(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMa
 #pragma unroll
           for (int kk = 0; kk < kBK / 16; ++kk) {
             // K-major: the next 16 k are 32 bytes along the swizzled row; MN-major: 16 rows down
-            const uint64_t a0 = PASS == 3 ? smem_desc_mn(st + kk * 2048, p.mn_lbo, p.mn_sbo)
-                                          : smem_desc(st + kk * 32);
-            const uint64_t a1 = PASS == 3 ? smem_desc_mn(st + a_bytes + kk * 2048, p.mn_lbo, p.mn_sbo)
-                                          : smem_desc(st + a_bytes + kk * 32);
-            for (int bx = 0; bx < p.nbox; ++bx) {
-              const uint32_t bo = st + NA * a_bytes + bx * p.BR * 128 + kk * 32;
-              const uint32_t dt = dbase + (uint32_t)(bx * p.BR);
-              mma_bf16(dt, a0, smem_desc(bo), idesc, (kb > 0 || kk > 0) ? 1u : 0u);
-              if (NB == 2) mma_bf16(dt, a0, smem_desc(bo + b_bytes), idesc, 1u);
-              if (NA == 2) mma_bf16(dt, a1, smem_desc(bo), idesc, 1u);
-            }
+            const uint64_t a0 = a_mn ? smem_desc_mn(st + kk * 2048, p.mn_lbo, p.mn_sbo)
+                                     : smem_desc(st + kk * 32);
+            const uint64_t a1 = a_mn ? smem_desc_mn(st + a_bytes + kk * 2048, p.mn_lbo, p.mn_sbo)
+                                     : smem_desc(st + a_bytes + kk * 32);
+            const uint32_t bo = st + NA * a_bytes + kk * 32;
+            mma_bf16(dt, a0, smem_desc(bo), idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+            if (NB == 2) mma_bf16(dt, a0, smem_desc(bo + b_bytes), idesc, 1u);
+            if (NA == 2) mma_bf16(dt, a1, smem_desc(bo), idesc, 1u);
           }
           mma_commit(&empty[s]);
         }
@@ -407,7 +456,7 @@ k_tc(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMa
       if (epi_bar_any(!ok || *abort_flag)) break;   // uniform across the epilogue warps
       tc_fence_after();
       const uint32_t trow = tmem + (uint32_t)b * p.tmem_cols + ((uint32_t)(32 * lg) << 16);
-      if (PASS == 1) {
+      if (ti.pass == 1) {
         const int64_t n = (int64_t)ti.a_row + 32 * lg + lane;     // global row of Phi
         for (int c0 = 0; c0 < p.Rpad; c0 += 16) {
           float v[16];
@@ -422,6 +471,14 @@ k_tc(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMa
               p.w_lo[(int64_t)j * p.rows_total + n] = lo;
             }
           }
+        }
+        if (PASS == 0) {
+          // publish this tile's part of W for the task's pass-2 tiles
+          tc_fence_before();
+          asm volatile("fence.proxy.async.global;" ::: "memory");
+          __threadfence();
+          epi_bar();
+          if (etid == 0) signal_pass1_done(&p.p1done[ti.t]);
         }
       } else {
         const int d = ti.a_row + 32 * lg + lane;
@@ -514,8 +571,12 @@ struct TcState {
   uint32_t tmem_cols, tmem_alloc;
   __nv_bfloat16 *phi_hi, *phi_lo, *phit_hi, *phit_lo, *w_hi, *w_lo;
   CUtensorMap tm_phi[2], tm_phit[2], tm_d[2], tm_w[2], tm_phimn[2];
-  int mn;                     // pass 2 reads Phi as an MN-major operand (no transposed copy)
+  // 0: both passes fused in one persistent launch, pass 2 reading Phi MN-major (default);
+  // 2: two launches, pass 2 reading a transposed copy of Phi; 3: two launches, MN-major
+  int mode;
   uint32_t mn_lbo, mn_sbo;
+  int *tile_code, *tile_task2, *n1, *p1done;   // fused tile list and its dependency counters
+  std::vector<int> tstart;                     // first fused tile of each task (host)
 };
 
 PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
@@ -589,27 +650,49 @@ cudaError_t run_passes(Ctx* c, TcState* s, const float* V, float* Z, int with_do
   a.V = V;
   a.Z = Z;
   a.part = with_dots ? c->part : nullptr;
+  a.tile_code = s->tile_code;
+  a.tile_task2 = s->tile_task2;
+  a.n1 = s->n1;
+  a.p1done = s->p1done;
   const int sms = c->sm_count > 0 ? c->sm_count : 1;
   const int ndt = c->Dp / kBM;
   const int nloop = c->per_task ? c->T : 1;
+  TcMaps maps;
+  maps.a[0][0] = s->tm_phi[0];
+  maps.a[0][1] = s->tm_phi[NA - 1];
+  maps.a[1][0] = s->mode == 2 ? s->tm_phit[0] : s->tm_phimn[0];
+  maps.a[1][1] = s->mode == 2 ? s->tm_phit[NA - 1] : s->tm_phimn[NA - 1];
+  maps.b[0][0] = s->tm_d[0];
+  maps.b[0][1] = s->tm_d[NB - 1];
+  maps.b[1][0] = s->tm_w[0];
+  maps.b[1][1] = s->tm_w[NB - 1];
   for (int t = 0; t < nloop; ++t) {
-    // all tasks in one persistent launch per pass, or (comparison schedule) one per task
+    // all tasks in one persistent launch, or (comparison schedule) one launch per task
+    if (s->mode == 0) {
+      cudaError_t e = cudaMemsetAsync(s->p1done, 0, sizeof(int) * c->T, c->stream);
+      if (e != cudaSuccess) return e;
+      a.tile_lo = c->per_task ? s->tstart[t] : 0;
+      a.ntiles = c->per_task ? s->tstart[t + 1] : s->tstart[c->T];
+      const int n = a.ntiles - a.tile_lo;
+      k_tc<0, NA, NB><<<n < sms ? n : sms, kTcThreads, s->smem_bytes, c->stream>>>(maps, a);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+      c->launches += 1;
+      continue;
+    }
     a.tile_lo = (c->per_task ? (int)(c->hrow[t] / kBM) : 0) * s->ncol;
     a.ntiles = (c->per_task ? (int)(c->hrow[t + 1] / kBM) : (int)(c->rows_total / kBM)) * s->ncol;
     int n = a.ntiles - a.tile_lo;
-    k_tc<1, NA, NB><<<n < sms ? n : sms, kTcThreads, s->smem_bytes, c->stream>>>(
-        s->tm_phi[0], s->tm_phi[NA - 1], s->tm_d[0], s->tm_d[NB - 1], a);
+    k_tc<1, NA, NB><<<n < sms ? n : sms, kTcThreads, s->smem_bytes, c->stream>>>(maps, a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     a.tile_lo = (c->per_task ? t * ndt : 0) * s->ncol;
     a.ntiles = (c->per_task ? (t + 1) * ndt : c->T * ndt) * s->ncol;
     n = a.ntiles - a.tile_lo;
-    if (s->mn)
-      k_tc<3, NA, NB><<<n < sms ? n : sms, kTcThreads, s->smem_bytes, c->stream>>>(
-          s->tm_phimn[0], s->tm_phimn[NA - 1], s->tm_w[0], s->tm_w[NB - 1], a);
+    if (s->mode == 3)
+      k_tc<3, NA, NB><<<n < sms ? n : sms, kTcThreads, s->smem_bytes, c->stream>>>(maps, a);
     else
-      k_tc<2, NA, NB><<<n < sms ? n : sms, kTcThreads, s->smem_bytes, c->stream>>>(
-          s->tm_phit[0], s->tm_phit[NA - 1], s->tm_w[0], s->tm_w[NB - 1], a);
+      k_tc<2, NA, NB><<<n < sms ? n : sms, kTcThreads, s->smem_bytes, c->stream>>>(maps, a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     c->launches += 2;
@@ -620,7 +703,7 @@ cudaError_t run_passes(Ctx* c, TcState* s, const float* V, float* Z, int with_do
 }  // namespace
 
 int tc_create(Ctx* c) {
-  TcState* s = static_cast<TcState*>(calloc(1, sizeof(TcState)));
+  TcState* s = new (std::nothrow) TcState();
   if (!s) return 1;
   c->tc = s;
   s->NA = c->precision == CMCS_BF16X3 ? 2 : 1;
@@ -648,36 +731,68 @@ int tc_create(Ctx* c) {
   auto alloc = [&](__nv_bfloat16** p, int64_t n) {
     return cudaMalloc(reinterpret_cast<void**>(p), sizeof(__nv_bfloat16) * (size_t)n) == cudaSuccess;
   };
-  bool okm = alloc(&s->phi_hi, rows * Dp) && alloc(&s->phit_hi, rows * Dp) &&
+  {
+    const char* mv = getenv("CMCS_TC_MODE");     // evaluation switch between the schedules
+    s->mode = mv ? atoi(mv) : 0;
+    if (s->mode != 2 && s->mode != 3) s->mode = 0;
+  }
+  s->mn_lbo = 8192;      // 64-column halves of the MN-major A tile are 8 KiB apart
+  s->mn_sbo = 1024;      // groups of 8 k rows are 1 KiB apart
+  bool okm = alloc(&s->phi_hi, rows * Dp) &&
              alloc(reinterpret_cast<__nv_bfloat16**>(&c->dhi), S * Dp) &&
              alloc(reinterpret_cast<__nv_bfloat16**>(&c->dlo), S * Dp) && alloc(&s->w_hi, R * rows) &&
              alloc(&s->w_lo, R * rows);
-  if (okm && s->NA == 2) okm = alloc(&s->phi_lo, rows * Dp) && alloc(&s->phit_lo, rows * Dp);
+  if (okm && s->NA == 2) okm = alloc(&s->phi_lo, rows * Dp);
+  if (okm && s->mode == 2) okm = alloc(&s->phit_hi, rows * Dp) && (s->NA == 1 || alloc(&s->phit_lo, rows * Dp));
+  // fused tile list: for every task its pass-1 tiles, then its pass-2 tiles
+  if (okm) {
+    const int ndt = (int)(Dp / kBM);
+    std::vector<int> code, task2, n1((size_t)c->T);
+    s->tstart.assign((size_t)c->T + 1, 0);
+    for (int t = 0; t < c->T; ++t) {
+      s->tstart[(size_t)t] = (int)code.size();
+      const int nr = (int)(c->hNp[t] / kBM) * s->ncol;
+      n1[(size_t)t] = nr;
+      for (int i = 0; i < nr; ++i) {
+        code.push_back(i << 2);
+        task2.push_back(t);
+      }
+      for (int i = 0; i < ndt * s->ncol; ++i) {
+        code.push_back((i << 2) | 1);
+        task2.push_back(t);
+      }
+    }
+    s->tstart[(size_t)c->T] = (int)code.size();
+    okm = cudaMalloc(reinterpret_cast<void**>(&s->tile_code), sizeof(int) * code.size()) == cudaSuccess &&
+          cudaMalloc(reinterpret_cast<void**>(&s->tile_task2), sizeof(int) * task2.size()) == cudaSuccess &&
+          cudaMalloc(reinterpret_cast<void**>(&s->n1), sizeof(int) * (size_t)c->T) == cudaSuccess &&
+          cudaMalloc(reinterpret_cast<void**>(&s->p1done), sizeof(int) * (size_t)c->T) == cudaSuccess;
+    if (okm) {
+      cudaMemcpyAsync(s->tile_code, code.data(), sizeof(int) * code.size(), cudaMemcpyHostToDevice, c->stream);
+      cudaMemcpyAsync(s->tile_task2, task2.data(), sizeof(int) * task2.size(), cudaMemcpyHostToDevice, c->stream);
+      cudaMemcpyAsync(s->n1, n1.data(), sizeof(int) * (size_t)c->T, cudaMemcpyHostToDevice, c->stream);
+      cudaStreamSynchronize(c->stream);    // the host vectors go out of scope
+    }
+  }
   if (!okm) {
     snprintf(c->err, sizeof(c->err), "tensor-core operator: device allocation failed");
     return 1;
   }
   k_split_bf16<<<4096, 256, 0, c->stream>>>(c->phi, s->phi_hi, s->phi_lo, rows * Dp);
-  k_transpose_split<<<dim3(Dp / 32, (unsigned)(rows / 32)), dim3(32, 8), 0, c->stream>>>(
-      c->phi, s->phit_hi, s->phit_lo, rows, (int)Dp);
+  if (s->mode == 2)
+    k_transpose_split<<<dim3(Dp / 32, (unsigned)(rows / 32)), dim3(32, 8), 0, c->stream>>>(
+        c->phi, s->phit_hi, s->phit_lo, rows, (int)Dp);
   cudaMemsetAsync(c->dhi, 0, sizeof(__nv_bfloat16) * S * Dp, c->stream);
   cudaMemsetAsync(c->dlo, 0, sizeof(__nv_bfloat16) * S * Dp, c->stream);
   bool ok = encode_2d(&s->tm_phi[0], s->phi_hi, Dp, rows, kBM) &&
-            encode_2d(&s->tm_phit[0], s->phit_hi, rows, Dp, kBM) &&
+            (s->mode != 2 || encode_2d(&s->tm_phit[0], s->phit_hi, rows, Dp, kBM)) &&
             encode_2d(&s->tm_d[0], c->dhi, Dp, S, s->BR) && encode_2d(&s->tm_d[1], c->dlo, Dp, S, s->BR) &&
             encode_2d(&s->tm_w[0], s->w_hi, rows, R, s->BR) && encode_2d(&s->tm_w[1], s->w_lo, rows, R, s->BR);
   if (ok && s->NA == 2)
     ok = encode_2d(&s->tm_phi[1], s->phi_lo, Dp, rows, kBM) &&
-         encode_2d(&s->tm_phit[1], s->phit_lo, rows, Dp, kBM);
+         (s->mode != 2 || encode_2d(&s->tm_phit[1], s->phit_lo, rows, Dp, kBM));
   if (ok) ok = encode_2d(&s->tm_phimn[0], s->phi_hi, Dp, rows, 64);
   if (ok && s->NA == 2) ok = encode_2d(&s->tm_phimn[1], s->phi_lo, Dp, rows, 64);
-  {
-    const char* mv = getenv("CMCS_TC_MN");
-    s->mn = mv ? atoi(mv) : 0;
-    s->mn_lbo = s->mn == 2 ? 1024 : 8192;
-    s->mn_sbo = s->mn == 2 ? 8192 : 1024;
-    if (s->mn) s->mn = 1;
-  }
   if (!ok) {
     snprintf(c->err, sizeof(c->err), "tensor-core operator: tensor map encoding failed");
     return 1;
@@ -687,6 +802,8 @@ int tc_create(Ctx* c) {
     e = s->NA == 2 ? set_smem_attr<2, 2, 2>(s->smem_bytes) : set_smem_attr<2, 1, 2>(s->smem_bytes);
   if (e == cudaSuccess)
     e = s->NA == 2 ? set_smem_attr<3, 2, 2>(s->smem_bytes) : set_smem_attr<3, 1, 2>(s->smem_bytes);
+  if (e == cudaSuccess)
+    e = s->NA == 2 ? set_smem_attr<0, 2, 2>(s->smem_bytes) : set_smem_attr<0, 1, 2>(s->smem_bytes);
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) {
     snprintf(c->err, sizeof(c->err), "tensor-core operator set-up: %s", cudaGetErrorString(e));
@@ -699,11 +816,12 @@ int tc_create(Ctx* c) {
 void tc_destroy(Ctx* c) {
   TcState* s = static_cast<TcState*>(c->tc);
   if (!s) return;
-  void* ptrs[] = {s->phi_hi, s->phi_lo, s->phit_hi, s->phit_lo, s->w_hi, s->w_lo, c->dhi, c->dlo};
+  void* ptrs[] = {s->phi_hi, s->phi_lo, s->phit_hi, s->phit_lo, s->w_hi, s->w_lo, c->dhi, c->dlo,
+                  s->tile_code, s->tile_task2, s->n1, s->p1done};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   c->dhi = c->dlo = nullptr;
-  free(s);
+  delete s;
   c->tc = nullptr;
 }
 
@@ -730,8 +848,9 @@ cudaError_t tc_refresh(Ctx* c) {
   if (!s) return cudaSuccess;
   const int64_t rows = c->rows_total, Dp = c->Dp;
   k_split_bf16<<<4096, 256, 0, c->stream>>>(c->phi, s->phi_hi, s->phi_lo, rows * Dp);
-  k_transpose_split<<<dim3(Dp / 32, (unsigned)(rows / 32)), dim3(32, 8), 0, c->stream>>>(
-      c->phi, s->phit_hi, s->phit_lo, rows, (int)Dp);
+  if (s->mode == 2)
+    k_transpose_split<<<dim3(Dp / 32, (unsigned)(rows / 32)), dim3(32, 8), 0, c->stream>>>(
+        c->phi, s->phit_hi, s->phit_lo, rows, (int)Dp);
   c->launches += 2;
   return cudaGetLastError();
 }

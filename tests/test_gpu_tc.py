@@ -96,3 +96,22 @@ def test_tc_estep_parity(small, precision, tol):
     q_rep, _, _ = replay_q(small, g, o, alpha)
     assert np.max(np.abs(g["q"] - q_rep)) <= 1e-4
     assert np.array_equal(g["assign"], np.argmax(o["q"], axis=1))
+
+
+@pytest.mark.parametrize("precision", ["bf16x3", "bf16"])
+def test_operator_schedules_agree(precision, monkeypatch):
+    """The fused launch (pass 1 and pass 2 of every task in one persistent kernel, pass 2 reading
+    Phi MN-major), the two-launch MN-major schedule and the two-launch schedule over a transposed
+    copy of Phi accumulate the same products in the same k order."""
+    wl = synth.make_workload("ragged", 3, 3, 200, (37, 300), nnz=5, sigma=0.01, K=70, seed=9)
+    R = wl.C * (wl.K + 1)
+    V = np.random.default_rng(23).standard_normal((wl.T, R, wl.D)).astype(np.float32)
+    Z = {}
+    for mode in ("0", "3", "2"):
+        monkeypatch.setenv("CMCS_TC_MODE", mode)
+        with make_ctx(wl, precision=precision) as ctx:
+            Z[mode] = ctx.apply(V)
+            Z[mode + "again"] = ctx.apply(V)
+    assert np.array_equal(Z["0"], Z["0again"])
+    assert np.array_equal(Z["0"], Z["3"])
+    np.testing.assert_allclose(Z["2"], Z["0"], rtol=1e-5, atol=1e-5 * np.abs(Z["0"]).max())
