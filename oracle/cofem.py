@@ -263,6 +263,41 @@ def exact_estep(Phi_list, y_list, alpha: np.ndarray, pi: np.ndarray, beta: float
                 loglik=log_likelihood(ell_tc, pi, consts))
 
 
+def solve_exact(Phi_t: np.ndarray, beta: float, alpha_c: np.ndarray, B: np.ndarray,
+                G: np.ndarray = None) -> np.ndarray:
+    """Sigma B with Sigma = (beta Phi_t^T Phi_t + diag alpha_c)^-1 (Eq. 3), by Cholesky: the
+    exact solutions of the systems A mu = b0 and A x_k = p_k (Eq. 7) that Alg. 1 and its
+    refinement approximate.  B is [D] or [D, m]; G = beta Phi_t^T Phi_t may be passed in to
+    share it across clusters."""
+    P = np.asarray(Phi_t, dtype=np.float64)
+    if G is None:
+        G = beta * (P.T @ P)
+    A = G + np.diag(np.asarray(alpha_c, dtype=np.float64))
+    L = np.linalg.cholesky(A)
+    w = solve_triangular(L, np.asarray(B, dtype=np.float64), lower=True)
+    return solve_triangular(L.T, w, lower=False)
+
+
+def mean_adjoint(Phi_t: np.ndarray, y_t: np.ndarray, beta: float, alpha_c: np.ndarray,
+                 g: np.ndarray, G: np.ndarray = None) -> dict:
+    """Reverse-mode derivative of the posterior mean mu = Sigma beta Phi_t^T y_t (Eq. 3) for a
+    loss L with dL/dmu = g.  With A = Sigma^-1 = beta Phi^T Phi + diag alpha and
+    b = beta Phi^T y, differentiating A mu = b gives d mu = Sigma (db - dA mu), so
+    dL = lam^T (db - dA mu) with lam = Sigma g (Sigma is symmetric).  Expanding db and dA:
+        dL/dy     = beta Phi lam
+        dL/dalpha = -lam * mu
+        dL/dPhi   = beta (y lam^T - (Phi mu) lam^T - (Phi lam) mu^T)."""
+    P = np.asarray(Phi_t, dtype=np.float64)
+    y = np.asarray(y_t, dtype=np.float64)
+    if G is None:
+        G = beta * (P.T @ P)
+    mu = solve_exact(P, beta, alpha_c, rhs_mean(P, y, beta), G)
+    lam = solve_exact(P, beta, alpha_c, np.asarray(g, dtype=np.float64), G)
+    Pmu, Plam = P @ mu, P @ lam
+    return dict(mu=mu, lam=lam, dy=beta * Plam, dalpha=-lam * mu,
+                dPhi=beta * (np.outer(y, lam) - np.outer(Pmu, lam) - np.outer(Plam, mu)))
+
+
 def cofem_estep(Phi_list, y_list, alpha: np.ndarray, pi: np.ndarray, beta: float, K: int,
                 seed: int, em_iter: int, tol: float, max_iter: int, probe_fn=None,
                 steps: np.ndarray = None, tasks=None, refine_tol: float = None,
