@@ -257,7 +257,7 @@ def run_ours(a):
         t_flop = prof["operator_flops"] / (pk_t * 1e12)
         t_byte = prof["operator_bytes"] / (pk_b * 1e9)
         per = max(1, prof["operator_calls"])
-        common = {"kernel": "operator (k_tc<1> + k_tc<2>, tcgen05 BF16 split)",
+        common = {"kernel": "operator (k_tc<1> + k_tc<3>, tcgen05 BF16 split; pass 2 reads Phi MN-major)",
                   "per_launch_flops": prof["operator_flops"] / per,
                   "per_launch_bytes": prof["operator_bytes"] / per,
                   "per_launch_ms": prof["operator_ms"] / per, "traffic": None,

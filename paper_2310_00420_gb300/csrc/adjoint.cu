@@ -10,19 +10,25 @@
 
 namespace cmcs {
 
-// dy[orow_t + n] = beta sum_c Wl[t][c][n]; Wl in the pass-1 layout with C columns per task
-__global__ void k_adj_dy(const float* __restrict__ Wl, const int* __restrict__ tile_task,
-                         const int64_t* __restrict__ drow, const int64_t* __restrict__ dN,
-                         const int64_t* __restrict__ orow, float* dy, int64_t rows, int C,
-                         float beta) {
+// dy[orow_t + n] = beta sum_c Phi_t lambda_tc [n], with Phi lambda as a compensated pair
+// (Wl + Wl_lo) in the pass-1 layout with C columns per task.  lambda = A^-1 g has large
+// components in the null space of Phi_t, which Phi_t cancels: a plain FP32 product would keep
+// few correct digits of the (much smaller) result, so both parts are summed in FP64.
+__global__ void k_adj_dy(const float* __restrict__ Wl, const float* __restrict__ Wl_lo,
+                         const int* __restrict__ tile_task, const int64_t* __restrict__ drow,
+                         const int64_t* __restrict__ dN, const int64_t* __restrict__ orow, float* dy,
+                         int64_t rows, int C, double beta) {
   const int64_t row = (int64_t)blockIdx.x * 256 + threadIdx.x;
   if (row >= rows) return;
   const int t = tile_task[row / 128];
   const int64_t rbeg = drow[t], Np = drow[t + 1] - rbeg, n = row - rbeg;
   if (n >= dN[t]) return;
-  float acc = 0.f;
-  for (int c = 0; c < C; ++c) acc += Wl[rbeg * C + (int64_t)c * Np + n];
-  dy[orow[t] + n] = beta * acc;
+  double acc = 0.0;
+  for (int c = 0; c < C; ++c) {
+    const int64_t i = rbeg * C + (int64_t)c * Np + n;
+    acc += (double)Wl[i] + (double)Wl_lo[i];
+  }
+  dy[orow[t] + n] = (float)(beta * acc);
 }
 
 // dalpha[c][d] = - sum_t lambda_tc[d] mu_tc[d]
@@ -40,8 +46,11 @@ __global__ void k_adj_dalpha(const float* __restrict__ lam, const float* __restr
 }
 
 // dPhi rows of tasks t0..t1-1 in the caller's unpadded layout, row index shifted by out_base
+// The row terms y_n - (Phi mu)_n and (Phi lambda)_n come from compensated pairs and are
+// rounded to FP32 once, after the cancellation.
 __global__ void k_adj_dphi(const float* __restrict__ lam, const float* __restrict__ mu,
-                           const float* __restrict__ Wl, const float* __restrict__ Wm,
+                           const float* __restrict__ Wl, const float* __restrict__ Wl_lo,
+                           const float* __restrict__ Wm, const float* __restrict__ Wm_lo,
                            const float* __restrict__ y, const int* __restrict__ tile_task,
                            const int64_t* __restrict__ drow, const int64_t* __restrict__ dN,
                            const int64_t* __restrict__ orow, float* out, int64_t row_lo,
@@ -55,21 +64,22 @@ __global__ void k_adj_dphi(const float* __restrict__ lam, const float* __restric
     const float yn = y[row];
     float acc = 0.f;
     for (int c = 0; c < C; ++c) {
-      const float wm = Wm[rbeg * C + (int64_t)c * Np + n];
-      const float wl = Wl[rbeg * C + (int64_t)c * Np + n];
+      const int64_t i = rbeg * C + (int64_t)c * Np + n;
+      const float res = (float)(((double)yn - (double)Wm[i]) - (double)Wm_lo[i]);
+      const float wl = (float)((double)Wl[i] + (double)Wl_lo[i]);
       const float l = lam[((int64_t)t * C + c) * Dp + d];
       const float m = mu[((int64_t)t * R + (int64_t)c * (K + 1)) * Dp + d];
-      acc = fmaf(yn - wm, l, acc);
+      acc = fmaf(res, l, acc);
       acc = fmaf(-wl, m, acc);
     }
     out[(orow[t] + n - out_base) * D + d] = beta * acc;
   }
 }
 
-cudaError_t launch_adj_dy(Ctx* c, const float* Wl, float* dy) {
+cudaError_t launch_adj_dy(Ctx* c, const float* Wl, const float* Wl_lo, float* dy) {
   c->launches += 1;
   k_adj_dy<<<(unsigned)((c->rows_total + 255) / 256), 256, 0, c->stream>>>(
-      Wl, c->tile_task, c->drow, c->dN, c->dorow, dy, c->rows_total, c->C, (float)c->beta);
+      Wl, Wl_lo, c->tile_task, c->drow, c->dN, c->dorow, dy, c->rows_total, c->C, c->beta);
   return cudaGetLastError();
 }
 
@@ -81,13 +91,15 @@ cudaError_t launch_adj_dalpha(Ctx* c, const float* lam, float* dalpha) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_adj_dphi(Ctx* c, const float* lam, const float* Wl, const float* Wm, float* out,
-                            int t0, int t1, int64_t out_row_base) {
+cudaError_t launch_adj_dphi(Ctx* c, const float* lam, const float* Wl, const float* Wl_lo,
+                            const float* Wm, const float* Wm_lo, float* out, int64_t lo,
+                            int64_t hi, int64_t out_row_base) {
   c->launches += 1;
-  const int64_t lo = c->hrow[t0], hi = c->hrow[t1];
   const int64_t nrows = hi - lo;
+  if (nrows <= 0) return cudaSuccess;
   dim3 grid((c->D + 255) / 256, (unsigned)(nrows < 65535 ? nrows : 65535));
-  k_adj_dphi<<<grid, 256, 0, c->stream>>>(lam, c->xacc, Wl, Wm, c->y, c->tile_task, c->drow, c->dN,
+  k_adj_dphi<<<grid, 256, 0, c->stream>>>(lam, c->xacc, Wl, Wl_lo, Wm, Wm_lo, c->y, c->tile_task,
+                                          c->drow, c->dN,
                                           c->dorow, out, lo, hi, out_row_base, c->C, c->R, c->K,
                                           c->Dp, c->D, (float)c->beta);
   return cudaGetLastError();

@@ -54,7 +54,7 @@ void free_ctx(Ctx* c) {
                   c->ractive, c->sweeps, c->rrel, c->rres, c->task_active, c->counters, c->gam, c->xi,
                   c->psteps, c->sest, c->quad, c->logdet, c->ell, c->q, c->assign, c->stats,
                   c->dN, c->opcount, c->dorow, c->stall_flag, c->adj_g, c->adj_x, c->adj_wl, c->adj_wm,
-                  c->adj_dy, c->adj_da};
+                  c->adj_wl_lo, c->adj_wm_lo, c->adj_dy, c->adj_da};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->prof_ev) {
@@ -514,6 +514,8 @@ cmcs_status cmcs_create(const cmcs_config* cfg, const float* Phi, const float* y
   CKC(dalloc(&c->adj_x, (size_t)(T * C * Dp)));
   CKC(dalloc(&c->adj_wl, (size_t)(C * c->rows_total)));
   CKC(dalloc(&c->adj_wm, (size_t)(C * c->rows_total)));
+  CKC(dalloc(&c->adj_wl_lo, (size_t)(C * c->rows_total)));
+  CKC(dalloc(&c->adj_wm_lo, (size_t)(C * c->rows_total)));
   CKC(dalloc(&c->adj_dy, (size_t)c->hrow[c->T]));
   CKC(dalloc(&c->adj_da, (size_t)(C * Dp)));
   CKC(cudaMemsetAsync(c->opcount, 0, sizeof(int64_t) * T, c->stream));
@@ -708,9 +710,10 @@ cmcs_status cmcs_adjoint(cmcs_ctx* h, const float* g, float* dy, float* dalpha, 
   s = refine_sweeps(&a, c->adj_g);
   if (s != CMCS_OK) return s;
   // gradients
-  CK(launch_phi_v(&a, c->adj_x, c->adj_wl, (int)C, 1));             // Phi lambda
-  CK(launch_phi_v(c, c->xacc, c->adj_wm, (int)C, c->K + 1));         // Phi mu
-  CK(launch_adj_dy(c, c->adj_wl, c->adj_dy));
+  // Phi lambda and Phi mu as compensated pairs (see k_adj_dy)
+  CK(launch_phi_v(&a, c->adj_x, c->adj_wl, c->adj_wl_lo, (int)C, 1));
+  CK(launch_phi_v(c, c->xacc, c->adj_wm, c->adj_wm_lo, (int)C, c->K + 1));
+  CK(launch_adj_dy(c, c->adj_wl, c->adj_wl_lo, c->adj_dy));
   CK(launch_adj_dalpha(c, c->adj_x, c->adj_da));
   const cudaMemcpyKind kout = kind_out(on_device);
   CK(cudaMemcpyAsync(dy, c->adj_dy, sizeof(float) * c->horow[c->T], kout, c->stream));
@@ -718,16 +721,19 @@ cmcs_status cmcs_adjoint(cmcs_ctx* h, const float* g, float* dy, float* dalpha, 
                        C, kout, c->stream));
   if (dPhi != nullptr) {
     if (on_device) {
-      CK(launch_adj_dphi(c, c->adj_x, c->adj_wl, c->adj_wm, dPhi, 0, c->T, 0));
+      CK(launch_adj_dphi(c, c->adj_x, c->adj_wl, c->adj_wl_lo, c->adj_wm, c->adj_wm_lo, dPhi, 0,
+                         c->rows_total, 0));
     } else {
-      for (int t = 0; t < c->T; ++t) {          // stage one task at a time in the work buffer ad
-        if ((size_t)c->hN[t] * D > (size_t)c->S * Dp) {
-          set_err(c, "cmcs_adjoint: host dPhi staging does not fit; pass device memory");
-          return CMCS_ERR_UNSUPPORTED;
+      // stage row blocks in the work buffer ad (S * Dp floats) and copy each out
+      const int64_t m = (int64_t)(((size_t)c->S * Dp) / D);
+      for (int t = 0; t < c->T; ++t) {
+        for (int64_t i = 0; i < c->hN[t]; i += m) {
+          const int64_t nr = c->hN[t] - i < m ? c->hN[t] - i : m;
+          CK(launch_adj_dphi(c, c->adj_x, c->adj_wl, c->adj_wl_lo, c->adj_wm, c->adj_wm_lo, c->ad,
+                             c->hrow[t] + i, c->hrow[t] + i + nr, c->horow[t] + i));
+          CK(cudaMemcpyAsync(dPhi + (c->horow[t] + i) * D, c->ad, sizeof(float) * nr * D,
+                             cudaMemcpyDeviceToHost, c->stream));
         }
-        CK(launch_adj_dphi(c, c->adj_x, c->adj_wl, c->adj_wm, c->ad, t, t + 1, c->horow[t]));
-        CK(cudaMemcpyAsync(dPhi + c->horow[t] * D, c->ad, sizeof(float) * c->hN[t] * D,
-                           cudaMemcpyDeviceToHost, c->stream));
       }
     }
   }

@@ -100,7 +100,7 @@ struct Ctx {
   int64_t* horow;    // host copy
   // adjoint work buffers: right-hand side and solution [T*C][Dp], Phi lambda and Phi mu
   // [C * rows_total], dy [sum N_t], dalpha [C][Dp]
-  float *adj_g, *adj_x, *adj_wl, *adj_wm, *adj_dy, *adj_da;
+  float *adj_g, *adj_x, *adj_wl, *adj_wm, *adj_wl_lo, *adj_wm_lo, *adj_dy, *adj_da;
   int* tile_task;    // [rows_total / 128] task owning each 128-row tile of phi
   int tn_plain, tn_ds; // operator tile widths (0: chosen from R)
   int per_task;        // 1: launch the operator once per task (comparison schedule)
@@ -171,12 +171,16 @@ cudaError_t launch_residual(Ctx* c, const float* X, const float* Bext, float* Ro
                             int all_systems = 0, int means_only = 0);
 cudaError_t launch_resid_norm(Ctx* c);
 // W[t][j'][n] = (Phi_t V_{t, j' * jstride})[n] for j' < Rc (FP32 SIMT pass 1 only)
-cudaError_t launch_phi_v(Ctx* c, const float* V, float* W, int Rc, int jstride);
+// W = Phi V for Rc columns (systems j = j' * jstride); with Wlo, as a compensated pair W + Wlo
+cudaError_t launch_phi_v(Ctx* c, const float* V, float* W, float* Wlo, int Rc, int jstride);
 // adjoint gradients (adjoint.cu)
-cudaError_t launch_adj_dy(Ctx* c, const float* Wl, float* dy);
+cudaError_t launch_adj_dy(Ctx* c, const float* Wl, const float* Wl_lo, float* dy);
 cudaError_t launch_adj_dalpha(Ctx* c, const float* lam, float* dalpha);
-cudaError_t launch_adj_dphi(Ctx* c, const float* lam, const float* Wl, const float* Wm, float* out,
-                            int t0, int t1, int64_t out_row_base);
+// dPhi for the padded rows [row_lo, row_hi) of the packed Phi, written to out at the caller's
+// unpadded row index minus out_base
+cudaError_t launch_adj_dphi(Ctx* c, const float* lam, const float* Wl, const float* Wl_lo,
+                            const float* Wm, const float* Wm_lo, float* out, int64_t row_lo,
+                            int64_t row_hi, int64_t out_base);
 // E-step tail and M-step (kernels_estep.cu)
 cudaError_t launch_quadrature(const float* gam, const float* xi, const int* steps, int nsys,
                               int ld, double* out, int* status, cudaStream_t st);

@@ -454,8 +454,9 @@ cudaError_t launch_operator(Ctx* c, const float* V, float* Z, int with_dots) {
   return pass2<false>(c, tn, a);
 }
 
-cudaError_t launch_phi_v(Ctx* c, const float* V, float* W, int Rc, int jstride) {
+cudaError_t launch_phi_v(Ctx* c, const float* V, float* W, float* Wlo, int Rc, int jstride) {
   c->launches += 1;
+  if (Wlo != nullptr) return pass1<true>(c, pick_tn(Rc, 4), V, W, Wlo, nullptr, Rc, jstride);
   return pass1<false>(c, pick_tn(Rc, 9), V, W, nullptr, nullptr, Rc, jstride);
 }
 

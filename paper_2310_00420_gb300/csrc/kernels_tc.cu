@@ -372,14 +372,22 @@ k_tc(const __grid_constant__ TcMaps maps, const TcArgs p) {
               // Phi itself (rows n = kcol .., columns d = a_row ..): two 64-column boxes
               tma_load_2d(ad, &maps.a[1][h], ti.a_row, kcol, &full[s]);
               tma_load_2d(ad + a_bytes / 2, &maps.a[1][h], ti.a_row + 64, kcol, &full[s]);
+            } else if (PASS == 2 || (PASS == 0 && pi == 1)) {
+              tma_load_2d(ad, &maps.a[1][h], kcol, ti.a_row, &full[s]);
             } else {
-              tma_load_2d(ad, &maps.a[pi][h], kcol, ti.a_row, &full[s]);
+              tma_load_2d(ad, &maps.a[0][h], kcol, ti.a_row, &full[s]);
             }
           }
+          // constant indices into the parameter block keep the maps in parameter space
           uint8_t* bst = st + NA * a_bytes;
           const int brow = ti.b_row + ti.col0;
-          tma_load_2d(bst, &maps.b[pi][0], kcol, brow, &full[s]);
-          if (NB == 2) tma_load_2d(bst + b_bytes, &maps.b[pi][1], kcol, brow, &full[s]);
+          if (pi == 0) {
+            tma_load_2d(bst, &maps.b[0][0], kcol, brow, &full[s]);
+            if (NB == 2) tma_load_2d(bst + b_bytes, &maps.b[0][1], kcol, brow, &full[s]);
+          } else {
+            tma_load_2d(bst, &maps.b[1][0], kcol, brow, &full[s]);
+            if (NB == 2) tma_load_2d(bst + b_bytes, &maps.b[1][1], kcol, brow, &full[s]);
+          }
           issued = it + 1;
         }
       }
@@ -571,8 +579,9 @@ struct TcState {
   uint32_t tmem_cols, tmem_alloc;
   __nv_bfloat16 *phi_hi, *phi_lo, *phit_hi, *phit_lo, *w_hi, *w_lo;
   CUtensorMap tm_phi[2], tm_phit[2], tm_d[2], tm_w[2], tm_phimn[2];
-  // 0: both passes fused in one persistent launch, pass 2 reading Phi MN-major (default);
-  // 2: two launches, pass 2 reading a transposed copy of Phi; 3: two launches, MN-major
+  // 3 (default): two persistent launches, pass 2 reading Phi itself as an MN-major operand;
+  // 2: two launches, pass 2 reading a transposed copy of Phi (twice the device memory);
+  // 0: both passes of every task in one launch, pass-2 tiles waiting on per-task counters
   int mode;
   uint32_t mn_lbo, mn_sbo;
   int *tile_code, *tile_task2, *n1, *p1done;   // fused tile list and its dependency counters
@@ -733,8 +742,8 @@ int tc_create(Ctx* c) {
   };
   {
     const char* mv = getenv("CMCS_TC_MODE");     // evaluation switch between the schedules
-    s->mode = mv ? atoi(mv) : 0;
-    if (s->mode != 2 && s->mode != 3) s->mode = 0;
+    s->mode = mv ? atoi(mv) : 3;
+    if (s->mode != 0 && s->mode != 2) s->mode = 3;
   }
   s->mn_lbo = 8192;      // 64-column halves of the MN-major A tile are 8 KiB apart
   s->mn_sbo = 1024;      // groups of 8 k rows are 1 KiB apart
@@ -744,23 +753,34 @@ int tc_create(Ctx* c) {
              alloc(&s->w_lo, R * rows);
   if (okm && s->NA == 2) okm = alloc(&s->phi_lo, rows * Dp);
   if (okm && s->mode == 2) okm = alloc(&s->phit_hi, rows * Dp) && (s->NA == 1 || alloc(&s->phit_lo, rows * Dp));
-  // fused tile list: for every task its pass-1 tiles, then its pass-2 tiles
+  // fused tile list.  The pass-1 tiles of task t + L go ahead of the pass-2 tiles of task t
+  // (lookahead L; every pass-2 tile comes after all pass-1 tiles of its task, so a CTA only
+  // ever waits on tiles earlier in the list).  L >= T - 1 puts all pass-1 tiles first: pass-2
+  // tiles of finished tasks then fill the last, partial wave of pass 1.
   if (okm) {
     const int ndt = (int)(Dp / kBM);
+    const char* lv = getenv("CMCS_TC_LOOKAHEAD");
+    int L = lv ? atoi(lv) : c->T;
+    if (L < 0) L = 0;
+    if (c->per_task) L = 0;     // one launch per task: its pass-1 tiles, then its pass-2 tiles
     std::vector<int> code, task2, n1((size_t)c->T);
     s->tstart.assign((size_t)c->T + 1, 0);
-    for (int t = 0; t < c->T; ++t) {
-      s->tstart[(size_t)t] = (int)code.size();
+    auto emit1 = [&](int t) {
+      s->tstart[(size_t)t] = (int)code.size();     // per-task launches: P1(t), P2(t) contiguous
       const int nr = (int)(c->hNp[t] / kBM) * s->ncol;
       n1[(size_t)t] = nr;
       for (int i = 0; i < nr; ++i) {
         code.push_back(i << 2);
         task2.push_back(t);
       }
+    };
+    for (int t = 0; t <= L && t < c->T; ++t) emit1(t);
+    for (int t = 0; t < c->T; ++t) {
       for (int i = 0; i < ndt * s->ncol; ++i) {
         code.push_back((i << 2) | 1);
         task2.push_back(t);
       }
+      if (t + L + 1 < c->T) emit1(t + L + 1);
     }
     s->tstart[(size_t)c->T] = (int)code.size();
     okm = cudaMalloc(reinterpret_cast<void**>(&s->tile_code), sizeof(int) * code.size()) == cudaSuccess &&
