@@ -3,8 +3,10 @@
 //
 // One CTA of 256 threads owns one system for the vector updates, so both inner products of a
 // CG step (d^T A d and r^T r) reduce inside the CTA: no grid-wide barrier or spin-wait exists.
-// d^T A d arrives as per-tile partials from the operator epilogue and is summed in a fixed
-// order; every reduction has a fixed tree order, so results are run-to-run deterministic.
+// With the SIMT operator d^T A d arrives as per-tile partials from the operator epilogue; with
+// the tensor-core operator the update kernel adds alpha_c * d to beta Phi^T Phi d and forms
+// d^T A d itself.  Every reduction has a fixed tree order, so results are run-to-run
+// deterministic.
 // Converged systems are masked (their CTA returns at once) and a task whose systems have all
 // converged is skipped by the operator.
 #include <cuda_bf16.h>
@@ -116,27 +118,69 @@ k_cg_init(int mode, float* __restrict__ x, float* __restrict__ r, float* __restr
 // ---- one CG step after the operator has produced ad = A d (Alg. 1, loop body) ----------
 // NV > 0: each thread keeps its NV float4s of r_{u+1} and d_u in registers between the two
 // phases (D_pad <= 1024 NV); NV = 0: generic loop that re-reads them.
-template <int NV>
+// RAW = false: ad = A d and d^T A d arrives as per-tile partials from the operator epilogue.
+// RAW = true (tensor-core operator): ad = beta Phi^T Phi d only; this kernel adds alpha_c * d
+// and forms d^T A d itself, so the operator's epilogue reads neither d nor alpha.
+template <int NV, bool RAW>
 __global__ void __launch_bounds__(256)
 k_cg_update(float* __restrict__ x, float* __restrict__ r, float* __restrict__ d,
-            const float* __restrict__ ad, const float* __restrict__ part, int ndt, float* rr,
-            const float* bb, int* steps, int* active, int* task_active, int* counters,
-            float* gam, float* xih, int* psteps, int record, int R, int K, int C, int Dp, int S,
-            int U, float tol2, __nv_bfloat16* dhi, __nv_bfloat16* dlo) {
+            const float* __restrict__ ad, const float* __restrict__ part,
+            const float* __restrict__ alpha, int ndt, float* rr, const float* bb, int* steps,
+            int* active, int* task_active, int* counters, float* gam, float* xih, int* psteps,
+            int record, int R, int K, int C, int Dp, int S, int U, float tol2,
+            __nv_bfloat16* dhi, __nv_bfloat16* dlo) {
   __shared__ float sh[33];
   __shared__ float s_dad;
   const int64_t sys = blockIdx.x;
   if (active[sys] == 0) return;
   const int t = (int)(sys / R), j = (int)(sys % R);
-  if (threadIdx.x < 32) {
-    float v = 0.f;
-    for (int q = threadIdx.x; q < ndt; q += 32) v += part[(int64_t)q * S + sys];
+  float* xs = x + sys * Dp;
+  float* rs = r + sys * Dp;
+  float* ds = d + sys * Dp;
+  const float* as = ad + sys * Dp;
+  const float* al = alpha + (int64_t)(j / (K + 1)) * Dp;
+  float4 dk[NV > 0 ? NV : 1], ak[(RAW && NV > 0) ? NV : 1];
+  // A d for four coordinates (RAW: beta Phi^T Phi d + alpha_c * d)
+  auto adv = [&](int i, float4 dv) {
+    float4 av = *reinterpret_cast<const float4*>(as + i);
+    if constexpr (RAW) {
+      const float4 a4 = *reinterpret_cast<const float4*>(al + i);
+      av.x = fmaf(a4.x, dv.x, av.x); av.y = fmaf(a4.y, dv.y, av.y);
+      av.z = fmaf(a4.z, dv.z, av.z); av.w = fmaf(a4.w, dv.w, av.w);
+    }
+    return av;
+  };
+  float dad;
+  if constexpr (RAW) {
+    float a2 = 0.f;
+    auto pre = [&](int i, float4& dout, float4& aout) {
+      dout = *reinterpret_cast<const float4*>(ds + i);
+      aout = adv(i, dout);
+      a2 = fmaf(dout.x, aout.x, a2); a2 = fmaf(dout.y, aout.y, a2);
+      a2 = fmaf(dout.z, aout.z, a2); a2 = fmaf(dout.w, aout.w, a2);
+    };
+    if constexpr (NV > 0) {
 #pragma unroll
-    for (int m = 16; m > 0; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
-    if (threadIdx.x == 0) s_dad = v;
+      for (int q = 0; q < NV; ++q) {
+        const int i = (threadIdx.x + 256 * q) * 4;
+        if (i < Dp) pre(i, dk[q], ak[q]);
+      }
+    } else {
+      float4 d0, a0;
+      for (int i = threadIdx.x * 4; i < Dp; i += 256 * 4) pre(i, d0, a0);
+    }
+    dad = block_sum(a2, sh);                       // d_u^T A d_u
+  } else {
+    if (threadIdx.x < 32) {
+      float v = 0.f;
+      for (int q = threadIdx.x; q < ndt; q += 32) v += part[(int64_t)q * S + sys];
+#pragma unroll
+      for (int m = 16; m > 0; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
+      if (threadIdx.x == 0) s_dad = v;
+    }
+    __syncthreads();
+    dad = s_dad;
   }
-  __syncthreads();
-  const float dad = s_dad;
   const float rr0 = rr[sys];
   if (!(dad > 0.f) || !isfinite(dad)) {            // breakdown: stop this system
     if (threadIdx.x == 0) {
@@ -148,17 +192,19 @@ k_cg_update(float* __restrict__ x, float* __restrict__ r, float* __restrict__ d,
     return;
   }
   const float g = rr0 / dad;                       // gamma_u
-  float* xs = x + sys * Dp;
-  float* rs = r + sys * Dp;
-  float* ds = d + sys * Dp;
-  const float* as = ad + sys * Dp;
   float acc = 0.f;
-  float4 rk[NV > 0 ? NV : 1], dk[NV > 0 ? NV : 1];
-  auto step1 = [&](int i, float4& ro, float4& dout) {
+  float4 rk[NV > 0 ? NV : 1];
+  auto step1 = [&](int i, int q, float4& ro, float4& dout) {
     float4 xv = *reinterpret_cast<float4*>(xs + i);
     float4 rv = *reinterpret_cast<float4*>(rs + i);
-    const float4 dv = *reinterpret_cast<const float4*>(ds + i);
-    const float4 av = *reinterpret_cast<const float4*>(as + i);
+    float4 dv, av;
+    if constexpr (RAW && NV > 0) {
+      dv = dk[q];
+      av = ak[q];
+    } else {
+      dv = *reinterpret_cast<const float4*>(ds + i);
+      av = adv(i, dv);
+    }
     xv.x = fmaf(g, dv.x, xv.x); xv.y = fmaf(g, dv.y, xv.y);
     xv.z = fmaf(g, dv.z, xv.z); xv.w = fmaf(g, dv.w, xv.w);
     rv.x = fmaf(-g, av.x, rv.x); rv.y = fmaf(-g, av.y, rv.y);
@@ -176,10 +222,10 @@ k_cg_update(float* __restrict__ x, float* __restrict__ r, float* __restrict__ d,
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
       const int i = (threadIdx.x + 256 * q) * 4;
-      if (i < Dp) step1(i, rk[q], dk[q]);
+      if (i < Dp) step1(i, q, rk[q], dk[q]);
     }
   } else {
-    for (int i = threadIdx.x * 4; i < Dp; i += 256 * 4) step1(i, rk[0], dk[0]);
+    for (int i = threadIdx.x * 4; i < Dp; i += 256 * 4) step1(i, 0, rk[0], dk[0]);
   }
   const float rr1 = block_sum(acc, sh);            // r_{u+1}^T r_{u+1}
   const float xi = rr1 / rr0;                      // xi_u
@@ -420,18 +466,24 @@ cudaError_t launch_cg_update(Ctx* c, int record) {
   const float tol2 = (float)(c->cg_tol * c->cg_tol);
   const int nv = (c->Dp + 1023) / 1024;
 #define UPD(NV)                                                                                  \
-  k_cg_update<NV><<<c->S, 256, 0, c->stream>>>(c->x, c->r, c->d, c->ad, c->part, c->Dp / 128,   \
-                                               c->rr, c->bb, c->steps, c->active,              \
-                                               c->task_active, c->counters, c->gam, c->xi,     \
-                                               c->psteps, record, c->R, c->K, c->C, c->Dp, c->S, \
-                                               c->U, tol2, static_cast<__nv_bfloat16*>(c->dhi), \
-                                               static_cast<__nv_bfloat16*>(c->dlo))
-  if (nv <= 1) UPD(1);
-  else if (nv <= 2) UPD(2);
-  else if (nv <= 4) UPD(4);
-  else if (nv <= 8) UPD(8);
-  else if (nv <= 16) UPD(16);
-  else UPD(0);
+  if (c->tc != nullptr)                                                                          \
+    k_cg_update<NV, true><<<c->S, 256, 0, c->stream>>>(                                          \
+        c->x, c->r, c->d, c->ad, c->part, c->alpha, c->Dp / 128, c->rr, c->bb, c->steps,        \
+        c->active, c->task_active, c->counters, c->gam, c->xi, c->psteps, record, c->R, c->K,    \
+        c->C, c->Dp, c->S, c->U, tol2, static_cast<__nv_bfloat16*>(c->dhi),                      \
+        static_cast<__nv_bfloat16*>(c->dlo));                                                    \
+  else                                                                                           \
+    k_cg_update<NV, false><<<c->S, 256, 0, c->stream>>>(                                         \
+        c->x, c->r, c->d, c->ad, c->part, c->alpha, c->Dp / 128, c->rr, c->bb, c->steps,        \
+        c->active, c->task_active, c->counters, c->gam, c->xi, c->psteps, record, c->R, c->K,    \
+        c->C, c->Dp, c->S, c->U, tol2, static_cast<__nv_bfloat16*>(c->dhi),                      \
+        static_cast<__nv_bfloat16*>(c->dlo))
+  if (nv <= 1) { UPD(1); }
+  else if (nv <= 2) { UPD(2); }
+  else if (nv <= 4) { UPD(4); }
+  else if (nv <= 8) { UPD(8); }
+  else if (nv <= 16) { UPD(16); }
+  else { UPD(0); }
 #undef UPD
   return cudaGetLastError();
 }

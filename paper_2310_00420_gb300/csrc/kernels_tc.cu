@@ -61,6 +61,8 @@ struct TcArgs {
   int* status;
   const int* stall;       // test hook: nonzero makes the MMA warp wait on a barrier nothing arrives at
   uint32_t mn_lbo, mn_sbo; // MN-major A descriptor strides (pass 2 reading Phi directly)
+  int raw;                 // pass 2 stores beta Phi^T W only (the CG update adds alpha * V and
+                           // forms d^T A d itself); otherwise the full A V, with partials if part
   const int* tile_code;    // fused launches: per tile (local << 2) | (pass - 1)
   const int* tile_task2;   // fused launches: task of each tile
   int* p1done;             // fused launches: finished pass-1 tiles per task (zeroed per launch)
@@ -492,35 +494,48 @@ k_tc(const __grid_constant__ TcMaps maps, const TcArgs p) {
         const int d = ti.a_row + 32 * lg + lane;
         if (p.opcount != nullptr && ti.dtile == 0 && ti.col0 == 0 && etid == 0)
           atomicAdd(&p.opcount[ti.t], 1ull);
-        for (int c0 = 0; c0 < p.Rpad; c0 += 16) {
-          float vv[16], aa[16];
+        if (p.raw) {
+          // beta Phi^T W only: one TMEM read and one coalesced store per column
+          for (int c0 = 0; c0 < p.Rpad; c0 += 16) {
+            float acc[16];
+            tmem_ld16(trow + c0, acc);
 #pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            const int j = ti.col0 + c0 + i;
-            const int jj = j < p.R ? j : 0;
-            const int64_t sys = (int64_t)ti.t * p.R + jj;
-            vv[i] = j < p.R ? __ldg(p.V + sys * p.Dp + d) : 0.f;
-            aa[i] = j < p.R ? __ldg(p.alpha + (int64_t)(jj / (p.K + 1)) * p.Dp + d) : 0.f;
+            for (int i = 0; i < 16; ++i) {
+              const int j = ti.col0 + c0 + i;
+              if (j < p.R) p.Z[((int64_t)ti.t * p.R + j) * p.Dp + d] = p.beta * acc[i];
+            }
           }
-          float acc[16], dot[16];
-          tmem_ld16(trow + c0, acc);
+        } else {
+          for (int c0 = 0; c0 < p.Rpad; c0 += 16) {
+            float vv[16], aa[16];
 #pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            const int j = ti.col0 + c0 + i;
-            const float ad = fmaf(p.beta, acc[i], aa[i] * vv[i]);
-            if (j < p.R) p.Z[((int64_t)ti.t * p.R + j) * p.Dp + d] = ad;
-            dot[i] = vv[i] * ad;
+            for (int i = 0; i < 16; ++i) {
+              const int j = ti.col0 + c0 + i;
+              const int jj = j < p.R ? j : 0;
+              const int64_t sys = (int64_t)ti.t * p.R + jj;
+              vv[i] = j < p.R ? __ldg(p.V + sys * p.Dp + d) : 0.f;
+              aa[i] = j < p.R ? __ldg(p.alpha + (int64_t)(jj / (p.K + 1)) * p.Dp + d) : 0.f;
+            }
+            float acc[16], dot[16];
+            tmem_ld16(trow + c0, acc);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+              const int j = ti.col0 + c0 + i;
+              const float ad = fmaf(p.beta, acc[i], aa[i] * vv[i]);
+              if (j < p.R) p.Z[((int64_t)ti.t * p.R + j) * p.Dp + d] = ad;
+              dot[i] = vv[i] * ad;
+            }
+            const float tot = warp_reduce16(dot, lane);
+            if ((lane & 1) == 0) red[lg * p.Rpad + c0 + reduce16_index(lane)] = tot;
           }
-          const float tot = warp_reduce16(dot, lane);
-          if ((lane & 1) == 0) red[lg * p.Rpad + c0 + reduce16_index(lane)] = tot;
+          epi_bar();
+          if (p.part != nullptr) {
+            for (int jl = etid; jl < p.Rpad && ti.col0 + jl < p.R; jl += 128)
+              p.part[(int64_t)ti.dtile * p.S + (int64_t)ti.t * p.R + ti.col0 + jl] =
+                  ((red[jl] + red[p.Rpad + jl]) + red[2 * p.Rpad + jl]) + red[3 * p.Rpad + jl];
+          }
+          epi_bar();
         }
-        epi_bar();
-        if (p.part != nullptr) {
-          for (int jl = etid; jl < p.Rpad && ti.col0 + jl < p.R; jl += 128)
-            p.part[(int64_t)ti.dtile * p.S + (int64_t)ti.t * p.R + ti.col0 + jl] =
-                ((red[jl] + red[p.Rpad + jl]) + red[2 * p.Rpad + jl]) + red[3 * p.Rpad + jl];
-        }
-        epi_bar();
       }
       tc_fence_before();
       mbar_arrive(&tempty[b]);
@@ -658,7 +673,8 @@ cudaError_t run_passes(Ctx* c, TcState* s, const float* V, float* Z, int with_do
   a.opcount = c->prof_on ? reinterpret_cast<unsigned long long*>(c->opcount) : nullptr;
   a.V = V;
   a.Z = Z;
-  a.part = with_dots ? c->part : nullptr;
+  a.raw = with_dots;             // the CG step: its update kernel completes A d and d^T A d
+  a.part = nullptr;
   a.tile_code = s->tile_code;
   a.tile_task2 = s->tile_task2;
   a.n1 = s->n1;
