@@ -7,7 +7,9 @@
 //         (M = D, N = R, K = N_t), with the per-system partial d^T A d of each 128-wide
 //         coordinate tile written for the CG update (deterministic, no atomics).
 // Tiles: 256 threads as 16 x 16; each thread owns 8 rows (two runs of 4, so shared-memory
-// reads are conflict-free float4s) by TN columns; BK = 16; shared memory double-buffered.
+// reads are conflict-free float4s) by TN columns; BK = 16; the next k-tile is prefetched into
+// registers.  The plain kernels double-buffer shared memory; the DS kernels keep one buffer
+// (at most ~15 KB), which measured faster for them (fewer registers, more resident CTAs).
 // The residual variant ("DS") keeps every accumulator as an unevaluated FP32 pair hi + lo:
 // products are split exactly with an FMA (TwoProduct) and added with Knuth's TwoSum, the
 // compensated dot product of Ogita, Rump and Oishi (SIAM J. Sci. Comput. 26(6), 2005),
@@ -55,104 +57,111 @@ __global__ void __launch_bounds__(256)
 k_pass1(const float* __restrict__ phi, const float* __restrict__ V, float* __restrict__ W,
         float* __restrict__ Wlo, const int64_t* __restrict__ drow,
         const int* __restrict__ tile_task, const int* __restrict__ task_active, int R, int Dp,
-        int Rc, int jstride, int g0) {
+        int Rc, int jstride, int g0, int ntiles) {
   // columns j' = 0 .. Rc-1 of the tile are systems j = j' * jstride of the task (all R
   // systems when Rc = R, jstride = 1; the mean systems only when Rc = C, jstride = K + 1)
   constexpr int BN = 16 * TN;
   constexpr int NB = (BN * 4 + 255) / 256;
-  __shared__ __align__(16) float As[2][16][132];
-  __shared__ __align__(16) float Bs[2][16][BN + 4];
+  constexpr int NBUF = DS ? 1 : 2;     // DS: one shared-memory buffer (see top)
+  __shared__ __align__(16) float As[NBUF][16][132];
+  __shared__ __align__(16) float Bs[NBUF][16][BN + 4];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  const int g = g0 + blockIdx.y;
-  const int t = tile_task[g];
-  if (task_active != nullptr && task_active[t] == 0) return;
-  const int64_t row0 = (int64_t)g * 128;
-  const int64_t rbeg = drow[t];
-  const int64_t Np = drow[t + 1] - rbeg;
-  const int64_t nl0 = row0 - rbeg;
-  const int j0 = blockIdx.x * BN;
-  const float* Ag = phi + row0 * Dp;
-  const float* Vg = V + (int64_t)t * R * Dp;
+  // tiles (row tile, column tile), column tiles of a row tile adjacent; a grid smaller than
+  // the tile count makes the kernel persistent
+  const int ncx = (Rc + BN - 1) / BN;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int g = g0 + tile / ncx;
+    const int t = tile_task[g];
+    if (task_active != nullptr && task_active[t] == 0) continue;
+    const int64_t row0 = (int64_t)g * 128;
+    const int64_t rbeg = drow[t];
+    const int64_t Np = drow[t + 1] - rbeg;
+    const int64_t nl0 = row0 - rbeg;
+    const int j0 = (tile % ncx) * BN;
+    const float* Ag = phi + row0 * Dp;
+    const float* Vg = V + (int64_t)t * R * Dp;
 
-  float hi[8][TN], lo[8][TN];
+    float hi[8][TN], lo[8][TN];
 #pragma unroll
-  for (int i = 0; i < 8; ++i)
+    for (int i = 0; i < 8; ++i)
 #pragma unroll
-    for (int jj = 0; jj < TN; ++jj) hi[i][jj] = lo[i][jj] = 0.f;
+      for (int jj = 0; jj < TN; ++jj) hi[i][jj] = lo[i][jj] = 0.f;
 
-  float4 ra[2], rb[NB];
-  auto load = [&](int k0) {
+    float4 ra[2], rb[NB];
+    auto load = [&](int k0) {
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const int idx = tid + 256 * q, row = idx >> 2, c4 = idx & 3;
-      ra[q] = *reinterpret_cast<const float4*>(Ag + (int64_t)row * Dp + k0 + c4 * 4);
-    }
-#pragma unroll
-    for (int q = 0; q < NB; ++q) {
-      const int idx = tid + 256 * q, row = idx >> 2, c4 = idx & 3, j = j0 + row;
-      rb[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (idx < BN * 4 && j < Rc)
-        rb[q] = *reinterpret_cast<const float4*>(Vg + (int64_t)j * jstride * Dp + k0 + c4 * 4);
-    }
-  };
-  auto store = [&](int buf) {
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const int idx = tid + 256 * q, row = idx >> 2, c4 = idx & 3;
-      As[buf][c4 * 4 + 0][row] = ra[q].x;
-      As[buf][c4 * 4 + 1][row] = ra[q].y;
-      As[buf][c4 * 4 + 2][row] = ra[q].z;
-      As[buf][c4 * 4 + 3][row] = ra[q].w;
-    }
-#pragma unroll
-    for (int q = 0; q < NB; ++q) {
-      const int idx = tid + 256 * q, row = idx >> 2, c4 = idx & 3;
-      if (idx < BN * 4) {
-        Bs[buf][c4 * 4 + 0][row] = rb[q].x;
-        Bs[buf][c4 * 4 + 1][row] = rb[q].y;
-        Bs[buf][c4 * 4 + 2][row] = rb[q].z;
-        Bs[buf][c4 * 4 + 3][row] = rb[q].w;
+      for (int q = 0; q < 2; ++q) {
+        const int idx = tid + 256 * q, row = idx >> 2, c4 = idx & 3;
+        ra[q] = *reinterpret_cast<const float4*>(Ag + (int64_t)row * Dp + k0 + c4 * 4);
       }
-    }
-  };
+#pragma unroll
+      for (int q = 0; q < NB; ++q) {
+        const int idx = tid + 256 * q, row = idx >> 2, c4 = idx & 3, j = j0 + row;
+        rb[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (idx < BN * 4 && j < Rc)
+          rb[q] = *reinterpret_cast<const float4*>(Vg + (int64_t)j * jstride * Dp + k0 + c4 * 4);
+      }
+    };
+    auto store = [&](int buf) {
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int idx = tid + 256 * q, row = idx >> 2, c4 = idx & 3;
+        As[buf][c4 * 4 + 0][row] = ra[q].x;
+        As[buf][c4 * 4 + 1][row] = ra[q].y;
+        As[buf][c4 * 4 + 2][row] = ra[q].z;
+        As[buf][c4 * 4 + 3][row] = ra[q].w;
+      }
+#pragma unroll
+      for (int q = 0; q < NB; ++q) {
+        const int idx = tid + 256 * q, row = idx >> 2, c4 = idx & 3;
+        if (idx < BN * 4) {
+          Bs[buf][c4 * 4 + 0][row] = rb[q].x;
+          Bs[buf][c4 * 4 + 1][row] = rb[q].y;
+          Bs[buf][c4 * 4 + 2][row] = rb[q].z;
+          Bs[buf][c4 * 4 + 3][row] = rb[q].w;
+        }
+      }
+    };
 
-  load(0);
-  store(0);
-  __syncthreads();
-  const int nk = Dp / 16;
-  for (int kt = 0; kt < nk; ++kt) {
-    const int buf = kt & 1;
-    if (kt + 1 < nk) load((kt + 1) * 16);
-#pragma unroll
-    for (int k = 0; k < 16; ++k) {
-      const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][k][tx * 4]);
-      const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][k][64 + tx * 4]);
-      const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-      float b[TN];
-#pragma unroll
-      for (int jj = 0; jj < TN; ++jj) b[jj] = Bs[buf][k][ty + 16 * jj];
-#pragma unroll
-      for (int i = 0; i < 8; ++i)
-#pragma unroll
-        for (int jj = 0; jj < TN; ++jj) mac<DS>(hi[i][jj], lo[i][jj], a[i], b[jj]);
-    }
-    if (kt + 1 < nk) store(buf ^ 1);
+    load(0);
+    store(0);
     __syncthreads();
-  }
-
-  float* Wt = W + rbeg * Rc;
-  float* Wlt = DS ? Wlo + rbeg * Rc : nullptr;
+    const int nk = Dp / 16;
+    for (int kt = 0; kt < nk; ++kt) {
+      const int buf = NBUF == 2 ? (kt & 1) : 0;
+      if (kt + 1 < nk) load((kt + 1) * 16);
 #pragma unroll
-  for (int jj = 0; jj < TN; ++jj) {
-    const int j = j0 + ty + 16 * jj;
-    if (j >= Rc) continue;
-    float* wr = Wt + (int64_t)j * Np + nl0;
-    *reinterpret_cast<float4*>(wr + tx * 4) = make_float4(hi[0][jj], hi[1][jj], hi[2][jj], hi[3][jj]);
-    *reinterpret_cast<float4*>(wr + 64 + tx * 4) = make_float4(hi[4][jj], hi[5][jj], hi[6][jj], hi[7][jj]);
-    if constexpr (DS) {
-      float* wl = Wlt + (int64_t)j * Np + nl0;
-      *reinterpret_cast<float4*>(wl + tx * 4) = make_float4(lo[0][jj], lo[1][jj], lo[2][jj], lo[3][jj]);
-      *reinterpret_cast<float4*>(wl + 64 + tx * 4) = make_float4(lo[4][jj], lo[5][jj], lo[6][jj], lo[7][jj]);
+      for (int k = 0; k < 16; ++k) {
+        const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][k][tx * 4]);
+        const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][k][64 + tx * 4]);
+        const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+        float b[TN];
+#pragma unroll
+        for (int jj = 0; jj < TN; ++jj) b[jj] = Bs[buf][k][ty + 16 * jj];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+          for (int jj = 0; jj < TN; ++jj) mac<DS>(hi[i][jj], lo[i][jj], a[i], b[jj]);
+      }
+      if constexpr (NBUF == 1) __syncthreads();
+      if (kt + 1 < nk) store(buf ^ (NBUF - 1));
+      __syncthreads();
+    }
+
+    float* Wt = W + rbeg * Rc;
+    float* Wlt = DS ? Wlo + rbeg * Rc : nullptr;
+#pragma unroll
+    for (int jj = 0; jj < TN; ++jj) {
+      const int j = j0 + ty + 16 * jj;
+      if (j >= Rc) continue;
+      float* wr = Wt + (int64_t)j * Np + nl0;
+      *reinterpret_cast<float4*>(wr + tx * 4) = make_float4(hi[0][jj], hi[1][jj], hi[2][jj], hi[3][jj]);
+      *reinterpret_cast<float4*>(wr + 64 + tx * 4) = make_float4(hi[4][jj], hi[5][jj], hi[6][jj], hi[7][jj]);
+      if constexpr (DS) {
+        float* wl = Wlt + (int64_t)j * Np + nl0;
+        *reinterpret_cast<float4*>(wl + tx * 4) = make_float4(lo[0][jj], lo[1][jj], lo[2][jj], lo[3][jj]);
+        *reinterpret_cast<float4*>(wl + 64 + tx * 4) = make_float4(lo[4][jj], lo[5][jj], lo[6][jj], lo[7][jj]);
+      }
     }
   }
 }
@@ -177,7 +186,8 @@ struct P2Args {
   unsigned long long* opcount;  // [T] applications per task (plain pass only, may be null)
   int R, K, C, Dp, D, S;
   int Rc, jstride;        // columns processed: systems j = j' * jstride, j' < Rc
-  int t0;                 // first task (grid z covers tasks t0 ..)
+  int t0;                 // first task of the launch
+  int ntiles;             // (task, coordinate tile, column tile) tiles from task t0 on
   float beta_f;
   double beta_d;
   uint64_t seed;
@@ -188,150 +198,155 @@ template <int TN, bool DS>
 __global__ void __launch_bounds__(256) k_pass2(P2Args p) {
   constexpr int BN = 16 * TN;
   constexpr int NB = (BN * 4 + 255) / 256;
-  __shared__ __align__(16) float As[2][16][128];
-  __shared__ __align__(16) float Bs[2][16][BN + 4];
-  __shared__ __align__(16) float Bl[DS ? 2 : 1][16][DS ? BN + 4 : 1];
+  constexpr int NBUF = DS ? 1 : 2;
+  __shared__ __align__(16) float As[NBUF][16][128];
+  __shared__ __align__(16) float Bs[NBUF][16][BN + 4];
+  __shared__ __align__(16) float Bl[NBUF][16][DS ? BN + 4 : 1];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  const int t = p.t0 + blockIdx.z;
-  if (p.task_active != nullptr && p.task_active[t] == 0) return;
-  const int dt = blockIdx.y;
-  const int d0 = dt * 128;
-  const int j0 = blockIdx.x * BN;
-  if (!DS && p.opcount != nullptr && blockIdx.x == 0 && dt == 0 && threadIdx.x == 0)
-    atomicAdd(&p.opcount[t], 1ull);
-  const int64_t rbeg = p.drow[t];
-  const int64_t Np = p.drow[t + 1] - rbeg;
-  const float* Ag = p.phi + rbeg * p.Dp + d0;
-  const float* Wt = p.W + rbeg * p.Rc;
-  const float* Wlt = DS ? p.Wlo + rbeg * p.Rc : nullptr;
+  const int ncx = (p.Rc + BN - 1) / BN, ndt = p.Dp / 128;
+  for (int tile = blockIdx.x; tile < p.ntiles; tile += gridDim.x) {
+    const int t = p.t0 + tile / (ndt * ncx);
+    if (p.task_active != nullptr && p.task_active[t] == 0) continue;
+    const int dt = (tile / ncx) % ndt;
+    const int d0 = dt * 128;
+    const int j0 = (tile % ncx) * BN;
+    if (!DS && p.opcount != nullptr && j0 == 0 && dt == 0 && threadIdx.x == 0)
+      atomicAdd(&p.opcount[t], 1ull);
+    const int64_t rbeg = p.drow[t];
+    const int64_t Np = p.drow[t + 1] - rbeg;
+    const float* Ag = p.phi + rbeg * p.Dp + d0;
+    const float* Wt = p.W + rbeg * p.Rc;
+    const float* Wlt = DS ? p.Wlo + rbeg * p.Rc : nullptr;
 
-  float hi[8][TN], lo[8][TN];
+    float hi[8][TN], lo[8][TN];
 #pragma unroll
-  for (int i = 0; i < 8; ++i)
+    for (int i = 0; i < 8; ++i)
 #pragma unroll
-    for (int jj = 0; jj < TN; ++jj) hi[i][jj] = lo[i][jj] = 0.f;
+      for (int jj = 0; jj < TN; ++jj) hi[i][jj] = lo[i][jj] = 0.f;
 
-  float4 ra[2], rb[NB], rl[DS ? NB : 1];
-  auto load = [&](int64_t n0) {
+    float4 ra[2], rb[NB], rl[DS ? NB : 1];
+    auto load = [&](int64_t n0) {
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const int idx = tid + 256 * q, row = idx >> 5, c4 = idx & 31;
-      ra[q] = *reinterpret_cast<const float4*>(Ag + (n0 + row) * p.Dp + c4 * 4);
-    }
-#pragma unroll
-    for (int q = 0; q < NB; ++q) {
-      const int idx = tid + 256 * q, row = idx >> 2, c4 = idx & 3, j = j0 + row;
-      rb[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-      if constexpr (DS) rl[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (idx < BN * 4 && j < p.Rc) {
-        rb[q] = *reinterpret_cast<const float4*>(Wt + (int64_t)j * Np + n0 + c4 * 4);
-        if constexpr (DS) rl[q] = *reinterpret_cast<const float4*>(Wlt + (int64_t)j * Np + n0 + c4 * 4);
+      for (int q = 0; q < 2; ++q) {
+        const int idx = tid + 256 * q, row = idx >> 5, c4 = idx & 31;
+        ra[q] = *reinterpret_cast<const float4*>(Ag + (n0 + row) * p.Dp + c4 * 4);
       }
-    }
-  };
-  auto store = [&](int buf) {
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const int idx = tid + 256 * q, row = idx >> 5, c4 = idx & 31;
-      *reinterpret_cast<float4*>(&As[buf][row][c4 * 4]) = ra[q];
-    }
-#pragma unroll
-    for (int q = 0; q < NB; ++q) {
-      const int idx = tid + 256 * q, row = idx >> 2, c4 = idx & 3;
-      if (idx < BN * 4) {
-        Bs[buf][c4 * 4 + 0][row] = rb[q].x;
-        Bs[buf][c4 * 4 + 1][row] = rb[q].y;
-        Bs[buf][c4 * 4 + 2][row] = rb[q].z;
-        Bs[buf][c4 * 4 + 3][row] = rb[q].w;
-        if constexpr (DS) {
-          Bl[buf][c4 * 4 + 0][row] = rl[q].x;
-          Bl[buf][c4 * 4 + 1][row] = rl[q].y;
-          Bl[buf][c4 * 4 + 2][row] = rl[q].z;
-          Bl[buf][c4 * 4 + 3][row] = rl[q].w;
+      for (int q = 0; q < NB; ++q) {
+        const int idx = tid + 256 * q, row = idx >> 2, c4 = idx & 3, j = j0 + row;
+        rb[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if constexpr (DS) rl[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (idx < BN * 4 && j < p.Rc) {
+          rb[q] = *reinterpret_cast<const float4*>(Wt + (int64_t)j * Np + n0 + c4 * 4);
+          if constexpr (DS) rl[q] = *reinterpret_cast<const float4*>(Wlt + (int64_t)j * Np + n0 + c4 * 4);
         }
       }
-    }
-  };
-
-  load(0);
-  store(0);
-  __syncthreads();
-  const int64_t nk = Np / 16;
-  for (int64_t kt = 0; kt < nk; ++kt) {
-    const int buf = (int)(kt & 1);
-    if (kt + 1 < nk) load((kt + 1) * 16);
+    };
+    auto store = [&](int buf) {
 #pragma unroll
-    for (int k = 0; k < 16; ++k) {
-      const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][k][tx * 4]);
-      const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][k][64 + tx * 4]);
-      const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-      float b[TN], bl[TN];
-#pragma unroll
-      for (int jj = 0; jj < TN; ++jj) {
-        b[jj] = Bs[buf][k][ty + 16 * jj];
-        bl[jj] = DS ? Bl[buf][k][ty + 16 * jj] : 0.f;
+      for (int q = 0; q < 2; ++q) {
+        const int idx = tid + 256 * q, row = idx >> 5, c4 = idx & 31;
+        *reinterpret_cast<float4*>(&As[buf][row][c4 * 4]) = ra[q];
       }
 #pragma unroll
-      for (int i = 0; i < 8; ++i)
-#pragma unroll
-        for (int jj = 0; jj < TN; ++jj) mac2<DS>(hi[i][jj], lo[i][jj], a[i], b[jj], bl[jj]);
-    }
-    if (kt + 1 < nk) store(buf ^ 1);
+      for (int q = 0; q < NB; ++q) {
+        const int idx = tid + 256 * q, row = idx >> 2, c4 = idx & 3;
+        if (idx < BN * 4) {
+          Bs[buf][c4 * 4 + 0][row] = rb[q].x;
+          Bs[buf][c4 * 4 + 1][row] = rb[q].y;
+          Bs[buf][c4 * 4 + 2][row] = rb[q].z;
+          Bs[buf][c4 * 4 + 3][row] = rb[q].w;
+          if constexpr (DS) {
+            Bl[buf][c4 * 4 + 0][row] = rl[q].x;
+            Bl[buf][c4 * 4 + 1][row] = rl[q].y;
+            Bl[buf][c4 * 4 + 2][row] = rl[q].z;
+            Bl[buf][c4 * 4 + 3][row] = rl[q].w;
+          }
+        }
+      }
+    };
+
+    load(0);
+    store(0);
     __syncthreads();
-  }
-
-  // epilogue
+    const int64_t nk = Np / 16;
+    for (int64_t kt = 0; kt < nk; ++kt) {
+      const int buf = NBUF == 2 ? (int)(kt & 1) : 0;
+      if (kt + 1 < nk) load((kt + 1) * 16);
 #pragma unroll
-  for (int jj = 0; jj < TN; ++jj) {
-    const int jc = j0 + ty + 16 * jj;
-    const bool valid = jc < p.Rc;
-    const int j = jc * p.jstride;
-    const int64_t sys = (int64_t)t * p.R + j;
-    const int c = j / (p.K + 1);
-    const int k = j - c * (p.K + 1);
-    float dot = 0.f;
-    if (valid) {
+      for (int k = 0; k < 16; ++k) {
+        const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][k][tx * 4]);
+        const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][k][64 + tx * 4]);
+        const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+        float b[TN], bl[TN];
 #pragma unroll
-      for (int half = 0; half < 2; ++half) {
-        const int dd = d0 + half * 64 + tx * 4;
-        const float4 v = *reinterpret_cast<const float4*>(p.V + sys * p.Dp + dd);
-        const float4 al = *reinterpret_cast<const float4*>(p.alpha + (int64_t)c * p.Dp + dd);
-        const float vv[4] = {v.x, v.y, v.z, v.w};
-        const float aa[4] = {al.x, al.y, al.z, al.w};
-        float out[4];
-        if constexpr (!DS) {
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            out[e] = fmaf(p.beta_f, hi[half * 4 + e][jj], aa[e] * vv[e]);
-            dot = fmaf(vv[e], out[e], dot);
-          }
-        } else {
-          const bool on = (p.ractive == nullptr) || (p.ractive[sys] != 0);
-          uint32_t bits = 0;
-          if (on && p.Bext == nullptr && k > 0)
-            bits = probe_bits32(p.seed, p.em_iter, t, c, p.C, k - 1, dd & ~31);
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const int d = dd + e;
-            double b = 0.0;
-            if (p.Bext != nullptr) {
-              b = (double)p.Bext[sys * p.Dp + d];
-            } else if (d < p.D) {
-              b = (k == 0) ? (double)p.b0hi[(int64_t)t * p.Dp + d] + (double)p.b0lo[(int64_t)t * p.Dp + d]
-                           : (double)probe_sign(bits, (d & 31));
-            }
-            const double z = (double)hi[half * 4 + e][jj] + (double)lo[half * 4 + e][jj];
-            const double rv = b - p.beta_d * z - (double)aa[e] * (double)vv[e];
-            out[e] = on ? (float)rv : 0.f;
-          }
+        for (int jj = 0; jj < TN; ++jj) {
+          b[jj] = Bs[buf][k][ty + 16 * jj];
+          bl[jj] = DS ? Bl[buf][k][ty + 16 * jj] : 0.f;
         }
-        *reinterpret_cast<float4*>(p.Z + sys * p.Dp + dd) = make_float4(out[0], out[1], out[2], out[3]);
-      }
-    }
-    if constexpr (!DS) {
 #pragma unroll
-      for (int m = 1; m < 16; m <<= 1) dot += __shfl_xor_sync(0xffffffffu, dot, m);
-      if (tx == 0 && valid && p.part != nullptr) p.part[(int64_t)dt * p.S + sys] = dot;
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+          for (int jj = 0; jj < TN; ++jj) mac2<DS>(hi[i][jj], lo[i][jj], a[i], b[jj], bl[jj]);
+      }
+      if constexpr (NBUF == 1) __syncthreads();
+      if (kt + 1 < nk) store(buf ^ (NBUF - 1));
+      __syncthreads();
+    }
+
+    // epilogue
+#pragma unroll
+    for (int jj = 0; jj < TN; ++jj) {
+      const int jc = j0 + ty + 16 * jj;
+      const bool valid = jc < p.Rc;
+      const int j = jc * p.jstride;
+      const int64_t sys = (int64_t)t * p.R + j;
+      const int c = j / (p.K + 1);
+      const int k = j - c * (p.K + 1);
+      float dot = 0.f;
+      if (valid) {
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+          const int dd = d0 + half * 64 + tx * 4;
+          const float4 v = *reinterpret_cast<const float4*>(p.V + sys * p.Dp + dd);
+          const float4 al = *reinterpret_cast<const float4*>(p.alpha + (int64_t)c * p.Dp + dd);
+          const float vv[4] = {v.x, v.y, v.z, v.w};
+          const float aa[4] = {al.x, al.y, al.z, al.w};
+          float out[4];
+          if constexpr (!DS) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              out[e] = fmaf(p.beta_f, hi[half * 4 + e][jj], aa[e] * vv[e]);
+              dot = fmaf(vv[e], out[e], dot);
+            }
+          } else {
+            const bool on = (p.ractive == nullptr) || (p.ractive[sys] != 0);
+            uint32_t bits = 0;
+            if (on && p.Bext == nullptr && k > 0)
+              bits = probe_bits32(p.seed, p.em_iter, t, c, p.C, k - 1, dd & ~31);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const int d = dd + e;
+              double b = 0.0;
+              if (p.Bext != nullptr) {
+                b = (double)p.Bext[sys * p.Dp + d];
+              } else if (d < p.D) {
+                b = (k == 0) ? (double)p.b0hi[(int64_t)t * p.Dp + d] + (double)p.b0lo[(int64_t)t * p.Dp + d]
+                             : (double)probe_sign(bits, (d & 31));
+              }
+              const double z = (double)hi[half * 4 + e][jj] + (double)lo[half * 4 + e][jj];
+              const double rv = b - p.beta_d * z - (double)aa[e] * (double)vv[e];
+              out[e] = on ? (float)rv : 0.f;
+            }
+          }
+          *reinterpret_cast<float4*>(p.Z + sys * p.Dp + dd) = make_float4(out[0], out[1], out[2], out[3]);
+        }
+      }
+      if constexpr (!DS) {
+#pragma unroll
+        for (int m = 1; m < 16; m <<= 1) dot += __shfl_xor_sync(0xffffffffu, dot, m);
+        if (tx == 0 && valid && p.part != nullptr) p.part[(int64_t)dt * p.S + sys] = dot;
+      }
     }
   }
 }
@@ -363,16 +378,20 @@ int pick_tn(int R, int max_tn) {
 
 namespace {
 
+// one CTA per tile (the kernels also accept fewer CTAs, looping over the tiles)
 template <bool DS>
 cudaError_t pass1(Ctx* c, int tn, const float* V, float* W, float* Wlo, const int* mask, int Rc,
                   int jstride, int g0 = 0, int ng = -1) {
   const int bn = 16 * tn;
   if (ng < 0) ng = (int)(c->rows_total / 128);
-  dim3 grid((Rc + bn - 1) / bn, (unsigned)ng);
+  const int ntiles = ((Rc + bn - 1) / bn) * ng;
+  if (ntiles <= 0) return cudaSuccess;
+  const unsigned grid = (unsigned)ntiles;
+  cudaStream_t st = c->stream;
 #define P1CASE(TN)                                                                          \
   case TN:                                                                                  \
-    k_pass1<TN, DS><<<grid, 256, 0, c->stream>>>(c->phi, V, W, Wlo, c->drow, c->tile_task, \
-                                                 mask, c->R, c->Dp, Rc, jstride, g0);       \
+    k_pass1<TN, DS><<<grid, 256, 0, st>>>(c->phi, V, W, Wlo, c->drow, c->tile_task, mask,  \
+                                          c->R, c->Dp, Rc, jstride, g0, ntiles);            \
     break;
   switch (tn) {
     P1CASE(1) P1CASE(2) P1CASE(3) P1CASE(4) P1CASE(6) P1CASE(8) P1CASE(9)
@@ -383,12 +402,16 @@ cudaError_t pass1(Ctx* c, int tn, const float* V, float* W, float* Wlo, const in
 }
 
 template <bool DS>
-cudaError_t pass2(Ctx* c, int tn, const P2Args& a, int nt = -1) {
+cudaError_t pass2(Ctx* c, int tn, const P2Args& a0, int nt = -1) {
   const int bn = 16 * tn;
-  dim3 grid((a.Rc + bn - 1) / bn, c->Dp / 128, nt < 0 ? c->T : nt);
+  P2Args a = a0;
+  a.ntiles = ((a.Rc + bn - 1) / bn) * (c->Dp / 128) * (nt < 0 ? c->T - a.t0 : nt);
+  if (a.ntiles <= 0) return cudaSuccess;
+  const unsigned grid = (unsigned)a.ntiles;
+  cudaStream_t st = c->stream;
 #define P2CASE(TN)                                          \
   case TN:                                                  \
-    k_pass2<TN, DS><<<grid, 256, 0, c->stream>>>(a);        \
+    k_pass2<TN, DS><<<grid, 256, 0, st>>>(a);               \
     break;
   switch (tn) {
     P2CASE(1) P2CASE(2) P2CASE(3) P2CASE(4) P2CASE(6) P2CASE(8) P2CASE(9)

@@ -750,6 +750,11 @@ int tc_create(Ctx* c) {
     snprintf(c->err, sizeof(c->err), "tensor-core operator: stage of %d bytes does not fit", s->stage_bytes);
     return 1;
   }
+  {
+    const char* sv = getenv("CMCS_TC_STAGES");   // evaluation switch: a shallower pipeline
+    const int v = sv ? atoi(sv) : 0;
+    if (v >= 2 && v < s->stages) s->stages = v;
+  }
   s->smem_bytes = s->stages * s->stage_bytes + 1024 + (2 * s->stages + 6) * 8 + 16 + 4 * s->Rpad * 4 + 64;
 
   const int64_t rows = c->rows_total, Dp = c->Dp, S = c->S, R = c->R;
