@@ -20,6 +20,13 @@ namespace cmcs {
 
 namespace {
 
+// k-steps unrolled in the DS kernels: the fully unrolled body (16 k x TN x 8 compensated
+// multiply-adds of ~10 instructions) overflows the instruction cache
+#ifndef CMCS_DS_UNROLL
+#define CMCS_DS_UNROLL 4
+#endif
+constexpr int kUnrollDS = CMCS_DS_UNROLL;
+
 template <bool DS>
 __device__ __forceinline__ void mac(float& hi, float& lo, float a, float b) {
   if constexpr (DS) {
@@ -130,7 +137,7 @@ k_pass1(const float* __restrict__ phi, const float* __restrict__ V, float* __res
     for (int kt = 0; kt < nk; ++kt) {
       const int buf = NBUF == 2 ? (kt & 1) : 0;
       if (kt + 1 < nk) load((kt + 1) * 16);
-#pragma unroll
+#pragma unroll(DS ? kUnrollDS : 16)
       for (int k = 0; k < 16; ++k) {
         const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][k][tx * 4]);
         const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][k][64 + tx * 4]);
@@ -273,7 +280,7 @@ __global__ void __launch_bounds__(256) k_pass2(P2Args p) {
     for (int64_t kt = 0; kt < nk; ++kt) {
       const int buf = NBUF == 2 ? (int)(kt & 1) : 0;
       if (kt + 1 < nk) load((kt + 1) * 16);
-#pragma unroll
+#pragma unroll(DS ? kUnrollDS : 16)
       for (int k = 0; k < 16; ++k) {
         const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][k][tx * 4]);
         const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][k][64 + tx * 4]);
