@@ -138,6 +138,19 @@ def aggregate(ms_local: float, steps: int, world: int, device: str = "cuda"):
     return world * steps / (ms_max / 1e3), ms_max
 
 
+# DRAM bytes (read + write) of one operator application, k_tc<1> + k_tc<3>, from one ncu capture
+# of the current kernels on the 8-task slice of plain-scale, scaled by 32 / 8 tasks
+# (profiles/operator_tc_bf16x3_plain-scale.md).  None for other workloads, and to be reset to
+# None whenever those kernels change.
+_TRAFFIC_PLAIN_SCALE_BF16X3 = 4 * ((571.604736 + 4.069120) + (548.607232 + 24.622592)) * 1e6
+
+
+def _operator_traffic(wl, precision: str):
+    if wl.name == "plain-scale" and wl.T == 32 and precision == "bf16x3":
+        return _TRAFFIC_PLAIN_SCALE_BF16X3
+    return None
+
+
 def _workload(name: str, seed: int, tasks: int = 0):
     from paper_2310_00420_gb300 import synth
     wl = synth.WORKLOADS[name](seed=seed)
@@ -260,7 +273,8 @@ def run_ours(a):
         common = {"kernel": "operator (k_tc<1> + k_tc<3>, tcgen05 BF16 split; pass 2 reads Phi MN-major)",
                   "per_launch_flops": prof["operator_flops"] / per,
                   "per_launch_bytes": prof["operator_bytes"] / per,
-                  "per_launch_ms": prof["operator_ms"] / per, "traffic": None,
+                  "per_launch_ms": prof["operator_ms"] / per,
+                  "traffic": _operator_traffic(wl, a.precision),
                   "peak_source": f"MEASURED_PEAKS.json ({src}): HBM {pk_b} GB/s, "
                                  f"BF16 sustained {pk_t} TFLOP/s",
                   "tflops_achieved": op_tflops, "tensor_frac": op_tflops / pk_t}
