@@ -75,7 +75,9 @@ typedef struct {
   uint64_t seed;          /* keys the Philox draws: alpha initialisation and probes       */
   int precision;          /* cmcs_precision                                               */
   int refine_max;         /* refinement sweeps after the first CG solve, 0..64            */
-  double refine_tol;      /* stop refining a system once ||delta|| <= refine_tol * ||x||  */
+  double refine_tol;      /* stop refining a system once its estimated relative error is
+                             <= refine_tol: after sweep 1 ||delta_1|| / ||x||, after sweep k
+                             rho ||delta_k|| / ((1 - rho) ||x||), rho = ||delta_k|| / ||delta_k-1|| */
   double alpha_min;       /* M-step clamp, > 0                                            */
   double alpha_max;       /* M-step clamp, > alpha_min                                    */
   int schedule;           /* 0: every task in one operator launch per pass (default);

@@ -266,7 +266,7 @@ k_cg_update(float* __restrict__ x, float* __restrict__ r, float* __restrict__ d,
   }
 }
 
-// ---- refinement: xacc += delta; stop once ||delta|| <= refine_tol ||xacc|| -------------
+// ---- refinement: xacc += delta; stop once the estimated relative error <= refine_tol ----
 __global__ void __launch_bounds__(256)
 k_refine_update(float* __restrict__ xacc, const float* __restrict__ delta, int* ractive,
                 int* sweeps, float* rrel, int* counters, int Dp, float rtol) {
@@ -301,7 +301,15 @@ k_refine_update(float* __restrict__ xacc, const float* __restrict__ delta, int* 
       atomicAdd(&counters[3], 1);
     } else {
       rrel[sys] = rel;
-      if (rel <= rtol || !(xn2 > 0.f)) {
+      // stop once the remaining relative error is estimated below rtol: the first correction
+      // itself, then the next correction predicted from the contraction rho = rel / prev of
+      // the last two (the error left is about rho rel / (1 - rho) of ||x||)
+      bool stop = rel <= rtol || !(xn2 > 0.f);
+      if (!stop && sw > 1 && prev > 0.f) {
+        const float rho = rel / prev;
+        stop = rho * rel <= rtol * (1.f - rho);
+      }
+      if (stop) {
         ractive[sys] = 0;
       } else {
         atomicAdd(&counters[1], 1);
