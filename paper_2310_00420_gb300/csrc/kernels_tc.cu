@@ -63,6 +63,8 @@ struct TcArgs {
   uint32_t mn_lbo, mn_sbo; // MN-major A descriptor strides (pass 2 reading Phi directly)
   int raw;                 // pass 2 stores beta Phi^T W only (the CG update adds alpha * V and
                            // forms d^T A d itself); otherwise the full A V, with partials if part
+  int early;               // pass 1 counts its finished tiles per task and lets pass 2 launch at
+                           // once; pass 2 waits per tile on those counts instead of the grid
   const int* tile_code;    // fused launches: per tile (local << 2) | (pass - 1)
   const int* tile_task2;   // fused launches: task of each tile
   int* p1done;             // fused launches: finished pass-1 tiles per task (zeroed per launch)
@@ -331,6 +333,9 @@ k_tc(const __grid_constant__ TcMaps maps, const TcArgs p) {
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
+  // pass 2 may be scheduled now: its CTAs take the SMs this grid frees, and each of its tiles
+  // waits for the pass-1 tiles of its own task (all CTAs of this grid are resident by then)
+  if (PASS == 1 && p.early) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
   const uint32_t a_bytes = kBM * kBK * 2;                  // 16 KiB per A operand
   const uint32_t b_bytes = (uint32_t)p.Rpad * kBK * 2;     // per B operand
@@ -347,7 +352,8 @@ k_tc(const __grid_constant__ TcMaps maps, const TcArgs p) {
         if (!tile_info<PASS>(p, tile, ti)) continue;
         const bool a_mn = PASS == 3 || (PASS == 0 && ti.pass == 2);
         const int pi = ti.pass - 1;
-        if (PASS == 0 && ti.pass == 2 && !wait_pass1_done(&p.p1done[ti.t], p.n1[ti.t])) {
+        if (((PASS == 0 && ti.pass == 2) || (PASS == 3 && p.early)) &&
+            !wait_pass1_done(&p.p1done[ti.t], p.n1[ti.t])) {
           *abort_flag = 1;                 // W of this task never completed
           atomicOr(p.status, 8);
           break;
@@ -482,7 +488,7 @@ k_tc(const __grid_constant__ TcMaps maps, const TcArgs p) {
             }
           }
         }
-        if (PASS == 0) {
+        if (PASS == 0 || (PASS == 1 && p.early)) {
           // publish this tile's part of W for the task's pass-2 tiles
           tc_fence_before();
           asm volatile("fence.proxy.async.global;" ::: "memory");
@@ -600,6 +606,7 @@ struct TcState {
   int mode;
   uint32_t mn_lbo, mn_sbo;
   int *tile_code, *tile_task2, *n1, *p1done;   // fused tile list and its dependency counters
+  int early;                                   // mode 3: pass 2 launched programmatically
   std::vector<int> tstart;                     // first fused tile of each task (host)
 };
 
@@ -705,6 +712,13 @@ cudaError_t run_passes(Ctx* c, TcState* s, const float* V, float* Z, int with_do
       c->launches += 1;
       continue;
     }
+    // default schedule: pass 2 launched programmatically, its tiles starting on the SMs that
+    // pass 1's partial last wave leaves idle (the per-task counters order the data)
+    a.early = (s->mode == 3 && !c->per_task && s->early) ? 1 : 0;
+    if (a.early) {
+      cudaError_t e = cudaMemsetAsync(s->p1done, 0, sizeof(int) * c->T, c->stream);
+      if (e != cudaSuccess) return e;
+    }
     a.tile_lo = (c->per_task ? (int)(c->hrow[t] / kBM) : 0) * s->ncol;
     a.ntiles = (c->per_task ? (int)(c->hrow[t + 1] / kBM) : (int)(c->rows_total / kBM)) * s->ncol;
     int n = a.ntiles - a.tile_lo;
@@ -714,11 +728,24 @@ cudaError_t run_passes(Ctx* c, TcState* s, const float* V, float* Z, int with_do
     a.tile_lo = (c->per_task ? t * ndt : 0) * s->ncol;
     a.ntiles = (c->per_task ? (t + 1) * ndt : c->T * ndt) * s->ncol;
     n = a.ntiles - a.tile_lo;
-    if (s->mode == 3)
+    if (a.early) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3((unsigned)(n < sms ? n : sms));
+      cfg.blockDim = dim3(kTcThreads);
+      cfg.dynamicSmemBytes = (size_t)s->smem_bytes;
+      cfg.stream = c->stream;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+      attr[0].val.programmaticStreamSerializationAllowed = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      e = cudaLaunchKernelEx(&cfg, k_tc<3, NA, NB>, maps, a);
+    } else if (s->mode == 3) {
       k_tc<3, NA, NB><<<n < sms ? n : sms, kTcThreads, s->smem_bytes, c->stream>>>(maps, a);
-    else
+    } else {
       k_tc<2, NA, NB><<<n < sms ? n : sms, kTcThreads, s->smem_bytes, c->stream>>>(maps, a);
-    e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     c->launches += 2;
   }
@@ -765,6 +792,8 @@ int tc_create(Ctx* c) {
     const char* mv = getenv("CMCS_TC_MODE");     // evaluation switch between the schedules
     s->mode = mv ? atoi(mv) : 3;
     if (s->mode != 0 && s->mode != 2) s->mode = 3;
+    const char* ev = getenv("CMCS_TC_EARLY");    // evaluation switch: 0 launches pass 2 plainly
+    s->early = ev ? atoi(ev) != 0 : 1;
   }
   s->mn_lbo = 8192;      // 64-column halves of the MN-major A tile are 8 KiB apart
   s->mn_sbo = 1024;      // groups of 8 k rows are 1 KiB apart

@@ -101,17 +101,23 @@ def test_tc_estep_parity(small, precision, tol):
 @pytest.mark.parametrize("precision", ["bf16x3", "bf16"])
 def test_operator_schedules_agree(precision, monkeypatch):
     """The fused launch (pass 1 and pass 2 of every task in one persistent kernel, pass 2 reading
-    Phi MN-major), the two-launch MN-major schedule and the two-launch schedule over a transposed
-    copy of Phi accumulate the same products in the same k order."""
+    Phi MN-major), the two-launch MN-major schedule (pass 2 launched programmatically, its tiles
+    waiting on per-task counts of finished pass-1 tiles, or launched after pass 1) and the
+    two-launch schedule over a transposed copy of Phi accumulate the same products in the same
+    k order."""
     wl = synth.make_workload("ragged", 3, 3, 200, (37, 300), nnz=5, sigma=0.01, K=70, seed=9)
     R = wl.C * (wl.K + 1)
     V = np.random.default_rng(23).standard_normal((wl.T, R, wl.D)).astype(np.float32)
     Z = {}
-    for mode in ("0", "3", "2"):
+    for mode, early in (("0", "1"), ("3", "1"), ("3", "0"), ("2", "0")):
         monkeypatch.setenv("CMCS_TC_MODE", mode)
+        monkeypatch.setenv("CMCS_TC_EARLY", early)
         with make_ctx(wl, precision=precision) as ctx:
-            Z[mode] = ctx.apply(V)
-            Z[mode + "again"] = ctx.apply(V)
-    assert np.array_equal(Z["0"], Z["0again"])
-    assert np.array_equal(Z["0"], Z["3"])
+            Z[mode + early] = ctx.apply(V)
+            Z[mode + early + "again"] = ctx.apply(V)
+    Z["0"], Z["2"] = Z["01"], Z["20"]
+    assert np.array_equal(Z["01"], Z["01again"])
+    assert np.array_equal(Z["31"], Z["31again"])
+    assert np.array_equal(Z["0"], Z["31"])
+    assert np.array_equal(Z["31"], Z["30"])          # pass 2 launched early or after pass 1
     np.testing.assert_allclose(Z["2"], Z["0"], rtol=1e-5, atol=1e-5 * np.abs(Z["0"]).max())
