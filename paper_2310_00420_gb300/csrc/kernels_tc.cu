@@ -35,6 +35,8 @@ constexpr int kBM = 128;                   // rows of an output tile (MMA M)
 constexpr int kBK = 64;                    // K per stage: one 128-byte row of BF16
 constexpr int kEpiWarps = 4;               // warps 2..5 drain TMEM
 constexpr int kTcThreads = 64 + 32 * kEpiWarps;
+constexpr int kTq = 4;                      // tile queue slots (dynamically scheduled pass 2)
+constexpr int kTqBytes = 2 * kTq * 8 + kTq * 4 + 48;
 constexpr uint64_t kWaitNs = 2000000000ull; // wall time before an mbarrier wait is declared stuck
 constexpr int kSmemBudget = 225 * 1024;
 
@@ -68,6 +70,7 @@ struct TcArgs {
   const int* tile_code;    // fused launches: per tile (local << 2) | (pass - 1)
   const int* tile_task2;   // fused launches: task of each tile
   int* p1done;             // fused launches: finished pass-1 tiles per task (zeroed per launch)
+  int* tile_ctr;           // early pass 2: next tile to hand out (zeroed per launch)
   const int* n1;           // fused launches: pass-1 tiles per task
 };
 
@@ -311,6 +314,13 @@ k_tc(const __grid_constant__ TcMaps maps, const TcArgs p) {
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(never + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   float* red = reinterpret_cast<float*>(tmem_slot + 4);          // [4][Rpad] (pass 2)
+  // early pass 2 hands its tiles out dynamically (CTAs start at different times): the producer
+  // takes the next tile from a global counter and queues its index for the MMA issuer and
+  // the epilogue; -1 ends the sequence
+  uint64_t* tq_full = reinterpret_cast<uint64_t*>(red + 4 * p.Rpad);
+  uint64_t* tq_empty = tq_full + kTq;
+  volatile int* tq = reinterpret_cast<volatile int*>(tq_empty + kTq);
+  const bool dyn = PASS == 3 && p.early;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // once a wait has expired in this E-step, later launches do nothing (the host reports it)
   if (*reinterpret_cast<volatile int*>(p.status) & 8) return;
@@ -326,6 +336,10 @@ k_tc(const __grid_constant__ TcMaps maps, const TcArgs p) {
     }
     mbar_init(mdone, 1);
     mbar_init(never, 1);
+    for (int q = 0; q < kTq; ++q) {
+      mbar_init(&tq_full[q], 1);
+      mbar_init(&tq_empty[q], 1 + 32 * kEpiWarps);
+    }
     *abort_flag = 0;
     fence_mbar_init();
   }
@@ -340,16 +354,45 @@ k_tc(const __grid_constant__ TcMaps maps, const TcArgs p) {
   const uint32_t a_bytes = kBM * kBK * 2;                  // 16 KiB per A operand
   const uint32_t b_bytes = (uint32_t)p.Rpad * kBK * 2;     // per B operand
   uint32_t issued = 0;                                      // k-blocks the producer issued
+  // next queued tile (bounded wait; -2 if it expired, which takes the abort path)
+  auto tq_pop = [&](uint32_t& q) -> int {
+    const uint32_t slot = q % kTq;
+    if (!mbar_wait(&tq_full[slot], (q / kTq) & 1)) {
+      *abort_flag = 1;
+      atomicOr(p.status, 8);
+      return -2;
+    }
+    const int v = tq[slot];
+    mbar_arrive(&tq_empty[slot]);
+    ++q;
+    return v;
+  };
 
   if (warp == 0) {
     // ---- TMA producer
     if (lane == 0) {
-      uint32_t it = 0;
+      uint32_t it = 0, qi = 0;
       bool stop = false;
-      for (int tile = p.tile_lo + blockIdx.x; tile < p.ntiles && !stop && !*abort_flag;
-           tile += gridDim.x) {
+      auto next = [&](int cur) {
+        return dyn ? p.tile_lo + atomicAdd(p.tile_ctr, 1) : cur + (int)gridDim.x;
+      };
+      auto push = [&](int v) {
+        const uint32_t slot = qi % kTq;
+        if (qi >= (uint32_t)kTq && !mbar_wait(&tq_empty[slot], ((qi / kTq) - 1) & 1)) return false;
+        tq[slot] = v;
+        mbar_arrive(&tq_full[slot]);
+        ++qi;
+        return true;
+      };
+      for (int tile = dyn ? next(0) : p.tile_lo + (int)blockIdx.x;
+           tile < p.ntiles && !stop && !*abort_flag; tile = next(tile)) {
         TileInfo ti;
         if (!tile_info<PASS>(p, tile, ti)) continue;
+        if (dyn && !push(tile)) {
+          *abort_flag = 1;
+          atomicOr(p.status, 8);
+          break;
+        }
         const bool a_mn = PASS == 3 || (PASS == 0 && ti.pass == 2);
         const int pi = ti.pass - 1;
         if (((PASS == 0 && ti.pass == 2) || (PASS == 3 && p.early)) &&
@@ -399,6 +442,10 @@ k_tc(const __grid_constant__ TcMaps maps, const TcArgs p) {
           issued = it + 1;
         }
       }
+      if (dyn && !push(-1)) {          // the end of the sequence
+        *abort_flag = 1;
+        atomicOr(p.status, 8);
+      }
     }
   } else if (warp == 1) {
     // ---- MMA issuer
@@ -410,7 +457,10 @@ k_tc(const __grid_constant__ TcMaps maps, const TcArgs p) {
         *abort_flag = 1;               // the bounded wait expired: take the abort path
         atomicOr(p.status, 8);
       }
-      for (int tile = p.tile_lo + blockIdx.x; tile < p.ntiles && !*abort_flag; tile += gridDim.x) {
+      uint32_t qm = 0;
+      for (int tile = dyn ? tq_pop(qm) : p.tile_lo + (int)blockIdx.x;
+           tile >= 0 && tile < p.ntiles && !*abort_flag;
+           tile = dyn ? tq_pop(qm) : tile + (int)gridDim.x) {
         TileInfo ti;
         if (!tile_info<PASS>(p, tile, ti)) continue;
         const bool a_mn = PASS == 3 || (PASS == 0 && ti.pass == 2);
@@ -459,8 +509,10 @@ k_tc(const __grid_constant__ TcMaps maps, const TcArgs p) {
     // ---- epilogue: warp w may read TMEM lanes 32 (w % 4) .. 32 (w % 4) + 31
     const int lg = warp & 3;
     const int etid = threadIdx.x - 64;                 // 0..127 among the epilogue warps
-    uint32_t lt = 0;
-    for (int tile = p.tile_lo + blockIdx.x; tile < p.ntiles; tile += gridDim.x) {
+    uint32_t lt = 0, qe = 0;
+    for (int tile = dyn ? tq_pop(qe) : p.tile_lo + (int)blockIdx.x;;
+         tile = dyn ? tq_pop(qe) : tile + (int)gridDim.x) {
+      if (dyn ? epi_bar_any(tile < 0) : tile >= p.ntiles) break;   // uniform over the warps
       TileInfo ti;
       if (!tile_info<PASS>(p, tile, ti)) continue;
       const int b = (int)(lt % p.nbuf);
@@ -686,6 +738,7 @@ cudaError_t run_passes(Ctx* c, TcState* s, const float* V, float* Z, int with_do
   a.tile_task2 = s->tile_task2;
   a.n1 = s->n1;
   a.p1done = s->p1done;
+  a.tile_ctr = s->p1done + c->T;
   const int sms = c->sm_count > 0 ? c->sm_count : 1;
   const int ndt = c->Dp / kBM;
   const int nloop = c->per_task ? c->T : 1;
@@ -715,8 +768,8 @@ cudaError_t run_passes(Ctx* c, TcState* s, const float* V, float* Z, int with_do
     // default schedule: pass 2 launched programmatically, its tiles starting on the SMs that
     // pass 1's partial last wave leaves idle (the per-task counters order the data)
     a.early = (s->mode == 3 && !c->per_task && s->early) ? 1 : 0;
-    if (a.early) {
-      cudaError_t e = cudaMemsetAsync(s->p1done, 0, sizeof(int) * c->T, c->stream);
+    if (a.early) {       // the per-task counts and the tile counter (p1done[T])
+      cudaError_t e = cudaMemsetAsync(s->p1done, 0, sizeof(int) * ((size_t)c->T + 1), c->stream);
       if (e != cudaSuccess) return e;
     }
     a.tile_lo = (c->per_task ? (int)(c->hrow[t] / kBM) : 0) * s->ncol;
@@ -770,7 +823,7 @@ int tc_create(Ctx* c) {
   s->nbuf = 2 * s->tmem_cols <= 512 ? 2 : 1;     // double-buffer the accumulator when it fits
   s->tmem_alloc = s->tmem_cols * (uint32_t)s->nbuf;
   s->stage_bytes = s->NA * kBM * kBK * 2 + s->NB * s->Rpad * kBK * 2;
-  const int extra = 1024 + (2 * 6 + 5) * 8 + 16 + 4 * s->Rpad * 4 + 64;
+  const int extra = 1024 + (2 * 6 + 5) * 8 + 16 + 4 * s->Rpad * 4 + 64 + kTqBytes;
   s->stages = (kSmemBudget - extra) / s->stage_bytes;
   if (s->stages > 6) s->stages = 6;
   if (s->stages < 2) {
@@ -782,7 +835,7 @@ int tc_create(Ctx* c) {
     const int v = sv ? atoi(sv) : 0;
     if (v >= 2 && v < s->stages) s->stages = v;
   }
-  s->smem_bytes = s->stages * s->stage_bytes + 1024 + (2 * s->stages + 6) * 8 + 16 + 4 * s->Rpad * 4 + 64;
+  s->smem_bytes = s->stages * s->stage_bytes + 1024 + (2 * s->stages + 6) * 8 + 16 + 4 * s->Rpad * 4 + 64 + kTqBytes;
 
   const int64_t rows = c->rows_total, Dp = c->Dp, S = c->S, R = c->R;
   auto alloc = [&](__nv_bfloat16** p, int64_t n) {
@@ -836,7 +889,7 @@ int tc_create(Ctx* c) {
     okm = cudaMalloc(reinterpret_cast<void**>(&s->tile_code), sizeof(int) * code.size()) == cudaSuccess &&
           cudaMalloc(reinterpret_cast<void**>(&s->tile_task2), sizeof(int) * task2.size()) == cudaSuccess &&
           cudaMalloc(reinterpret_cast<void**>(&s->n1), sizeof(int) * (size_t)c->T) == cudaSuccess &&
-          cudaMalloc(reinterpret_cast<void**>(&s->p1done), sizeof(int) * (size_t)c->T) == cudaSuccess;
+          cudaMalloc(reinterpret_cast<void**>(&s->p1done), sizeof(int) * ((size_t)c->T + 1)) == cudaSuccess;
     if (okm) {
       cudaMemcpyAsync(s->tile_code, code.data(), sizeof(int) * code.size(), cudaMemcpyHostToDevice, c->stream);
       cudaMemcpyAsync(s->tile_task2, task2.data(), sizeof(int) * task2.size(), cudaMemcpyHostToDevice, c->stream);
@@ -898,7 +951,7 @@ void tc_destroy(Ctx* c) {
 int tc_max_stages(Ctx* c) {
   TcState* s = static_cast<TcState*>(c->tc);
   if (!s) return 0;
-  const int extra = 1024 + (2 * 6 + 5) * 8 + 16 + 4 * s->Rpad * 4 + 64;
+  const int extra = 1024 + (2 * 6 + 5) * 8 + 16 + 4 * s->Rpad * 4 + 64 + kTqBytes;
   int m = (kSmemBudget - extra) / s->stage_bytes;
   return m > 6 ? 6 : m;
 }
@@ -908,7 +961,7 @@ int tc_set_stages(Ctx* c, int stages) {
   if (!s) return 0;
   if (stages >= 2 && stages <= tc_max_stages(c)) {
     s->stages = stages;
-    s->smem_bytes = s->stages * s->stage_bytes + 1024 + (2 * s->stages + 6) * 8 + 16 + 4 * s->Rpad * 4 + 64;
+    s->smem_bytes = s->stages * s->stage_bytes + 1024 + (2 * s->stages + 6) * 8 + 16 + 4 * s->Rpad * 4 + 64 + kTqBytes;
   }
   return s->stages;
 }
