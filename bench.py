@@ -148,7 +148,7 @@ def aggregate(ms_local: float, steps: int, world: int, device: str = "cuda"):
 # of the current kernels on the 8-task slice of plain-scale, scaled by 32 / 8 tasks
 # (profiles/operator_tc_bf16x3_plain-scale.md).  None for other workloads, and to be reset to
 # None whenever those kernels change.
-_TRAFFIC_PLAIN_SCALE_BF16X3 = 4 * ((571.604736 + 4.069120) + (548.607232 + 24.622592)) * 1e6
+_TRAFFIC_PLAIN_SCALE_BF16X3 = 4 * ((571.656704 + 3.679744) + (548.578048 + 25.114368)) * 1e6
 
 
 def _operator_traffic(wl, precision: str):

@@ -26,6 +26,10 @@ namespace {
 #define CMCS_DS_UNROLL 4
 #endif
 constexpr int kUnrollDS = CMCS_DS_UNROLL;
+#ifndef CMCS_DS_P2_MINB
+#define CMCS_DS_P2_MINB 2
+#endif
+constexpr int kP2MinBlocksDS = CMCS_DS_P2_MINB;     // DS pass 2: two resident CTAs (50.6 vs 51.6 ms)
 
 template <bool DS>
 __device__ __forceinline__ void mac(float& hi, float& lo, float a, float b) {
@@ -202,7 +206,7 @@ struct P2Args {
 };
 
 template <int TN, bool DS>
-__global__ void __launch_bounds__(256) k_pass2(P2Args p) {
+__global__ void __launch_bounds__(256, DS ? kP2MinBlocksDS : 1) k_pass2(P2Args p) {
   constexpr int BN = 16 * TN;
   constexpr int NB = (BN * 4 + 255) / 256;
   constexpr int NBUF = DS ? 1 : 2;
