@@ -1,21 +1,29 @@
 // Tensor-core operator for CMCS_BF16_REFINE and CMCS_BF16X3 (tcgen05 MMA, TMA, TMEM; sm_103a).
 //
 // Same two passes as the FP32 operator (Eq. 7 applied to all R = C*(K+1) right-hand sides of a
-// task), each a K-major BF16 GEMM with FP32 accumulation in tensor memory:
-//   pass 1: W[j][n] = sum_d Phi[n][d] V[j][d]          A = Phi  [rows][D_pad], B = V [S][D_pad]
-//   pass 2: Z[j][d] = beta sum_n PhiT[d][n] W[j][n] + alpha_c[d] V[j][d]
-//                                                       A = PhiT [D_pad][rows], B = W [R][rows]
-// FP32 operands enter as unevaluated BF16 pairs x = x_hi + x_lo.  BF16_REFINE multiplies the
-// BF16-rounded Phi by (V_hi + V_lo) (two MMAs per k-step); BF16X3 also splits Phi and adds
-// Phi_lo V_hi (three MMAs), about 16 significant bits per product.
+// task), BF16 GEMMs with FP32 accumulation in tensor memory:
+//   pass 1: W[j][n] = sum_d Phi[n][d] V[j][d]       A = Phi [rows][D_pad] K-major, B = V [S][D_pad]
+//   pass 2: Z[j][d] = beta sum_n Phi[n][d] W[j][n] (+ alpha_c[d] V[j][d])
+//                                                   A = the same Phi planes read MN-major,
+//                                                   B = W [R][rows]
+// In a CG step pass 2 stores beta Phi^T W only and the CG update adds alpha_c d (and forms
+// d^T A d); cmcs_apply gets the full A V.  FP32 operands enter as unevaluated BF16 pairs
+// x = x_hi + x_lo.  BF16_REFINE multiplies the BF16-rounded Phi by (V_hi + V_lo) (two MMAs per
+// k-step); BF16X3 also splits Phi and adds Phi_lo V_hi (three MMAs), about 16 significant bits
+// per product.
 //
 // Persistent kernel, one CTA (6 warps) per SM, looping over output tiles of 128 rows by up to
-// 256 columns (R wider than 256 is split into column tiles).  Warp 0 lane 0 streams A and B tiles with TMA (128-byte
-// swizzle) through a ring of shared-memory stages; warp 1 lane 0 issues tcgen05.mma from
-// shared-memory descriptors into one of two TMEM accumulators; warps 2-5 drain the other
-// accumulator (tcgen05.ld, 32 rows each), so a tile's epilogue overlaps the next tile's
-// mainloop.  Every mbarrier wait is bounded: on expiry the kernel records status bit 8, stops
+// 256 columns (R wider than 256 is split into column tiles).  Warp 0 lane 0 streams A and B
+// tiles with TMA (128-byte swizzle) through a ring of shared-memory stages; warp 1 lane 0
+// issues tcgen05.mma from shared-memory descriptors into one of two TMEM accumulators; warps
+// 2-5 drain the other accumulator (tcgen05.ld, 32 rows each), so a tile's epilogue overlaps
+// the next tile's mainloop.  Pass 2 is launched programmatically: its CTAs start on the SMs
+// pass 1 frees, take tiles from a global counter (the producer queues each tile index in
+// shared memory for the MMA issuer and the epilogue) and wait per tile for their task's
+// pass-1 tiles.  Every wait is bounded: on expiry the kernel records status bit 8, stops
 // issuing, waits (bounded) for its copies and MMAs in flight and still frees its TMEM.
+// Kept for comparison (CMCS_TC_MODE): pass 2 on a transposed copy of Phi (2) and both passes
+// in one fused launch (0).
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -69,9 +77,10 @@ struct TcArgs {
                            // once; pass 2 waits per tile on those counts instead of the grid
   const int* tile_code;    // fused launches: per tile (local << 2) | (pass - 1)
   const int* tile_task2;   // fused launches: task of each tile
-  int* p1done;             // fused launches: finished pass-1 tiles per task (zeroed per launch)
+  int* p1done;             // fused or early launches: finished pass-1 tiles per task (zeroed per
+                           // application)
   int* tile_ctr;           // early pass 2: next tile to hand out (zeroed per launch)
-  const int* n1;           // fused launches: pass-1 tiles per task
+  const int* n1;           // fused or early launches: pass-1 tiles per task
 };
 
 // all tensor maps of the operator: a[pass-1][hi/lo] (pass 2 reads Phi MN-major), b[pass-1][hi/lo]
@@ -241,7 +250,7 @@ __device__ __forceinline__ bool tile_info(const TcArgs& p, int tile_in, TileInfo
   return p.task_active == nullptr || p.task_active[ti.t] != 0;
 }
 
-// release / acquire of the per-task count of finished pass-1 tiles (fused launches); W is
+// release / acquire of the per-task count of finished pass-1 tiles (fused or early launches); W is
 // written with generic stores and read by TMA (async proxy), hence the proxy fences
 __device__ __forceinline__ void signal_pass1_done(int* cnt) {
   asm volatile("fence.proxy.async.global;" ::: "memory");
@@ -657,7 +666,7 @@ struct TcState {
   // 0: both passes of every task in one launch, pass-2 tiles waiting on per-task counters
   int mode;
   uint32_t mn_lbo, mn_sbo;
-  int *tile_code, *tile_task2, *n1, *p1done;   // fused tile list and its dependency counters
+  int *tile_code, *tile_task2, *n1, *p1done;   // fused tile list; per-task counts [T] + tile counter
   int early;                                   // mode 3: pass 2 launched programmatically
   std::vector<int> tstart;                     // first fused tile of each task (host)
 };
