@@ -58,6 +58,17 @@ __device__ __forceinline__ float probe_sign(uint32_t bits, int sh) {
   return ((bits >> sh) & 1u) ? -1.0f : 1.0f;
 }
 
+// whether any of the columns j' in [j0, j0 + bn) of task t (systems t R + j' jstride) is
+// still refining; block-uniform.  A residual tile with none is skipped: such systems are
+// not refined again, so their residual entries are never read.
+__device__ __forceinline__ bool tile_refining(const int* ractive, int t, int R, int j0, int bn,
+                                              int Rc, int jstride) {
+  int any = 0;
+  for (int jj = threadIdx.x; jj < bn; jj += blockDim.x)
+    if (j0 + jj < Rc && ractive[(int64_t)t * R + (int64_t)(j0 + jj) * jstride] != 0) any = 1;
+  return __syncthreads_or(any) != 0;
+}
+
 }  // namespace
 
 // --------------------------------------------------------------------------------------
@@ -67,8 +78,8 @@ template <int TN, bool DS>
 __global__ void __launch_bounds__(256)
 k_pass1(const float* __restrict__ phi, const float* __restrict__ V, float* __restrict__ W,
         float* __restrict__ Wlo, const int64_t* __restrict__ drow,
-        const int* __restrict__ tile_task, const int* __restrict__ task_active, int R, int Dp,
-        int Rc, int jstride, int g0, int ntiles) {
+        const int* __restrict__ tile_task, const int* __restrict__ task_active,
+        const int* __restrict__ ractive, int R, int Dp, int Rc, int jstride, int g0, int ntiles) {
   // columns j' = 0 .. Rc-1 of the tile are systems j = j' * jstride of the task (all R
   // systems when Rc = R, jstride = 1; the mean systems only when Rc = C, jstride = K + 1)
   constexpr int BN = 16 * TN;
@@ -89,6 +100,7 @@ k_pass1(const float* __restrict__ phi, const float* __restrict__ V, float* __res
     const int64_t Np = drow[t + 1] - rbeg;
     const int64_t nl0 = row0 - rbeg;
     const int j0 = (tile % ncx) * BN;
+    if (DS && ractive != nullptr && !tile_refining(ractive, t, R, j0, BN, Rc, jstride)) continue;
     const float* Ag = phi + row0 * Dp;
     const float* Vg = V + (int64_t)t * R * Dp;
 
@@ -221,6 +233,8 @@ __global__ void __launch_bounds__(256, DS ? kP2MinBlocksDS : 1) k_pass2(P2Args p
     const int dt = (tile / ncx) % ndt;
     const int d0 = dt * 128;
     const int j0 = (tile % ncx) * BN;
+    if (DS && p.ractive != nullptr && !tile_refining(p.ractive, t, p.R, j0, BN, p.Rc, p.jstride))
+      continue;
     if (!DS && p.opcount != nullptr && j0 == 0 && dt == 0 && threadIdx.x == 0)
       atomicAdd(&p.opcount[t], 1ull);
     const int64_t rbeg = p.drow[t];
@@ -392,7 +406,7 @@ namespace {
 // one CTA per tile (the kernels also accept fewer CTAs, looping over the tiles)
 template <bool DS>
 cudaError_t pass1(Ctx* c, int tn, const float* V, float* W, float* Wlo, const int* mask, int Rc,
-                  int jstride, int g0 = 0, int ng = -1) {
+                  int jstride, int g0 = 0, int ng = -1, const int* ractive = nullptr) {
   const int bn = 16 * tn;
   if (ng < 0) ng = (int)(c->rows_total / 128);
   const int ntiles = ((Rc + bn - 1) / bn) * ng;
@@ -402,7 +416,7 @@ cudaError_t pass1(Ctx* c, int tn, const float* V, float* W, float* Wlo, const in
 #define P1CASE(TN)                                                                          \
   case TN:                                                                                  \
     k_pass1<TN, DS><<<grid, 256, 0, st>>>(c->phi, V, W, Wlo, c->drow, c->tile_task, mask,  \
-                                          c->R, c->Dp, Rc, jstride, g0, ntiles);            \
+                                          ractive, c->R, c->Dp, Rc, jstride, g0, ntiles);   \
     break;
   switch (tn) {
     P1CASE(1) P1CASE(2) P1CASE(3) P1CASE(4) P1CASE(6) P1CASE(8) P1CASE(9)
@@ -499,7 +513,9 @@ cudaError_t launch_residual(Ctx* c, const float* X, const float* Bext, float* Ro
   const int Rc = means_only ? c->C : c->R;
   const int js = means_only ? c->K + 1 : 1;
   const int tn = c->tn_ds > 0 ? c->tn_ds : pick_tn(Rc, 4);
-  cudaError_t e = pass1<true>(c, tn, X, c->w, c->wlo, nullptr, Rc, js);
+  // systems no longer refining: their tiles are skipped, their residual entries not read
+  const int* ractive = (Bext || all_systems) ? nullptr : c->ractive;
+  cudaError_t e = pass1<true>(c, tn, X, c->w, c->wlo, nullptr, Rc, js, 0, -1, ractive);
   if (e != cudaSuccess) return e;
   P2Args a = base_args(c);
   a.Rc = Rc;
@@ -507,7 +523,7 @@ cudaError_t launch_residual(Ctx* c, const float* X, const float* Bext, float* Ro
   a.V = X;
   a.Z = Rout;
   a.Bext = Bext;
-  a.ractive = (Bext || all_systems) ? nullptr : c->ractive;
+  a.ractive = ractive;
   c->launches += 2;
   return pass2<true>(c, tn, a);
 }
