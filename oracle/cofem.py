@@ -55,6 +55,31 @@ def apply_A(Phi_t: np.ndarray, beta: float, alpha_c: np.ndarray, V: np.ndarray) 
     return beta * (Phi_t.T @ (Phi_t @ V)) + alpha_c[:, None] * V
 
 
+def apply_A_fourier(mask_t: np.ndarray, beta: float, alpha_c: np.ndarray,
+                    V: np.ndarray) -> np.ndarray:
+    """A V for the structured sensing matrix Phi_t = Omega_t F of Sec. 4 (F the unitary DFT,
+    Omega_t the rows selected by the 0/1 mask_t) with real z: A = beta Re(Phi^H Phi) +
+    diag(alpha_c), and Phi^H Phi = F^H diag(mask) F, applied with FFTs (Sec. 3.3: CG needs
+    only products with A).  V is [D] or [D, m]."""
+    V = np.asarray(V, dtype=np.float64)
+    m = np.asarray(mask_t, dtype=np.float64)
+    ax = 0
+    spec = np.fft.fft(V, axis=ax)
+    shape = (-1,) + (1,) * (V.ndim - 1)
+    out = np.fft.ifft(m.reshape(shape) * spec, axis=ax).real
+    return beta * out + np.asarray(alpha_c, dtype=np.float64).reshape(shape) * V
+
+
+def rhs_mean_fourier(mask_t: np.ndarray, y_t: np.ndarray, beta: float) -> np.ndarray:
+    """b0 = beta Re(Phi_t^H y_t) for Phi_t = Omega_t F: the measured coefficients y_t (in
+    ascending frequency order) placed at their frequencies, then F^H = sqrt(D) ifft."""
+    m = np.asarray(mask_t)
+    D = m.shape[0]
+    Y = np.zeros(D, dtype=np.complex128)
+    Y[np.nonzero(m)[0]] = np.asarray(y_t, dtype=np.complex128)
+    return beta * (np.sqrt(D) * np.fft.ifft(Y)).real
+
+
 def task_const(y_t: np.ndarray, beta: float) -> float:
     """The c-independent part of log p(y_t | alpha_c):  log p = ell/2 - task_const, with
     task_const = (N log 2pi - N log beta + beta ||y||^2) / 2 (from Eqs. 1 and 3)."""

@@ -5,8 +5,9 @@ ground-truth sparse signals z_t and their ground-truth cluster labels.  It holds
 the inference method's arithmetic and is the one module that both the CUDA path and the
 FP64 oracle use.
 
-Generative recipe (the model of Eq. 1 with the simulation protocol of Sec. 4, except that
-Phi_t is a dense Gaussian matrix instead of a subsampled DFT):
+Two sensing setups.  ``make_fourier`` follows Sec. 4 itself (Phi_t = Omega_t F, a subsampled
+unitary DFT; see FourierWorkload).  ``make_workload`` follows the model of Eq. 1 with the
+simulation protocol of Sec. 4, except that Phi_t is a dense Gaussian matrix:
 
 * Phi_t has i.i.d. entries N(0, 1/N_t), stored row-major (N_t x D), FP32.
 * Ground-truth clusters partition the tasks (contiguous blocks of equal size, or
@@ -157,6 +158,105 @@ def make_workload(name: str, T: int, C: int, D: int, N, *, sparsity: float = Non
                     cg_max_iter, em_iters, seed)
 
 
+@dataclass
+class FourierWorkload:
+    """The paper's own sensing setup (Sec. 4): Phi_t = Omega_t F with F the unitary D x D DFT
+    and Omega_t a random row subset (N_t frequencies) of the identity; z_t real and sparse;
+    y_t = Phi_t z_t + eps_t with complex noise whose real and imaginary parts are each
+    N(0, sigma^2).  Stored as a 0/1 frequency mask per task and the measured coefficients in
+    ascending frequency order."""
+
+    name: str
+    T: int
+    C: int
+    D: int
+    N: np.ndarray                 # int64 [T], frequencies sampled per task
+    mask: np.ndarray              # uint8 [T, D]
+    y: np.ndarray                 # complex64 [sum N_t], task t's in ascending frequency order
+    row_off: np.ndarray           # int64 [T+1] into y
+    z: np.ndarray                 # float32 [T, D]
+    labels: np.ndarray            # int64 [T]
+    sigma: float
+    beta: float
+    pi: np.ndarray
+    K: int
+    cg_tol: float
+    cg_max_iter: int
+    em_iters: int
+    seed: int
+
+    def freqs(self, t: int) -> np.ndarray:
+        return np.nonzero(self.mask[t])[0]
+
+    def yt(self, t: int) -> np.ndarray:
+        return self.y[self.row_off[t]:self.row_off[t + 1]]
+
+    def phi_real(self, t: int) -> np.ndarray:
+        """The real [Re Phi_t; Im Phi_t] (2 N_t x D, FP64) whose normal equations are those of
+        the complex model with real z: A = beta Re(Phi^H Phi) + diag(alpha)."""
+        k = self.freqs(t).astype(np.float64)
+        d = np.arange(self.D, dtype=np.float64)
+        ang = -2.0 * np.pi * np.outer(k, d) / self.D
+        s = 1.0 / np.sqrt(self.D)
+        return np.concatenate([np.cos(ang) * s, np.sin(ang) * s], axis=0)
+
+    def y_real(self, t: int) -> np.ndarray:
+        yt = self.yt(t)
+        return np.concatenate([yt.real.astype(np.float64), yt.imag.astype(np.float64)])
+
+
+def make_fourier(name: str, T: int, C: int, D: int, N: int, *, sparsity: float = 0.05,
+                 perturb: float = 0.0, sigma: float = 0.05, gt_clusters: int = None,
+                 K: int = 15, cg_tol: float = 1e-5, cg_max_iter: int = 50, em_iters: int = 50,
+                 seed: int = 0) -> FourierWorkload:
+    """Generate a Fourier workload (supports and values as in ``make_workload``)."""
+    G = gt_clusters if gt_clusters is not None else C
+    sizes = _group_sizes(T, G, "equal", _rng(seed, _TAG_SIZES))
+    labels = np.repeat(np.arange(G, dtype=np.int64), sizes)
+    nnz = max(1, int(round(sparsity * D)))
+    r_sup = _rng(seed, _TAG_SUPPORT)
+    cluster_support = [np.sort(r_sup.choice(D, size=nnz, replace=False)) for _ in range(G)]
+    n_swap = int(round(perturb * nnz))
+    r_val = _rng(seed, _TAG_VALUES)
+    z = np.zeros((T, D), dtype=np.float32)
+    for t in range(T):
+        sup = cluster_support[labels[t]].copy()
+        if n_swap > 0:
+            drop = r_sup.choice(nnz, size=n_swap, replace=False)
+            outside = np.setdiff1d(np.arange(D), sup, assume_unique=True)
+            sup[drop] = r_sup.choice(outside, size=n_swap, replace=False)
+        z[t, sup] = r_val.standard_normal(nnz).astype(np.float32)
+    r_mask = _rng(seed, _TAG_PHI)
+    mask = np.zeros((T, D), dtype=np.uint8)
+    for t in range(T):
+        mask[t, r_mask.choice(D, size=N, replace=False)] = 1
+    r_noise = _rng(seed, _TAG_NOISE)
+    off = np.arange(T + 1, dtype=np.int64) * N
+    y = np.empty(T * N, dtype=np.complex64)
+    for t in range(T):
+        spec = np.fft.fft(z[t].astype(np.float64)) / np.sqrt(D)
+        k = np.nonzero(mask[t])[0]
+        noise = sigma * (r_noise.standard_normal(N) + 1j * r_noise.standard_normal(N))
+        y[off[t]:off[t + 1]] = (spec[k] + noise).astype(np.complex64)
+    return FourierWorkload(name, T, C, D, np.full(T, N, dtype=np.int64), mask, y, off, z, labels,
+                           sigma, 1.0 / sigma ** 2, np.full(C, 1.0 / C), K, cg_tol, cg_max_iter,
+                           em_iters, seed)
+
+
+def fourier_small(seed: int = 0) -> FourierWorkload:
+    """T=4, C=2, D=256, N=64 (D/4); 5% sparsity in 2 clusters of 2 tasks; sigma 0.05; K=15;
+    CG tol 1e-8 (max 100)."""
+    return make_fourier("fourier-small", 4, 2, 256, 64, K=15, cg_tol=1e-8, cg_max_iter=100,
+                        em_iters=10, seed=seed)
+
+
+def fourier(seed: int = 0) -> FourierWorkload:
+    """The paper's Fourier setting at D=8192: T=40 tasks in 4 clusters, N = D/4, 5% sparsity,
+    10% per-task support perturbation, sigma 0.05, K=15 probes, U=50 CG steps (tol 1e-5)."""
+    return make_fourier("fourier", 40, 4, 8192, 2048, perturb=0.10, K=15, cg_tol=1e-5,
+                        cg_max_iter=50, em_iters=50, seed=seed)
+
+
 def uniform_alpha(C: int, D: int, seed: int, tag: int = _TAG_ALPHA) -> np.ndarray:
     """A seeded Uniform(0,1) state for alpha (FP32 values), for tests that start from a
     given alpha instead of the library's own initial draw."""
@@ -205,4 +305,6 @@ WORKLOADS = {
     "batching": batching,
     "precision": precision,
     "differentiation": differentiation,
+    "fourier-small": fourier_small,
+    "fourier": fourier,
 }
