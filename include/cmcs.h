@@ -137,6 +137,21 @@ typedef enum {
 cmcs_status cmcs_create(const cmcs_config *cfg, const float *Phi, const float *y, int on_device,
                         void *stream, cmcs_ctx **out);
 
+/* Create a context for the structured sensing matrices of Sec. 4, Phi_t = Omega_t F: F the
+ * unitary D x D DFT (F_kd = e^{-2 pi i k d / D} / sqrt(D)) and Omega_t the rows selected by
+ * mask (uint8 [T][D], nonzero = frequency k sampled for task t; cfg->N[t] must equal the
+ * count).  y: float [sum N_t][2], the complex measurements (real, imaginary) of each task in
+ * ascending frequency order.  The signals z_t are real; reading the real and imaginary parts
+ * of y_t as 2 N_t real measurements of noise precision beta gives
+ *     A_tc = beta Re(Phi_t^H Phi_t) + diag(alpha_c),   b0_t = beta Re(Phi_t^H y_t),
+ * applied by FFT in O(D log D) per system (Sec. 3.3) instead of O(N_t D).  Requires
+ * cfg->precision == CMCS_FP32 and D a power of two in [128, 8192] (else
+ * CMCS_ERR_UNSUPPORTED).  The CG operator runs FP32 FFTs; the refinement residual runs FP64
+ * FFTs.  Every call below works on such a context except cmcs_set_data and cmcs_adjoint
+ * (CMCS_ERR_UNSUPPORTED).  mask and y are host or device per on_device. */
+cmcs_status cmcs_create_dft(const cmcs_config *cfg, const uint8_t *mask, const float *y,
+                            int on_device, void *stream, cmcs_ctx **out);
+
 /* Replace alpha (float [C][D], every entry > 0) and set the EM iteration counter, which keys
  * the probes of the next E-step (Alg. 2 draws fresh probes every iteration). */
 cmcs_status cmcs_set_alpha(cmcs_ctx *ctx, const float *alpha, int on_device, int64_t em_iter);

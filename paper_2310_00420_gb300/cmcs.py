@@ -24,7 +24,7 @@ PRECISIONS = {"fp32": FP32, "bf16": BF16_REFINE, "bf16_refine": BF16_REFINE, "bf
  OUT_GAMMA, OUT_XI, OUT_B0, OUT_SWEEPS, OUT_RESID) = range(14)
 
 # exported symbols, in the order include/cmcs.h declares them
-EXPORTS = ("cmcs_create", "cmcs_set_alpha", "cmcs_estep", "cmcs_em_iter", "cmcs_read",
+EXPORTS = ("cmcs_create", "cmcs_create_dft", "cmcs_set_alpha", "cmcs_estep", "cmcs_em_iter", "cmcs_read",
            "cmcs_result", "cmcs_apply", "cmcs_probes", "cmcs_lanczos_quadrature",
            "cmcs_profile", "cmcs_profile_read", "cmcs_apply_noalloc", "cmcs_set_data",
            "cmcs_adjoint", "cmcs_test_stall", "cmcs_last_error", "cmcs_destroy")
@@ -75,6 +75,7 @@ def lib():
     L = ctypes.CDLL(LIB_PATH)
     vp, i, i64, st = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_int
     L.cmcs_create.argtypes = [ctypes.POINTER(Config), vp, vp, i, vp, ctypes.POINTER(vp)]
+    L.cmcs_create_dft.argtypes = [ctypes.POINTER(Config), vp, vp, i, vp, ctypes.POINTER(vp)]
     L.cmcs_set_alpha.argtypes = [vp, vp, i, i64]
     L.cmcs_estep.argtypes = [vp]
     L.cmcs_em_iter.argtypes = [vp, i]
@@ -156,9 +157,12 @@ class Context:
                  cg_tol: float = 1e-5, seed: int = 0, precision="fp32", refine_max: int = 0,
                  refine_tol: float = 1e-6, alpha_min: float = 1e-10, alpha_max: float = 1e10,
                  schedule: str = "batched", graphs: bool = True, autotune: bool = False,
-                 stream=None):
+                 mask=None, stream=None):
+        """Dense Phi [sum N_t][D] with y [sum N_t]; or, with Phi None and mask given, the
+        Fourier operator of cmcs_create_dft: mask uint8 [T][D], y float32 [sum N_t][2]."""
         N = np.ascontiguousarray(np.asarray(N, dtype=np.int64))
-        self.T, self.C, self.D, self.K = int(len(N)), int(C), int(Phi.shape[1]), int(K)
+        D = int(mask.shape[1]) if mask is not None else int(Phi.shape[1])
+        self.T, self.C, self.D, self.K = int(len(N)), int(C), D, int(K)
         self.U = int(cg_max_iter)
         pi = np.full(C, 1.0 / C) if pi is None else np.ascontiguousarray(np.asarray(pi, np.float64))
         self._N, self._pi = N, pi                     # keep alive during create
@@ -171,13 +175,15 @@ class Context:
                      {"batched": 0, "per_task": 1}[schedule], 1 if graphs else 0,
                      1 if autotune else 0)
         self.cfg = cfg
-        p_phi, dev1 = _ptr(Phi)
+        self.fourier = mask is not None
+        p_phi, dev1 = _ptr(mask if self.fourier else Phi)
         p_y, dev2 = _ptr(y)
         if dev1 != dev2:
-            raise ValueError("Phi and y must both be host arrays or both device tensors")
+            raise ValueError("Phi (or mask) and y must both be host arrays or both device tensors")
         self._stream = _stream_handle(stream)
         h = ctypes.c_void_p()
-        _check(lib().cmcs_create(ctypes.byref(cfg), p_phi, p_y, dev1, self._stream, ctypes.byref(h)))
+        create = lib().cmcs_create_dft if self.fourier else lib().cmcs_create
+        _check(create(ctypes.byref(cfg), p_phi, p_y, dev1, self._stream, ctypes.byref(h)))
         self.h = h
 
     @classmethod
@@ -191,6 +197,20 @@ class Context:
             Phi = torch.from_numpy(Phi).cuda()
             y = torch.from_numpy(y).cuda()
         return cls(Phi, y, wl.N, **args)
+
+    @classmethod
+    def from_fourier(cls, wl, device: bool = True, **kw):
+        """A context for a synth.FourierWorkload (Phi_t = Omega_t F, cmcs_create_dft)."""
+        args = dict(C=wl.C, K=wl.K, beta=wl.beta, pi=wl.pi, cg_max_iter=wl.cg_max_iter,
+                    cg_tol=wl.cg_tol, seed=wl.seed)
+        args.update(kw)
+        mask = np.ascontiguousarray(wl.mask.astype(np.uint8))
+        y = np.ascontiguousarray(np.stack([wl.y.real, wl.y.imag], axis=-1).astype(np.float32))
+        if device:
+            import torch
+            mask = torch.from_numpy(mask).cuda()
+            y = torch.from_numpy(y).cuda()
+        return cls(None, y, wl.N, mask=mask, **args)
 
     # ---- lifecycle ----
     def close(self):

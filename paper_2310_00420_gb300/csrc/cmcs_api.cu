@@ -72,6 +72,7 @@ void free_ctx(Ctx* c) {
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
   if (c->tc) tc_destroy(c);
+  dft_destroy(c);
   free(c->hN);
   free(c->hNp);
   free(c->hrow);
@@ -368,17 +369,25 @@ void set_global_error(const char* msg) { snprintf(g_create_err, sizeof(g_create_
 
 extern "C" {
 
-cmcs_status cmcs_create(const cmcs_config* cfg, const float* Phi, const float* y, int on_device,
-                        void* stream, cmcs_ctx** out) {
+namespace {
+
+// one context for dense Phi (mask == NULL) or for the structured Phi_t = Omega_t F (Phi == NULL)
+cmcs_status create_ctx(const cmcs_config* cfg, const float* Phi, const float* y,
+                       const uint8_t* mask, int on_device, void* stream, cmcs_ctx** out) {
   Ctx* c = nullptr;
   if (!out) {
     set_err(nullptr, "out is NULL");
     return CMCS_ERR_INVALID_ARG;
   }
   *out = nullptr;
-  if (validate(cfg) != CMCS_OK || !Phi || !y || (on_device != 0 && on_device != 1)) {
+  if (validate(cfg) != CMCS_OK || (!Phi && !mask) || !y || (on_device != 0 && on_device != 1)) {
     set_err(nullptr, "invalid configuration or null input");
     return CMCS_ERR_INVALID_ARG;
+  }
+  if (mask && (cfg->precision != CMCS_FP32 || !dft_size_ok(cfg->D))) {
+    set_err(nullptr, "the Fourier operator needs precision CMCS_FP32 and D a power of two in "
+                     "[128, %d]", kDftMaxD);
+    return CMCS_ERR_UNSUPPORTED;
   }
   cmcs_ctx* h = static_cast<cmcs_ctx*>(calloc(1, sizeof(cmcs_ctx)));
   if (!h) {
@@ -402,6 +411,7 @@ cmcs_status cmcs_create(const cmcs_config* cfg, const float* Phi, const float* y
   c->alpha_max = cfg->alpha_max;
   c->precision = cfg->precision;
   c->seed = cfg->seed;
+  c->op = mask ? 1 : 0;
   c->em_iter = 0;
   c->stream = static_cast<cudaStream_t>(stream);
   c->per_task = cfg->schedule;
@@ -425,10 +435,12 @@ cmcs_status cmcs_create(const cmcs_config* cfg, const float* Phi, const float* y
   }
   c->hrow[0] = 0;
   c->horow[0] = 0;
+  // rows of the measurement vector: N_t, or 2 N_t real values [Re y_t; Im y_t] for Fourier
+  const int64_t rowmul = mask ? 2 : 1;
   for (int t = 0; t < c->T; ++t) {
-    c->horow[t + 1] = c->horow[t] + cfg->N[t];
-    c->hN[t] = cfg->N[t];
-    c->hNp[t] = round_up(cfg->N[t], kNAlign);
+    c->horow[t + 1] = c->horow[t] + rowmul * cfg->N[t];
+    c->hN[t] = rowmul * cfg->N[t];
+    c->hNp[t] = round_up(c->hN[t], kNAlign);
     c->hrow[t + 1] = c->hrow[t] + c->hNp[t];
   }
   for (int k = 0; k < c->C; ++k) c->hpi[k] = cfg->pi[k];
@@ -464,7 +476,7 @@ cmcs_status cmcs_create(const cmcs_config* cfg, const float* Phi, const float* y
   CKC(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device));
   const int64_t Dp = c->Dp, S = c->S, T = c->T, C = c->C, K = c->K;
   const int64_t ntiles = c->rows_total / 128;
-  CKC(dalloc(&c->phi, (size_t)(c->rows_total * Dp)));
+  if (!mask) CKC(dalloc(&c->phi, (size_t)(c->rows_total * Dp)));
   CKC(dalloc(&c->y, (size_t)c->rows_total));
   CKC(dalloc(&c->drow, (size_t)(T + 1)));
   CKC(dalloc(&c->dN, (size_t)T));
@@ -521,7 +533,7 @@ cmcs_status cmcs_create(const cmcs_config* cfg, const float* Phi, const float* y
   CKC(cudaMemsetAsync(c->opcount, 0, sizeof(int64_t) * T, c->stream));
 
   // zero everything that padding relies on
-  CKC(cudaMemsetAsync(c->phi, 0, sizeof(float) * c->rows_total * Dp, c->stream));
+  if (!mask) CKC(cudaMemsetAsync(c->phi, 0, sizeof(float) * c->rows_total * Dp, c->stream));
   CKC(cudaMemsetAsync(c->y, 0, sizeof(float) * c->rows_total, c->stream));
   for (void* p : {(void*)c->x, (void*)c->r, (void*)c->d, (void*)c->ad, (void*)c->xacc})
     CKC(cudaMemsetAsync(p, 0, sizeof(float) * S * Dp, c->stream));
@@ -534,10 +546,22 @@ cmcs_status cmcs_create(const cmcs_config* cfg, const float* Phi, const float* y
   CKC(cudaMemsetAsync(c->q, 0, sizeof(double) * T * C, c->stream));
   CKC(cudaMemsetAsync(c->stats, 0, sizeof(double) * 4, c->stream));
 
-  // Phi and y into the padded layout
+  // Phi and y into the padded layout (Fourier: the mask, spectra and stacked y)
   const cudaMemcpyKind kin = kind_in(on_device);
+  if (mask) {
+    CKC(cudaStreamSynchronize(c->stream));
+    const int e = dft_create(c, mask, y, on_device);
+    if (e == 5) {
+      set_err(c, "the mask's sampled frequencies per task differ from N");
+      return fail(CMCS_ERR_INVALID_ARG);
+    }
+    if (e != 0) {
+      set_err(c, "Fourier operator set-up failed (%d): %s", e, cudaGetErrorString(cudaGetLastError()));
+      return fail(CMCS_ERR_CUDA);
+    }
+  }
   int64_t src_row = 0;
-  for (int t = 0; t < c->T; ++t) {
+  for (int t = 0; !mask && t < c->T; ++t) {
     CKC(cudaMemcpy2DAsync(c->phi + c->hrow[t] * Dp, sizeof(float) * Dp, Phi + src_row * c->D,
                           sizeof(float) * c->D, sizeof(float) * c->D, (size_t)c->hN[t], kin,
                           c->stream));
@@ -566,7 +590,7 @@ cmcs_status cmcs_create(const cmcs_config* cfg, const float* Phi, const float* y
   }
   CKC(cudaStreamSynchronize(c->stream));
   CKC(cudaGetLastError());
-  if (cfg->autotune) {
+  if (cfg->autotune && !mask) {
     st = autotune(c);
     if (st != CMCS_OK) return fail(st);
   }
@@ -574,6 +598,28 @@ cmcs_status cmcs_create(const cmcs_config* cfg, const float* Phi, const float* y
 #undef CKC
   *out = h;
   return CMCS_OK;
+}
+
+}  // namespace
+
+cmcs_status cmcs_create(const cmcs_config* cfg, const float* Phi, const float* y, int on_device,
+                        void* stream, cmcs_ctx** out) {
+  if (!Phi) {
+    if (out) *out = nullptr;
+    set_err(nullptr, "invalid configuration or null input");
+    return CMCS_ERR_INVALID_ARG;
+  }
+  return create_ctx(cfg, Phi, y, nullptr, on_device, stream, out);
+}
+
+cmcs_status cmcs_create_dft(const cmcs_config* cfg, const uint8_t* mask, const float* y,
+                            int on_device, void* stream, cmcs_ctx** out) {
+  if (!mask) {
+    if (out) *out = nullptr;
+    set_err(nullptr, "invalid configuration or null input");
+    return CMCS_ERR_INVALID_ARG;
+  }
+  return create_ctx(cfg, nullptr, y, mask, on_device, stream, out);
 }
 
 void cmcs_destroy(cmcs_ctx* h) {
@@ -628,8 +674,14 @@ cmcs_status cmcs_profile_read(const cmcs_ctx* hc, cmcs_profile_data* out) {
   double fl = 0.0, by = 0.0;
   for (int t = 0; t < c->T; ++t) {
     const double n = (double)c->hN[t], D = (double)c->D, R = (double)c->R;
-    fl += (double)cnt[t] * 4.0 * n * D * R;
-    by += (double)cnt[t] * (sphi * n * D + 4.0 * R * (2.0 * D + 2.0 * n));
+    if (c->op == 1) {
+      // one complex FFT pair (5 D log2 D each) serves two systems; V read, Z written, mask
+      fl += (double)cnt[t] * R * (5.0 * D * (double)c->dft_L + 4.0 * D);
+      by += (double)cnt[t] * (8.0 * R * D + 4.0 * D);
+    } else {
+      fl += (double)cnt[t] * 4.0 * n * D * R;
+      by += (double)cnt[t] * (sphi * n * D + 4.0 * R * (2.0 * D + 2.0 * n));
+    }
   }
   out->operator_calls = c->prof_calls;
   out->operator_ms = c->prof_ms;
@@ -665,6 +717,10 @@ cmcs_status cmcs_set_alpha(cmcs_ctx* h, const float* alpha, int on_device, int64
 cmcs_status cmcs_set_data(cmcs_ctx* h, const float* Phi, const float* y, int on_device) {
   if (!h || !Phi || !y || (on_device != 0 && on_device != 1)) return CMCS_ERR_INVALID_ARG;
   Ctx* c = &h->c;
+  if (c->op == 1) {
+    set_err(c, "cmcs_set_data: not available for the Fourier operator");
+    return CMCS_ERR_UNSUPPORTED;
+  }
   const cudaMemcpyKind kin = kind_in(on_device);
   int64_t src_row = 0;
   for (int t = 0; t < c->T; ++t) {
@@ -683,6 +739,10 @@ cmcs_status cmcs_adjoint(cmcs_ctx* h, const float* g, float* dy, float* dalpha, 
                          int on_device) {
   if (!h || !g || !dy || !dalpha || (on_device != 0 && on_device != 1)) return CMCS_ERR_INVALID_ARG;
   Ctx* c = &h->c;
+  if (c->op == 1) {
+    set_err(c, "cmcs_adjoint: not available for the Fourier operator");
+    return CMCS_ERR_UNSUPPORTED;
+  }
   const size_t D = c->D, Dp = c->Dp, T = c->T, C = c->C;
   // the adjoint systems A_tc lambda_tc = g_tc as a narrow problem: R = C columns per task, K = 0,
   // FP32 operator and compensated refinement; its solution goes to adj_x, not to the means

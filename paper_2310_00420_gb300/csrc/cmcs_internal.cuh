@@ -148,6 +148,15 @@ struct Ctx {
 
   // tensor-core operator (precision 1 and 2); null otherwise
   void* tc;
+  // structured sensing of Sec. 4 (op == 1): Phi_t = Omega_t F applied by FFT (kernels_dft.cu)
+  int op;
+  int dft_L;              // log2 D
+  float* dft_mask;        // [T][D] symmetrised mask in bit-reversed order
+  void* dft_tw32;         // float2 [D/2] twiddles
+  void* dft_tw64;         // double2 [D/2] twiddles
+  int* dft_freq;          // [sum N_t] sampled frequencies, ascending per task
+  int64_t* dft_off;       // [T+1]
+  float* dft_y;           // [sum N_t][2] measured coefficients
   void *dhi, *dlo;     // [S][Dp] BF16 hi and lo parts of the CG direction d (tensor-core path)
 
   char err[512];
@@ -173,6 +182,15 @@ cudaError_t launch_resid_norm(Ctx* c);
 // W[t][j'][n] = (Phi_t V_{t, j' * jstride})[n] for j' < Rc (FP32 SIMT pass 1 only)
 // W = Phi V for Rc columns (systems j = j' * jstride); with Wlo, as a compensated pair W + Wlo
 cudaError_t launch_phi_v(Ctx* c, const float* V, float* W, float* Wlo, int Rc, int jstride);
+// structured (Fourier) operator (kernels_dft.cu)
+constexpr int kDftMaxD = 8192;     // one pair's FP64 spectrum in shared memory
+bool dft_size_ok(int D);
+int dft_create(Ctx* c, const uint8_t* mask, const float* y, int on_device);
+void dft_destroy(Ctx* c);
+cudaError_t launch_dft_apply(Ctx* c, const float* V, float* Z, int with_dots);
+cudaError_t launch_dft_residual(Ctx* c, const float* X, const float* Bext, float* Rout,
+                                int all_systems, int means_only);
+cudaError_t launch_dft_b0(Ctx* c);
 // adjoint gradients (adjoint.cu)
 cudaError_t launch_adj_dy(Ctx* c, const float* Wl, const float* Wl_lo, float* dy);
 cudaError_t launch_adj_dalpha(Ctx* c, const float* lam, float* dalpha);

@@ -476,13 +476,13 @@ cudaError_t launch_cg_update(Ctx* c, int record) {
 #define UPD(NV)                                                                                  \
   if (c->tc != nullptr)                                                                          \
     k_cg_update<NV, true><<<c->S, 256, 0, c->stream>>>(                                          \
-        c->x, c->r, c->d, c->ad, c->part, c->alpha, c->Dp / 128, c->rr, c->bb, c->steps,        \
+        c->x, c->r, c->d, c->ad, c->part, c->alpha, c->op == 1 ? 1 : c->Dp / 128, c->rr, c->bb, c->steps,        \
         c->active, c->task_active, c->counters, c->gam, c->xi, c->psteps, record, c->R, c->K,    \
         c->C, c->Dp, c->S, c->U, tol2, static_cast<__nv_bfloat16*>(c->dhi),                      \
         static_cast<__nv_bfloat16*>(c->dlo));                                                    \
   else                                                                                           \
     k_cg_update<NV, false><<<c->S, 256, 0, c->stream>>>(                                         \
-        c->x, c->r, c->d, c->ad, c->part, c->alpha, c->Dp / 128, c->rr, c->bb, c->steps,        \
+        c->x, c->r, c->d, c->ad, c->part, c->alpha, c->op == 1 ? 1 : c->Dp / 128, c->rr, c->bb, c->steps,        \
         c->active, c->task_active, c->counters, c->gam, c->xi, c->psteps, record, c->R, c->K,    \
         c->C, c->Dp, c->S, c->U, tol2, static_cast<__nv_bfloat16*>(c->dhi),                      \
         static_cast<__nv_bfloat16*>(c->dlo))
@@ -512,6 +512,7 @@ cudaError_t launch_sest(Ctx* c) {
 }
 
 cudaError_t launch_b0(Ctx* c) {
+  if (c->op == 1) return launch_dft_b0(c);
   c->launches += 1;
   dim3 grid(c->Dp / 128, c->T);
   k_b0<<<grid, 128, 0, c->stream>>>(c->phi, c->y, c->drow, c->b0hi, c->b0lo, c->Dp, c->beta);

@@ -474,6 +474,7 @@ P2Args base_args(Ctx* c) {
 }  // namespace
 
 cudaError_t launch_operator(Ctx* c, const float* V, float* Z, int with_dots) {
+  if (c->op == 1) return launch_dft_apply(c, V, Z, with_dots);
   if (c->tc != nullptr) return tc_operator(c, V, Z, with_dots);
   const int* mask = with_dots ? c->task_active : nullptr;
   const int tn = c->tn_plain > 0 ? c->tn_plain : pick_tn(c->R, 9);
@@ -510,6 +511,7 @@ cudaError_t launch_phi_v(Ctx* c, const float* V, float* W, float* Wlo, int Rc, i
 
 cudaError_t launch_residual(Ctx* c, const float* X, const float* Bext, float* Rout,
                             int all_systems, int means_only) {
+  if (c->op == 1) return launch_dft_residual(c, X, Bext, Rout, all_systems, means_only);
   const int Rc = means_only ? c->C : c->R;
   const int js = means_only ? c->K + 1 : 1;
   const int tn = c->tn_ds > 0 ? c->tn_ds : pick_tn(Rc, 4);
