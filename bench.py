@@ -168,8 +168,11 @@ def _workload(name: str, seed: int, tasks: int = 0):
 def _oracle_pair(wl, alpha, em_iter, t, c, refine_tol, refine_max):
     """The FP64 oracle's E-step for one (task, cluster) pair: K + 1 CG solves + refinement."""
     from oracle import cofem
-    P = [wl.phi(t).astype(np.float64)]
-    Y = [wl.yt(t).astype(np.float64)]
+    if hasattr(wl, "phi_real"):          # Fourier workload: the real-stacked dense matrix
+        P, Y = [wl.phi_real(t)], [wl.y_real(t)]
+    else:
+        P = [wl.phi(t).astype(np.float64)]
+        Y = [wl.yt(t).astype(np.float64)]
     t0 = time.perf_counter()
     o = cofem.cofem_estep(P, Y, np.asarray(alpha[c:c + 1], np.float64), np.array([1.0]), wl.beta,
                           wl.K, wl.seed, em_iter, wl.cg_tol, wl.cg_max_iter, tasks=[t],
@@ -222,12 +225,19 @@ def run_ours(a):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     wl = _workload(a.workload, rank, a.tasks)
+    fourier = hasattr(wl, "mask")        # Phi_t = Omega_t F, applied by FFT (FP32 only)
+    if fourier:
+        a.precision = "fp32"
+        a.no_fp32_form = True
     kw = dict(C=wl.C, K=wl.K, beta=wl.beta, pi=wl.pi, cg_max_iter=wl.cg_max_iter, cg_tol=wl.cg_tol,
               seed=wl.seed, precision=a.precision, refine_max=a.refine_max, refine_tol=a.refine_tol,
               schedule=a.schedule, graphs=not a.no_graphs)
-    Phi_d = torch.from_numpy(wl.Phi).cuda()
-    y_d = torch.from_numpy(wl.y).cuda()
-    ctx = cmcs.Context(Phi_d, y_d, wl.N, **kw)
+    if fourier:
+        ctx = cmcs.Context.from_fourier(wl, device=True, **kw)
+    else:
+        Phi_d = torch.from_numpy(wl.Phi).cuda()
+        y_d = torch.from_numpy(wl.y).cuda()
+        ctx = cmcs.Context(Phi_d, y_d, wl.N, **kw)
     for _ in range(a.warmup):
         ctx.em_iter(1)
     ctx.profile(True)
@@ -259,7 +269,18 @@ def run_ours(a):
     peaks, src = _peaks()
     op_tflops = prof["operator_flops"] / (prof["operator_ms"] * 1e-3) / 1e12 if prof["operator_ms"] else 0.0
     op_gbs = prof["operator_bytes"] / (prof["operator_ms"] * 1e-3) / 1e9 if prof["operator_ms"] else 0.0
-    if a.precision == "fp32":
+    if fourier:
+        # FFT operator: one CTA per pair of systems, spectra in shared memory; its algorithmic
+        # bytes (V read, Z written) at the measured HBM bandwidth
+        roof = {"bound": "hbm", "achieved": op_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": op_gbs / peaks["hbm_gbs"], "traffic": None,
+                "kernel": "operator (k_dft_apply, FP32 FFT of system pairs in shared memory)",
+                "peak_source": f"MEASURED_PEAKS.json ({src}): HBM {peaks['hbm_gbs']} GB/s",
+                "per_launch_flops": prof["operator_flops"] / max(1, prof["operator_calls"]),
+                "per_launch_bytes": prof["operator_bytes"] / max(1, prof["operator_calls"]),
+                "per_launch_ms": prof["operator_ms"] / max(1, prof["operator_calls"]),
+                "fp32_tflops_achieved": op_tflops}
+    elif a.precision == "fp32":
         roof = {"bound": "alu", "achieved": op_tflops, "peak": FP32_ALU_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": op_tflops / FP32_ALU_PEAK_TFLOPS,
                 "traffic": None,
@@ -319,8 +340,13 @@ def run_ours(a):
     # (H2D inside), set alpha, one EM iteration, read q, alpha and the reconstructions (D2H)
     e2e = None
     if not a.no_e2e:
-        Phi_h = torch.from_numpy(wl.Phi).pin_memory()
-        y_h = torch.from_numpy(wl.y).pin_memory()
+        if fourier:
+            Phi_h = torch.from_numpy(np.ascontiguousarray(wl.mask.astype(np.uint8))).pin_memory()
+            y_h = torch.from_numpy(np.ascontiguousarray(
+                np.stack([wl.y.real, wl.y.imag], axis=-1).astype(np.float32))).pin_memory()
+        else:
+            Phi_h = torch.from_numpy(wl.Phi).pin_memory()
+            y_h = torch.from_numpy(wl.y).pin_memory()
         alpha_h = torch.from_numpy(ctx.read(cmcs.OUT_ALPHA)).pin_memory()
         it = ctx.summary()["em_iters_done"]
         outs = {"q": torch.empty((wl.T, wl.C), dtype=torch.float64).pin_memory(),
@@ -330,7 +356,10 @@ def run_ours(a):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(a.steps):
-            c2 = cmcs.Context(Phi_h, y_h, wl.N, **kw)
+            if fourier:
+                c2 = cmcs.Context(None, y_h, wl.N, mask=Phi_h, **kw)
+            else:
+                c2 = cmcs.Context(Phi_h, y_h, wl.N, **kw)
             c2.set_alpha(alpha_h, it)
             c2.em_iter(1)
             c2.read(cmcs.OUT_Q, out=outs["q"])
@@ -341,7 +370,8 @@ def run_ours(a):
         barrier()
         e2e_value, _ = aggregate((time.perf_counter() - t0) * 1e3, a.steps, world)
         e2e = {"value": e2e_value, "unit": UNIT,
-               "h2d_bytes_per_step": int(wl.Phi.nbytes + wl.y.nbytes + wl.C * wl.D * 4),
+               "h2d_bytes_per_step": int(Phi_h.numel() * Phi_h.element_size() +
+                                         y_h.numel() * y_h.element_size() + wl.C * wl.D * 4),
                "d2h_bytes_per_step": int(sum(v.numel() * v.element_size() for v in outs.values()))}
 
     ctx.close()
@@ -350,7 +380,8 @@ def run_ours(a):
         """EM iterations/s of another form on the same workload (same warm-up and steps)."""
         kw2 = dict(kw)
         kw2.update(over)
-        c3 = cmcs.Context(Phi_d, y_d, wl.N, **kw2)
+        c3 = (cmcs.Context.from_fourier(wl, device=True, **kw2) if fourier
+              else cmcs.Context(Phi_d, y_d, wl.N, **kw2))
         for _ in range(a.warmup):
             c3.em_iter(1)
         c3.profile(True)
@@ -385,7 +416,9 @@ def run_ours(a):
                                        f"K={wl.K} tol={wl.cg_tol} max_iter={wl.cg_max_iter}",
                            "precision": a.precision, "refine_max": a.refine_max,
                            "refine_tol": a.refine_tol, "parallelism": f"{world} replicas",
-                           "l2": f"inputs larger than L2 (Phi {wl.Phi.nbytes / 1e9:.1f} GB)"},
+                           "l2": (f"inputs larger than L2 (CG vectors {5 * systems * wl.D * 4 / 1e9:.1f} GB)"
+                                  if fourier else
+                                  f"inputs larger than L2 (Phi {wl.Phi.nbytes / 1e9:.1f} GB)")},
                 "cg_solves_per_s": value * systems,
                 "cg_steps_mean": summ["cg_steps_mean"], "cg_capped": summ["cg_capped"],
                 "refine_sweeps_max": summ["refine_sweeps_max"],

@@ -10,10 +10,11 @@
 // complex FFT of v1 + i v2 therefore applies the operator to two systems of a task at once:
 // the real part of the result belongs to v1, the imaginary part to v2.
 //
-// One CTA per pair of systems holds the pair's spectrum in shared memory: a radix-2
+// One CTA per pair of systems holds the pair's spectrum in shared memory: a
 // decimation-in-frequency FFT (natural order in, bit-reversed out), the mask multiply (the
 // mask is stored in bit-reversed order), and a decimation-in-time inverse (bit-reversed in,
-// natural out), so no permutation pass is needed.  The CG operator runs in FP32; the
+// natural out), so no permutation pass is needed.  Each pass over shared memory applies three
+// radix-2 stages in registers (eight elements per thread).  The CG operator runs in FP32; the
 // refinement residual b - A x runs the same transform in FP64 (the DFT is unitary, so its
 // rounding error stays ~log2(D) units of FP64, below the double-single residual of the dense
 // path).  Twiddles come from tables computed on the host in FP64.
@@ -48,20 +49,113 @@ __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_doub
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
 
+// Shared-memory index with one pad element per 32: the passes with small spacing would
+// otherwise hit the same banks with power-of-two strides.
+__device__ __forceinline__ int pad(int i) { return i + (i >> 5); }
+
+template <typename CT> __device__ __forceinline__ CT cmake(double x, double y);
+template <> __device__ __forceinline__ float2 cmake<float2>(double x, double y) {
+  return make_float2((float)x, (float)y);
+}
+template <> __device__ __forceinline__ double2 cmake<double2>(double x, double y) {
+  return make_double2(x, y);
+}
+
+// e^{-2 pi i k / n} for n in {2, 4, 8}, k < n / 2
+template <typename CT>
+__device__ __forceinline__ CT root_of_unity(int n, int k) {
+  const double h = 0.70710678118654752440;       // sqrt(2) / 2
+  if (k == 0) return cmake<CT>(1.0, 0.0);
+  if (n == 4 || (n == 8 && k == 2)) return cmake<CT>(0.0, -1.0);
+  if (k == 1) return cmake<CT>(h, -h);
+  return cmake<CT>(-h, -h);
+}
+
+// Radix-2 butterflies, R stages per pass over shared memory: each thread loads 2^R elements
+// spaced sub apart, applies the R stages in registers and stores them back.  Within a pass
+// every twiddle is w^(2^q) times an 8th, 4th or 2nd root of unity, with w = W_span^j for the
+// group's offset j: one table load per group and pass.
+// Decimation in frequency, stages of half-size 2^s down to 2^(s-R+1):
+template <typename CT, int R>
+__device__ __forceinline__ void dif_pass(CT* X, const CT* __restrict__ tw, int D, int s) {
+  const int lsub = s - R + 1, sub = 1 << lsub, span = 1 << (s + 1);
+  for (int g = threadIdx.x; g < (D >> R); g += blockDim.x) {
+    const int j = g & (sub - 1);
+    const int base = (g >> lsub) * span + j;
+    CT wq = tw[j * (D / span)];
+    CT x[1 << R];
+#pragma unroll
+    for (int m = 0; m < (1 << R); ++m) x[m] = X[pad(base + m * sub)];
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      const int step = 1 << (R - 1 - q);
+#pragma unroll
+      for (int m = 0; m < (1 << R); ++m) {
+        if (m & step) continue;
+        const int k = m & (step - 1);
+        const CT t = k == 0 ? wq : cmul(wq, root_of_unity<CT>(1 << (R - q), k));
+        const CT u = x[m], v = x[m + step];
+        x[m] = cadd(u, v);
+        x[m + step] = cmul(csub(u, v), t);
+      }
+      wq = cmul(wq, wq);
+    }
+#pragma unroll
+    for (int m = 0; m < (1 << R); ++m) X[pad(base + m * sub)] = x[m];
+  }
+  __syncthreads();
+}
+
+// decimation in time with conjugate twiddles, stages of half-size 2^s up to 2^(s+R-1)
+template <typename CT, int R>
+__device__ __forceinline__ void dit_pass(CT* X, const CT* __restrict__ tw, int D, int s) {
+  const int sub = 1 << s, span = 1 << (s + R);
+  for (int g = threadIdx.x; g < (D >> R); g += blockDim.x) {
+    const int j = g & (sub - 1);
+    const int base = (g >> s) * span + j;
+    CT pw[R];                                     // w, w^2, w^4 with w = W_span^j
+    pw[0] = tw[j * (D / span)];
+#pragma unroll
+    for (int q = 1; q < R; ++q) pw[q] = cmul(pw[q - 1], pw[q - 1]);
+    CT x[1 << R];
+#pragma unroll
+    for (int m = 0; m < (1 << R); ++m) x[m] = X[pad(base + m * sub)];
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      const int step = 1 << q;
+#pragma unroll
+      for (int m = 0; m < (1 << R); ++m) {
+        if (m & step) continue;
+        const int k = m & (step - 1);
+        const CT t = k == 0 ? pw[R - 1 - q] : cmul(pw[R - 1 - q], root_of_unity<CT>(1 << (q + 1), k));
+        const CT u = x[m];
+        const CT v = cmulc(x[m + step], t);
+        x[m] = cadd(u, v);
+        x[m + step] = csub(u, v);
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < (1 << R); ++m) X[pad(base + m * sub)] = x[m];
+  }
+  __syncthreads();
+}
+
 // forward DFT X_k = sum_n x_n e^{-2 pi i k n / D} in place: natural order in, bit-reversed out;
 // tw[k] = e^{-2 pi i k / D}, k < D/2
 template <typename CT>
 __device__ void fft_dif(CT* X, const CT* __restrict__ tw, int D, int L) {
-  for (int s = L - 1; s >= 0; --s) {          // butterflies of half-size 2^s
-    const int len = 1 << s, tstep = D >> (s + 1);
-    for (int b = threadIdx.x; b < (D >> 1); b += blockDim.x) {
-      const int j = b & (len - 1);
-      const int i = ((b >> s) << (s + 1)) + j;
-      const CT u = X[i], v = X[i + len];
-      X[i] = cadd(u, v);
-      X[i + len] = cmul(csub(u, v), tw[j * tstep]);
+  int s = L - 1;
+  while (s >= 0) {
+    if (s >= 2) {
+      dif_pass<CT, 3>(X, tw, D, s);
+      s -= 3;
+    } else if (s == 1) {
+      dif_pass<CT, 2>(X, tw, D, s);
+      s -= 2;
+    } else {
+      dif_pass<CT, 1>(X, tw, D, s);
+      s -= 1;
     }
-    __syncthreads();
   }
 }
 
@@ -69,17 +163,18 @@ __device__ void fft_dif(CT* X, const CT* __restrict__ tw, int D, int L) {
 // order out
 template <typename CT>
 __device__ void ifft_dit(CT* X, const CT* __restrict__ tw, int D, int L) {
-  for (int s = 0; s < L; ++s) {
-    const int len = 1 << s, tstep = D >> (s + 1);
-    for (int b = threadIdx.x; b < (D >> 1); b += blockDim.x) {
-      const int j = b & (len - 1);
-      const int i = ((b >> s) << (s + 1)) + j;
-      const CT u = X[i];
-      const CT v = cmulc(X[i + len], tw[j * tstep]);
-      X[i] = cadd(u, v);
-      X[i + len] = csub(u, v);
+  int s = 0;
+  while (s < L) {
+    if (L - s >= 3) {
+      dit_pass<CT, 3>(X, tw, D, s);
+      s += 3;
+    } else if (L - s == 2) {
+      dit_pass<CT, 2>(X, tw, D, s);
+      s += 2;
+    } else {
+      dit_pass<CT, 1>(X, tw, D, s);
+      s += 1;
     }
-    __syncthreads();
   }
 }
 
@@ -122,13 +217,14 @@ k_dft_apply(const float* __restrict__ V, float* __restrict__ Z, float* __restric
   const int64_t s1 = (int64_t)t * R + j1, s2 = has2 ? s1 + 1 : s1;
   const float* v1 = V + s1 * Dp;
   const float* v2 = V + s2 * Dp;
-  for (int i = threadIdx.x; i < D; i += blockDim.x) Xf[i] = make_float2(v1[i], has2 ? v2[i] : 0.f);
+  for (int i = threadIdx.x; i < D; i += blockDim.x) Xf[pad(i)] = make_float2(v1[i], has2 ? v2[i] : 0.f);
   __syncthreads();
   fft_dif(Xf, tw, D, L);
   const float* m = mask_br + (int64_t)t * D;
   for (int i = threadIdx.x; i < D; i += blockDim.x) {
     const float mk = m[i];
-    Xf[i] = make_float2(Xf[i].x * mk, Xf[i].y * mk);
+    const float2 v = Xf[pad(i)];
+    Xf[pad(i)] = make_float2(v.x * mk, v.y * mk);
   }
   __syncthreads();
   ifft_dit(Xf, tw, D, L);
@@ -138,12 +234,13 @@ k_dft_apply(const float* __restrict__ V, float* __restrict__ Z, float* __restric
   float dot1 = 0.f, dot2 = 0.f;
   for (int i = threadIdx.x; i < D; i += blockDim.x) {
     const float x1 = v1[i];
-    const float z1 = fmaf(scale, Xf[i].x, a1[i] * x1);
+    const float2 xf = Xf[pad(i)];
+    const float z1 = fmaf(scale, xf.x, a1[i] * x1);
     Z[s1 * Dp + i] = z1;
     dot1 = fmaf(x1, z1, dot1);
     if (has2) {
       const float x2 = v2[i];
-      const float z2 = fmaf(scale, Xf[i].y, a2[i] * x2);
+      const float z2 = fmaf(scale, xf.y, a2[i] * x2);
       Z[s2 * Dp + i] = z2;
       dot2 = fmaf(x2, z2, dot2);
     }
@@ -182,13 +279,14 @@ k_dft_residual(const float* __restrict__ X, const float* __restrict__ Bext,
   const float* x1 = X + s1 * Dp;
   const float* x2 = X + s2 * Dp;
   for (int i = threadIdx.x; i < D; i += blockDim.x)
-    Xd[i] = make_double2(on1 ? (double)x1[i] : 0.0, on2 ? (double)x2[i] : 0.0);
+    Xd[pad(i)] = make_double2(on1 ? (double)x1[i] : 0.0, on2 ? (double)x2[i] : 0.0);
   __syncthreads();
   fft_dif(Xd, tw, D, L);
   const float* m = mask_br + (int64_t)t * D;
   for (int i = threadIdx.x; i < D; i += blockDim.x) {
     const double mk = (double)m[i];
-    Xd[i] = make_double2(Xd[i].x * mk, Xd[i].y * mk);
+    const double2 v = Xd[pad(i)];
+    Xd[pad(i)] = make_double2(v.x * mk, v.y * mk);
   }
   __syncthreads();
   ifft_dit(Xd, tw, D, L);
@@ -216,7 +314,8 @@ k_dft_residual(const float* __restrict__ X, const float* __restrict__ Bext,
           b = ((bits >> (i & 31)) & 1u) ? -1.0 : 1.0;
         }
         const double xv = (double)(q == 0 ? x1[i] : x2[i]);
-        const double z = fma(scale, q == 0 ? Xd[i].x : Xd[i].y, (double)(q == 0 ? a1[i] : a2[i]) * xv);
+        const double2 xd = Xd[pad(i)];
+        const double z = fma(scale, q == 0 ? xd.x : xd.y, (double)(q == 0 ? a1[i] : a2[i]) * xv);
         rv = b - z;
       }
       Rout[s * Dp + i] = (float)rv;
@@ -233,18 +332,18 @@ k_dft_b0(const float2* __restrict__ y, const int* __restrict__ freq,
          const double2* __restrict__ tw, int Dp, int D, int L, double beta) {
   extern __shared__ double2 Xd[];
   const int t = blockIdx.x;
-  for (int i = threadIdx.x; i < D; i += blockDim.x) Xd[i] = make_double2(0.0, 0.0);
+  for (int i = threadIdx.x; i < D; i += blockDim.x) Xd[pad(i)] = make_double2(0.0, 0.0);
   __syncthreads();
   for (int64_t q = off[t] + threadIdx.x; q < off[t + 1]; q += blockDim.x) {
     const int k = freq[q];
     const int pos = (int)(__brev((unsigned)k) >> (32 - L));
-    Xd[pos] = make_double2((double)y[q].x, (double)y[q].y);
+    Xd[pad(pos)] = make_double2((double)y[q].x, (double)y[q].y);
   }
   __syncthreads();
   ifft_dit(Xd, tw, D, L);
   const double scale = beta / sqrt((double)D);
   for (int i = threadIdx.x; i < D; i += blockDim.x) {
-    const double b = scale * Xd[i].x;
+    const double b = scale * Xd[pad(i)].x;
     const float hi = (float)b;
     b0hi[(int64_t)t * Dp + i] = hi;
     b0lo[(int64_t)t * Dp + i] = (float)(b - (double)hi);
@@ -320,7 +419,7 @@ int dft_create(Ctx* c, const uint8_t* mask, const float* y, int on_device) {
                       sizeof(float), (size_t)n, kin) == cudaSuccess;
   }
   if (!ok) return 3;
-  const int sm32 = (int)sizeof(float2) * D, sm64 = (int)sizeof(double2) * D;
+  const int sm32 = (int)sizeof(float2) * (D + D / 32), sm64 = (int)sizeof(double2) * (D + D / 32);
   if (cudaFuncSetAttribute(k_dft_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, sm32) != cudaSuccess ||
       cudaFuncSetAttribute(k_dft_residual, cudaFuncAttributeMaxDynamicSharedMemorySize, sm64) != cudaSuccess ||
       cudaFuncSetAttribute(k_dft_b0, cudaFuncAttributeMaxDynamicSharedMemorySize, sm64) != cudaSuccess)
@@ -337,7 +436,7 @@ void dft_destroy(Ctx* c) {
 cudaError_t launch_dft_apply(Ctx* c, const float* V, float* Z, int with_dots) {
   const int npair = (c->R + 1) / 2;
   c->launches += 1;
-  k_dft_apply<<<c->T * npair, kDftThreads, sizeof(float2) * c->D, c->stream>>>(
+  k_dft_apply<<<c->T * npair, kDftThreads, sizeof(float2) * (c->D + c->D / 32), c->stream>>>(
       V, Z, with_dots ? c->part : nullptr, c->dft_mask, static_cast<const float2*>(c->dft_tw32),
       c->alpha, with_dots ? c->task_active : nullptr,
       c->prof_on ? reinterpret_cast<unsigned long long*>(c->opcount) : nullptr, c->R, c->K, c->Dp,
@@ -351,7 +450,7 @@ cudaError_t launch_dft_residual(Ctx* c, const float* X, const float* Bext, float
   const int js = means_only ? c->K + 1 : 1;
   const int npair = (Rc + 1) / 2;
   c->launches += 1;
-  k_dft_residual<<<c->T * npair, kDftThreads, sizeof(double2) * c->D, c->stream>>>(
+  k_dft_residual<<<c->T * npair, kDftThreads, sizeof(double2) * (c->D + c->D / 32), c->stream>>>(
       X, Bext, c->b0hi, c->b0lo, Rout, (Bext || all_systems) ? nullptr : c->ractive, c->dft_mask,
       static_cast<const double2*>(c->dft_tw64), c->alpha, c->R, c->K, c->C, c->Dp, c->D, c->dft_L,
       Rc, js, npair, c->beta, c->seed, c->em_iter);
@@ -360,7 +459,7 @@ cudaError_t launch_dft_residual(Ctx* c, const float* X, const float* Bext, float
 
 cudaError_t launch_dft_b0(Ctx* c) {
   c->launches += 1;
-  k_dft_b0<<<c->T, kDftThreads, sizeof(double2) * c->D, c->stream>>>(
+  k_dft_b0<<<c->T, kDftThreads, sizeof(double2) * (c->D + c->D / 32), c->stream>>>(
       reinterpret_cast<const float2*>(c->dft_y), c->dft_freq, c->dft_off, c->b0hi, c->b0lo,
       static_cast<const double2*>(c->dft_tw64), c->Dp, c->D, c->dft_L, c->beta);
   return cudaGetLastError();
