@@ -270,11 +270,12 @@ def run_ours(a):
     op_tflops = prof["operator_flops"] / (prof["operator_ms"] * 1e-3) / 1e12 if prof["operator_ms"] else 0.0
     op_gbs = prof["operator_bytes"] / (prof["operator_ms"] * 1e-3) / 1e9 if prof["operator_ms"] else 0.0
     if fourier:
-        # FFT operator: one CTA per pair of systems, spectra in shared memory; its algorithmic
-        # bytes (V read, Z written) at the measured HBM bandwidth
+        # FFT operator fused with the CG update: one CTA per pair of systems, spectra in shared
+        # memory; its algorithmic bytes (d, x, r read and written) at the measured HBM bandwidth
         roof = {"bound": "hbm", "achieved": op_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": op_gbs / peaks["hbm_gbs"], "traffic": None,
-                "kernel": "operator (k_dft_apply, FP32 FFT of system pairs in shared memory)",
+                "kernel": "CG step (k_dft_cg_step: FP32 FFT operator of system pairs in shared memory "
+                          "fused with the CG update)",
                 "peak_source": f"MEASURED_PEAKS.json ({src}): HBM {peaks['hbm_gbs']} GB/s",
                 "per_launch_flops": prof["operator_flops"] / max(1, prof["operator_calls"]),
                 "per_launch_bytes": prof["operator_bytes"] / max(1, prof["operator_calls"]),

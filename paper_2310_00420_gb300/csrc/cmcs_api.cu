@@ -108,7 +108,7 @@ static_assert(kCheckEvery <= kProfEvents, "events of one chunk");
 
 // operator application, bracketed by profiling events when enabled (pair prof_nev of the
 // current chunk of CG steps)
-cudaError_t timed_operator(Ctx* c) {
+cudaError_t timed_operator(Ctx* c, int record) {
   const bool ev = c->prof_on && c->prof_nev < kProfEvents;
   // while capturing, external records become event-record nodes of the graph
   const unsigned flags = c->capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
@@ -116,7 +116,8 @@ cudaError_t timed_operator(Ctx* c) {
     cudaError_t er = cudaEventRecordWithFlags(c->prof_ev[2 * c->prof_nev], c->stream, flags);
     if (er != cudaSuccess) return er;
   }
-  cudaError_t e = launch_operator(c, c->d, c->ad, 1);
+  // Fourier: the operator and the CG update are one kernel
+  cudaError_t e = c->op == 1 ? launch_dft_cg_step(c, record) : launch_operator(c, c->d, c->ad, 1);
   if (ev && e == cudaSuccess) {
     e = cudaEventRecordWithFlags(c->prof_ev[2 * c->prof_nev + 1], c->stream, flags);
     c->prof_nev++;
@@ -140,8 +141,8 @@ void fold_events(Ctx* c) {
 // n CG steps (operator + update) launched directly
 cmcs_status cg_steps_direct(Ctx* c, int record, int n) {
   for (int i = 0; i < n; ++i) {
-    CK(timed_operator(c));
-    CK(launch_cg_update(c, record));
+    CK(timed_operator(c, record));
+    if (c->op != 1) CK(launch_cg_update(c, record));
     c->op_applies++;
   }
   return CMCS_OK;
@@ -675,9 +676,10 @@ cmcs_status cmcs_profile_read(const cmcs_ctx* hc, cmcs_profile_data* out) {
   for (int t = 0; t < c->T; ++t) {
     const double n = (double)c->hN[t], D = (double)c->D, R = (double)c->R;
     if (c->op == 1) {
-      // one complex FFT pair (5 D log2 D each) serves two systems; V read, Z written, mask
-      fl += (double)cnt[t] * R * (5.0 * D * (double)c->dft_L + 4.0 * D);
-      by += (double)cnt[t] * (8.0 * R * D + 4.0 * D);
+      // one CG step fused with the operator: one complex FFT pair (5 D log2 D each) per two
+      // systems plus the update; d, x, r read, x, r, d written, the mask
+      fl += (double)cnt[t] * R * (5.0 * D * (double)c->dft_L + 12.0 * D);
+      by += (double)cnt[t] * (24.0 * R * D + 4.0 * D);
     } else {
       fl += (double)cnt[t] * 4.0 * n * D * R;
       by += (double)cnt[t] * (sphi * n * D + 4.0 * R * (2.0 * D + 2.0 * n));

@@ -191,6 +191,8 @@ cudaError_t launch_dft_apply(Ctx* c, const float* V, float* Z, int with_dots);
 cudaError_t launch_dft_residual(Ctx* c, const float* X, const float* Bext, float* Rout,
                                 int all_systems, int means_only);
 cudaError_t launch_dft_b0(Ctx* c);
+// one whole CG step (operator and update) for every active system of a Fourier context
+cudaError_t launch_dft_cg_step(Ctx* c, int record);
 // adjoint gradients (adjoint.cu)
 cudaError_t launch_adj_dy(Ctx* c, const float* Wl, const float* Wl_lo, float* dy);
 cudaError_t launch_adj_dalpha(Ctx* c, const float* lam, float* dalpha);
