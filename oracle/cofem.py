@@ -26,6 +26,9 @@ Readings where the paper leaves a choice (each applied identically on the GPU):
   cluster whose total responsibility is below 1e-300 keeps its previous alpha.
 * The returned responsibilities and means are those of the last E-step (Alg. 2 returns
   mu_{t, a_t} after the loop); ties in argmax go to the lowest cluster index.
+* Variants, off by default: learned priors (``pi_update``, floored at 1e-300 so that log pi
+  stays finite), probes shared across clusters, and Jacobi-preconditioned CG (``pcg``, whose
+  stopping test is Alg. 1's on the symmetrically scaled system); see ``cofem_estep``.
 """
 from __future__ import annotations
 
@@ -110,6 +113,22 @@ def log_likelihood(ell_tc: np.ndarray, pi: np.ndarray, consts: np.ndarray) -> fl
     return float(np.mean(lse - consts))
 
 
+def pi_update(q: np.ndarray, pi_floor: float = 1e-300) -> np.ndarray:
+    """Cluster priors learned by EM (Sec. 2 notes that pi may be learned): the maximiser of
+    sum_t sum_c q_tc log pi_c over the simplex, pi_c = (1/T) sum_t q_tc.  Reading: a cluster
+    whose share underflows is floored at pi_floor and the priors are renormalised, so that
+    log pi stays finite (the cluster then stays empty, as it would in exact arithmetic)."""
+    pi = np.maximum(np.asarray(q, dtype=np.float64).mean(axis=0), pi_floor)
+    return pi / pi.sum()
+
+
+def jacobi_diag(Phi_t: np.ndarray, beta: float, alpha_c: np.ndarray) -> np.ndarray:
+    """The diagonal m of A = beta Phi_t^T Phi_t + diag(alpha_c) (Eq. 7):
+    m_d = beta sum_n Phi_nd^2 + alpha_d, the Jacobi preconditioner M = diag(m)."""
+    P = np.asarray(Phi_t, dtype=np.float64)
+    return beta * np.einsum("nd,nd->d", P, P) + np.asarray(alpha_c, dtype=np.float64)
+
+
 def m_step(q: np.ndarray, mu: np.ndarray, s: np.ndarray, alpha_prev: np.ndarray,
            alpha_min: float = 1e-10, alpha_max: float = 1e10) -> np.ndarray:
     """Eq. 5: alpha_cd = sum_t q_tc / sum_t q_tc (mu_tcd^2 + s_tcd), with the clamps above.
@@ -192,11 +211,70 @@ def cg(apply, B: np.ndarray, tol: float, max_iter: int, steps: np.ndarray = None
     return CGResult(X, gam, xi, U, rel)
 
 
+def pcg(apply, B: np.ndarray, minv: np.ndarray, tol: float, max_iter: int,
+        steps: np.ndarray = None) -> CGResult:
+    """Alg. 1 with a diagonal (Jacobi) preconditioner M = diag(m), minv = 1/m of shape [D]:
+    x_1 = 0, r_1 = b, z_1 = M^-1 r_1, d_1 = z_1 and, per step,
+        gamma_u = r_u^T z_u / d_u^T A d_u,   x_{u+1} = x_u + gamma_u d_u,
+        r_{u+1} = r_u - gamma_u A d_u,       z_{u+1} = M^-1 r_{u+1},
+        xi_u = r_{u+1}^T z_{u+1} / r_u^T z_u, d_{u+1} = z_{u+1} + xi_u d_u.
+    Substituting x = M^-1/2 xh, r = M^1/2 rh, d = M^-1/2 dh turns these into Alg. 1 on
+    Ah = M^-1/2 A M^-1/2 with right-hand side bh = M^-1/2 b and the same gamma_u and xi_u, so
+    the matrix of Eq. 9 built from them is the Lanczos matrix of Ah started at bh / ||bh||.
+    Reading of the stopping test: the one of Alg. 1 on that system, r^T z <= tol^2 b^T M^-1 b
+    (||rh|| <= tol ||bh||); the other stops and ``steps`` are as in ``cg``."""
+    D, m = B.shape
+    mi = np.asarray(minv, dtype=np.float64).reshape(D, 1)
+    X = np.zeros((D, m))
+    R = B.astype(np.float64).copy()
+    Z = mi * R
+    Dd = Z.copy()
+    rz = np.einsum("ij,ij->j", R, Z)
+    bz = rz.copy()
+    gam = np.zeros((m, max_iter))
+    xi = np.zeros((m, max_iter))
+    U = np.zeros(m, dtype=np.int64)
+    active = (rz > 0.0) if steps is None else ((np.asarray(steps) > 0) & (rz > 0.0))
+    for u in range(max_iter):
+        idx = np.nonzero(active)[0]
+        if idx.size == 0:
+            break
+        Dd_a = Dd[:, idx]
+        AD = apply(Dd_a, idx)
+        dAd = np.einsum("ij,ij->j", Dd_a, AD)
+        ok = dAd > 0.0
+        if not ok.all():
+            active[idx[~ok]] = False
+            idx, Dd_a, AD, dAd = idx[ok], Dd_a[:, ok], AD[:, ok], dAd[ok]
+            if idx.size == 0:
+                break
+        g = rz[idx] / dAd                                   # gamma_u
+        X[:, idx] += g * Dd_a
+        R_a = R[:, idx] - g * AD                            # r_{u+1}
+        Z_a = mi * R_a                                      # z_{u+1}
+        rz_new = np.einsum("ij,ij->j", R_a, Z_a)
+        x_u = rz_new / rz[idx]                              # xi_u
+        R[:, idx] = R_a
+        Dd[:, idx] = Z_a + x_u * Dd_a                       # d_{u+1}
+        gam[idx, u] = g
+        xi[idx, u] = x_u
+        U[idx] += 1
+        rz[idx] = rz_new
+        if steps is None:
+            done = (rz_new <= (tol * tol) * bz[idx]) | (rz_new == 0.0)
+        else:
+            done = U[idx] >= np.asarray(steps)[idx]
+        active[idx[done]] = False
+    rel = np.sqrt(rz / np.where(bz > 0, bz, 1.0))
+    return CGResult(X, gam, xi, U, rel)
+
+
 def refine(apply, B: np.ndarray, X: np.ndarray, tol: float, max_iter: int, refine_tol: float,
-           refine_max: int):
+           refine_max: int, minv: np.ndarray = None):
     """Iterative refinement of the CG solutions X of A X = B: each sweep forms the residual
-    B - A X, solves A delta = residual by Alg. 1 (x_1 = 0, same tol and step cap) and adds
-    delta; column i stops once ||delta_i|| <= refine_tol * ||x_i||.  Returns (X, sweeps [m])."""
+    B - A X, solves A delta = residual by Alg. 1 (x_1 = 0, same tol and step cap; ``pcg``
+    with the same preconditioner when minv is given) and adds delta; column i stops once
+    ||delta_i|| <= refine_tol * ||x_i||.  Returns (X, sweeps [m])."""
     X = X.copy()
     m = B.shape[1]
     sweeps = np.zeros(m, dtype=np.int64)
@@ -206,7 +284,11 @@ def refine(apply, B: np.ndarray, X: np.ndarray, tol: float, max_iter: int, refin
         if idx.size == 0:
             break
         Rres = B[:, idx] - apply(X[:, idx], idx)
-        res = cg(lambda V, sub: apply(V, idx[sub]), Rres, tol, max_iter)
+        sub_apply = lambda V, sub: apply(V, idx[sub])
+        if minv is None:
+            res = cg(sub_apply, Rres, tol, max_iter)
+        else:
+            res = pcg(sub_apply, Rres, minv, tol, max_iter)
         X[:, idx] += res.x
         sweeps[idx] += 1
         dn = np.linalg.norm(res.x, axis=0)
@@ -326,7 +408,8 @@ def mean_adjoint(Phi_t: np.ndarray, y_t: np.ndarray, beta: float, alpha_c: np.nd
 def cofem_estep(Phi_list, y_list, alpha: np.ndarray, pi: np.ndarray, beta: float, K: int,
                 seed: int, em_iter: int, tol: float, max_iter: int, probe_fn=None,
                 steps: np.ndarray = None, tasks=None, refine_tol: float = None,
-                refine_max: int = 8, clusters=None, C_total: int = None) -> dict:
+                refine_max: int = 8, clusters=None, C_total: int = None,
+                probe_share: bool = False, precond: bool = False) -> dict:
     """Alg. 2, inner loop (one E-step): for every (t, c) solve A mu = b0 and A x_k = p_k by CG
     (Eq. 7, Alg. 1), s = (1/K) sum_k p_k * x_k (Eq. 4), the log-det estimate of Eq. 11 from the
     CG coefficients of the probe systems, ell (Eq. 3) and the responsibilities (Eq. 3).
@@ -335,7 +418,17 @@ def cofem_estep(Phi_list, y_list, alpha: np.ndarray, pi: np.ndarray, beta: float
     step counts; tasks gives the global task index of each entry of Phi_list (for the probe
     counter) when the list is a subset; likewise clusters gives the global index of each row
     of alpha and C_total the full cluster count (bounded samples).  With refine_tol set, mu and every x_k are refined
-    (``refine``) after the first CG solve, which alone supplies the Lanczos coefficients."""
+    (``refine``) after the first CG solve, which alone supplies the Lanczos coefficients.
+
+    Variants (off by default):
+    * probe_share: every cluster of task t uses the probes of cluster 0, p_{t,c,k} = p_{t,0,k}
+      (common random numbers across c, so the estimation noise of ell_tc - ell_tc' shrinks).
+    * precond: Jacobi-preconditioned CG (``pcg``) with M = diag(m), m = ``jacobi_diag``.  The
+      probe systems become A x_k = w * p_k with w = sqrt(m), so that the scaled system
+      Ah xh = M^-1/2 (w * p_k) = p_k starts its Lanczos process at a Rademacher vector; then
+      diag(A^-1) = M^-1/2 diag(Ah^-1) M^-1/2 gives s = (1/K) sum_k p_k * x_k / w, and
+      log det A = log det Ah + sum_d log m_d gives nu = (Eq. 11 on the pcg coefficients)
+      - sum_d log m_d."""
     P, Y = _task_arrays(Phi_list, y_list)
     T, (C, D) = len(P), alpha.shape
     tasks = list(range(T)) if tasks is None else list(tasks)
@@ -354,18 +447,30 @@ def cofem_estep(Phi_list, y_list, alpha: np.ndarray, pi: np.ndarray, beta: float
         b0 = rhs_mean(P[t], Y[t], beta)
         for c in range(C):
             if probe_fn is None:
-                Pk = philox.probes(seed, em_iter, tasks[t], clusters[c], C_total, K, D)
+                pc = 0 if probe_share else clusters[c]
+                Pk = philox.probes(seed, em_iter, tasks[t], pc, C_total, K, D)
             else:
                 Pk = np.asarray(probe_fn(t, c), dtype=np.float64)
-            B = np.concatenate([b0[:, None], Pk.T], axis=1)              # [D, K+1]
             op = lambda V, idx, t=t, c=c: apply_A(P[t], beta, alpha[c], V)
-            res = cg(op, B, tol, max_iter, None if steps is None else steps[t, c])
+            st = None if steps is None else steps[t, c]
+            if precond:
+                m_d = jacobi_diag(P[t], beta, alpha[c])
+                w = np.sqrt(m_d)
+                B = np.concatenate([b0[:, None], w[:, None] * Pk.T], axis=1)
+                res = pcg(op, B, 1.0 / m_d, tol, max_iter, st)
+            else:
+                B = np.concatenate([b0[:, None], Pk.T], axis=1)          # [D, K+1]
+                res = cg(op, B, tol, max_iter, st)
             X = res.x
             if refine_tol is not None:
-                X, _ = refine(op, B, X, tol, max_iter, refine_tol, refine_max)
+                X, _ = refine(op, B, X, tol, max_iter, refine_tol, refine_max,
+                              minv=(1.0 / m_d) if precond else None)
             mu[t, c] = X[:, 0]
             s[t, c] = np.mean(Pk.T * X[:, 1:], axis=1)
             nu[t, c] = logdet_estimate(res.gamma[1:], res.xi[1:], res.steps[1:], D)
+            if precond:
+                s[t, c] /= w
+                nu[t, c] -= float(np.sum(np.log(m_d)))
             ell_tc[t, c] = ell(nu[t, c], alpha[c], b0, mu[t, c])
             U[t, c] = res.steps
             gam[t, c] = res.gamma
@@ -384,14 +489,18 @@ def em(Phi_list, y_list, pi: np.ndarray, beta: float, n_iter: int, *, method: st
        K: int = 16, seed: int = 0, tol: float = 1e-5, max_iter: int = 100,
        alpha0: np.ndarray = None, em_iter_offset: int = 0, alpha_min: float = 1e-10,
        alpha_max: float = 1e10, D: int = None, C: int = None, refine_tol: float = None,
-       refine_max: int = 8) -> dict:
+       refine_max: int = 8, learn_pi: bool = False, probe_share: bool = False,
+       precond: bool = False) -> dict:
     """n_iter EM iterations from alpha0 (default: the Alg. 2 Uniform(0,1) draw).  Returns the
-    last E-step's outputs, the final alpha, the hard assignments argmax_c q_tc and the
-    reconstructions mu_{t, a_t}, plus the log-likelihood seen by every E-step."""
+    last E-step's outputs, the final alpha (and pi), the hard assignments argmax_c q_tc and
+    the reconstructions mu_{t, a_t}, plus the log-likelihood seen by every E-step.  With
+    learn_pi each M-step also sets pi = ``pi_update(q)``; probe_share and precond select the
+    E-step variants of ``cofem_estep``."""
     if alpha0 is None:
         alpha = philox.alpha_init(seed, C, D)
     else:
         alpha = np.asarray(alpha0, dtype=np.float64).copy()
+    pi = np.asarray(pi, dtype=np.float64).copy()
     trace = []
     alphas = [alpha.copy()]
     est = None
@@ -400,11 +509,14 @@ def em(Phi_list, y_list, pi: np.ndarray, beta: float, n_iter: int, *, method: st
             est = exact_estep(Phi_list, y_list, alpha, pi, beta)
         else:
             est = cofem_estep(Phi_list, y_list, alpha, pi, beta, K, seed, em_iter_offset + it,
-                              tol, max_iter, refine_tol=refine_tol, refine_max=refine_max)
+                              tol, max_iter, refine_tol=refine_tol, refine_max=refine_max,
+                              probe_share=probe_share, precond=precond)
         trace.append(est["loglik"])
         alpha = m_step(est["q"], est["mu"], est["s"], alpha, alpha_min, alpha_max)
+        if learn_pi:
+            pi = pi_update(est["q"])
         alphas.append(alpha.copy())
     assign = np.argmax(est["q"], axis=1)
     recon = est["mu"][np.arange(len(assign)), assign]
-    return dict(last=est, alpha=alpha, alphas=alphas, assign=assign, recon=recon,
+    return dict(last=est, alpha=alpha, pi=pi, alphas=alphas, assign=assign, recon=recon,
                 loglik_trace=np.array(trace))
