@@ -56,6 +56,13 @@ def _args():
     ap.add_argument("--refine-tol", type=float, default=1e-5)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--precond", action="store_true",
+                    help="Jacobi-preconditioned CG (method variant)")
+    ap.add_argument("--learn-pi", action="store_true", help="learn the cluster priors")
+    ap.add_argument("--probe-share", action="store_true",
+                    help="probes shared across the clusters of a task")
+    ap.add_argument("--compare-precond", action="store_true",
+                    help="also time the Jacobi-preconditioned form on the same workload")
     return ap.parse_args()
 
 
@@ -165,7 +172,8 @@ def _workload(name: str, seed: int, tasks: int = 0):
     return wl
 
 
-def _oracle_pair(wl, alpha, em_iter, t, c, refine_tol, refine_max):
+def _oracle_pair(wl, alpha, em_iter, t, c, refine_tol, refine_max, precond=False,
+                 probe_share=False):
     """The FP64 oracle's E-step for one (task, cluster) pair: K + 1 CG solves + refinement."""
     from oracle import cofem
     if hasattr(wl, "phi_real"):          # Fourier workload: the real-stacked dense matrix
@@ -176,7 +184,8 @@ def _oracle_pair(wl, alpha, em_iter, t, c, refine_tol, refine_max):
     t0 = time.perf_counter()
     o = cofem.cofem_estep(P, Y, np.asarray(alpha[c:c + 1], np.float64), np.array([1.0]), wl.beta,
                           wl.K, wl.seed, em_iter, wl.cg_tol, wl.cg_max_iter, tasks=[t],
-                          clusters=[c], C_total=wl.C, refine_tol=refine_tol, refine_max=refine_max)
+                          clusters=[c], C_total=wl.C, refine_tol=refine_tol, refine_max=refine_max,
+                          precond=precond, probe_share=probe_share)
     return o, time.perf_counter() - t0
 
 
@@ -231,7 +240,9 @@ def run_ours(a):
         a.no_fp32_form = True
     kw = dict(C=wl.C, K=wl.K, beta=wl.beta, pi=wl.pi, cg_max_iter=wl.cg_max_iter, cg_tol=wl.cg_tol,
               seed=wl.seed, precision=a.precision, refine_max=a.refine_max, refine_tol=a.refine_tol,
-              schedule=a.schedule, graphs=not a.no_graphs)
+              schedule=a.schedule, graphs=not a.no_graphs, precond=a.precond,
+              learn_pi=a.learn_pi, probe_share=a.probe_share)
+    variant = dict(precond=a.precond, probe_share=a.probe_share)
     if fourier:
         ctx = cmcs.Context.from_fourier(wl, device=True, **kw)
     else:
@@ -325,12 +336,12 @@ def run_ours(a):
         mu_g = ctx.read(cmcs.OUT_MU)
         s_g = ctx.read(cmcs.OUT_S)
         t_s, c_s = 5, 2 % wl.C
-        o, dt = _oracle_pair(wl, alpha, it, t_s, c_s, 1e-12, 40)
+        o, dt = _oracle_pair(wl, alpha, it, t_s, c_s, 1e-12, 40, **variant)
         rel = lambda g_, r_: float(np.linalg.norm(g_ - r_) / np.linalg.norm(r_))
         err = {"pair": [t_s, c_s], "mu_rel": rel(mu_g[t_s, c_s], o["mu"][0, 0]),
                "s_rel": rel(s_g[t_s, c_s], o["s"][0, 0])}
         if world == 1:
-            _, dt_b = _oracle_pair(wl, alpha, it, t_s, c_s, a.refine_tol, a.refine_max)
+            _, dt_b = _oracle_pair(wl, alpha, it, t_s, c_s, a.refine_tol, a.refine_max, **variant)
             cpu = {"value": 1.0 / (dt_b * wl.T * wl.C), "unit": UNIT, "cores": _cpu_cores(),
                    "kind": "oracle",
                    "sample": f"one (task, cluster) pair of the E-step ({wl.K + 1} FP64 CG solves "
@@ -395,8 +406,11 @@ def run_ours(a):
         torch.cuda.synchronize()
         ms3 = f0.elapsed_time(f1)
         pr = c3.profile_read()
+        sm3 = c3.summary()
         c3.close()
         return {"value": a.steps / (ms3 / 1e3), "unit": UNIT, "ms_per_step": ms3 / a.steps,
+                "cg_steps_mean": sm3["cg_steps_mean"], "cg_capped": sm3["cg_capped"],
+                "operator_applies": sm3["operator_applies"],
                 "operator_ms_per_application": pr["operator_ms"] / max(1, pr["operator_calls"]),
                 "operator_tflops": pr["operator_flops"] / (pr["operator_ms"] * 1e-3) / 1e12
                 if pr["operator_ms"] else None, **{k: v for k, v in over.items()}}
@@ -407,6 +421,9 @@ def run_ours(a):
     per_task = None
     if a.compare_schedule:
         per_task = timed_leg(schedule="per_task")
+    precond_form = None
+    if a.compare_precond and not a.precond:
+        precond_form = timed_leg(precond=True)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms_max / a.steps,
@@ -417,6 +434,9 @@ def run_ours(a):
                                        f"K={wl.K} tol={wl.cg_tol} max_iter={wl.cg_max_iter}",
                            "precision": a.precision, "refine_max": a.refine_max,
                            "refine_tol": a.refine_tol, "parallelism": f"{world} replicas",
+                           "variants": [v for v, on in (("precond", a.precond),
+                                                        ("learn_pi", a.learn_pi),
+                                                        ("probe_share", a.probe_share)) if on],
                            "l2": (f"inputs larger than L2 (CG vectors {5 * systems * wl.D * 4 / 1e9:.1f} GB)"
                                   if fourier else
                                   f"inputs larger than L2 (Phi {wl.Phi.nbytes / 1e9:.1f} GB)")},
@@ -429,7 +449,8 @@ def run_ours(a):
                 "operator_applies_per_step": prof["operator_calls"] / a.steps,
                 "roofline": roof, "cpu_baseline": cpu, "err_vs_fp64": err, "e2e": e2e,
                 "clocks": clk, "gpu_launches": prof["kernel_launches"],
-                "fp32_form": fp32_form, "per_task_schedule": per_task}
+                "fp32_form": fp32_form, "per_task_schedule": per_task,
+                "precond_form": precond_form}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -85,6 +85,15 @@ typedef struct {
   int graphs;             /* 1: capture chunks of CG steps in CUDA graphs and replay them  */
   int autotune;           /* 1: at create, time the operator variants (SIMT tile width or
                              tensor-core pipeline depth) and keep the fastest              */
+  /* Variants of the method, all 0 (off) by default. */
+  int learn_pi;           /* 1: every M-step also learns the priors (Sec. 2 allows it):
+                             pi_c = max((1/T) sum_t q_tc, 1e-300), renormalised to sum 1   */
+  int probe_share;        /* 1: every cluster of task t uses the same probes,
+                             p_{t,c,k} = p_{t,0,k} (common random numbers across c)         */
+  int precond;            /* 1: Jacobi-preconditioned CG, M = diag(A), m_d = beta ||Phi_t e_d||^2
+                             + alpha_cd: probe systems A x_k = sqrt(m) * p_k, stopping test
+                             r^T M^-1 r <= cg_tol^2 b^T M^-1 b, s = (1/K) sum_k p_k x_k /
+                             sqrt(m) and log det Sigma = Eq. 11's estimate - sum_d log m_d  */
 } cmcs_config;
 
 /* Summary of the most recent E-step and the EM state. */
@@ -124,8 +133,10 @@ typedef enum {
   CMCS_OUT_XI = 10,      /* float  [T][C][K][cg_max_iter] CG coefficients xi_u, zero past U */
   CMCS_OUT_B0 = 11,      /* float  [T][D]     beta Phi_t^T y_t (Eq. 7)                      */
   CMCS_OUT_SWEEPS = 12,  /* int32  [T][C][K+1] refinement sweeps taken per system           */
-  CMCS_OUT_RESID = 13    /* float  [T][C][K+1] ||b - A x|| / ||b|| of the returned means
+  CMCS_OUT_RESID = 13,   /* float  [T][C][K+1] ||b - A x|| / ||b|| of the returned means
                                               (index 0; other entries and refine_max = 0: 0) */
+  CMCS_OUT_PI = 14       /* double [C]        cluster priors in force (learned: after the
+                                              last M-step; else the configured ones)        */
 } cmcs_output;
 
 /* Create a context: validates cfg, copies Phi and y into library-owned device memory (padded

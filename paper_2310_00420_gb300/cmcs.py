@@ -21,7 +21,7 @@ FP32, BF16_REFINE, BF16X3 = 0, 1, 2
 PRECISIONS = {"fp32": FP32, "bf16": BF16_REFINE, "bf16_refine": BF16_REFINE, "bf16x3": BF16X3}
 
 (OUT_MU, OUT_S, OUT_Q, OUT_LOGDET, OUT_ELL, OUT_ALPHA, OUT_ASSIGN, OUT_RECON, OUT_STEPS,
- OUT_GAMMA, OUT_XI, OUT_B0, OUT_SWEEPS, OUT_RESID) = range(14)
+ OUT_GAMMA, OUT_XI, OUT_B0, OUT_SWEEPS, OUT_RESID, OUT_PI) = range(15)
 
 # exported symbols, in the order include/cmcs.h declares them
 EXPORTS = ("cmcs_create", "cmcs_create_dft", "cmcs_set_alpha", "cmcs_estep", "cmcs_em_iter", "cmcs_read",
@@ -37,7 +37,9 @@ class Config(ctypes.Structure):
                 ("cg_tol", ctypes.c_double), ("seed", ctypes.c_uint64), ("precision", ctypes.c_int),
                 ("refine_max", ctypes.c_int), ("refine_tol", ctypes.c_double),
                 ("alpha_min", ctypes.c_double), ("alpha_max", ctypes.c_double),
-                ("schedule", ctypes.c_int), ("graphs", ctypes.c_int), ("autotune", ctypes.c_int)]
+                ("schedule", ctypes.c_int), ("graphs", ctypes.c_int), ("autotune", ctypes.c_int),
+                ("learn_pi", ctypes.c_int), ("probe_share", ctypes.c_int),
+                ("precond", ctypes.c_int)]
 
 
 class Summary(ctypes.Structure):
@@ -147,6 +149,7 @@ _OUT_META = {  # what: (dtype, shape function of (T, C, D, K, U))
     OUT_B0: (np.float32, lambda T, C, D, K, U: (T, D)),
     OUT_SWEEPS: (np.int32, lambda T, C, D, K, U: (T, C, K + 1)),
     OUT_RESID: (np.float32, lambda T, C, D, K, U: (T, C, K + 1)),
+    OUT_PI: (np.float64, lambda T, C, D, K, U: (C,)),
 }
 
 
@@ -157,9 +160,11 @@ class Context:
                  cg_tol: float = 1e-5, seed: int = 0, precision="fp32", refine_max: int = 0,
                  refine_tol: float = 1e-6, alpha_min: float = 1e-10, alpha_max: float = 1e10,
                  schedule: str = "batched", graphs: bool = True, autotune: bool = False,
+                 learn_pi: bool = False, probe_share: bool = False, precond: bool = False,
                  mask=None, stream=None):
         """Dense Phi [sum N_t][D] with y [sum N_t]; or, with Phi None and mask given, the
-        Fourier operator of cmcs_create_dft: mask uint8 [T][D], y float32 [sum N_t][2]."""
+        Fourier operator of cmcs_create_dft: mask uint8 [T][D], y float32 [sum N_t][2].
+        learn_pi, probe_share and precond switch on the method variants of cmcs_config."""
         N = np.ascontiguousarray(np.asarray(N, dtype=np.int64))
         D = int(mask.shape[1]) if mask is not None else int(Phi.shape[1])
         self.T, self.C, self.D, self.K = int(len(N)), int(C), D, int(K)
@@ -173,7 +178,8 @@ class Context:
                      float(cg_tol), int(seed) & (2**64 - 1), prec, int(refine_max),
                      float(refine_tol), float(alpha_min), float(alpha_max),
                      {"batched": 0, "per_task": 1}[schedule], 1 if graphs else 0,
-                     1 if autotune else 0)
+                     1 if autotune else 0, 1 if learn_pi else 0, 1 if probe_share else 0,
+                     1 if precond else 0)
         self.cfg = cfg
         self.fourier = mask is not None
         p_phi, dev1 = _ptr(mask if self.fourier else Phi)

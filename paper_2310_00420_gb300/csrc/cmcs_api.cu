@@ -54,7 +54,8 @@ void free_ctx(Ctx* c) {
                   c->ractive, c->sweeps, c->rrel, c->rres, c->task_active, c->counters, c->gam, c->xi,
                   c->psteps, c->sest, c->quad, c->logdet, c->ell, c->q, c->assign, c->stats,
                   c->dN, c->opcount, c->dorow, c->stall_flag, c->adj_g, c->adj_x, c->adj_wl, c->adj_wm,
-                  c->adj_wl_lo, c->adj_wm_lo, c->adj_dy, c->adj_da};
+                  c->adj_wl_lo, c->adj_wm_lo, c->adj_dy, c->adj_da, c->pi, c->colnorm, c->pminv,
+                  c->pw, c->sumlogm};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->prof_ev) {
@@ -249,6 +250,7 @@ cmcs_status estep(Ctx* c) {
   CK(cudaMemsetAsync(c->counters, 0, sizeof(int) * 4, c->stream));
   CK(cudaMemsetAsync(c->psteps, 0, sizeof(int) * (size_t)c->T * c->C * c->K, c->stream));
   c->op_applies = 0;
+  CK(launch_precond(c));              // Jacobi preconditioner of the current alpha
   // first solve: Alg. 1 from x = 0 on b0 and the probes, recording gamma and xi
   CK(launch_cg_init(c, 0));
   cmcs_status s = run_cg(c, 1);
@@ -358,6 +360,9 @@ cmcs_status validate(const cmcs_config* cfg) {
   if (cfg->schedule != 0 && cfg->schedule != 1) return CMCS_ERR_INVALID_ARG;
   if (cfg->graphs != 0 && cfg->graphs != 1) return CMCS_ERR_INVALID_ARG;
   if (cfg->autotune != 0 && cfg->autotune != 1) return CMCS_ERR_INVALID_ARG;
+  if (cfg->learn_pi != 0 && cfg->learn_pi != 1) return CMCS_ERR_INVALID_ARG;
+  if (cfg->probe_share != 0 && cfg->probe_share != 1) return CMCS_ERR_INVALID_ARG;
+  if (cfg->precond != 0 && cfg->precond != 1) return CMCS_ERR_INVALID_ARG;
   return CMCS_OK;
 }
 
@@ -411,6 +416,9 @@ cmcs_status create_ctx(const cmcs_config* cfg, const float* Phi, const float* y,
   c->alpha_min = cfg->alpha_min;
   c->alpha_max = cfg->alpha_max;
   c->precision = cfg->precision;
+  c->learn_pi = cfg->learn_pi;
+  c->pshare = cfg->probe_share;
+  c->precond = cfg->precond;
   c->seed = cfg->seed;
   c->op = mask ? 1 : 0;
   c->em_iter = 0;
@@ -487,6 +495,14 @@ cmcs_status create_ctx(const cmcs_config* cfg, const float* Phi, const float* y,
   CKC(dalloc(&c->alpha, (size_t)(C * Dp)));
   CKC(dalloc(&c->sumlogalpha, (size_t)C));
   CKC(dalloc(&c->logpi, (size_t)C));
+  CKC(dalloc(&c->pi, (size_t)C));
+  if (c->precond) {
+    CKC(dalloc(&c->colnorm, (size_t)(T * Dp)));
+    CKC(dalloc(&c->pminv, (size_t)(T * C * Dp)));
+    CKC(dalloc(&c->pw, (size_t)(T * C * Dp)));
+    CKC(dalloc(&c->sumlogm, (size_t)(T * C)));
+    CKC(cudaMemsetAsync(c->colnorm, 0, sizeof(float) * T * Dp, c->stream));
+  }
   CKC(dalloc(&c->tconst, (size_t)T));
   CKC(dalloc(&c->x, (size_t)(S * Dp)));
   CKC(dalloc(&c->r, (size_t)(S * Dp)));
@@ -579,7 +595,9 @@ cmcs_status create_ctx(const cmcs_config* cfg, const float* Phi, const float* y,
   CKC(cudaMemcpyAsync(c->dorow, c->horow, sizeof(int64_t) * (T + 1), cudaMemcpyHostToDevice, c->stream));
   CKC(cudaMemcpyAsync(c->tile_task, ttask.data(), sizeof(int) * ntiles, cudaMemcpyHostToDevice, c->stream));
   CKC(cudaMemcpyAsync(c->logpi, lpi.data(), sizeof(double) * C, cudaMemcpyHostToDevice, c->stream));
+  CKC(cudaMemcpyAsync(c->pi, c->hpi, sizeof(double) * C, cudaMemcpyHostToDevice, c->stream));
   CKC(launch_b0(c));
+  CKC(launch_colnorm(c));
   CKC(launch_alpha_init(c));
   CKC(launch_sumlogalpha(c));
   CKC(launch_tconst_dev(c, c->dN));
@@ -733,6 +751,7 @@ cmcs_status cmcs_set_data(cmcs_ctx* h, const float* Phi, const float* y, int on_
   }
   CK(launch_b0(c));
   CK(launch_tconst_dev(c, c->dN));
+  CK(launch_colnorm(c));
   if (c->tc != nullptr) CK(tc_refresh(c));
   return sync_check(c);
 }
@@ -765,6 +784,7 @@ cmcs_status cmcs_adjoint(cmcs_ctx* h, const float* g, float* dy, float* dalpha, 
   CK(cudaMemcpyAsync(a.r, c->adj_g, sizeof(float) * T * C * Dp, cudaMemcpyDeviceToDevice, c->stream));
   CK(cudaMemsetAsync(c->task_active, 0, sizeof(int) * T, c->stream));
   CK(cudaMemsetAsync(c->counters, 0, sizeof(int) * 4, c->stream));
+  CK(launch_precond(c));              // the adjoint systems (t, c) share A_tc's preconditioner
   CK(launch_cg_init(&a, 2));
   cmcs_status s = run_cg(&a, 0);
   if (s != CMCS_OK) return s;
@@ -825,6 +845,7 @@ cmcs_status cmcs_em_iter(cmcs_ctx* h, int n) {
     if (s != CMCS_OK) return s;
     CK(launch_mstep(c));
     CK(launch_sumlogalpha(c));
+    if (c->learn_pi) CK(launch_pi_update(c));
     c->em_iter++;
   }
   return sync_check(c);
@@ -888,6 +909,9 @@ cmcs_status cmcs_read(const cmcs_ctx* hc, int what, void* dst, int on_device) {
       break;
     case CMCS_OUT_RESID:
       CK(cudaMemcpyAsync(dst, c->rres, sizeof(float) * c->S, k, c->stream));
+      break;
+    case CMCS_OUT_PI:
+      CK(cudaMemcpyAsync(dst, c->pi, sizeof(double) * C, k, c->stream));
       break;
     default:
       set_err(c, "unknown output %d", what);

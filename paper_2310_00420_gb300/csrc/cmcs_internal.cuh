@@ -63,12 +63,18 @@ __device__ inline uint32_t probe_bits32(uint64_t seed, int64_t em_iter, int t, i
   return pick_word(w, (d_base >> 5) & 3);
 }
 
+// cluster index the probes of cluster c are drawn for: c, or 0 when probes are shared
+__host__ __device__ inline int probe_cluster(int c, int pshare) { return pshare ? 0 : c; }
+
 // ---- context --------------------------------------------------------------------------
 struct Ctx {
   // configuration
   int T, C, D, K, R, S, Dp, U;    // U = cg_max_iter
   double beta, cg_tol, refine_tol, alpha_min, alpha_max;
   int precision, refine_max;
+  int learn_pi;      // each M-step also sets pi_c = max(mean_t q_tc, 1e-300), renormalised
+  int pshare;        // probes shared across clusters: p_{t,c,k} = p_{t,0,k}
+  int precond;       // Jacobi-preconditioned CG (buffers colnorm, pminv, pw, sumlogm)
   uint64_t seed;
   int64_t em_iter;
   cudaStream_t stream;
@@ -110,6 +116,10 @@ struct Ctx {
   float* alpha;        // [C][Dp]
   double* sumlogalpha; // [C]
   double* logpi;       // [C]
+  double* pi;          // [C] priors in force
+  float* colnorm;      // [T][Dp] beta-free diagonal of Phi_t^T Phi_t (precond only)
+  float *pminv, *pw;   // [T*C][Dp] 1/m and sqrt(m), m = beta colnorm + alpha_c (precond only)
+  double* sumlogm;     // [T*C] sum_{d<D} log m_d (precond only)
   double* tconst;      // [T]  (N_t log 2pi - N_t log beta + beta ||y_t||^2) / 2
   float *x, *r, *d, *ad, *xacc;  // [S][Dp]
   float *w, *wlo;      // [R * rows_total]
@@ -173,6 +183,12 @@ cudaError_t launch_cg_init(Ctx* c, int mode /*0 first solve, 1 refinement*/);
 cudaError_t launch_cg_update(Ctx* c, int record);
 cudaError_t launch_refine_update(Ctx* c);
 cudaError_t launch_sest(Ctx* c);
+// Jacobi preconditioner of the current alpha: pminv, pw and sumlogm (no-op without precond)
+cudaError_t launch_precond(Ctx* c);
+// column norms of Phi_t for the preconditioner (dense Phi; Fourier contexts fill N_t / D)
+cudaError_t launch_colnorm(Ctx* c);
+// learned priors from the responsibilities of the last E-step (pi and logpi)
+cudaError_t launch_pi_update(Ctx* c);
 // operator (kernels_op.cu): AD = A D for all active tasks
 cudaError_t launch_operator(Ctx* c, const float* V, float* Z, int with_dots);
 // accurate residual: r = B - A xacc, B = b0 (k = 0) or the probe (k >= 1) when Bext == null

@@ -12,6 +12,8 @@
 #include <cuda_bf16.h>
 #include <math.h>
 
+#include <vector>
+
 #include "cmcs_internal.cuh"
 
 namespace cmcs {
@@ -66,35 +68,51 @@ __device__ __forceinline__ void store_split4(__nv_bfloat16* hi, __nv_bfloat16* l
 // mode 0: b = b0_t (k = 0) or the probe p_{t,c,k} (k >= 1); mode 1: b = the residual
 // already in r (refinement), systems no longer refining have r = 0; mode 2: b = a given
 // right-hand side already in r (first solve of the adjoint system).
+// With the Jacobi preconditioner (pminv != null): probe right-hand sides are sqrt(m) * p,
+// d_1 = z_1 = M^-1 r_1 and rr = r^T z.
 __global__ void __launch_bounds__(256)
 k_cg_init(int mode, float* __restrict__ x, float* __restrict__ r, float* __restrict__ d,
           const float* __restrict__ b0hi, float* rr, float* bb, int* steps, int* active,
           int* ractive, int* sweeps, float* rrel, int* task_active, int* counters, int R,
           int K, int C, int Dp, int D, uint64_t seed, int64_t em_iter, int refine,
-          __nv_bfloat16* dhi, __nv_bfloat16* dlo) {
+          __nv_bfloat16* dhi, __nv_bfloat16* dlo, const float* __restrict__ pminv,
+          const float* __restrict__ pw, int pshare) {
   __shared__ float sh[33];
   const int64_t sys = blockIdx.x;
   const int t = (int)(sys / R), j = (int)(sys % R), c = j / (K + 1), k = j % (K + 1);
   float* xs = x + sys * Dp;
   float* rs = r + sys * Dp;
   float* ds = d + sys * Dp;
+  const int64_t tcoff = ((int64_t)t * C + c) * Dp;
   float acc = 0.f;
   for (int i = threadIdx.x * 4; i < Dp; i += 256 * 4) {
     float4 b;
     if (mode == 0) {
-      b = (k == 0) ? *reinterpret_cast<const float4*>(b0hi + (int64_t)t * Dp + i)
-                   : probe4(seed, em_iter, t, c, C, k - 1, i, D);
+      if (k == 0) {
+        b = *reinterpret_cast<const float4*>(b0hi + (int64_t)t * Dp + i);
+      } else {
+        b = probe4(seed, em_iter, t, probe_cluster(c, pshare), C, k - 1, i, D);
+        if (pw != nullptr) {
+          const float4 w = *reinterpret_cast<const float4*>(pw + tcoff + i);
+          b = make_float4(b.x * w.x, b.y * w.y, b.z * w.z, b.w * w.w);
+        }
+      }
       *reinterpret_cast<float4*>(rs + i) = b;
     } else {
       b = *reinterpret_cast<const float4*>(rs + i);
     }
+    float4 z = b;
+    if (pminv != nullptr) {
+      const float4 mi = *reinterpret_cast<const float4*>(pminv + tcoff + i);
+      z = make_float4(b.x * mi.x, b.y * mi.y, b.z * mi.z, b.w * mi.w);
+    }
     *reinterpret_cast<float4*>(xs + i) = make_float4(0.f, 0.f, 0.f, 0.f);
-    *reinterpret_cast<float4*>(ds + i) = b;
-    if (dhi != nullptr) store_split4(dhi, dlo, sys * Dp + i, b);
-    acc = fmaf(b.x, b.x, acc);
-    acc = fmaf(b.y, b.y, acc);
-    acc = fmaf(b.z, b.z, acc);
-    acc = fmaf(b.w, b.w, acc);
+    *reinterpret_cast<float4*>(ds + i) = z;
+    if (dhi != nullptr) store_split4(dhi, dlo, sys * Dp + i, z);
+    acc = fmaf(b.x, z.x, acc);
+    acc = fmaf(b.y, z.y, acc);
+    acc = fmaf(b.z, z.z, acc);
+    acc = fmaf(b.w, z.w, acc);
   }
   const float rr0 = block_sum(acc, sh);
   if (threadIdx.x == 0) {
@@ -121,6 +139,7 @@ k_cg_init(int mode, float* __restrict__ x, float* __restrict__ r, float* __restr
 // RAW = false: ad = A d and d^T A d arrives as per-tile partials from the operator epilogue.
 // RAW = true (tensor-core operator): ad = beta Phi^T Phi d only; this kernel adds alpha_c * d
 // and forms d^T A d itself, so the operator's epilogue reads neither d nor alpha.
+// pminv != null: Jacobi-preconditioned step, z = M^-1 r, rr = r^T z, d = z + xi d.
 template <int NV, bool RAW>
 __global__ void __launch_bounds__(256)
 k_cg_update(float* __restrict__ x, float* __restrict__ r, float* __restrict__ d,
@@ -128,7 +147,7 @@ k_cg_update(float* __restrict__ x, float* __restrict__ r, float* __restrict__ d,
             const float* __restrict__ alpha, int ndt, float* rr, const float* bb, int* steps,
             int* active, int* task_active, int* counters, float* gam, float* xih, int* psteps,
             int record, int R, int K, int C, int Dp, int S, int U, float tol2,
-            __nv_bfloat16* dhi, __nv_bfloat16* dlo) {
+            __nv_bfloat16* dhi, __nv_bfloat16* dlo, const float* __restrict__ pminv) {
   __shared__ float sh[33];
   __shared__ float s_dad;
   const int64_t sys = blockIdx.x;
@@ -139,6 +158,13 @@ k_cg_update(float* __restrict__ x, float* __restrict__ r, float* __restrict__ d,
   float* ds = d + sys * Dp;
   const float* as = ad + sys * Dp;
   const float* al = alpha + (int64_t)(j / (K + 1)) * Dp;
+  const float* mi = pminv != nullptr ? pminv + ((int64_t)t * C + j / (K + 1)) * Dp : nullptr;
+  // z = M^-1 r for four coordinates (r itself without the preconditioner)
+  auto zof = [&](int i, float4 rv) {
+    if (mi == nullptr) return rv;
+    const float4 m4 = *reinterpret_cast<const float4*>(mi + i);
+    return make_float4(rv.x * m4.x, rv.y * m4.y, rv.z * m4.z, rv.w * m4.w);
+  };
   float4 dk[NV > 0 ? NV : 1], ak[(RAW && NV > 0) ? NV : 1];
   // A d for four coordinates (RAW: beta Phi^T Phi d + alpha_c * d)
   auto adv = [&](int i, float4 dv) {
@@ -211,11 +237,12 @@ k_cg_update(float* __restrict__ x, float* __restrict__ r, float* __restrict__ d,
     rv.z = fmaf(-g, av.z, rv.z); rv.w = fmaf(-g, av.w, rv.w);
     *reinterpret_cast<float4*>(xs + i) = xv;
     *reinterpret_cast<float4*>(rs + i) = rv;
-    acc = fmaf(rv.x, rv.x, acc);
-    acc = fmaf(rv.y, rv.y, acc);
-    acc = fmaf(rv.z, rv.z, acc);
-    acc = fmaf(rv.w, rv.w, acc);
-    ro = rv;
+    const float4 zv = zof(i, rv);
+    acc = fmaf(rv.x, zv.x, acc);
+    acc = fmaf(rv.y, zv.y, acc);
+    acc = fmaf(rv.z, zv.z, acc);
+    acc = fmaf(rv.w, zv.w, acc);
+    ro = zv;
     dout = dv;
   };
   if constexpr (NV > 0) {
@@ -227,9 +254,9 @@ k_cg_update(float* __restrict__ x, float* __restrict__ r, float* __restrict__ d,
   } else {
     for (int i = threadIdx.x * 4; i < Dp; i += 256 * 4) step1(i, 0, rk[0], dk[0]);
   }
-  const float rr1 = block_sum(acc, sh);            // r_{u+1}^T r_{u+1}
+  const float rr1 = block_sum(acc, sh);            // r_{u+1}^T z_{u+1} (z = r: r^T r)
   const float xi = rr1 / rr0;                      // xi_u
-  auto step2 = [&](int i, float4 rv, float4 dv) {
+  auto step2 = [&](int i, float4 rv, float4 dv) {  // rv: z_{u+1}
     dv.x = fmaf(xi, dv.x, rv.x); dv.y = fmaf(xi, dv.y, rv.y);
     dv.z = fmaf(xi, dv.z, rv.z); dv.w = fmaf(xi, dv.w, rv.w);
     *reinterpret_cast<float4*>(ds + i) = dv;
@@ -243,7 +270,8 @@ k_cg_update(float* __restrict__ x, float* __restrict__ r, float* __restrict__ d,
     }
   } else {
     for (int i = threadIdx.x * 4; i < Dp; i += 256 * 4)
-      step2(i, *reinterpret_cast<const float4*>(rs + i), *reinterpret_cast<const float4*>(ds + i));
+      step2(i, zof(i, *reinterpret_cast<const float4*>(rs + i)),
+            *reinterpret_cast<const float4*>(ds + i));
   }
   if (threadIdx.x == 0) {
     const int u = steps[sys];
@@ -359,8 +387,10 @@ cudaError_t launch_resid_norm(Ctx* c) {
 
 // ---- diagonal estimator s_tc = (1/K) sum_k p_k * x_k (Eq. 4) ----------------------------
 __global__ void __launch_bounds__(128)
+// With the Jacobi preconditioner the probe systems solve A x_k = sqrt(m) p_k, and
+// s = (1/K) sum_k p_k x_k / sqrt(m) (pw = sqrt(m); null: plain probes).
 k_sest(const float* __restrict__ xacc, float* __restrict__ sest, int R, int K, int C, int Dp,
-       int D, uint64_t seed, int64_t em_iter) {
+       int D, uint64_t seed, int64_t em_iter, const float* __restrict__ pw, int pshare) {
   const int tc = blockIdx.y;
   const int t = tc / C, c = tc % C;
   const int i = (blockIdx.x * 128 + threadIdx.x) * 4;
@@ -368,7 +398,7 @@ k_sest(const float* __restrict__ xacc, float* __restrict__ sest, int R, int K, i
   float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
   const int64_t base = ((int64_t)t * R + (int64_t)c * (K + 1)) * Dp;
   for (int k = 1; k <= K; ++k) {
-    const float4 p = probe4(seed, em_iter, t, c, C, k - 1, i, D);
+    const float4 p = probe4(seed, em_iter, t, probe_cluster(c, pshare), C, k - 1, i, D);
     const float4 xv = *reinterpret_cast<const float4*>(xacc + base + (int64_t)k * Dp + i);
     acc.x = fmaf(p.x, xv.x, acc.x);
     acc.y = fmaf(p.y, xv.y, acc.y);
@@ -376,8 +406,42 @@ k_sest(const float* __restrict__ xacc, float* __restrict__ sest, int R, int K, i
     acc.w = fmaf(p.w, xv.w, acc.w);
   }
   const float inv = 1.0f / (float)K;
-  *reinterpret_cast<float4*>(sest + (int64_t)tc * Dp + i) =
-      make_float4(acc.x * inv, acc.y * inv, acc.z * inv, acc.w * inv);
+  float4 sv = make_float4(acc.x * inv, acc.y * inv, acc.z * inv, acc.w * inv);
+  if (pw != nullptr) {
+    const float4 w = *reinterpret_cast<const float4*>(pw + (int64_t)tc * Dp + i);
+    sv = make_float4(sv.x / w.x, sv.y / w.y, sv.z / w.z, sv.w / w.w);
+  }
+  *reinterpret_cast<float4*>(sest + (int64_t)tc * Dp + i) = sv;
+}
+
+// ---- Jacobi preconditioner: m = beta ||Phi_t e_d||^2 + alpha_cd, the diagonal of A_tc ----
+__global__ void __launch_bounds__(128)
+k_colnorm(const float* __restrict__ phi, const int64_t* drow, float* colnorm, int Dp) {
+  const int t = blockIdx.y;
+  const int d = blockIdx.x * 128 + threadIdx.x;
+  if (d >= Dp) return;
+  double acc = 0.0;
+  for (int64_t n = drow[t]; n < drow[t + 1]; ++n) {
+    const double a = (double)phi[n * Dp + d];
+    acc = fma(a, a, acc);
+  }
+  colnorm[(int64_t)t * Dp + d] = (float)acc;
+}
+
+__global__ void __launch_bounds__(256)
+k_precond(const float* __restrict__ colnorm, const float* __restrict__ alpha, float* pminv,
+          float* pw, double* sumlogm, int C, int Dp, int D, double beta) {
+  __shared__ double sh[33];
+  const int tc = blockIdx.x, t = tc / C, c = tc % C;
+  double acc = 0.0;
+  for (int d = threadIdx.x; d < Dp; d += 256) {
+    const double m = beta * (double)colnorm[(int64_t)t * Dp + d] + (double)alpha[(int64_t)c * Dp + d];
+    pminv[(int64_t)tc * Dp + d] = (float)(1.0 / m);
+    pw[(int64_t)tc * Dp + d] = (float)sqrt(m);
+    if (d < D) acc += log(m);
+  }
+  const double tot = block_sum(acc, sh);
+  if (threadIdx.x == 0) sumlogm[tc] = tot;
 }
 
 // ---- b0_t = beta Phi_t^T y_t, kept as hi + lo (compensated sum, then FP64 scaling) ------
@@ -446,14 +510,14 @@ k_tconst(const float* y, const int64_t* drow, const int64_t* Nt, double* out, do
 
 // ---- probes as +-1 floats [T][C][K][D] ----------------------------------------------------
 __global__ void k_probes_out(float* dst, int T, int C, int K, int D, uint64_t seed,
-                             int64_t em_iter) {
+                             int64_t em_iter, int pshare) {
   const int64_t tck = blockIdx.y;
   const int k = (int)(tck % K);
   const int c = (int)((tck / K) % C);
   const int t = (int)(tck / ((int64_t)K * C));
   const int d = blockIdx.x * 256 + threadIdx.x;
   if (d >= D) return;
-  const uint32_t bits = probe_bits32(seed, em_iter, t, c, C, k, d & ~31);
+  const uint32_t bits = probe_bits32(seed, em_iter, t, probe_cluster(c, pshare), C, k, d & ~31);
   dst[tck * D + d] = ((bits >> (d & 31)) & 1u) ? -1.f : 1.f;
 }
 
@@ -465,7 +529,9 @@ cudaError_t launch_cg_init(Ctx* c, int mode) {
                                          c->task_active, c->counters, c->R, c->K, c->C, c->Dp,
                                          c->D, c->seed, c->em_iter, c->refine_max > 0 ? 1 : 0,
                                          static_cast<__nv_bfloat16*>(c->dhi),
-                                         static_cast<__nv_bfloat16*>(c->dlo));
+                                         static_cast<__nv_bfloat16*>(c->dlo),
+                                         c->precond ? c->pminv : nullptr,
+                                         c->precond ? c->pw : nullptr, c->pshare);
   return cudaGetLastError();
 }
 
@@ -479,13 +545,13 @@ cudaError_t launch_cg_update(Ctx* c, int record) {
         c->x, c->r, c->d, c->ad, c->part, c->alpha, c->op == 1 ? 1 : c->Dp / 128, c->rr, c->bb, c->steps,        \
         c->active, c->task_active, c->counters, c->gam, c->xi, c->psteps, record, c->R, c->K,    \
         c->C, c->Dp, c->S, c->U, tol2, static_cast<__nv_bfloat16*>(c->dhi),                      \
-        static_cast<__nv_bfloat16*>(c->dlo));                                                    \
+        static_cast<__nv_bfloat16*>(c->dlo), c->precond ? c->pminv : nullptr);                   \
   else                                                                                           \
     k_cg_update<NV, false><<<c->S, 256, 0, c->stream>>>(                                         \
         c->x, c->r, c->d, c->ad, c->part, c->alpha, c->op == 1 ? 1 : c->Dp / 128, c->rr, c->bb, c->steps,        \
         c->active, c->task_active, c->counters, c->gam, c->xi, c->psteps, record, c->R, c->K,    \
         c->C, c->Dp, c->S, c->U, tol2, static_cast<__nv_bfloat16*>(c->dhi),                      \
-        static_cast<__nv_bfloat16*>(c->dlo))
+        static_cast<__nv_bfloat16*>(c->dlo), c->precond ? c->pminv : nullptr)
   if (nv <= 1) { UPD(1); }
   else if (nv <= 2) { UPD(2); }
   else if (nv <= 4) { UPD(4); }
@@ -507,7 +573,34 @@ cudaError_t launch_sest(Ctx* c) {
   c->launches += 1;
   dim3 grid((c->Dp / 4 + 127) / 128, c->T * c->C);
   k_sest<<<grid, 128, 0, c->stream>>>(c->xacc, c->sest, c->R, c->K, c->C, c->Dp, c->D, c->seed,
-                                      c->em_iter);
+                                      c->em_iter, c->precond ? c->pw : nullptr, c->pshare);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_colnorm(Ctx* c) {
+  if (!c->precond) return cudaSuccess;
+  if (c->op == 1) {
+    // Phi_t = Omega_t F with F unitary: every column has ||Phi_t e_d||^2 = N_t / D
+    std::vector<float> h((size_t)c->T * c->Dp, 0.f);
+    for (int t = 0; t < c->T; ++t)
+      for (int d = 0; d < c->D; ++d)
+        h[(size_t)t * c->Dp + d] = (float)((double)(c->hN[t] / 2) / (double)c->D);
+    cudaError_t e = cudaMemcpyAsync(c->colnorm, h.data(), sizeof(float) * h.size(),
+                                    cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(c->stream);     // h is released on return
+  }
+  c->launches += 1;
+  dim3 grid(c->Dp / 128, c->T);
+  k_colnorm<<<grid, 128, 0, c->stream>>>(c->phi, c->drow, c->colnorm, c->Dp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_precond(Ctx* c) {
+  if (!c->precond) return cudaSuccess;
+  c->launches += 1;
+  k_precond<<<c->T * c->C, 256, 0, c->stream>>>(c->colnorm, c->alpha, c->pminv, c->pw, c->sumlogm,
+                                                c->C, c->Dp, c->D, c->beta);
   return cudaGetLastError();
 }
 
@@ -540,7 +633,8 @@ cudaError_t launch_tconst_dev(Ctx* c, const int64_t* dN) {
 
 cudaError_t launch_probes_out(const Ctx* c, int64_t em_iter, float* dst) {
   dim3 grid((c->D + 255) / 256, (unsigned)((int64_t)c->T * c->C * c->K));
-  k_probes_out<<<grid, 256, 0, c->stream>>>(dst, c->T, c->C, c->K, c->D, c->seed, em_iter);
+  k_probes_out<<<grid, 256, 0, c->stream>>>(dst, c->T, c->C, c->K, c->D, c->seed, em_iter,
+                                            c->pshare);
   return cudaGetLastError();
 }
 

@@ -261,14 +261,16 @@ k_dft_apply(const float* __restrict__ V, float* __restrict__ Z, float* __restric
 // r^T r and the new direction need no second kernel: d is read for the transform and (from
 // L2) for the updates; A d and then r stay in the shared buffer between the phases.  The
 // per-system bookkeeping is that of the separate CG update kernel (breakdown stop, gamma and
-// xi recorded for the first solve, convergence mask, step counts, counters).
+// xi recorded for the first solve, convergence mask, step counts, counters).  With pminv the
+// step is Jacobi-preconditioned: z = M^-1 r, rr = r^T z, d = z + xi d.
 __global__ void __launch_bounds__(kDftThreads)
 k_dft_cg_step(float* __restrict__ x, float* __restrict__ r, float* __restrict__ d,
               const float* __restrict__ mask_br, const float2* __restrict__ tw,
               const float* __restrict__ alpha, float* rr, const float* __restrict__ bb,
               int* steps, int* active, int* task_active, int* counters, float* gam, float* xih,
               int* psteps, unsigned long long* opcount, int record, int R, int K, int C, int Dp,
-              int D, int L, int npair, int U, float beta, float tol2) {
+              int D, int L, int npair, int U, float beta, float tol2,
+              const float* __restrict__ pminv) {
   extern __shared__ float2 Xf[];
   __shared__ float sh[33];
   __shared__ int s_go[2];
@@ -337,29 +339,34 @@ k_dft_cg_step(float* __restrict__ x, float* __restrict__ r, float* __restrict__ 
   if (!go1 && !go2) return;                         // block-uniform
   const float rr01 = rr[s1], rr02 = rr[s2];
   const float g1 = go1 ? rr01 / dad1 : 0.f, g2 = go2 ? rr02 / dad2 : 0.f;   // gamma_u
-  // x += gamma d, r -= gamma A d; r^T r
+  // x += gamma d, r -= gamma A d; z = M^-1 r (z = r without the preconditioner); r^T z
+  const float* mi1 = pminv != nullptr ? pminv + ((int64_t)t * C + j1 / (K + 1)) * Dp : nullptr;
+  const float* mi2 = (pminv != nullptr && has2) ? pminv + ((int64_t)t * C + j2 / (K + 1)) * Dp
+                                                : nullptr;
   float q1 = 0.f, q2 = 0.f;
   for (int i = threadIdx.x; i < D; i += blockDim.x) {
     const float2 ad = Xf[pad(i)];
-    float rv1 = 0.f, rv2 = 0.f;
+    float zv1 = 0.f, zv2 = 0.f;
     if (go1) {
       x1[i] = fmaf(g1, d1[i], x1[i]);
-      rv1 = fmaf(-g1, ad.x, r1[i]);
+      const float rv1 = fmaf(-g1, ad.x, r1[i]);
       r1[i] = rv1;
-      q1 = fmaf(rv1, rv1, q1);
+      zv1 = mi1 != nullptr ? rv1 * mi1[i] : rv1;
+      q1 = fmaf(rv1, zv1, q1);
     }
     if (go2) {
       x2[i] = fmaf(g2, d2[i], x2[i]);
-      rv2 = fmaf(-g2, ad.y, r2[i]);
+      const float rv2 = fmaf(-g2, ad.y, r2[i]);
       r2[i] = rv2;
-      q2 = fmaf(rv2, rv2, q2);
+      zv2 = mi2 != nullptr ? rv2 * mi2[i] : rv2;
+      q2 = fmaf(rv2, zv2, q2);
     }
-    Xf[pad(i)] = make_float2(rv1, rv2);
+    Xf[pad(i)] = make_float2(zv1, zv2);
   }
   const float rr11 = dft_block_sum(q1, sh);
   const float rr12 = dft_block_sum(q2, sh);
   const float xi1 = go1 ? rr11 / rr01 : 0.f, xi2 = go2 ? rr12 / rr02 : 0.f;   // xi_u
-  // d = r + xi d
+  // d = z + xi d
   for (int i = threadIdx.x; i < D; i += blockDim.x) {
     const float2 rv = Xf[pad(i)];
     if (go1) d1[i] = fmaf(xi1, d1[i], rv.x);
@@ -402,7 +409,8 @@ k_dft_residual(const float* __restrict__ X, const float* __restrict__ Bext,
                float* __restrict__ Rout, const int* __restrict__ ractive,
                const float* __restrict__ mask_br, const double2* __restrict__ tw,
                const float* __restrict__ alpha, int R, int K, int C, int Dp, int D, int L, int Rc,
-               int jstride, int npair, double beta, uint64_t seed, int64_t em_iter) {
+               int jstride, int npair, double beta, uint64_t seed, int64_t em_iter,
+               const float* __restrict__ pw, int pshare) {
   extern __shared__ double2 Xd[];
   const int t = blockIdx.x / npair, p = blockIdx.x - t * npair;
   const int jp1 = 2 * p, jp2 = 2 * p + 1;
@@ -446,8 +454,10 @@ k_dft_residual(const float* __restrict__ X, const float* __restrict__ Bext,
         } else if (k == 0) {
           b = b0;
         } else {
-          const uint32_t bits = probe_bits32(seed, em_iter, t, c, C, k - 1, i & ~31);
+          const uint32_t bits = probe_bits32(seed, em_iter, t, probe_cluster(c, pshare), C, k - 1,
+                                             i & ~31);
           b = ((bits >> (i & 31)) & 1u) ? -1.0 : 1.0;
+          if (pw != nullptr) b *= (double)pw[((int64_t)t * C + c) * Dp + i];   // sqrt(m) p
         }
         const double xv = (double)(q == 0 ? x1[i] : x2[i]);
         const double2 xd = Xd[pad(i)];
@@ -590,7 +600,7 @@ cudaError_t launch_dft_residual(Ctx* c, const float* X, const float* Bext, float
   k_dft_residual<<<c->T * npair, kDftThreads, sizeof(double2) * (c->D + c->D / 32), c->stream>>>(
       X, Bext, c->b0hi, c->b0lo, Rout, (Bext || all_systems) ? nullptr : c->ractive, c->dft_mask,
       static_cast<const double2*>(c->dft_tw64), c->alpha, c->R, c->K, c->C, c->Dp, c->D, c->dft_L,
-      Rc, js, npair, c->beta, c->seed, c->em_iter);
+      Rc, js, npair, c->beta, c->seed, c->em_iter, c->precond ? c->pw : nullptr, c->pshare);
   return cudaGetLastError();
 }
 
@@ -602,7 +612,7 @@ cudaError_t launch_dft_cg_step(Ctx* c, int record) {
       c->bb, c->steps, c->active, c->task_active, c->counters, c->gam, c->xi, c->psteps,
       c->prof_on ? reinterpret_cast<unsigned long long*>(c->opcount) : nullptr, record, c->R,
       c->K, c->C, c->Dp, c->D, c->dft_L, npair, c->U, (float)c->beta,
-      (float)(c->cg_tol * c->cg_tol));
+      (float)(c->cg_tol * c->cg_tol), c->precond ? c->pminv : nullptr);
   return cudaGetLastError();
 }
 

@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(256)
 k_ell(const float* __restrict__ xacc, const float* __restrict__ b0hi,
       const float* __restrict__ b0lo, const double* __restrict__ quad,
       const double* __restrict__ sumlogalpha, const float* __restrict__ rmu, double* logdet,
-      double* ell, int R, int K, int C, int Dp, int D) {
+      double* ell, int R, int K, int C, int Dp, int D, const double* __restrict__ sumlogm) {
   __shared__ double sh[33];
   const int tc = blockIdx.x, t = tc / C, c = tc % C;
   const int64_t off = ((int64_t)t * R + (int64_t)c * (K + 1)) * Dp;
@@ -161,7 +161,9 @@ k_ell(const float* __restrict__ xacc, const float* __restrict__ b0hi,
   if (threadIdx.x == 0) {
     double qs = 0.0;
     for (int k = 0; k < K; ++k) qs += quad[(int64_t)tc * K + k];
-    const double nu = -((double)D / (double)K) * qs;
+    // Jacobi-preconditioned CG: the quadrature is of M^-1/2 A M^-1/2, and log det A adds
+    // log det M = sum_d log m_d
+    const double nu = -((double)D / (double)K) * qs - (sumlogm != nullptr ? sumlogm[tc] : 0.0);
     logdet[tc] = nu;
     ell[tc] = nu + sumlogalpha[c] + b0mu;
   }
@@ -213,7 +215,8 @@ k_softmax(const double* __restrict__ ell, const double* __restrict__ logpi,
 cudaError_t launch_ell_softmax(Ctx* c, const float* rmu) {
   c->launches += 2;
   k_ell<<<c->T * c->C, 256, 0, c->stream>>>(c->xacc, c->b0hi, c->b0lo, c->quad, c->sumlogalpha,
-                                            rmu, c->logdet, c->ell, c->R, c->K, c->C, c->Dp, c->D);
+                                            rmu, c->logdet, c->ell, c->R, c->K, c->C, c->Dp, c->D,
+                                            c->precond ? c->sumlogm : nullptr);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_softmax<<<1, 256, 0, c->stream>>>(c->ell, c->logpi, c->tconst, c->q, c->assign, c->stats,
@@ -252,6 +255,36 @@ cudaError_t launch_mstep(Ctx* c) {
   dim3 grid((c->Dp + 255) / 256, c->C);
   k_mstep<<<grid, 256, 0, c->stream>>>(c->xacc, c->sest, c->q, c->alpha, c->T, c->C, c->R, c->K,
                                        c->Dp, c->D, c->alpha_min, c->alpha_max);
+  return cudaGetLastError();
+}
+
+// ---- learned priors: pi_c = max((1/T) sum_t q_tc, 1e-300), renormalised -----------------
+// (the maximiser of sum_tc q_tc log pi_c over the simplex; the floor keeps log pi finite)
+__global__ void __launch_bounds__(256)
+k_pi_update(const double* __restrict__ q, double* pi, double* logpi, int T, int C) {
+  __shared__ double tot;
+  for (int c = threadIdx.x; c < C; c += 256) {
+    double s = 0.0;
+    for (int t = 0; t < T; ++t) s += q[(int64_t)t * C + c];
+    pi[c] = fmax(s / (double)T, 1e-300);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0;
+    for (int c = 0; c < C; ++c) a += pi[c];
+    tot = a;
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < C; c += 256) {
+    const double v = pi[c] / tot;
+    pi[c] = v;
+    logpi[c] = log(v);
+  }
+}
+
+cudaError_t launch_pi_update(Ctx* c) {
+  c->launches += 1;
+  k_pi_update<<<1, 256, 0, c->stream>>>(c->q, c->pi, c->logpi, c->T, c->C);
   return cudaGetLastError();
 }
 

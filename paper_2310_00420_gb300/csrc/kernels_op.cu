@@ -215,6 +215,8 @@ struct P2Args {
   double beta_d;
   uint64_t seed;
   int64_t em_iter;
+  const float* pw;        // DS: sqrt(m) [T*C][Dp] scaling the probe right-hand sides, or null
+  int pshare;             // DS: probes shared across clusters
 };
 
 template <int TN, bool DS>
@@ -348,7 +350,10 @@ __global__ void __launch_bounds__(256, DS ? kP2MinBlocksDS : 1) k_pass2(P2Args p
             const bool on = (p.ractive == nullptr) || (p.ractive[sys] != 0);
             uint32_t bits = 0;
             if (on && p.Bext == nullptr && k > 0)
-              bits = probe_bits32(p.seed, p.em_iter, t, c, p.C, k - 1, dd & ~31);
+              bits = probe_bits32(p.seed, p.em_iter, t, probe_cluster(c, p.pshare), p.C, k - 1,
+                                  dd & ~31);
+            const float* wv = (p.pw != nullptr && k > 0)
+                                  ? p.pw + ((int64_t)t * p.C + c) * p.Dp : nullptr;
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
               const int d = dd + e;
@@ -358,6 +363,7 @@ __global__ void __launch_bounds__(256, DS ? kP2MinBlocksDS : 1) k_pass2(P2Args p
               } else if (d < p.D) {
                 b = (k == 0) ? (double)p.b0hi[(int64_t)t * p.Dp + d] + (double)p.b0lo[(int64_t)t * p.Dp + d]
                              : (double)probe_sign(bits, (d & 31));
+                if (wv != nullptr) b *= (double)wv[d];
               }
               const double z = (double)hi[half * 4 + e][jj] + (double)lo[half * 4 + e][jj];
               const double rv = b - p.beta_d * z - (double)aa[e] * (double)vv[e];
@@ -465,6 +471,8 @@ P2Args base_args(Ctx* c) {
   a.beta_d = c->beta;
   a.seed = c->seed;
   a.em_iter = c->em_iter;
+  a.pw = c->precond ? c->pw : nullptr;
+  a.pshare = c->pshare;
   a.Rc = c->R;
   a.jstride = 1;
   a.t0 = 0;
