@@ -156,10 +156,13 @@ cmcs_status cmcs_create(const cmcs_config *cfg, const float *Phi, const float *y
  * of y_t as 2 N_t real measurements of noise precision beta gives
  *     A_tc = beta Re(Phi_t^H Phi_t) + diag(alpha_c),   b0_t = beta Re(Phi_t^H y_t),
  * applied by FFT in O(D log D) per system (Sec. 3.3) instead of O(N_t D).  Requires
- * cfg->precision == CMCS_FP32 and D a power of two in [128, 8192] (else
- * CMCS_ERR_UNSUPPORTED).  The CG operator runs FP32 FFTs; the refinement residual runs FP64
- * FFTs.  Every call below works on such a context except cmcs_set_data and cmcs_adjoint
- * (CMCS_ERR_UNSUPPORTED).  mask and y are host or device per on_device. */
+ * cfg->precision == CMCS_FP32 and D either a power of two in [128, 8192] (one CTA transforms
+ * a pair of systems in shared memory, fused with the CG update) or D = 2^a 5^b with 16 | D,
+ * 128 <= D <= 2^20, e.g. 100,000 (four-step transforms, D = n1 n2 with n1, n2 <= 1024, in
+ * three launches per application); else CMCS_ERR_UNSUPPORTED.  The CG operator runs FP32
+ * FFTs; the refinement residual and b0 run FP64 FFTs.  Every call below works on such a
+ * context except cmcs_set_data and cmcs_adjoint (CMCS_ERR_UNSUPPORTED).  mask and y are host
+ * or device per on_device. */
 cmcs_status cmcs_create_dft(const cmcs_config *cfg, const uint8_t *mask, const float *y,
                             int on_device, void *stream, cmcs_ctx **out);
 

@@ -83,6 +83,27 @@ def rhs_mean_fourier(mask_t: np.ndarray, y_t: np.ndarray, beta: float) -> np.nda
     return beta * (np.sqrt(D) * np.fft.ifft(Y)).real
 
 
+class FourierSensing:
+    """Phi_t = Omega_t F of Sec. 4 held as its 0/1 frequency mask, for E-steps at sizes where
+    the dense real-stacked matrix does not fit.  Same reading as ``apply_A_fourier``: unitary
+    F, real z, the complex measurements taken as [Re y_t; Im y_t] (ascending frequency)."""
+
+    def __init__(self, mask_t: np.ndarray):
+        self.mask = np.asarray(mask_t)
+
+    def apply(self, beta: float, alpha_c: np.ndarray, V: np.ndarray) -> np.ndarray:
+        return apply_A_fourier(self.mask, beta, alpha_c, V)
+
+    def rhs(self, y_real: np.ndarray, beta: float) -> np.ndarray:
+        n = y_real.shape[0] // 2
+        return rhs_mean_fourier(self.mask, y_real[:n] + 1j * y_real[n:], beta)
+
+    def diag(self, beta: float, alpha_c: np.ndarray) -> np.ndarray:
+        """The diagonal of A: every column of Omega_t F has squared norm N_t / D."""
+        m = self.mask
+        return beta * float(np.count_nonzero(m)) / m.shape[0] + np.asarray(alpha_c, np.float64)
+
+
 def task_const(y_t: np.ndarray, beta: float) -> float:
     """The c-independent part of log p(y_t | alpha_c):  log p = ell/2 - task_const, with
     task_const = (N log 2pi - N log beta + beta ||y||^2) / 2 (from Eqs. 1 and 3)."""
@@ -338,7 +359,7 @@ def logdet_estimate(gamma: np.ndarray, xi: np.ndarray, steps: np.ndarray, D: int
 # --------------------------------------------------------------------------------------
 
 def _task_arrays(Phi_list, y_list):
-    P = [np.asarray(p, dtype=np.float64) for p in Phi_list]
+    P = [p if isinstance(p, FourierSensing) else np.asarray(p, dtype=np.float64) for p in Phi_list]
     Y = [np.asarray(v, dtype=np.float64) for v in y_list]
     return P, Y
 
@@ -420,6 +441,9 @@ def cofem_estep(Phi_list, y_list, alpha: np.ndarray, pi: np.ndarray, beta: float
     of alpha and C_total the full cluster count (bounded samples).  With refine_tol set, mu and every x_k are refined
     (``refine``) after the first CG solve, which alone supplies the Lanczos coefficients.
 
+    An entry of Phi_list may be a ``FourierSensing`` (Sec. 4's Phi_t = Omega_t F); its y_list
+    entry is then [Re y_t; Im y_t].
+
     Variants (off by default):
     * probe_share: every cluster of task t uses the probes of cluster 0, p_{t,c,k} = p_{t,0,k}
       (common random numbers across c, so the estimation noise of ell_tc - ell_tc' shrinks).
@@ -444,17 +468,21 @@ def cofem_estep(Phi_list, y_list, alpha: np.ndarray, pi: np.ndarray, beta: float
     rel = np.zeros((T, C, K + 1))
     consts = np.array([task_const(Y[t], beta) for t in range(T)])
     for t in range(T):
-        b0 = rhs_mean(P[t], Y[t], beta)
+        fs = isinstance(P[t], FourierSensing)
+        b0 = P[t].rhs(Y[t], beta) if fs else rhs_mean(P[t], Y[t], beta)
         for c in range(C):
             if probe_fn is None:
                 pc = 0 if probe_share else clusters[c]
                 Pk = philox.probes(seed, em_iter, tasks[t], pc, C_total, K, D)
             else:
                 Pk = np.asarray(probe_fn(t, c), dtype=np.float64)
-            op = lambda V, idx, t=t, c=c: apply_A(P[t], beta, alpha[c], V)
+            if fs:
+                op = lambda V, idx, t=t, c=c: P[t].apply(beta, alpha[c], V)
+            else:
+                op = lambda V, idx, t=t, c=c: apply_A(P[t], beta, alpha[c], V)
             st = None if steps is None else steps[t, c]
             if precond:
-                m_d = jacobi_diag(P[t], beta, alpha[c])
+                m_d = P[t].diag(beta, alpha[c]) if fs else jacobi_diag(P[t], beta, alpha[c])
                 w = np.sqrt(m_d)
                 B = np.concatenate([b0[:, None], w[:, None] * Pk.T], axis=1)
                 res = pcg(op, B, 1.0 / m_d, tol, max_iter, st)

@@ -117,8 +117,9 @@ cudaError_t timed_operator(Ctx* c, int record) {
     cudaError_t er = cudaEventRecordWithFlags(c->prof_ev[2 * c->prof_nev], c->stream, flags);
     if (er != cudaSuccess) return er;
   }
-  // Fourier: the operator and the CG update are one kernel
-  cudaError_t e = c->op == 1 ? launch_dft_cg_step(c, record) : launch_operator(c, c->d, c->ad, 1);
+  // Fourier with D in one CTA: the operator and the CG update are one kernel
+  cudaError_t e = (c->op == 1 && !c->dft_large) ? launch_dft_cg_step(c, record)
+                                                : launch_operator(c, c->d, c->ad, 1);
   if (ev && e == cudaSuccess) {
     e = cudaEventRecordWithFlags(c->prof_ev[2 * c->prof_nev + 1], c->stream, flags);
     c->prof_nev++;
@@ -143,7 +144,7 @@ void fold_events(Ctx* c) {
 cmcs_status cg_steps_direct(Ctx* c, int record, int n) {
   for (int i = 0; i < n; ++i) {
     CK(timed_operator(c, record));
-    if (c->op != 1) CK(launch_cg_update(c, record));
+    if (c->op != 1 || c->dft_large) CK(launch_cg_update(c, record));
     c->op_applies++;
   }
   return CMCS_OK;
@@ -391,8 +392,8 @@ cmcs_status create_ctx(const cmcs_config* cfg, const float* Phi, const float* y,
     return CMCS_ERR_INVALID_ARG;
   }
   if (mask && (cfg->precision != CMCS_FP32 || !dft_size_ok(cfg->D))) {
-    set_err(nullptr, "the Fourier operator needs precision CMCS_FP32 and D a power of two in "
-                     "[128, %d]", kDftMaxD);
+    set_err(nullptr, "the Fourier operator needs precision CMCS_FP32 and D either a power of two "
+                     "in [128, %d] or D = 2^a 5^b with 16 | D, up to %d", kDftMaxD, kDftMaxLarge);
     return CMCS_ERR_UNSUPPORTED;
   }
   cmcs_ctx* h = static_cast<cmcs_ctx*>(calloc(1, sizeof(cmcs_ctx)));
@@ -693,7 +694,13 @@ cmcs_status cmcs_profile_read(const cmcs_ctx* hc, cmcs_profile_data* out) {
   double fl = 0.0, by = 0.0;
   for (int t = 0; t < c->T; ++t) {
     const double n = (double)c->hN[t], D = (double)c->D, R = (double)c->R;
-    if (c->op == 1) {
+    if (c->op == 1 && c->dft_large) {
+      // the operator alone (three four-step launches): a forward and an inverse complex
+      // transform (5 D log2 D each) per two systems, mask and scaling; d read, A d written,
+      // the mask
+      fl += (double)cnt[t] * R * (5.0 * D * log2(D) + 4.0 * D);
+      by += (double)cnt[t] * (8.0 * R * D + 4.0 * D);
+    } else if (c->op == 1) {
       // one CG step fused with the operator: one complex FFT pair (5 D log2 D each) per two
       // systems plus the update; d, x, r read, x, r, d written, the mask
       fl += (double)cnt[t] * R * (5.0 * D * (double)c->dft_L + 12.0 * D);

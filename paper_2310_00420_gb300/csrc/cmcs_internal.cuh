@@ -167,6 +167,9 @@ struct Ctx {
   int* dft_freq;          // [sum N_t] sampled frequencies, ascending per task
   int64_t* dft_off;       // [T+1]
   float* dft_y;           // [sum N_t][2] measured coefficients
+  int dft_large;          // D beyond one CTA (or not a power of two): four-step transforms
+  int dft_ndt;            // partial d^T A d slots per system written by the Fourier operator
+  void* fs;               // four-step plan, tables and work buffer (kernels_dft_large.cu)
   void *dhi, *dlo;     // [S][Dp] BF16 hi and lo parts of the CG direction d (tensor-core path)
 
   char err[512];
@@ -199,7 +202,8 @@ cudaError_t launch_resid_norm(Ctx* c);
 // W = Phi V for Rc columns (systems j = j' * jstride); with Wlo, as a compensated pair W + Wlo
 cudaError_t launch_phi_v(Ctx* c, const float* V, float* W, float* Wlo, int Rc, int jstride);
 // structured (Fourier) operator (kernels_dft.cu)
-constexpr int kDftMaxD = 8192;     // one pair's FP64 spectrum in shared memory
+constexpr int kDftMaxD = 8192;     // one pair's FP64 spectrum in shared memory (single CTA)
+constexpr int kDftMaxLarge = 1 << 20;   // four-step transforms
 bool dft_size_ok(int D);
 int dft_create(Ctx* c, const uint8_t* mask, const float* y, int on_device);
 void dft_destroy(Ctx* c);
@@ -209,6 +213,14 @@ cudaError_t launch_dft_residual(Ctx* c, const float* X, const float* Bext, float
 cudaError_t launch_dft_b0(Ctx* c);
 // one whole CG step (operator and update) for every active system of a Fourier context
 cudaError_t launch_dft_cg_step(Ctx* c, int record);
+// four-step transforms for D = 2^a 5^b (16 | D, D <= 2^20) beyond one CTA (kernels_dft_large.cu)
+bool dft_large_ok(int D);
+int fs_create(Ctx* c, const uint8_t* hmask);   // hmask: host [T][D]
+void fs_destroy(Ctx* c);
+cudaError_t fs_apply(Ctx* c, const float* V, float* Z, int with_dots);
+cudaError_t fs_residual(Ctx* c, const float* X, const float* Bext, float* Rout, int all_systems,
+                        int means_only);
+cudaError_t fs_b0(Ctx* c);
 // adjoint gradients (adjoint.cu)
 cudaError_t launch_adj_dy(Ctx* c, const float* Wl, const float* Wl_lo, float* dy);
 cudaError_t launch_adj_dalpha(Ctx* c, const float* lam, float* dalpha);

@@ -542,13 +542,13 @@ cudaError_t launch_cg_update(Ctx* c, int record) {
 #define UPD(NV)                                                                                  \
   if (c->tc != nullptr)                                                                          \
     k_cg_update<NV, true><<<c->S, 256, 0, c->stream>>>(                                          \
-        c->x, c->r, c->d, c->ad, c->part, c->alpha, c->op == 1 ? 1 : c->Dp / 128, c->rr, c->bb, c->steps,        \
+        c->x, c->r, c->d, c->ad, c->part, c->alpha, c->op == 1 ? c->dft_ndt : c->Dp / 128, c->rr, c->bb, c->steps,        \
         c->active, c->task_active, c->counters, c->gam, c->xi, c->psteps, record, c->R, c->K,    \
         c->C, c->Dp, c->S, c->U, tol2, static_cast<__nv_bfloat16*>(c->dhi),                      \
         static_cast<__nv_bfloat16*>(c->dlo), c->precond ? c->pminv : nullptr);                   \
   else                                                                                           \
     k_cg_update<NV, false><<<c->S, 256, 0, c->stream>>>(                                         \
-        c->x, c->r, c->d, c->ad, c->part, c->alpha, c->op == 1 ? 1 : c->Dp / 128, c->rr, c->bb, c->steps,        \
+        c->x, c->r, c->d, c->ad, c->part, c->alpha, c->op == 1 ? c->dft_ndt : c->Dp / 128, c->rr, c->bb, c->steps,        \
         c->active, c->task_active, c->counters, c->gam, c->xi, c->psteps, record, c->R, c->K,    \
         c->C, c->Dp, c->S, c->U, tol2, static_cast<__nv_bfloat16*>(c->dhi),                      \
         static_cast<__nv_bfloat16*>(c->dlo), c->precond ? c->pminv : nullptr)

@@ -19,6 +19,7 @@
 // rounding error stays ~log2(D) units of FP64, below the double-single residual of the dense
 // path).  Twiddles come from tables computed on the host in FP64.
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <vector>
@@ -497,15 +498,22 @@ k_dft_b0(const float2* __restrict__ y, const int* __restrict__ freq,
 }
 
 // ---- host side ----------------------------------------------------------------------------
-bool dft_size_ok(int D) {
-  return D >= 128 && D <= kDftMaxD && (D & (D - 1)) == 0;
-}
+namespace {
+bool dft_small_ok(int D) { return D >= 128 && D <= kDftMaxD && (D & (D - 1)) == 0; }
+}  // namespace
+
+bool dft_size_ok(int D) { return dft_small_ok(D) || dft_large_ok(D); }
 
 int dft_create(Ctx* c, const uint8_t* mask, const float* y, int on_device) {
   const int T = c->T, D = c->D;
   int L = 0;
   while ((1 << L) < D) ++L;
   c->dft_L = L;
+  // CMCS_DFT_FOURSTEP=1 (evaluation switch) takes the four-step path at every supported D
+  const char* fsenv = getenv("CMCS_DFT_FOURSTEP");
+  const bool force = fsenv != nullptr && fsenv[0] == '1' && dft_large_ok(D);
+  c->dft_large = (dft_small_ok(D) && !force) ? 0 : 1;
+  c->dft_ndt = 1;
   std::vector<uint8_t> hm((size_t)T * D);
   if (on_device) {
     if (cudaMemcpy(hm.data(), mask, hm.size(), cudaMemcpyDeviceToHost) != cudaSuccess) return 1;
@@ -522,7 +530,7 @@ int dft_create(Ctx* c, const uint8_t* mask, const float* y, int on_device) {
       if (m[k]) freq.push_back(k);
     off[(size_t)t + 1] = (int64_t)freq.size();
     if (off[(size_t)t + 1] - off[(size_t)t] != c->hN[t] / 2) return 5;
-    for (int pos = 0; pos < D; ++pos) {
+    for (int pos = 0; !c->dft_large && pos < D; ++pos) {
       unsigned k = 0;
       for (int b = 0; b < L; ++b) k |= (unsigned)((pos >> b) & 1) << (L - 1 - b);
       const int kk = (int)k, km = (D - kk) & (D - 1);
@@ -565,6 +573,7 @@ int dft_create(Ctx* c, const uint8_t* mask, const float* y, int on_device) {
                       sizeof(float), (size_t)n, kin) == cudaSuccess;
   }
   if (!ok) return 3;
+  if (c->dft_large) return fs_create(c, hm.data());
   const int sm32 = (int)sizeof(float2) * (D + D / 32), sm64 = (int)sizeof(double2) * (D + D / 32);
   if (cudaFuncSetAttribute(k_dft_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, sm32) != cudaSuccess ||
       cudaFuncSetAttribute(k_dft_cg_step, cudaFuncAttributeMaxDynamicSharedMemorySize, sm32) != cudaSuccess ||
@@ -575,12 +584,14 @@ int dft_create(Ctx* c, const uint8_t* mask, const float* y, int on_device) {
 }
 
 void dft_destroy(Ctx* c) {
+  fs_destroy(c);
   void* ptrs[] = {c->dft_mask, c->dft_tw32, c->dft_tw64, c->dft_freq, c->dft_off, c->dft_y};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
 
 cudaError_t launch_dft_apply(Ctx* c, const float* V, float* Z, int with_dots) {
+  if (c->dft_large) return fs_apply(c, V, Z, with_dots);
   const int npair = (c->R + 1) / 2;
   c->launches += 1;
   k_dft_apply<<<c->T * npair, kDftThreads, sizeof(float2) * (c->D + c->D / 32), c->stream>>>(
@@ -593,6 +604,7 @@ cudaError_t launch_dft_apply(Ctx* c, const float* V, float* Z, int with_dots) {
 
 cudaError_t launch_dft_residual(Ctx* c, const float* X, const float* Bext, float* Rout,
                                 int all_systems, int means_only) {
+  if (c->dft_large) return fs_residual(c, X, Bext, Rout, all_systems, means_only);
   const int Rc = means_only ? c->C : c->R;
   const int js = means_only ? c->K + 1 : 1;
   const int npair = (Rc + 1) / 2;
@@ -605,6 +617,7 @@ cudaError_t launch_dft_residual(Ctx* c, const float* X, const float* Bext, float
 }
 
 cudaError_t launch_dft_cg_step(Ctx* c, int record) {
+  if (c->dft_large) return cudaErrorInvalidValue;   // the four-step path updates separately
   const int npair = (c->R + 1) / 2;
   c->launches += 1;
   k_dft_cg_step<<<c->T * npair, kDftThreads, sizeof(float2) * (c->D + c->D / 32), c->stream>>>(
@@ -617,6 +630,7 @@ cudaError_t launch_dft_cg_step(Ctx* c, int record) {
 }
 
 cudaError_t launch_dft_b0(Ctx* c) {
+  if (c->dft_large) return fs_b0(c);
   c->launches += 1;
   k_dft_b0<<<c->T, kDftThreads, sizeof(double2) * (c->D + c->D / 32), c->stream>>>(
       reinterpret_cast<const float2*>(c->dft_y), c->dft_freq, c->dft_off, c->b0hi, c->b0lo,

@@ -257,6 +257,26 @@ def fourier(seed: int = 0) -> FourierWorkload:
                         cg_max_iter=50, em_iters=50, seed=seed)
 
 
+def fourier_2k(seed: int = 0) -> FourierWorkload:
+    """A length that is not a power of two (D = 2000 = 2^4 5^3): T=4, C=2, N=500 (D/4); 5%
+    sparsity; sigma 0.05; K=15; CG tol 1e-8 (max 100)."""
+    return make_fourier("fourier-2k", 4, 2, 2000, 500, K=15, cg_tol=1e-8, cg_max_iter=100,
+                        em_iters=10, seed=seed)
+
+
+def fourier_16k(seed: int = 0) -> FourierWorkload:
+    """The Sec. 4 setting of ``fourier`` at D = 16384 (N = 4096)."""
+    return make_fourier("fourier-16k", 40, 4, 16384, 4096, perturb=0.10, K=15, cg_tol=1e-5,
+                        cg_max_iter=50, em_iters=50, seed=seed)
+
+
+def fourier_100k(seed: int = 0) -> FourierWorkload:
+    """The Sec. 4 setting of ``fourier`` at the largest length of the paper's timings,
+    D = 100,000 = 2^5 5^5 (N = 25,000)."""
+    return make_fourier("fourier-100k", 40, 4, 100000, 25000, perturb=0.10, K=15, cg_tol=1e-5,
+                        cg_max_iter=50, em_iters=50, seed=seed)
+
+
 def uniform_alpha(C: int, D: int, seed: int, tag: int = _TAG_ALPHA) -> np.ndarray:
     """A seeded Uniform(0,1) state for alpha (FP32 values), for tests that start from a
     given alpha instead of the library's own initial draw."""
@@ -307,4 +327,7 @@ WORKLOADS = {
     "differentiation": differentiation,
     "fourier-small": fourier_small,
     "fourier": fourier,
+    "fourier-2k": fourier_2k,
+    "fourier-16k": fourier_16k,
+    "fourier-100k": fourier_100k,
 }

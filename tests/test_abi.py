@@ -123,14 +123,16 @@ def test_create_rejects_null_inputs_and_bad_pi(L):
 
 
 def test_create_dft_validates_without_cuda(L):
-    """The Fourier constructor rejects a null mask, a D that is not a power of two in
-    [128, 8192], and any precision but FP32, before touching the GPU."""
+    """The Fourier constructor rejects a null mask, a D that is neither a power of two in
+    [128, 8192] nor 2^a 5^b with 16 | D up to 2^20, and any precision but FP32, before
+    touching the GPU."""
     h = ctypes.c_void_p()
     y = np.zeros((8, 2), np.float32)
     cfg, keep = _cfg(D=256)
     assert L.cmcs_create_dft(ctypes.byref(cfg), None, y.ctypes.data, 0, None,
                              ctypes.byref(h)) == cmcs.ERR_INVALID_ARG
-    for bad in (dict(D=200), dict(D=64), dict(D=16384), dict(D=256, precision=2)):
+    for bad in (dict(D=200), dict(D=64), dict(D=3072), dict(D=1 << 21), dict(D=256, precision=2),
+                dict(D=100000, precision=2)):
         cfg, keep = _cfg(**bad)
         mask = np.zeros((2, cfg.D), np.uint8)
         assert L.cmcs_create_dft(ctypes.byref(cfg), mask.ctypes.data, y.ctypes.data, 0, None,

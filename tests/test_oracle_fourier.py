@@ -49,3 +49,23 @@ def test_full_sampling_is_the_identity():
     y = np.fft.fft(z) / np.sqrt(D)
     np.testing.assert_allclose(cofem.rhs_mean_fourier(mask, y, 3.0), 3.0 * z, rtol=1e-12,
                                atol=1e-12)
+
+
+def test_fourier_sensing_estep_equals_dense_estep():
+    """The E-step on FourierSensing tasks (FFT-form A v, b0 and diagonal) equals the E-step on
+    the dense real-stacked matrices, plain and Jacobi-preconditioned, at a length that is not
+    a power of two."""
+    wl = synth.make_fourier("f", 3, 2, 160, 40, K=4, cg_tol=1e-12, cg_max_iter=200, seed=2)
+    alpha = np.random.default_rng(3).uniform(0.5, 50.0, size=(2, 160))
+    Y = [wl.y_real(t) for t in range(wl.T)]
+    dense = [wl.phi_real(t) for t in range(wl.T)]
+    ops = [cofem.FourierSensing(wl.mask[t]) for t in range(wl.T)]
+    for t in range(wl.T):
+        np.testing.assert_allclose(ops[t].diag(wl.beta, alpha[0]),
+                                   cofem.jacobi_diag(dense[t], wl.beta, alpha[0]), rtol=1e-12)
+    for pc in (False, True):
+        a = cofem.cofem_estep(dense, Y, alpha, wl.pi, wl.beta, wl.K, 1, 0, 1e-12, 200,
+                              precond=pc)
+        b = cofem.cofem_estep(ops, Y, alpha, wl.pi, wl.beta, wl.K, 1, 0, 1e-12, 200, precond=pc)
+        for key in ("mu", "s", "logdet", "q"):
+            np.testing.assert_allclose(b[key], a[key], rtol=1e-8, atol=1e-12)
