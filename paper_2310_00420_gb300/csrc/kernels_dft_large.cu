@@ -61,17 +61,21 @@ __device__ __forceinline__ CT fs_sub(CT a, CT b) { return Cx<CT>::mk(a.x - b.x, 
 
 }  // namespace
 
-// radices of one sub-transform of length L (product of r[0..n))
+// radices of one sub-transform of length L (product of r[0..n)), and for pass q the
+// multiply-high reciprocals of L / r[q] and of Ns = r[0] ... r[q-1] (see fs_div)
 struct FsRadix {
   int L, n;
   int r[kFsMaxRadices];
+  uint64_t mM[kFsMaxRadices], mN[kFsMaxRadices];
 };
 
 // the split D = n1 * n2 and the CTA shapes of the three passes
 struct FsPlan {
   int n1, n2;
-  int nb;     // columns i2 per CTA in the column passes (divides n2)
-  int nbr;    // rows k1 per CTA in the row pass (divides n1)
+  int nb;     // columns i2 per CTA in the FP64 column passes (divides n2, a power of two)
+  int nb32;   // the same for the FP32 column passes
+  int nbr;    // rows k1 per CTA in the row pass (the last block may be partial)
+  uint64_t mn2;   // reciprocal of n2
   FsRadix p1, p2;
 };
 
@@ -82,15 +86,29 @@ struct FsPairs {
 
 namespace {
 
+// floor(n / d) for 0 <= n < 2^15 and 1 <= d <= 1024 from m = ceil(2^32 / d): the high word of
+// n * m (m = 2^32 for d = 1).  Exact over that whole range (checked exhaustively on the host).
+__device__ __forceinline__ int fs_div(int n, uint64_t m) {
+  return (int)(__umulhi((unsigned)n, (unsigned)m) + ((m >> 32) != 0 ? (unsigned)n : 0u));
+}
+
 // one Stockham pass of radix RX over nseq sequences of length L (stride ls) from src to dst:
 // for j < L / RX, k = j mod Ns: v_r = src[j + r L/RX] W_{Ns RX}^{k r}, then the RX-point DFT,
-// written to dst[(j / Ns) Ns RX + k + r Ns]
+// written to dst[floor(j / Ns) Ns RX + k + r Ns]
 template <int RX, typename CT, bool INV>
 __device__ __forceinline__ void fs_pass(const CT* __restrict__ src, CT* __restrict__ dst, int L,
-                                        int Ns, int nseq, int ls, const CT* __restrict__ tab) {
+                                        int Ns, uint64_t mM, uint64_t mN, int nseq, int ls,
+                                        const CT* __restrict__ tab) {
   const int M = L / RX, ts = L / (Ns * RX);
+  // 5-point DFT constants W_5 = (c1, -s1), W_5^2 = (c2, -s2), from the table
+  CT w51, w52;
+  if constexpr (RX == 5) {
+    w51 = tab[L / 5];
+    w52 = tab[2 * (L / 5)];
+  }
   for (int idx = threadIdx.x; idx < nseq * M; idx += blockDim.x) {
-    const int s = idx / M, j = idx - s * M, k = j % Ns;
+    const int s = fs_div(idx, mM), j = idx - s * M;
+    const int jq = fs_div(j, mN), k = j - jq * Ns;
     const CT* in = src + s * ls;
     CT* out = dst + s * ls;
     CT v[RX];
@@ -114,20 +132,27 @@ __device__ __forceinline__ void fs_pass(const CT* __restrict__ src, CT* __restri
       y[1] = INV ? fs_sub(t1, mit3) : fs_add(t1, mit3);
       y[3] = INV ? fs_add(t1, mit3) : fs_sub(t1, mit3);
     } else {
-      // direct 5-point DFT, W_5^q = tab[q L / 5]
-      const int st = L / 5;
-#pragma unroll
-      for (int s5 = 0; s5 < 5; ++s5) {
-        CT a = v[0];
-#pragma unroll
-        for (int r = 1; r < 5; ++r) {
-          const CT w = tab[((r * s5) % 5) * st];
-          a = fs_add(a, INV ? fs_mulc(v[r], w) : fs_mul(v[r], w));
-        }
-        y[s5] = a;
-      }
+      // 5-point DFT in symmetric form: with t1 = v1 + v4, t2 = v2 + v3, t3 = v1 - v4,
+      // t4 = v2 - v3, cos/sin c_q, s_q of 2 pi q / 5:
+      //   y0 = v0 + t1 + t2,  y1, y4 = a1 -+ i b1,  y2, y3 = a2 -+ i b2 (forward; inverse +-)
+      //   a1 = v0 + c1 t1 + c2 t2, a2 = v0 + c2 t1 + c1 t2, b1 = s1 t3 + s2 t4, b2 = s2 t3 - s1 t4
+      using RT = typename Cx<CT>::R;
+      const RT c1 = w51.x, s1 = -w51.y, c2 = w52.x, s2 = -w52.y;
+      const CT t1 = fs_add(v[1], v[4]), t2 = fs_add(v[2], v[3]);
+      const CT t3 = fs_sub(v[1], v[4]), t4 = fs_sub(v[2], v[3]);
+      y[0] = fs_add(v[0], fs_add(t1, t2));
+      const CT a1 = Cx<CT>::mk(v[0].x + c1 * t1.x + c2 * t2.x, v[0].y + c1 * t1.y + c2 * t2.y);
+      const CT a2 = Cx<CT>::mk(v[0].x + c2 * t1.x + c1 * t2.x, v[0].y + c2 * t1.y + c1 * t2.y);
+      const CT b1 = Cx<CT>::mk(s1 * t3.x + s2 * t4.x, s1 * t3.y + s2 * t4.y);
+      const CT b2 = Cx<CT>::mk(s2 * t3.x - s1 * t4.x, s2 * t3.y - s1 * t4.y);
+      // -i b = (b.y, -b.x)
+      const CT mb1 = Cx<CT>::mk(b1.y, -b1.x), mb2 = Cx<CT>::mk(b2.y, -b2.x);
+      y[1] = INV ? fs_sub(a1, mb1) : fs_add(a1, mb1);
+      y[4] = INV ? fs_add(a1, mb1) : fs_sub(a1, mb1);
+      y[2] = INV ? fs_sub(a2, mb2) : fs_add(a2, mb2);
+      y[3] = INV ? fs_add(a2, mb2) : fs_sub(a2, mb2);
     }
-    const int base = (j / Ns) * Ns * RX + k;
+    const int base = jq * Ns * RX + k;
 #pragma unroll
     for (int r = 0; r < RX; ++r) out[base + r * Ns] = y[r];
   }
@@ -139,9 +164,9 @@ __device__ CT* fs_fft(CT* a, CT* b, const FsRadix& p, int nseq, int ls, const CT
   int Ns = 1;
   for (int q = 0; q < p.n; ++q) {
     const int R = p.r[q];
-    if (R == 4) fs_pass<4, CT, INV>(a, b, p.L, Ns, nseq, ls, tab);
-    else if (R == 2) fs_pass<2, CT, INV>(a, b, p.L, Ns, nseq, ls, tab);
-    else fs_pass<5, CT, INV>(a, b, p.L, Ns, nseq, ls, tab);
+    if (R == 4) fs_pass<4, CT, INV>(a, b, p.L, Ns, p.mM[q], p.mN[q], nseq, ls, tab);
+    else if (R == 2) fs_pass<2, CT, INV>(a, b, p.L, Ns, p.mM[q], p.mN[q], nseq, ls, tab);
+    else fs_pass<5, CT, INV>(a, b, p.L, Ns, p.mM[q], p.mN[q], nseq, ls, tab);
     __syncthreads();
     CT* t = a;
     a = b;
@@ -149,6 +174,21 @@ __device__ CT* fs_fft(CT* a, CT* b, const FsRadix& p, int nseq, int ls, const CT
     Ns *= R;
   }
   return a;
+}
+
+// W_D^m = W_D^(m - m mod 64) W_D^(m mod 64): two reads from a compact part of the table
+// (D / 64 entries at stride 64, and the first 64) instead of one scattered over all of it
+template <typename CT>
+__device__ __forceinline__ CT fs_twD(const CT* __restrict__ tabD, const CT* lo, int64_t m) {
+  return fs_mul(tabD[m & ~(int64_t)63], lo[m & 63]);
+}
+
+// the sub-transform's table (L entries) and the first 64 entries of W_D into shared memory
+template <typename CT>
+__device__ __forceinline__ void fs_stage_tables(CT* tw, CT* lo, const CT* __restrict__ tab, int L,
+                                                const CT* __restrict__ tabD) {
+  for (int i = threadIdx.x; i < L; i += blockDim.x) tw[i] = tab[i];
+  if (threadIdx.x < 64) lo[threadIdx.x] = tabD[threadIdx.x];
 }
 
 // the two systems of pair p of task t, and whether each takes part
@@ -179,27 +219,32 @@ k_fs_cols_fwd(const float* __restrict__ X, CT* __restrict__ Y, const CT* __restr
               const CT* __restrict__ tabD, FsPlan pl, FsPairs pp, const int* __restrict__ flags,
               const int* __restrict__ task_active) {
   extern __shared__ __align__(16) unsigned char fs_sm[];
+  const int nb = sizeof(CT) == sizeof(float2) ? pl.nb32 : pl.nb, lnb = __ffs(nb) - 1;
   const int ls = pl.n1 + 1;
   CT* A = reinterpret_cast<CT*>(fs_sm);
-  CT* B = A + pl.nb * ls;
+  CT* B = A + nb * ls;
+  CT* tw = B + nb * ls;
+  CT* lo = tw + pl.n1;
   const int pi = blockIdx.x;
   const FsSys q = fs_sys(pp, pi, flags);
   if (task_active != nullptr && task_active[q.t] == 0) return;     // block-uniform
   if (!q.on1 && !q.on2) return;
-  const int c0 = blockIdx.y * pl.nb;
+  fs_stage_tables(tw, lo, tab1, pl.n1, tabD);
+  const int c0 = blockIdx.y * nb;
   const float* x1 = X + q.s1 * pp.Dp;
   const float* x2 = X + q.s2 * pp.Dp;
-  for (int idx = threadIdx.x; idx < pl.n1 * pl.nb; idx += blockDim.x) {
-    const int i1 = idx / pl.nb, cc = idx - i1 * pl.nb;
+#pragma unroll 4
+  for (int idx = threadIdx.x; idx < pl.n1 * nb; idx += blockDim.x) {
+    const int i1 = idx >> lnb, cc = idx & (nb - 1);
     const int64_t n = (int64_t)pl.n2 * i1 + c0 + cc;
     A[cc * ls + i1] = Cx<CT>::mk(q.on1 ? x1[n] : 0.f, q.on2 ? x2[n] : 0.f);
   }
   __syncthreads();
-  const CT* res = fs_fft<CT, false>(A, B, pl.p1, pl.nb, ls, tab1);
+  const CT* res = fs_fft<CT, false>(A, B, pl.p1, nb, ls, tw);
   CT* Yp = Y + (int64_t)pi * pp.D;
-  for (int idx = threadIdx.x; idx < pl.n1 * pl.nb; idx += blockDim.x) {
-    const int k1 = idx / pl.nb, cc = idx - k1 * pl.nb, i2 = c0 + cc;
-    Yp[(int64_t)k1 * pl.n2 + i2] = fs_mul(res[cc * ls + k1], tabD[(int64_t)i2 * k1]);
+  for (int idx = threadIdx.x; idx < pl.n1 * nb; idx += blockDim.x) {
+    const int k1 = idx >> lnb, cc = idx & (nb - 1), i2 = c0 + cc;
+    Yp[(int64_t)k1 * pl.n2 + i2] = fs_mul(res[cc * ls + k1], fs_twD(tabD, lo, (int64_t)i2 * k1));
   }
 }
 
@@ -215,36 +260,45 @@ k_fs_rows(CT* __restrict__ Y, const CT* __restrict__ spec, const CT* __restrict_
   const int ls = pl.n2 + 1;
   CT* A = reinterpret_cast<CT*>(fs_sm);
   CT* B = A + pl.nbr * ls;
+  CT* tw = B + pl.nbr * ls;
+  CT* lo = tw + pl.n2;
   const int pi = blockIdx.x;
   const FsSys q = fs_sys(pp, pi, flags);
   if (task_active != nullptr && task_active[q.t] == 0) return;     // block-uniform
   if (!q.on1 && !q.on2) return;
+  fs_stage_tables(tw, lo, tab2, pl.n2, tabD);
   const int r0 = blockIdx.y * pl.nbr;
   CT* Yp = Y + (int64_t)pi * pp.D;
+  // the last row block may run past n1: its extra rows transform zeros and are not stored
+#pragma unroll 4
   for (int idx = threadIdx.x; idx < pl.nbr * pl.n2; idx += blockDim.x) {
-    const int rr = idx / pl.n2, i2 = idx - rr * pl.n2, k1 = r0 + rr;
-    A[rr * ls + i2] = SPEC ? spec[(int64_t)q.t * pp.D + k1 + (int64_t)pl.n1 * i2]
-                           : Yp[(int64_t)k1 * pl.n2 + i2];
+    const int rr = fs_div(idx, pl.mn2), i2 = idx - rr * pl.n2, k1 = r0 + rr;
+    CT v = Cx<CT>::mk(0, 0);
+    if (k1 < pl.n1)
+      v = SPEC ? spec[(int64_t)q.t * pp.D + k1 + (int64_t)pl.n1 * i2] : Yp[(int64_t)k1 * pl.n2 + i2];
+    A[rr * ls + i2] = v;
   }
   __syncthreads();
   CT* cur = A;
   CT* oth = B;
   if constexpr (!SPEC) {
-    cur = fs_fft<CT, false>(A, B, pl.p2, pl.nbr, ls, tab2);
+    cur = fs_fft<CT, false>(A, B, pl.p2, pl.nbr, ls, tw);
     oth = cur == A ? B : A;
     const float* mt = mask + (int64_t)q.t * pp.D;
     for (int idx = threadIdx.x; idx < pl.nbr * pl.n2; idx += blockDim.x) {
-      const int rr = idx / pl.n2, k2 = idx - rr * pl.n2, k1 = r0 + rr;
+      const int rr = fs_div(idx, pl.mn2), k2 = idx - rr * pl.n2, k1 = r0 + rr;
+      if (k1 >= pl.n1) continue;
       const typename Cx<CT>::R mk = (typename Cx<CT>::R)mt[k1 + (int64_t)pl.n1 * k2];
       const CT v = cur[rr * ls + k2];
       cur[rr * ls + k2] = Cx<CT>::mk(v.x * mk, v.y * mk);
     }
     __syncthreads();
   }
-  const CT* res = fs_fft<CT, true>(cur, oth, pl.p2, pl.nbr, ls, tab2);
+  const CT* res = fs_fft<CT, true>(cur, oth, pl.p2, pl.nbr, ls, tw);
   for (int idx = threadIdx.x; idx < pl.nbr * pl.n2; idx += blockDim.x) {
-    const int rr = idx / pl.n2, i2 = idx - rr * pl.n2, k1 = r0 + rr;
-    Yp[(int64_t)k1 * pl.n2 + i2] = fs_mulc(res[rr * ls + i2], tabD[(int64_t)i2 * k1]);
+    const int rr = fs_div(idx, pl.mn2), i2 = idx - rr * pl.n2, k1 = r0 + rr;
+    if (k1 < pl.n1)
+      Yp[(int64_t)k1 * pl.n2 + i2] = fs_mulc(res[rr * ls + i2], fs_twD(tabD, lo, (int64_t)i2 * k1));
   }
 }
 
@@ -280,21 +334,25 @@ k_fs_cols_inv(const CT* __restrict__ Y, const CT* __restrict__ tab1, FsPlan pl, 
               const int* __restrict__ flags, const int* __restrict__ task_active, FsEpi ep) {
   extern __shared__ __align__(16) unsigned char fs_sm[];
   __shared__ double red[2][kFsThreads / 32];
+  const int nb = sizeof(CT) == sizeof(float2) ? pl.nb32 : pl.nb, lnb = __ffs(nb) - 1;
   const int ls = pl.n1 + 1;
   CT* A = reinterpret_cast<CT*>(fs_sm);
-  CT* B = A + pl.nb * ls;
+  CT* B = A + nb * ls;
+  CT* tw = B + nb * ls;
   const int pi = blockIdx.x;
   const FsSys q = fs_sys(pp, pi, flags);
   if (task_active != nullptr && task_active[q.t] == 0) return;     // block-uniform
   if (!q.on1 && !q.on2) return;
-  const int c0 = blockIdx.y * pl.nb;
+  for (int i = threadIdx.x; i < pl.n1; i += blockDim.x) tw[i] = tab1[i];
+  const int c0 = blockIdx.y * nb;
   const CT* Yp = Y + (int64_t)pi * pp.D;
-  for (int idx = threadIdx.x; idx < pl.n1 * pl.nb; idx += blockDim.x) {
-    const int k1 = idx / pl.nb, cc = idx - k1 * pl.nb;
+#pragma unroll 4
+  for (int idx = threadIdx.x; idx < pl.n1 * nb; idx += blockDim.x) {
+    const int k1 = idx >> lnb, cc = idx & (nb - 1);
     A[cc * ls + k1] = Yp[(int64_t)k1 * pl.n2 + c0 + cc];
   }
   __syncthreads();
-  const CT* res = fs_fft<CT, true>(A, B, pl.p1, pl.nb, ls, tab1);
+  const CT* res = fs_fft<CT, true>(A, B, pl.p1, nb, ls, tw);
   const int D = pp.D, Dp = pp.Dp;
   if constexpr (MODE == kFsOp) {
     const float scale = (float)(ep.beta / (double)D);
@@ -306,8 +364,8 @@ k_fs_cols_inv(const CT* __restrict__ Y, const CT* __restrict__ tab1, FsPlan pl, 
     float* z1 = ep.Z + q.s1 * Dp;
     float* z2 = ep.Z + q.s2 * Dp;
     float dot1 = 0.f, dot2 = 0.f;
-    for (int idx = threadIdx.x; idx < pl.n1 * pl.nb; idx += blockDim.x) {
-      const int i1 = idx / pl.nb, cc = idx - i1 * pl.nb;
+    for (int idx = threadIdx.x; idx < pl.n1 * nb; idx += blockDim.x) {
+      const int i1 = idx >> lnb, cc = idx & (nb - 1);
       const int64_t n = (int64_t)pl.n2 * i1 + c0 + cc;
       const CT zc = res[cc * ls + i1];
       if (q.on1) {
@@ -351,8 +409,8 @@ k_fs_cols_inv(const CT* __restrict__ Y, const CT* __restrict__ tab1, FsPlan pl, 
       atomicAdd(&ep.opcount[q.t], 1ull);
   } else if constexpr (MODE == kFsResidual) {
     const double scale = ep.beta / (double)D;
-    for (int idx = threadIdx.x; idx < pl.n1 * pl.nb; idx += blockDim.x) {
-      const int i1 = idx / pl.nb, cc = idx - i1 * pl.nb;
+    for (int idx = threadIdx.x; idx < pl.n1 * nb; idx += blockDim.x) {
+      const int i1 = idx >> lnb, cc = idx & (nb - 1);
       const int64_t n = (int64_t)pl.n2 * i1 + c0 + cc;
       const CT zc = res[cc * ls + i1];
 #pragma unroll
@@ -386,8 +444,8 @@ k_fs_cols_inv(const CT* __restrict__ Y, const CT* __restrict__ tab1, FsPlan pl, 
   } else {
     // b0 = beta Re(F^H Y) = beta / sqrt(D) Re(sum_k Y_k e^{+2 pi i k n / D})
     const double scale = ep.beta / sqrt((double)D);
-    for (int idx = threadIdx.x; idx < pl.n1 * pl.nb; idx += blockDim.x) {
-      const int i1 = idx / pl.nb, cc = idx - i1 * pl.nb;
+    for (int idx = threadIdx.x; idx < pl.n1 * nb; idx += blockDim.x) {
+      const int i1 = idx >> lnb, cc = idx & (nb - 1);
       const int64_t n = (int64_t)pl.n2 * i1 + c0 + cc;
       const double b = scale * (double)res[cc * ls + i1].x;
       const float h = (float)b;
@@ -430,6 +488,8 @@ bool only_2_5(int64_t x) {
   return x == 1;
 }
 
+uint64_t recip(int d) { return ((uint64_t)1 << 32) / (uint64_t)d + (((uint64_t)1 << 32) % (uint64_t)d != 0); }
+
 FsRadix make_radix(int L) {
   FsRadix p{};
   p.L = L;
@@ -437,7 +497,16 @@ FsRadix make_radix(int L) {
   while (m % 4 == 0 && p.n < kFsMaxRadices) { p.r[p.n++] = 4; m /= 4; }
   while (m % 2 == 0 && p.n < kFsMaxRadices) { p.r[p.n++] = 2; m /= 2; }
   while (m % 5 == 0 && p.n < kFsMaxRadices) { p.r[p.n++] = 5; m /= 5; }
-  if (m != 1) p.n = -1;
+  if (m != 1) {
+    p.n = -1;
+    return p;
+  }
+  int Ns = 1;
+  for (int q = 0; q < p.n; ++q) {
+    p.mM[q] = recip(L / p.r[q]);
+    p.mN[q] = recip(Ns);
+    Ns *= p.r[q];
+  }
   return p;
 }
 
@@ -471,17 +540,29 @@ bool make_plan(int D, FsPlan* out) {
   pl.n2 = best2;
   pl.n1 = D / best2;
   pl.nb = pow2_share(pl.n2, 16, pl.n1);
-  pl.nbr = pow2_share(pl.n1, 16, pl.n2);
+  // FP32 column passes: 8 columns (32-byte rows) for more CTAs per SM, where that still
+  // leaves n2 / nb32 partial sums within the D / 128 slots
+  pl.nb32 = (pl.nb >= 8 && pl.n1 * 8 >= 128) ? 8 : pl.nb;
+  pl.nbr = 1;
+  while (pl.nbr < 8 && (size_t)2 * (pl.nbr * 2) * (pl.n2 + 1) * sizeof(double2) <= kFsSmemBudget)
+    pl.nbr *= 2;
+  pl.mn2 = recip(pl.n2);
   pl.p1 = make_radix(pl.n1);
   pl.p2 = make_radix(pl.n2);
   if (pl.p1.n < 0 || pl.p2.n < 0) return false;
-  if ((int64_t)pl.n1 * pl.nb < 128) return false;     // partial sums fit the D/128 slots
+  if ((int64_t)pl.n1 * pl.nb32 < 128) return false;   // partial sums fit the D/128 slots
   *out = pl;
   return true;
 }
 
-size_t cols_smem(const FsPlan& pl, size_t cs) { return 2 * (size_t)pl.nb * (pl.n1 + 1) * cs; }
-size_t rows_smem(const FsPlan& pl, size_t cs) { return 2 * (size_t)pl.nbr * (pl.n2 + 1) * cs; }
+int cols_nb(const FsPlan& pl, size_t cs) { return cs == sizeof(float2) ? pl.nb32 : pl.nb; }
+// two ping-pong buffers, the sub-transform's table and the first 64 entries of W_D
+size_t cols_smem(const FsPlan& pl, size_t cs) {
+  return (2 * (size_t)cols_nb(pl, cs) * (pl.n1 + 1) + pl.n1 + 64) * cs;
+}
+size_t rows_smem(const FsPlan& pl, size_t cs) {
+  return (2 * (size_t)pl.nbr * (pl.n2 + 1) + pl.n2 + 64) * cs;
+}
 
 template <typename CT>
 cudaError_t set_attrs(const FsPlan& pl) {
@@ -522,13 +603,13 @@ cudaError_t run_passes(Ctx* c, const FsPairs& pp, const float* X, const CT* spec
   const unsigned np = (unsigned)((int64_t)c->T * pp.npair);
   const size_t sc = cols_smem(pl, sizeof(CT)), sr = rows_smem(pl, sizeof(CT));
   if (!SPEC) {
-    k_fs_cols_fwd<CT><<<dim3(np, pl.n2 / pl.nb), kFsThreads, sc, c->stream>>>(
+    k_fs_cols_fwd<CT><<<dim3(np, pl.n2 / cols_nb(pl, sizeof(CT))), kFsThreads, sc, c->stream>>>(
         X, Y, tab1, tabD, pl, pp, flags, task_active);
     c->launches += 1;
   }
-  k_fs_rows<CT, SPEC><<<dim3(np, pl.n1 / pl.nbr), kFsThreads, sr, c->stream>>>(
+  k_fs_rows<CT, SPEC><<<dim3(np, (pl.n1 + pl.nbr - 1) / pl.nbr), kFsThreads, sr, c->stream>>>(
       Y, spec, tab2, tabD, fs->mask, pl, pp, flags, task_active);
-  k_fs_cols_inv<CT, MODE><<<dim3(np, pl.n2 / pl.nb), kFsThreads, sc, c->stream>>>(
+  k_fs_cols_inv<CT, MODE><<<dim3(np, pl.n2 / cols_nb(pl, sizeof(CT))), kFsThreads, sc, c->stream>>>(
       Y, tab1, pl, pp, flags, task_active, ep);
   c->launches += 2;
   return cudaGetLastError();
@@ -589,7 +670,7 @@ int fs_create(Ctx* c, const uint8_t* hmask) {
        cudaMemcpy(fs->mask, mt.data(), sizeof(float) * mt.size(), cudaMemcpyHostToDevice) == cudaSuccess;
   if (!ok) return 3;
   if (set_attrs<float2>(pl) != cudaSuccess || set_attrs<double2>(pl) != cudaSuccess) return 4;
-  c->dft_ndt = pl.n2 / pl.nb;
+  c->dft_ndt = pl.n2 / pl.nb32;
   return 0;
 }
 

@@ -204,6 +204,17 @@ class FourierWorkload:
         yt = self.yt(t)
         return np.concatenate([yt.real.astype(np.float64), yt.imag.astype(np.float64)])
 
+    def subset(self, tasks) -> "FourierWorkload":
+        """The workload restricted to the given tasks (same masks, measurements and labels)."""
+        tasks = np.asarray(list(tasks), dtype=np.int64)
+        N = self.N[tasks]
+        off = np.concatenate([[0], np.cumsum(N)]).astype(np.int64)
+        y = np.concatenate([self.yt(int(t)) for t in tasks]) if len(tasks) else self.y[:0]
+        return FourierWorkload(f"{self.name}[{len(tasks)}]", len(tasks), self.C, self.D, N,
+                               self.mask[tasks].copy(), y, off, self.z[tasks].copy(),
+                               self.labels[tasks].copy(), self.sigma, self.beta, self.pi.copy(),
+                               self.K, self.cg_tol, self.cg_max_iter, self.em_iters, self.seed)
+
 
 def make_fourier(name: str, T: int, C: int, D: int, N: int, *, sparsity: float = 0.05,
                  perturb: float = 0.0, sigma: float = 0.05, gt_clusters: int = None,
