@@ -31,6 +31,11 @@ if ROOT not in sys.path:
 import numpy as np  # noqa: E402
 
 METRIC = "CoFEM EM iterations/s (plain-scale workload, one replica per GPU)"
+
+
+def _metric(workload: str) -> str:
+    """The metric's name for the workload timed (the default is plain-scale)."""
+    return METRIC if workload == "plain-scale" else METRIC.replace("plain-scale", workload)
 UNIT = "EM iters/s"
 FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
 
@@ -215,7 +220,7 @@ def run_reference(a):
         times.append(dt)
     per_iter = statistics.mean(times) * pairs            # extrapolated full EM iteration
     value = 1.0 / per_iter
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+    line = {"impl": "reference", "metric": _metric(a.workload), "value": value, "unit": UNIT,
             "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
             "ms_per_step": per_iter * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -432,7 +437,7 @@ def run_ours(a):
     if a.compare_precond and not a.precond:
         precond_form = timed_leg(precond=True)
     if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        line = {"metric": _metric(a.workload), "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms_max / a.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": {"fp32": "f32", "bf16": "bf16+f32", "bf16x3": "bf16x2+f32"}[a.precision],

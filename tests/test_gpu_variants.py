@@ -184,3 +184,32 @@ def test_precond_adjoint_matches_exact():
     ref_dy = np.concatenate(ref_dy)
     assert np.linalg.norm(dy - ref_dy) <= 1e-4 * np.linalg.norm(ref_dy)
     assert rel_err_rows(da, ref_da).max() <= 1e-4
+
+
+def test_em_parity_with_all_variants(small):
+    """Ten EM iterations with learned priors, shared probes and the Jacobi preconditioner on
+    both sides, from the library's own alpha draw: alpha, pi, q, assignments and the
+    reconstructions against the oracle's EM loop."""
+    P, Y = task_lists(small)
+    with make_ctx(small, refine_max=12, refine_tol=1e-6, learn_pi=True, probe_share=True,
+                  precond=True) as ctx:
+        ctx.em_iter(small.em_iters)
+        a_g, pi_g = ctx.read(cmcs.OUT_ALPHA), ctx.read(cmcs.OUT_PI)
+        q_g, asg = ctx.read(cmcs.OUT_Q), ctx.read(cmcs.OUT_ASSIGN)
+        recon = ctx.read(cmcs.OUT_RECON)
+        summ = ctx.summary()
+    o = cofem.em(P, Y, small.pi, small.beta, small.em_iters, K=small.K, seed=small.seed,
+                 tol=small.cg_tol, max_iter=small.cg_max_iter, C=small.C, D=small.D,
+                 refine_tol=1e-12, refine_max=40, learn_pi=True, probe_share=True,
+                 precond=True)
+    assert summ["refine_diverged"] == 0
+    assert np.array_equal(asg, o["assign"])
+    assert np.max(np.abs(q_g - o["last"]["q"])) <= FREE_Q_TOL
+    assert np.max(np.abs(pi_g - o["pi"])) <= FREE_Q_TOL
+    # learned priors can empty a cluster (here all tasks end in one); the alpha of a cluster
+    # with next to no responsibility is a ratio of sums weighted by ~1e-10, so alpha is
+    # compared for the occupied clusters
+    occupied = o["last"]["q"].sum(axis=0) > 0.5
+    assert occupied.any()
+    assert rel_err_rows(a_g[occupied], o["alpha"][occupied]).max() <= REL_TOL
+    assert rel_err_rows(recon, o["recon"]).max() <= REL_TOL
