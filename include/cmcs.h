@@ -94,6 +94,10 @@ typedef struct {
                              + alpha_cd: probe systems A x_k = sqrt(m) * p_k, stopping test
                              r^T M^-1 r <= cg_tol^2 b^T M^-1 b, s = (1/K) sum_k p_k x_k /
                              sqrt(m) and log det Sigma = Eq. 11's estimate - sum_d log m_d  */
+  int warm_start;         /* 1: from the second E-step on, each mean system starts from the
+                             previous E-step's mean (x_1 = mu_prev: CG on b0 - A mu_prev, with
+                             the compensated residual, stopped at ||r|| <= cg_tol ||b0||); the
+                             probe systems keep x_1 = 0, which the Lanczos estimate needs     */
 } cmcs_config;
 
 /* Summary of the most recent E-step and the EM state. */

@@ -181,22 +181,25 @@ class CGResult:
     rel_resid: np.ndarray  # [m] ||r_{U+1}|| / ||b|| of the recursive residual
 
 
-def cg(apply, B: np.ndarray, tol: float, max_iter: int, steps: np.ndarray = None) -> CGResult:
+def cg(apply, B: np.ndarray, tol: float, max_iter: int, steps: np.ndarray = None,
+       ref: np.ndarray = None) -> CGResult:
     """Alg. 1 with x_1 = 0, r_1 = d_1 = b, for every column of B (independent systems).
 
     apply(V) returns A V for the columns given.  If ``steps`` is given, column i runs exactly
-    steps[i] steps (replay of a step count measured elsewhere) instead of the tol test."""
+    steps[i] steps (replay of a step count measured elsewhere) instead of the tol test.  ref
+    (squared norms per column, default ||b||^2) is what the tol test compares against; a column
+    already within tol of it takes no step."""
     D, m = B.shape
     X = np.zeros((D, m))
     R = B.astype(np.float64).copy()
     Dd = R.copy()
     rr = np.einsum("ij,ij->j", R, R)
-    bb = rr.copy()
+    bb = rr.copy() if ref is None else np.asarray(ref, dtype=np.float64).copy()
     gam = np.zeros((m, max_iter))
     xi = np.zeros((m, max_iter))
     U = np.zeros(m, dtype=np.int64)
     if steps is None:
-        active = rr > 0.0
+        active = (rr > 0.0) & ((ref is None) | (rr > (tol * tol) * bb))
     else:
         active = (np.asarray(steps) > 0) & (rr > 0.0)
     for u in range(max_iter):
@@ -233,7 +236,7 @@ def cg(apply, B: np.ndarray, tol: float, max_iter: int, steps: np.ndarray = None
 
 
 def pcg(apply, B: np.ndarray, minv: np.ndarray, tol: float, max_iter: int,
-        steps: np.ndarray = None) -> CGResult:
+        steps: np.ndarray = None, ref: np.ndarray = None) -> CGResult:
     """Alg. 1 with a diagonal (Jacobi) preconditioner M = diag(m), minv = 1/m of shape [D]:
     x_1 = 0, r_1 = b, z_1 = M^-1 r_1, d_1 = z_1 and, per step,
         gamma_u = r_u^T z_u / d_u^T A d_u,   x_{u+1} = x_u + gamma_u d_u,
@@ -243,7 +246,8 @@ def pcg(apply, B: np.ndarray, minv: np.ndarray, tol: float, max_iter: int,
     Ah = M^-1/2 A M^-1/2 with right-hand side bh = M^-1/2 b and the same gamma_u and xi_u, so
     the matrix of Eq. 9 built from them is the Lanczos matrix of Ah started at bh / ||bh||.
     Reading of the stopping test: the one of Alg. 1 on that system, r^T z <= tol^2 b^T M^-1 b
-    (||rh|| <= tol ||bh||); the other stops and ``steps`` are as in ``cg``."""
+    (||rh|| <= tol ||bh||); the other stops, ``steps`` and ``ref`` (here in the M^-1 norm) are
+    as in ``cg``."""
     D, m = B.shape
     mi = np.asarray(minv, dtype=np.float64).reshape(D, 1)
     X = np.zeros((D, m))
@@ -251,11 +255,14 @@ def pcg(apply, B: np.ndarray, minv: np.ndarray, tol: float, max_iter: int,
     Z = mi * R
     Dd = Z.copy()
     rz = np.einsum("ij,ij->j", R, Z)
-    bz = rz.copy()
+    bz = rz.copy() if ref is None else np.asarray(ref, dtype=np.float64).copy()
     gam = np.zeros((m, max_iter))
     xi = np.zeros((m, max_iter))
     U = np.zeros(m, dtype=np.int64)
-    active = (rz > 0.0) if steps is None else ((np.asarray(steps) > 0) & (rz > 0.0))
+    if steps is None:
+        active = (rz > 0.0) & ((ref is None) | (rz > (tol * tol) * bz))
+    else:
+        active = (np.asarray(steps) > 0) & (rz > 0.0)
     for u in range(max_iter):
         idx = np.nonzero(active)[0]
         if idx.size == 0:
@@ -430,7 +437,7 @@ def cofem_estep(Phi_list, y_list, alpha: np.ndarray, pi: np.ndarray, beta: float
                 seed: int, em_iter: int, tol: float, max_iter: int, probe_fn=None,
                 steps: np.ndarray = None, tasks=None, refine_tol: float = None,
                 refine_max: int = 8, clusters=None, C_total: int = None,
-                probe_share: bool = False, precond: bool = False) -> dict:
+                probe_share: bool = False, precond: bool = False, mu_init=None) -> dict:
     """Alg. 2, inner loop (one E-step): for every (t, c) solve A mu = b0 and A x_k = p_k by CG
     (Eq. 7, Alg. 1), s = (1/K) sum_k p_k * x_k (Eq. 4), the log-det estimate of Eq. 11 from the
     CG coefficients of the probe systems, ell (Eq. 3) and the responsibilities (Eq. 3).
@@ -452,7 +459,12 @@ def cofem_estep(Phi_list, y_list, alpha: np.ndarray, pi: np.ndarray, beta: float
       Ah xh = M^-1/2 (w * p_k) = p_k starts its Lanczos process at a Rademacher vector; then
       diag(A^-1) = M^-1/2 diag(Ah^-1) M^-1/2 gives s = (1/K) sum_k p_k * x_k / w, and
       log det A = log det Ah + sum_d log m_d gives nu = (Eq. 11 on the pcg coefficients)
-      - sum_d log m_d."""
+      - sum_d log m_d.
+    * mu_init [T, C, D]: the mean system starts from x_1 = mu_init (the previous E-step's
+      means).  It is Alg. 1 on A delta = b0 - A mu_init from delta = 0, stopped at the cold
+      start's absolute target ||r|| <= tol ||b0|| (||b0|| in the M^-1 norm with precond), and
+      mu = mu_init + delta.  The probe systems keep x_1 = 0, which their Lanczos reading
+      needs."""
     P, Y = _task_arrays(Phi_list, y_list)
     T, (C, D) = len(P), alpha.shape
     tasks = list(range(T)) if tasks is None else list(tasks)
@@ -485,11 +497,23 @@ def cofem_estep(Phi_list, y_list, alpha: np.ndarray, pi: np.ndarray, beta: float
                 m_d = P[t].diag(beta, alpha[c]) if fs else jacobi_diag(P[t], beta, alpha[c])
                 w = np.sqrt(m_d)
                 B = np.concatenate([b0[:, None], w[:, None] * Pk.T], axis=1)
-                res = pcg(op, B, 1.0 / m_d, tol, max_iter, st)
             else:
                 B = np.concatenate([b0[:, None], Pk.T], axis=1)          # [D, K+1]
-                res = cg(op, B, tol, max_iter, st)
+            Bs, ref, x0 = B, None, None
+            if mu_init is not None:
+                x0 = np.asarray(mu_init[t, c], dtype=np.float64)
+                Bs = B.copy()
+                Bs[:, 0] = B[:, 0] - op(x0[:, None], None)[:, 0]
+                # the tol test's reference: the cold start's ||b||^2 (b^T M^-1 b with precond)
+                ref = np.einsum("ij,ij->j", B, B / m_d[:, None] if precond else B)
+            if precond:
+                res = pcg(op, Bs, 1.0 / m_d, tol, max_iter, st, ref=ref)
+            else:
+                res = cg(op, Bs, tol, max_iter, st, ref=ref)
             X = res.x
+            if x0 is not None:
+                X = X.copy()
+                X[:, 0] += x0
             if refine_tol is not None:
                 X, _ = refine(op, B, X, tol, max_iter, refine_tol, refine_max,
                               minv=(1.0 / m_d) if precond else None)
@@ -518,12 +542,13 @@ def em(Phi_list, y_list, pi: np.ndarray, beta: float, n_iter: int, *, method: st
        alpha0: np.ndarray = None, em_iter_offset: int = 0, alpha_min: float = 1e-10,
        alpha_max: float = 1e10, D: int = None, C: int = None, refine_tol: float = None,
        refine_max: int = 8, learn_pi: bool = False, probe_share: bool = False,
-       precond: bool = False) -> dict:
+       precond: bool = False, warm_start: bool = False) -> dict:
     """n_iter EM iterations from alpha0 (default: the Alg. 2 Uniform(0,1) draw).  Returns the
     last E-step's outputs, the final alpha (and pi), the hard assignments argmax_c q_tc and
     the reconstructions mu_{t, a_t}, plus the log-likelihood seen by every E-step.  With
-    learn_pi each M-step also sets pi = ``pi_update(q)``; probe_share and precond select the
-    E-step variants of ``cofem_estep``."""
+    learn_pi each M-step also sets pi = ``pi_update(q)``; probe_share, precond and warm_start
+    (each E-step's mean systems start from the previous E-step's means) select the E-step
+    variants of ``cofem_estep``."""
     if alpha0 is None:
         alpha = philox.alpha_init(seed, C, D)
     else:
@@ -536,9 +561,10 @@ def em(Phi_list, y_list, pi: np.ndarray, beta: float, n_iter: int, *, method: st
         if method == "exact":
             est = exact_estep(Phi_list, y_list, alpha, pi, beta)
         else:
+            mu0 = est["mu"] if (warm_start and est is not None) else None
             est = cofem_estep(Phi_list, y_list, alpha, pi, beta, K, seed, em_iter_offset + it,
                               tol, max_iter, refine_tol=refine_tol, refine_max=refine_max,
-                              probe_share=probe_share, precond=precond)
+                              probe_share=probe_share, precond=precond, mu_init=mu0)
         trace.append(est["loglik"])
         alpha = m_step(est["q"], est["mu"], est["s"], alpha, alpha_min, alpha_max)
         if learn_pi:

@@ -39,7 +39,7 @@ class Config(ctypes.Structure):
                 ("alpha_min", ctypes.c_double), ("alpha_max", ctypes.c_double),
                 ("schedule", ctypes.c_int), ("graphs", ctypes.c_int), ("autotune", ctypes.c_int),
                 ("learn_pi", ctypes.c_int), ("probe_share", ctypes.c_int),
-                ("precond", ctypes.c_int)]
+                ("precond", ctypes.c_int), ("warm_start", ctypes.c_int)]
 
 
 class Summary(ctypes.Structure):
@@ -161,10 +161,11 @@ class Context:
                  refine_tol: float = 1e-6, alpha_min: float = 1e-10, alpha_max: float = 1e10,
                  schedule: str = "batched", graphs: bool = True, autotune: bool = False,
                  learn_pi: bool = False, probe_share: bool = False, precond: bool = False,
-                 mask=None, stream=None):
+                 warm_start: bool = False, mask=None, stream=None):
         """Dense Phi [sum N_t][D] with y [sum N_t]; or, with Phi None and mask given, the
         Fourier operator of cmcs_create_dft: mask uint8 [T][D], y float32 [sum N_t][2].
-        learn_pi, probe_share and precond switch on the method variants of cmcs_config."""
+        learn_pi, probe_share, precond and warm_start switch on the method variants of
+        cmcs_config."""
         N = np.ascontiguousarray(np.asarray(N, dtype=np.int64))
         D = int(mask.shape[1]) if mask is not None else int(Phi.shape[1])
         self.T, self.C, self.D, self.K = int(len(N)), int(C), D, int(K)
@@ -179,7 +180,7 @@ class Context:
                      float(refine_tol), float(alpha_min), float(alpha_max),
                      {"batched": 0, "per_task": 1}[schedule], 1 if graphs else 0,
                      1 if autotune else 0, 1 if learn_pi else 0, 1 if probe_share else 0,
-                     1 if precond else 0)
+                     1 if precond else 0, 1 if warm_start else 0)
         self.cfg = cfg
         self.fourier = mask is not None
         p_phi, dev1 = _ptr(mask if self.fourier else Phi)

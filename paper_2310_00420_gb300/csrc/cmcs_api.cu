@@ -252,10 +252,19 @@ cmcs_status estep(Ctx* c) {
   CK(cudaMemsetAsync(c->psteps, 0, sizeof(int) * (size_t)c->T * c->C * c->K, c->stream));
   c->op_applies = 0;
   CK(launch_precond(c));              // Jacobi preconditioner of the current alpha
+  // warm start: the mean systems solve for a correction to the previous means, from the
+  // compensated residual b0 - A mu_prev
+  const int warm = c->warm_start && c->have_prev;
+  c->have_prev = 0;                   // set again once this E-step has completed
+  if (warm) {
+    CK(launch_residual(c, c->xacc, nullptr, c->r, 1, 1));
+    c->op_applies++;
+  }
   // first solve: Alg. 1 from x = 0 on b0 and the probes, recording gamma and xi
-  CK(launch_cg_init(c, 0));
+  CK(launch_cg_init(c, 0, warm));
   cmcs_status s = run_cg(c, 1);
   if (s != CMCS_OK) return s;
+  if (warm) CK(launch_add_means(c));  // mu = mu_prev + delta
   CK(cudaMemcpyAsync(c->steps0, c->steps, sizeof(int) * c->S, cudaMemcpyDeviceToDevice, c->stream));
   // the Lanczos coefficients are final: their eigen step (Eqs. 9-11) runs on the side stream,
   // overlapping the refinement sweeps
@@ -288,8 +297,10 @@ cmcs_status estep(Ctx* c) {
   fold_events(c);
   if (c->hcounters[2] != 0) {
     set_err(c, "non-finite value or eigen failure in the E-step (flags 0x%x)", c->hcounters[2]);
+    c->have_prev = 0;
     return CMCS_ERR_NUMERIC;
   }
+  c->have_prev = 1;
   return CMCS_OK;
 }
 
@@ -364,6 +375,7 @@ cmcs_status validate(const cmcs_config* cfg) {
   if (cfg->learn_pi != 0 && cfg->learn_pi != 1) return CMCS_ERR_INVALID_ARG;
   if (cfg->probe_share != 0 && cfg->probe_share != 1) return CMCS_ERR_INVALID_ARG;
   if (cfg->precond != 0 && cfg->precond != 1) return CMCS_ERR_INVALID_ARG;
+  if (cfg->warm_start != 0 && cfg->warm_start != 1) return CMCS_ERR_INVALID_ARG;
   return CMCS_OK;
 }
 
@@ -420,6 +432,7 @@ cmcs_status create_ctx(const cmcs_config* cfg, const float* Phi, const float* y,
   c->learn_pi = cfg->learn_pi;
   c->pshare = cfg->probe_share;
   c->precond = cfg->precond;
+  c->warm_start = cfg->warm_start;
   c->seed = cfg->seed;
   c->op = mask ? 1 : 0;
   c->em_iter = 0;
@@ -759,6 +772,7 @@ cmcs_status cmcs_set_data(cmcs_ctx* h, const float* Phi, const float* y, int on_
   CK(launch_b0(c));
   CK(launch_tconst_dev(c, c->dN));
   CK(launch_colnorm(c));
+  c->have_prev = 0;                   // the previous means belong to the old data
   if (c->tc != nullptr) CK(tc_refresh(c));
   return sync_check(c);
 }

@@ -75,6 +75,8 @@ struct Ctx {
   int learn_pi;      // each M-step also sets pi_c = max(mean_t q_tc, 1e-300), renormalised
   int pshare;        // probes shared across clusters: p_{t,c,k} = p_{t,0,k}
   int precond;       // Jacobi-preconditioned CG (buffers colnorm, pminv, pw, sumlogm)
+  int warm_start;    // mean systems start from the previous E-step's means
+  int have_prev;     // xacc holds the means of an earlier E-step of this problem
   uint64_t seed;
   int64_t em_iter;
   cudaStream_t stream;
@@ -182,7 +184,9 @@ cudaError_t launch_sumlogalpha(Ctx* c);
 cudaError_t launch_tconst_dev(Ctx* c, const int64_t* dN);
 cudaError_t launch_probes_out(const Ctx* c, int64_t em_iter, float* dst);
 // CG (kernels_cg.cu)
-cudaError_t launch_cg_init(Ctx* c, int mode /*0 first solve, 1 refinement*/);
+cudaError_t launch_cg_init(Ctx* c, int mode /*0 first solve, 1 refinement*/, int warm = 0);
+// x of the mean systems += xacc of the mean systems (warm start: mu = mu_prev + delta)
+cudaError_t launch_add_means(Ctx* c);
 cudaError_t launch_cg_update(Ctx* c, int record);
 cudaError_t launch_refine_update(Ctx* c);
 cudaError_t launch_sest(Ctx* c);

@@ -70,25 +70,41 @@ __device__ __forceinline__ void store_split4(__nv_bfloat16* hi, __nv_bfloat16* l
 // right-hand side already in r (first solve of the adjoint system).
 // With the Jacobi preconditioner (pminv != null): probe right-hand sides are sqrt(m) * p,
 // d_1 = z_1 = M^-1 r_1 and rr = r^T z.
+// warm (mode 0): the mean systems (k = 0) start from the previous means, so r already holds
+// b0 - A mu_prev; their tol test keeps the cold start's reference b0^T M^-1 b0, and a system
+// already within tol of it takes no step.
 __global__ void __launch_bounds__(256)
 k_cg_init(int mode, float* __restrict__ x, float* __restrict__ r, float* __restrict__ d,
           const float* __restrict__ b0hi, float* rr, float* bb, int* steps, int* active,
           int* ractive, int* sweeps, float* rrel, int* task_active, int* counters, int R,
           int K, int C, int Dp, int D, uint64_t seed, int64_t em_iter, int refine,
           __nv_bfloat16* dhi, __nv_bfloat16* dlo, const float* __restrict__ pminv,
-          const float* __restrict__ pw, int pshare) {
+          const float* __restrict__ pw, int pshare, int warm, float tol2) {
   __shared__ float sh[33];
   const int64_t sys = blockIdx.x;
   const int t = (int)(sys / R), j = (int)(sys % R), c = j / (K + 1), k = j % (K + 1);
+  const bool wm = mode == 0 && warm != 0 && k == 0;      // block-uniform
   float* xs = x + sys * Dp;
   float* rs = r + sys * Dp;
   float* ds = d + sys * Dp;
   const int64_t tcoff = ((int64_t)t * C + c) * Dp;
-  float acc = 0.f;
+  float acc = 0.f, accr = 0.f;
   for (int i = threadIdx.x * 4; i < Dp; i += 256 * 4) {
     float4 b;
     if (mode == 0) {
-      if (k == 0) {
+      if (wm) {
+        b = *reinterpret_cast<const float4*>(rs + i);           // b0 - A mu_prev
+        float4 b0 = *reinterpret_cast<const float4*>(b0hi + (int64_t)t * Dp + i);
+        float4 z0 = b0;
+        if (pminv != nullptr) {
+          const float4 mi = *reinterpret_cast<const float4*>(pminv + tcoff + i);
+          z0 = make_float4(b0.x * mi.x, b0.y * mi.y, b0.z * mi.z, b0.w * mi.w);
+        }
+        accr = fmaf(b0.x, z0.x, accr);
+        accr = fmaf(b0.y, z0.y, accr);
+        accr = fmaf(b0.z, z0.z, accr);
+        accr = fmaf(b0.w, z0.w, accr);
+      } else if (k == 0) {
         b = *reinterpret_cast<const float4*>(b0hi + (int64_t)t * Dp + i);
       } else {
         b = probe4(seed, em_iter, t, probe_cluster(c, pshare), C, k - 1, i, D);
@@ -115,16 +131,17 @@ k_cg_init(int mode, float* __restrict__ x, float* __restrict__ r, float* __restr
     acc = fmaf(b.w, z.w, acc);
   }
   const float rr0 = block_sum(acc, sh);
+  const float ref = wm ? block_sum(accr, sh) : rr0;
   if (threadIdx.x == 0) {
     rr[sys] = rr0;
-    bb[sys] = rr0;
+    bb[sys] = ref;
     steps[sys] = 0;
     if (mode != 1) {
       ractive[sys] = refine;
       sweeps[sys] = 0;
       rrel[sys] = 0.f;
     }
-    const int on = (rr0 > 0.f) && (mode != 1 || ractive[sys] != 0);
+    const int on = (rr0 > 0.f) && (mode != 1 || ractive[sys] != 0) && !(wm && rr0 <= tol2 * ref);
     active[sys] = on;
     if (on) {
       atomicAdd(&task_active[t], 1);
@@ -522,7 +539,7 @@ __global__ void k_probes_out(float* dst, int T, int C, int K, int D, uint64_t se
 }
 
 // --------------------------------------------------------------------------------------
-cudaError_t launch_cg_init(Ctx* c, int mode) {
+cudaError_t launch_cg_init(Ctx* c, int mode, int warm) {
   c->launches += 1;
   k_cg_init<<<c->S, 256, 0, c->stream>>>(mode, c->x, c->r, c->d, c->b0hi, c->rr, c->bb,
                                          c->steps, c->active, c->ractive, c->sweeps, c->rrel,
@@ -531,7 +548,22 @@ cudaError_t launch_cg_init(Ctx* c, int mode) {
                                          static_cast<__nv_bfloat16*>(c->dhi),
                                          static_cast<__nv_bfloat16*>(c->dlo),
                                          c->precond ? c->pminv : nullptr,
-                                         c->precond ? c->pw : nullptr, c->pshare);
+                                         c->precond ? c->pw : nullptr, c->pshare, warm,
+                                         (float)(c->cg_tol * c->cg_tol));
+  return cudaGetLastError();
+}
+
+// ---- warm start: x of the mean systems += the previous means -----------------------------
+__global__ void __launch_bounds__(256)
+k_add_means(float* __restrict__ x, const float* __restrict__ prev, int R, int K, int C, int Dp) {
+  const int tc = blockIdx.x, t = tc / C, c = tc % C;
+  const int64_t off = ((int64_t)t * R + (int64_t)c * (K + 1)) * Dp;
+  for (int i = threadIdx.x; i < Dp; i += 256) x[off + i] += prev[off + i];
+}
+
+cudaError_t launch_add_means(Ctx* c) {
+  c->launches += 1;
+  k_add_means<<<c->T * c->C, 256, 0, c->stream>>>(c->x, c->xacc, c->R, c->K, c->C, c->Dp);
   return cudaGetLastError();
 }
 

@@ -213,3 +213,28 @@ def test_em_parity_with_all_variants(small):
     assert occupied.any()
     assert rel_err_rows(a_g[occupied], o["alpha"][occupied]).max() <= REL_TOL
     assert rel_err_rows(recon, o["recon"]).max() <= REL_TOL
+
+
+def test_warm_start_em_parity(small):
+    """Ten EM iterations whose mean systems start from the previous E-step's means, on both
+    sides: alpha, q, assignments and reconstructions against the oracle's EM loop; the mean
+    systems of the last E-step take fewer CG steps than from x_1 = 0."""
+    P, Y = task_lists(small)
+    steps = {}
+    for warm in (False, True):
+        with make_ctx(small, refine_max=12, refine_tol=1e-6, warm_start=warm) as ctx:
+            ctx.em_iter(small.em_iters)
+            steps[warm] = ctx.read(cmcs.OUT_STEPS)[:, :, 0]
+            if warm:
+                a_g, q_g = ctx.read(cmcs.OUT_ALPHA), ctx.read(cmcs.OUT_Q)
+                asg, recon = ctx.read(cmcs.OUT_ASSIGN), ctx.read(cmcs.OUT_RECON)
+                summ = ctx.summary()
+    o = cofem.em(P, Y, small.pi, small.beta, small.em_iters, K=small.K, seed=small.seed,
+                 tol=small.cg_tol, max_iter=small.cg_max_iter, C=small.C, D=small.D,
+                 refine_tol=1e-12, refine_max=40, warm_start=True)
+    assert summ["refine_diverged"] == 0
+    assert np.array_equal(asg, o["assign"])
+    assert np.max(np.abs(q_g - o["last"]["q"])) <= FREE_Q_TOL
+    assert rel_err_rows(a_g, o["alpha"]).max() <= REL_TOL
+    assert rel_err_rows(recon, o["recon"]).max() <= REL_TOL
+    assert np.all(steps[True] <= steps[False]) and np.any(steps[True] < steps[False])

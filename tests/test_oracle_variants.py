@@ -180,3 +180,46 @@ def test_pcg_refinement_reaches_direct_solve():
     X, sweeps = cofem.refine(op, B, r.x, 1e-5, 60, 1e-12, 30, minv=minv)
     assert np.linalg.norm(X - Xs) <= 1e-9 * np.linalg.norm(Xs)
     assert sweeps.max() >= 1
+
+
+# ---- warm-started mean systems -----------------------------------------------------------
+
+def test_warm_start_from_exact_means_takes_no_step():
+    Phi, y, alpha, pi, beta = _problem(T=2, C=2, D=16, N=7, seed=9)
+    kw = dict(K=3, seed=1, em_iter=0, tol=1e-8, max_iter=60)
+    for pc in (False, True):
+        ex = cofem.exact_estep(Phi, y, alpha, pi, beta)
+        w = cofem.cofem_estep(Phi, y, alpha, pi, beta, mu_init=ex["mu"], precond=pc, **kw)
+        assert np.all(w["steps"][:, :, 0] == 0)
+        np.testing.assert_allclose(w["mu"], ex["mu"], rtol=1e-12)
+
+
+def test_warm_start_reaches_the_same_solution_with_fewer_steps():
+    """From a nearby start (the exact means perturbed by 1e-3) the mean systems reach the
+    same converged means in fewer steps; the probe systems are untouched."""
+    Phi, y, alpha, pi, beta = _problem(T=2, C=2, D=40, N=15, seed=10, beta=1e3)
+    alpha = 10.0 ** np.random.default_rng(11).uniform(-1, 2, size=alpha.shape)
+    kw = dict(K=4, seed=2, em_iter=1, tol=1e-10, max_iter=200)
+    ex = cofem.exact_estep(Phi, y, alpha, pi, beta)
+    start = ex["mu"] * (1 + 1e-3 * np.random.default_rng(12).standard_normal(ex["mu"].shape))
+    for pc in (False, True):
+        cold = cofem.cofem_estep(Phi, y, alpha, pi, beta, precond=pc, **kw)
+        warm = cofem.cofem_estep(Phi, y, alpha, pi, beta, mu_init=start, precond=pc, **kw)
+        # both stop at ||r|| <= 1e-10 ||b0||: errors of order kappa * 1e-10 (kappa ~ 1e4 here)
+        for e in (warm, cold):
+            assert np.linalg.norm(e["mu"] - ex["mu"]) <= 1e-5 * np.linalg.norm(ex["mu"])
+        assert np.all(warm["steps"][:, :, 0] < cold["steps"][:, :, 0])
+        np.testing.assert_array_equal(warm["steps"][:, :, 1:], cold["steps"][:, :, 1:])
+        # the probe systems run the same solves (the batched products' order of summation
+        # may differ with the set of active columns)
+        np.testing.assert_allclose(warm["s"], cold["s"], rtol=1e-10)
+        np.testing.assert_allclose(warm["logdet"], cold["logdet"], rtol=1e-12)
+
+
+def test_exact_em_with_warm_start_matches_cold_em():
+    Phi, y, alpha, pi, beta = _problem(T=3, C=2, D=14, N=6, seed=13, beta=200.0)
+    kw = dict(K=8, seed=3, tol=1e-12, max_iter=100, alpha0=alpha)
+    cold = cofem.em(Phi, y, pi, beta, 4, **kw)
+    warm = cofem.em(Phi, y, pi, beta, 4, warm_start=True, **kw)
+    np.testing.assert_allclose(warm["alpha"], cold["alpha"], rtol=1e-8)
+    np.testing.assert_allclose(warm["last"]["q"], cold["last"]["q"], atol=1e-10)
