@@ -66,6 +66,8 @@ def _args():
     ap.add_argument("--learn-pi", action="store_true", help="learn the cluster priors")
     ap.add_argument("--probe-share", action="store_true",
                     help="probes shared across the clusters of a task")
+    ap.add_argument("--warm-start", action="store_true",
+                    help="mean systems start from the previous E-step's means")
     ap.add_argument("--compare-precond", action="store_true",
                     help="also time the Jacobi-preconditioned form on the same workload")
     return ap.parse_args()
@@ -251,7 +253,7 @@ def run_ours(a):
     kw = dict(C=wl.C, K=wl.K, beta=wl.beta, pi=wl.pi, cg_max_iter=wl.cg_max_iter, cg_tol=wl.cg_tol,
               seed=wl.seed, precision=a.precision, refine_max=a.refine_max, refine_tol=a.refine_tol,
               schedule=a.schedule, graphs=not a.no_graphs, precond=a.precond,
-              learn_pi=a.learn_pi, probe_share=a.probe_share)
+              learn_pi=a.learn_pi, probe_share=a.probe_share, warm_start=a.warm_start)
     variant = dict(precond=a.precond, probe_share=a.probe_share)
     if fourier:
         ctx = cmcs.Context.from_fourier(wl, device=True, **kw)
@@ -448,7 +450,8 @@ def run_ours(a):
                            "refine_tol": a.refine_tol, "parallelism": f"{world} replicas",
                            "variants": [v for v, on in (("precond", a.precond),
                                                         ("learn_pi", a.learn_pi),
-                                                        ("probe_share", a.probe_share)) if on],
+                                                        ("probe_share", a.probe_share),
+                                                        ("warm_start", a.warm_start)) if on],
                            "l2": (f"inputs larger than L2 (CG vectors {5 * systems * wl.D * 4 / 1e9:.1f} GB)"
                                   if fourier else
                                   f"inputs larger than L2 (Phi {wl.Phi.nbytes / 1e9:.1f} GB)")},
