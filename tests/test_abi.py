@@ -54,7 +54,8 @@ int main(void) {
   O(cmcs_config, cg_tol); O(cmcs_config, seed); O(cmcs_config, precision);
   O(cmcs_config, refine_max); O(cmcs_config, refine_tol); O(cmcs_config, alpha_min);
   O(cmcs_config, alpha_max); O(cmcs_config, schedule); O(cmcs_config, graphs);
-  O(cmcs_config, autotune);
+  O(cmcs_config, autotune); O(cmcs_config, learn_pi); O(cmcs_config, probe_share);
+  O(cmcs_config, precond); O(cmcs_config, warm_start);
   O(cmcs_summary, loglik); O(cmcs_summary, cg_steps_max); O(cmcs_summary, cg_steps_mean);
   O(cmcs_summary, cg_capped); O(cmcs_summary, refine_sweeps_max);
   O(cmcs_summary, refine_rel_max); O(cmcs_summary, min_margin);
@@ -107,6 +108,21 @@ def test_create_rejects_invalid_config_without_cuda(L, bad):
     assert st == cmcs.ERR_INVALID_ARG
     assert not h.value
     assert L.cmcs_last_error(None)
+
+
+@pytest.mark.parametrize("flag", ["learn_pi", "probe_share", "precond", "warm_start",
+                                  "schedule", "graphs", "autotune"])
+def test_create_rejects_bad_switches_without_cuda(L, flag):
+    """Every 0/1 switch of cmcs_config accepts only 0 and 1."""
+    Phi = np.zeros((128, 32), np.float32)
+    y = np.zeros(128, np.float32)
+    h = ctypes.c_void_p()
+    for v in (2, -1):
+        cfg, keep = _cfg()
+        setattr(cfg, flag, v)
+        assert L.cmcs_create(ctypes.byref(cfg), Phi.ctypes.data, y.ctypes.data, 0, None,
+                             ctypes.byref(h)) == cmcs.ERR_INVALID_ARG, (flag, v)
+        assert not h.value
 
 
 def test_create_rejects_null_inputs_and_bad_pi(L):

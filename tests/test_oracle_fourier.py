@@ -69,3 +69,14 @@ def test_fourier_sensing_estep_equals_dense_estep():
         b = cofem.cofem_estep(ops, Y, alpha, wl.pi, wl.beta, wl.K, 1, 0, 1e-12, 200, precond=pc)
         for key in ("mu", "s", "logdet", "q"):
             np.testing.assert_allclose(b[key], a[key], rtol=1e-8, atol=1e-12)
+
+
+def test_fourier_workload_subset_keeps_tasks():
+    wl = synth.fourier_small()
+    sub = wl.subset([1, 3])
+    assert sub.T == 2 and list(sub.N) == [wl.N[1], wl.N[3]]
+    np.testing.assert_array_equal(sub.mask, wl.mask[[1, 3]])
+    for i, t in enumerate((1, 3)):
+        np.testing.assert_array_equal(sub.yt(i), wl.yt(t))
+        np.testing.assert_array_equal(sub.phi_real(i), wl.phi_real(t))
+    assert sub.row_off[-1] == sub.y.shape[0]
