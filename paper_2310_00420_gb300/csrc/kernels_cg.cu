@@ -2,13 +2,15 @@
 // (Eq. 4) and the set-up kernels (b0 = beta Phi^T y, alpha ~ Uniform(0,1), probes).
 //
 // One CTA of 256 threads owns one system for the vector updates, so both inner products of a
-// CG step (d^T A d and r^T r) reduce inside the CTA: no grid-wide barrier or spin-wait exists.
-// With the SIMT operator d^T A d arrives as per-tile partials from the operator epilogue; with
-// the tensor-core operator the update kernel adds alpha_c * d to beta Phi^T Phi d and forms
+// CG step (d^T A d and r^T r, or r^T M^-1 r with the Jacobi preconditioner) reduce inside the
+// CTA: no grid-wide barrier or spin-wait exists.  With the SIMT and four-step Fourier
+// operators d^T A d arrives as per-tile partials from the operator epilogue; with the
+// tensor-core operator the update kernel adds alpha_c * d to beta Phi^T Phi d and forms
 // d^T A d itself.  Every reduction has a fixed tree order, so results are run-to-run
 // deterministic.
 // Converged systems are masked (their CTA returns at once) and a task whose systems have all
-// converged is skipped by the operator.
+// converged is skipped by the operator.  Also here: the Jacobi preconditioner's column norms
+// and per-E-step diagonal, and the warm start's addition of the previous means.
 #include <cuda_bf16.h>
 #include <math.h>
 
