@@ -185,3 +185,27 @@ def test_cofem_approaches_exact_em_as_k_grows():
         errs.append((np.abs(co["s"] - ex["s"]).max(), np.abs(co["logdet"] - ex["logdet"]).max()))
     assert errs[1][0] < errs[0][0] and errs[1][1] < errs[0][1]
     assert errs[1][1] < 0.05 * np.abs(ex["logdet"]).max()
+
+
+def test_logdet_estimate_meets_the_cited_bound_at_its_K_and_U():
+    """Sec. 3.2's cited result: with K >= 24/eps^2 log(2/eta) probes and
+    U >= sqrt(kappa)/4 log(O(kappa)/(eps sqrt(kappa))) CG steps, Eq. 11 is within
+    eps |log det Sigma| with probability > 1 - eta.  kappa = 100, eps = eta = 0.1 (so K = 7190
+    and, taking the O(kappa) constant as kappa, U = 12 < D = 30); over 20 independent probe
+    sets the estimate must be within the bound at least 1 - eta of the time."""
+    D, kappa, eps, eta = 30, 100.0, 0.1, 0.1
+    K = int(np.ceil(24.0 / eps ** 2 * np.log(2.0 / eta)))
+    U = int(np.ceil(np.sqrt(kappa) / 4.0 * np.log(kappa / (eps * np.sqrt(kappa)))))
+    assert (K, U) == (7190, 12)
+    rng = np.random.default_rng(14)
+    Q, _ = np.linalg.qr(rng.standard_normal((D, D)))
+    lam = np.geomspace(1.0, kappa, D)
+    A = (Q * lam) @ Q.T
+    logdet_sigma = -float(np.sum(np.log(lam)))
+    hits = 0
+    for seed in range(20):
+        P = np.sign(np.random.default_rng(100 + seed).standard_normal((D, K)))
+        res = cofem.cg(lambda V, idx=None: A @ V, P, 0.0, U, steps=np.full(K, U))
+        nu = cofem.logdet_estimate(res.gamma, res.xi, res.steps, D)
+        hits += abs(nu - logdet_sigma) <= eps * abs(logdet_sigma)
+    assert hits >= (1.0 - eta) * 20
