@@ -238,3 +238,28 @@ def test_warm_start_em_parity(small):
     assert rel_err_rows(a_g, o["alpha"]).max() <= REL_TOL
     assert rel_err_rows(recon, o["recon"]).max() <= REL_TOL
     assert np.all(steps[True] <= steps[False]) and np.any(steps[True] < steps[False])
+
+
+@pytest.mark.parametrize("wl_name", ["fourier-small", "fourier-2k"])
+def test_all_variants_on_the_fourier_operator(wl_name):
+    """Three EM iterations with every variant on (learned priors, shared probes, Jacobi,
+    warm start) on the Fourier operator, single-CTA (D = 256) and four-step (D = 2000) paths,
+    against the oracle's EM loop on the dense real-stacked matrices."""
+    wl = synth.WORKLOADS[wl_name]()
+    n = 3
+    kw = dict(learn_pi=True, probe_share=True, precond=True, warm_start=True)
+    with cmcs.Context.from_fourier(wl, device=True, refine_max=16, refine_tol=1e-6, **kw) as ctx:
+        ctx.em_iter(n)
+        a_g, pi_g = ctx.read(cmcs.OUT_ALPHA), ctx.read(cmcs.OUT_PI)
+        q_g, asg = ctx.read(cmcs.OUT_Q), ctx.read(cmcs.OUT_ASSIGN)
+        summ = ctx.summary()
+    P = [wl.phi_real(t) for t in range(wl.T)]
+    Y = [wl.y_real(t) for t in range(wl.T)]
+    o = cofem.em(P, Y, wl.pi, wl.beta, n, K=wl.K, seed=wl.seed, tol=wl.cg_tol,
+                 max_iter=wl.cg_max_iter, C=wl.C, D=wl.D, refine_tol=1e-12, refine_max=40, **kw)
+    assert summ["refine_diverged"] == 0
+    assert np.array_equal(asg, o["assign"])
+    assert np.max(np.abs(q_g - o["last"]["q"])) <= FREE_Q_TOL
+    assert np.max(np.abs(pi_g - o["pi"])) <= FREE_Q_TOL
+    occupied = o["last"]["q"].sum(axis=0) > 0.5
+    assert rel_err_rows(a_g[occupied], o["alpha"][occupied]).max() <= REL_TOL
