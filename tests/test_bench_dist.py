@@ -45,3 +45,24 @@ def test_single_rank_aggregation():
     import bench
     value, ms_max = bench.aggregate(500.0, steps=4, world=1, device="cpu")
     assert ms_max == 500.0 and value == 8.0
+
+
+def test_metric_names_the_workload_and_fourier_path_selection(monkeypatch):
+    import bench
+    assert bench._metric("plain-scale") == bench.METRIC
+    assert "fourier-100k" in bench._metric("fourier-100k")
+    assert "plain-scale" not in bench._metric("fourier-100k")
+    monkeypatch.delenv("CMCS_DFT_FOURSTEP", raising=False)
+    assert bench._single_cta_fft(8192) and bench._single_cta_fft(128)
+    assert not bench._single_cta_fft(16384) and not bench._single_cta_fft(100000)
+    assert not bench._single_cta_fft(2000)
+    monkeypatch.setenv("CMCS_DFT_FOURSTEP", "1")
+    assert not bench._single_cta_fft(8192)
+
+
+def test_workload_subsets_for_the_bench():
+    import bench
+    wl = bench._workload("fourier-small", 0, tasks=2)
+    assert wl.T == 2 and wl.mask.shape == (2, 256)
+    wl = bench._workload("plain-small", 0, tasks=3)
+    assert wl.T == 3
