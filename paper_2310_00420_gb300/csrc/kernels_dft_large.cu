@@ -176,19 +176,28 @@ __device__ CT* fs_fft(CT* a, CT* b, const FsRadix& p, int nseq, int ls, const CT
   return a;
 }
 
-// W_D^m = W_D^(m - m mod 64) W_D^(m mod 64): two reads from a compact part of the table
-// (D / 64 entries at stride 64, and the first 64) instead of one scattered over all of it
+// W_D^m for m < D <= 2^20 from three small tables in shared memory:
+// W_D^m = top[m >> 12] mid[(m >> 6) & 63] lo[m & 63], with top[a] = W_D^(4096 a),
+// mid[b] = W_D^(64 b), lo[c] = W_D^c
+constexpr int kFsTwTop = 256;               // 2^20 / 4096
+constexpr int kFsTwSmem = 64 + 64 + kFsTwTop;
 template <typename CT>
-__device__ __forceinline__ CT fs_twD(const CT* __restrict__ tabD, const CT* lo, int64_t m) {
-  return fs_mul(tabD[m & ~(int64_t)63], lo[m & 63]);
+__device__ __forceinline__ CT fs_twD(const CT* tw3, int64_t m) {
+  const int mi = (int)m;
+  return fs_mul(fs_mul(tw3[128 + (mi >> 12)], tw3[64 + ((mi >> 6) & 63)]), tw3[mi & 63]);
 }
 
-// the sub-transform's table (L entries) and the first 64 entries of W_D into shared memory
+// the sub-transform's table (L entries) and the three W_D tables (lo, mid, top: see fs_twD)
+// into shared memory
 template <typename CT>
-__device__ __forceinline__ void fs_stage_tables(CT* tw, CT* lo, const CT* __restrict__ tab, int L,
-                                                const CT* __restrict__ tabD) {
+__device__ __forceinline__ void fs_stage_tables(CT* tw, CT* tw3, const CT* __restrict__ tab,
+                                                int L, const CT* __restrict__ tabD, int D) {
   for (int i = threadIdx.x; i < L; i += blockDim.x) tw[i] = tab[i];
-  if (threadIdx.x < 64) lo[threadIdx.x] = tabD[threadIdx.x];
+  for (int i = threadIdx.x; i < kFsTwSmem; i += blockDim.x) {
+    int64_t e = i < 64 ? i : (i < 128 ? (int64_t)(i - 64) * 64 : (int64_t)(i - 128) * 4096);
+    if (e >= D) e = 0;          // beyond the table: never read (m < D)
+    tw3[i] = tabD[e];
+  }
 }
 
 // the two systems of pair p of task t, and whether each takes part
@@ -224,12 +233,12 @@ k_fs_cols_fwd(const float* __restrict__ X, CT* __restrict__ Y, const CT* __restr
   CT* A = reinterpret_cast<CT*>(fs_sm);
   CT* B = A + nb * ls;
   CT* tw = B + nb * ls;
-  CT* lo = tw + pl.n1;
+  CT* tw3 = tw + pl.n1;
   const int pi = blockIdx.x;
   const FsSys q = fs_sys(pp, pi, flags);
   if (task_active != nullptr && task_active[q.t] == 0) return;     // block-uniform
   if (!q.on1 && !q.on2) return;
-  fs_stage_tables(tw, lo, tab1, pl.n1, tabD);
+  fs_stage_tables(tw, tw3, tab1, pl.n1, tabD, pp.D);
   const int c0 = blockIdx.y * nb;
   const float* x1 = X + q.s1 * pp.Dp;
   const float* x2 = X + q.s2 * pp.Dp;
@@ -244,7 +253,7 @@ k_fs_cols_fwd(const float* __restrict__ X, CT* __restrict__ Y, const CT* __restr
   CT* Yp = Y + (int64_t)pi * pp.D;
   for (int idx = threadIdx.x; idx < pl.n1 * nb; idx += blockDim.x) {
     const int k1 = idx >> lnb, cc = idx & (nb - 1), i2 = c0 + cc;
-    Yp[(int64_t)k1 * pl.n2 + i2] = fs_mul(res[cc * ls + k1], fs_twD(tabD, lo, (int64_t)i2 * k1));
+    Yp[(int64_t)k1 * pl.n2 + i2] = fs_mul(res[cc * ls + k1], fs_twD(tw3, (int64_t)i2 * k1));
   }
 }
 
@@ -261,12 +270,12 @@ k_fs_rows(CT* __restrict__ Y, const CT* __restrict__ spec, const CT* __restrict_
   CT* A = reinterpret_cast<CT*>(fs_sm);
   CT* B = A + pl.nbr * ls;
   CT* tw = B + pl.nbr * ls;
-  CT* lo = tw + pl.n2;
+  CT* tw3 = tw + pl.n2;
   const int pi = blockIdx.x;
   const FsSys q = fs_sys(pp, pi, flags);
   if (task_active != nullptr && task_active[q.t] == 0) return;     // block-uniform
   if (!q.on1 && !q.on2) return;
-  fs_stage_tables(tw, lo, tab2, pl.n2, tabD);
+  fs_stage_tables(tw, tw3, tab2, pl.n2, tabD, pp.D);
   const int r0 = blockIdx.y * pl.nbr;
   CT* Yp = Y + (int64_t)pi * pp.D;
   // the last row block may run past n1: its extra rows transform zeros and are not stored
@@ -298,7 +307,7 @@ k_fs_rows(CT* __restrict__ Y, const CT* __restrict__ spec, const CT* __restrict_
   for (int idx = threadIdx.x; idx < pl.nbr * pl.n2; idx += blockDim.x) {
     const int rr = fs_div(idx, pl.mn2), i2 = idx - rr * pl.n2, k1 = r0 + rr;
     if (k1 < pl.n1)
-      Yp[(int64_t)k1 * pl.n2 + i2] = fs_mulc(res[rr * ls + i2], fs_twD(tabD, lo, (int64_t)i2 * k1));
+      Yp[(int64_t)k1 * pl.n2 + i2] = fs_mulc(res[rr * ls + i2], fs_twD(tw3, (int64_t)i2 * k1));
   }
 }
 
@@ -556,12 +565,12 @@ bool make_plan(int D, FsPlan* out) {
 }
 
 int cols_nb(const FsPlan& pl, size_t cs) { return cs == sizeof(float2) ? pl.nb32 : pl.nb; }
-// two ping-pong buffers, the sub-transform's table and the first 64 entries of W_D
+// two ping-pong buffers, the sub-transform's table and the three W_D tables
 size_t cols_smem(const FsPlan& pl, size_t cs) {
-  return (2 * (size_t)cols_nb(pl, cs) * (pl.n1 + 1) + pl.n1 + 64) * cs;
+  return (2 * (size_t)cols_nb(pl, cs) * (pl.n1 + 1) + pl.n1 + kFsTwSmem) * cs;
 }
 size_t rows_smem(const FsPlan& pl, size_t cs) {
-  return (2 * (size_t)pl.nbr * (pl.n2 + 1) + pl.n2 + 64) * cs;
+  return (2 * (size_t)pl.nbr * (pl.n2 + 1) + pl.n2 + kFsTwSmem) * cs;
 }
 
 template <typename CT>
