@@ -97,7 +97,9 @@ typedef struct {
   int warm_start;         /* 1: from the second E-step on, each mean system starts from the
                              previous E-step's mean (x_1 = mu_prev: CG on b0 - A mu_prev, with
                              the compensated residual, stopped at ||r|| <= cg_tol ||b0||); the
-                             probe systems keep x_1 = 0, which the Lanczos estimate needs     */
+                             probe systems keep x_1 = 0, which the Lanczos estimate needs.
+                             cmcs_set_alpha keeps the previous means as the start (any start
+                             is valid); cmcs_set_data and a failed E-step drop them          */
 } cmcs_config;
 
 /* Summary of the most recent E-step and the EM state. */
