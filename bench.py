@@ -9,6 +9,11 @@ inputs, solutions refined to the accuracy the parity tests check.  The default p
 as a BF16 pair on the tcgen05 tensor cores (FP32-class products, FP32 accumulation); the
 plain FP32 SIMT form is timed beside it on the same workload ("fp32_form").
 
+Beside the headline the default run times, in the same JSON line, the precision workload
+(T=16, D=16384, K=64: BF16X3 and FP32 forms, error against exact FP64 solves) and the
+batching workload (T=256 uneven tasks: one launch per pass against a per-task launch loop),
+each on a short stated sample.
+
 Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on a bounded
 sample of the same workload instead.  Multi-GPU (torchrun): every rank runs an independent
 replica (its own seed); value is the replicas' total throughput (weak scaling).
@@ -37,7 +42,6 @@ def _metric(workload: str) -> str:
     """The metric's name for the workload timed (the default is plain-scale)."""
     return METRIC if workload == "plain-scale" else METRIC.replace("plain-scale", workload)
 UNIT = "EM iters/s"
-FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
 
 
 def _args():
@@ -61,6 +65,8 @@ def _args():
     ap.add_argument("--refine-tol", type=float, default=1e-5)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-legs", action="store_true",
+                    help="skip the precision and batching workload legs of the default run")
     ap.add_argument("--precond", action="store_true",
                     help="Jacobi-preconditioned CG (method variant)")
     ap.add_argument("--learn-pi", action="store_true", help="learn the cluster priors")
@@ -158,17 +164,52 @@ def aggregate(ms_local: float, steps: int, world: int, device: str = "cuda"):
     return world * steps / (ms_max / 1e3), ms_max
 
 
-# DRAM bytes (read + write) of one operator application, k_tc<1> + k_tc<3>, from one ncu capture
-# of the current kernels on the 8-task slice of plain-scale, scaled by 32 / 8 tasks
-# (profiles/operator_tc_bf16x3_plain-scale.md).  None for other workloads, and to be reset to
-# None whenever those kernels change.
-_TRAFFIC_PLAIN_SCALE_BF16X3 = 4 * ((571.656704 + 3.679744) + (548.578048 + 25.114368)) * 1e6
+# DRAM bytes (read + write) of one operator application of the tensor-core operator (k_tc<1> +
+# k_tc<3>) on plain-scale with BF16X3, from one ncu capture on the 8-task slice scaled by
+# 32 / 8 tasks, keyed to the SHA-256 prefix of the kernel source it was taken on: once that
+# source changes the figure no longer describes the kernel and traffic is reported as null.
+_TRAFFIC = {"kernels_tc.cu": "acb0f4231cdbee5b",
+            "plain-scale/bf16x3": 4 * ((571.656704 + 3.679744) + (548.578048 + 25.114368)) * 1e6}
+
+
+def _source_sha(name: str) -> str:
+    import hashlib
+    path = os.path.join(ROOT, "paper_2310_00420_gb300", "csrc", name)
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
 def _operator_traffic(wl, precision: str):
     if wl.name == "plain-scale" and wl.T == 32 and precision == "bf16x3":
-        return _TRAFFIC_PLAIN_SCALE_BF16X3
+        if _source_sha("kernels_tc.cu") == _TRAFFIC["kernels_tc.cu"]:
+            return _TRAFFIC["plain-scale/bf16x3"]
     return None
+
+
+def _fp32_sgemm_peak():
+    """FP32 throughput measured the way the BF16 peak is: cuBLAS SGEMM (TF32 off) at
+    8192^3, best of 10 with CUDA events; TFLOP/s."""
+    import torch
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        n = 8192
+        a = torch.randn(n, n, device="cuda")
+        b = torch.randn(n, n, device="cuda")
+        c = a @ b
+        best = None
+        for _ in range(10):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b, out=c)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        del a, b, c
+        return 2.0 * n ** 3 / (best * 1e-3) / 1e12
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
 
 
 def _single_cta_fft(D: int) -> bool:
@@ -206,6 +247,28 @@ def _cpu_cores():
     return int(n) if n else (os.cpu_count() or 1)
 
 
+# (task, cluster) pairs the CPU oracle times, spread over tasks and clusters
+N_CPU_PAIRS = 8
+
+
+def _cpu_pairs(wl):
+    return [((7 * i) % wl.T, i % wl.C) for i in range(min(N_CPU_PAIRS, wl.T * wl.C))]
+
+
+def _cpu_sample(wl, pairs, times, refine_tol, refine_max):
+    """The cpu_baseline object for oracle E-step times of the given pairs (seconds each)."""
+    per_iter = statistics.mean(times) * wl.T * wl.C            # extrapolated EM iteration
+    return {"value": 1.0 / per_iter, "unit": UNIT, "cores": _cpu_cores(), "kind": "oracle",
+            "extrapolated": True, "pairs_timed": len(times), "seconds_timed": float(sum(times)),
+            "pair_seconds": {"mean": statistics.mean(times), "min": min(times),
+                             "max": max(times)},
+            "alpha_state": "initial draw of Alg. 2 (EM iteration 0)",
+            "sample": f"{len(times)} (task, cluster) pairs of the E-step spread over tasks and "
+                      f"clusters {pairs}, each {wl.K + 1} FP64 CG solves + refinement "
+                      f"(refine_tol {refine_tol}, at most {refine_max} sweeps) at the initial "
+                      f"alpha; EM iteration extrapolated x{wl.T * wl.C} pairs from the mean"}
+
+
 def run_reference(a):
     rank, world, _ = _dist()
     if rank != 0:
@@ -213,27 +276,141 @@ def run_reference(a):
     from oracle import philox
     wl = _workload(a.workload, 0, a.tasks)
     alpha = philox.alpha_init(wl.seed, wl.C, wl.D)
-    pairs = wl.T * wl.C
+    pairs = _cpu_pairs(wl)
     for i in range(a.warmup):
-        _oracle_pair(wl, alpha, i, i % wl.T, i % wl.C, a.refine_tol, a.refine_max)
-    times = []
+        t, c = pairs[i % len(pairs)]
+        _oracle_pair(wl, alpha, 0, t, c, a.refine_tol, a.refine_max)
+    times, used = [], []
     for i in range(a.steps):
-        _, dt = _oracle_pair(wl, alpha, i, (7 * i) % wl.T, i % wl.C, a.refine_tol, a.refine_max)
+        t, c = pairs[i % len(pairs)]
+        _, dt = _oracle_pair(wl, alpha, 0, t, c, a.refine_tol, a.refine_max)
         times.append(dt)
-    per_iter = statistics.mean(times) * pairs            # extrapolated full EM iteration
-    value = 1.0 / per_iter
+        used.append((t, c))
+    cpu = _cpu_sample(wl, sorted(set(used)), times, a.refine_tol, a.refine_max)
+    value = cpu["value"]
     line = {"impl": "reference", "metric": _metric(a.workload), "value": value, "unit": UNIT,
             "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
-            "ms_per_step": per_iter * 1e3, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": 1e3 / value, "extrapolated": True,
+            "ms_per_sample": 1e3 * statistics.mean(times),
+            "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"{wl.name} T={wl.T} C={wl.C} D={wl.D} N={int(wl.N[0])} "
                                    f"K={wl.K} tol={wl.cg_tol} max_iter={wl.cg_max_iter}",
-                       "refine_tol": a.refine_tol, "refine_max": a.refine_max},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": _cpu_cores(), "kind": "oracle",
-                             "sample": f"one (task, cluster) pair per step ({wl.K + 1} FP64 CG "
-                                       f"solves + refinement), EM iteration extrapolated x{pairs}"},
+                       "refine_tol": a.refine_tol, "refine_max": a.refine_max,
+                       "step": "one (task, cluster) pair of the E-step per timed step; "
+                               "ms_per_step is the EM iteration extrapolated from their mean"},
+            "cpu_baseline": cpu,
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def _time_ctx(ctx, warmup: int, steps: int) -> dict:
+    """EM iterations/s of a context (CUDA events around `steps` iterations after `warmup`),
+    with its operator profile and CG statistics."""
+    import torch
+    for _ in range(warmup):
+        ctx.em_iter(1)
+    ctx.profile(True)
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record()
+    for _ in range(steps):
+        ctx.em_iter(1)
+    f1.record()
+    torch.cuda.synchronize()
+    ms = f0.elapsed_time(f1)
+    pr = ctx.profile_read()
+    sm = ctx.summary()
+    ctx.profile(False)
+    calls = max(1, pr["operator_calls"])
+    return {"value": steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
+            "warmup": warmup, "steps": steps,
+            "cg_steps_mean": sm["cg_steps_mean"], "cg_capped": sm["cg_capped"],
+            "operator_applies": sm["operator_applies"],
+            "operator_ms_per_application": pr["operator_ms"] / calls,
+            "operator_gbs": pr["operator_bytes"] / (pr["operator_ms"] * 1e-3) / 1e9
+            if pr["operator_ms"] else None,
+            "operator_tflops": pr["operator_flops"] / (pr["operator_ms"] * 1e-3) / 1e12
+            if pr["operator_ms"] else None,
+            "residual_ms_per_step": pr["residual_ms"] / steps,
+            "resid_rel_max": sm["resid_rel_max"], "refine_diverged": sm["refine_diverged"]}
+
+
+def precision_leg(a, peaks) -> dict:
+    """The precision workload (T=16, C=4, D=16384, N=4096, K=64; R = 260 in two tensor-core
+    column tiles): EM iterations/s of the BF16X3 tensor-core path and of the plain FP32 form,
+    the operator's HBM fraction, and the error of mu and s on a sampled pair against the
+    oracle's exact FP64 solves (Cholesky, Eq. 3), with the M-step's alpha against the oracle's
+    M-step on the same E-step outputs."""
+    import torch
+    from oracle import cofem, philox
+    from paper_2310_00420_gb300 import cmcs
+    wl = _workload("precision", 0)
+    kw = dict(C=wl.C, K=wl.K, beta=wl.beta, pi=wl.pi, cg_max_iter=wl.cg_max_iter,
+              cg_tol=wl.cg_tol, seed=wl.seed, refine_max=a.refine_max, refine_tol=a.refine_tol)
+    Phi_d = torch.from_numpy(wl.Phi).cuda()
+    y_d = torch.from_numpy(wl.y).cuda()
+    out = {"workload": f"{wl.name} T={wl.T} C={wl.C} D={wl.D} N={int(wl.N[0])} K={wl.K} "
+                       f"tol={wl.cg_tol} max_iter={wl.cg_max_iter}"}
+    ctx = cmcs.Context(Phi_d, y_d, wl.N, precision="bf16x3", **kw)
+    tc = _time_ctx(ctx, 1, 2)
+    tc["hbm_frac"] = tc["operator_gbs"] / peaks["hbm_gbs"] if tc["operator_gbs"] else None
+    # sampled pair against exact FP64 solves with the same probes
+    alpha = ctx.read(cmcs.OUT_ALPHA)
+    it = ctx.summary()["em_iters_done"]
+    ctx.set_alpha(alpha, it)
+    ctx.em_iter(1)
+    mu_g, s_g, q_g = ctx.read(cmcs.OUT_MU), ctx.read(cmcs.OUT_S), ctx.read(cmcs.OUT_Q)
+    alpha_next = ctx.read(cmcs.OUT_ALPHA)
+    ctx.close()
+    t, c = 3, 2
+    P = wl.phi(t).astype(np.float64)
+    yv = wl.yt(t).astype(np.float64)
+    pk = philox.probes(wl.seed, it, t, c, wl.C, wl.K, wl.D)
+    B = np.concatenate([cofem.rhs_mean(P, yv, wl.beta)[:, None], pk.T], axis=1)
+    t0 = time.perf_counter()
+    X = cofem.solve_exact(P, wl.beta, alpha[c].astype(np.float64), B)
+    dt = time.perf_counter() - t0
+    rel = lambda g_, r_: float(np.linalg.norm(g_ - r_) / np.linalg.norm(r_))
+    a_ref = cofem.m_step(q_g, mu_g.astype(np.float64), s_g.astype(np.float64),
+                         alpha.astype(np.float64))
+    tc["err_vs_fp64"] = {"pair": [t, c], "mu_rel": rel(mu_g[t, c], X[:, 0]),
+                         "s_rel": rel(s_g[t, c], np.mean(pk.T * X[:, 1:], axis=1)),
+                         "alpha_mstep_rel": max(rel(alpha_next[j], a_ref[j]) for j in range(wl.C)),
+                         "oracle": f"exact Cholesky solves of the pair ({dt:.1f} s); alpha: the "
+                                   f"oracle's M-step (Eq. 5, FP64) on the GPU's q, mu, s"}
+    out["bf16x3"] = tc
+    del ctx
+    c2 = cmcs.Context(Phi_d, y_d, wl.N, precision="fp32", **kw)
+    out["fp32_form"] = _time_ctx(c2, 0, 1)
+    c2.close()
+    del Phi_d, y_d
+    torch.cuda.empty_cache()
+    return out
+
+
+def batching_leg(a) -> dict:
+    """The batching workload (T=256 tasks with uneven N_t in [256, 2048], D=4096, C=8, K=16):
+    every task in one persistent launch per operator pass (CG chunks replayed from CUDA graphs)
+    against a launch loop over the tasks, same precision, same EM iterations."""
+    import torch
+    from paper_2310_00420_gb300 import cmcs
+    wl = _workload("batching", 0)
+    kw = dict(C=wl.C, K=wl.K, beta=wl.beta, pi=wl.pi, cg_max_iter=wl.cg_max_iter,
+              cg_tol=wl.cg_tol, seed=wl.seed, refine_max=a.refine_max, refine_tol=a.refine_tol,
+              precision="bf16x3")
+    Phi_d = torch.from_numpy(wl.Phi).cuda()
+    y_d = torch.from_numpy(wl.y).cuda()
+    out = {"workload": f"{wl.name} T={wl.T} C={wl.C} D={wl.D} N_t in [{int(wl.N.min())}, "
+                       f"{int(wl.N.max())}] K={wl.K} tol={wl.cg_tol} max_iter={wl.cg_max_iter}"}
+    for sched in ("batched", "per_task"):
+        c2 = cmcs.Context(Phi_d, y_d, wl.N, schedule=sched, **kw)
+        out[sched] = _time_ctx(c2, 1, 1)
+        c2.close()
+    out["speedup"] = out["batched"]["value"] / out["per_task"]["value"]
+    del Phi_d, y_d
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_ours(a):
@@ -307,11 +484,12 @@ def run_ours(a):
                 "per_launch_ms": prof["operator_ms"] / max(1, prof["operator_calls"]),
                 "fp32_tflops_achieved": op_tflops}
     elif a.precision == "fp32":
-        roof = {"bound": "alu", "achieved": op_tflops, "peak": FP32_ALU_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": op_tflops / FP32_ALU_PEAK_TFLOPS,
+        fp32_peak = _fp32_sgemm_peak()
+        roof = {"bound": "alu", "achieved": op_tflops, "peak": fp32_peak,
+                "unit": "TFLOP/s", "frac": op_tflops / fp32_peak,
                 "traffic": None,
                 "kernel": "operator (k_pass1 + k_pass2, FP32 SIMT)",
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (derived)",
+                "peak_source": "measured here: cuBLAS SGEMM 8192^3, TF32 off, best of 10",
                 "per_launch_flops": prof["operator_flops"] / max(1, prof["operator_calls"]),
                 "per_launch_ms": prof["operator_ms"] / max(1, prof["operator_calls"]),
                 "hbm_gbs_achieved": op_gbs, "hbm_frac": op_gbs / peaks["hbm_gbs"]}
@@ -355,12 +533,12 @@ def run_ours(a):
         err = {"pair": [t_s, c_s], "mu_rel": rel(mu_g[t_s, c_s], o["mu"][0, 0]),
                "s_rel": rel(s_g[t_s, c_s], o["s"][0, 0])}
         if world == 1:
-            _, dt_b = _oracle_pair(wl, alpha, it, t_s, c_s, a.refine_tol, a.refine_max, **variant)
-            cpu = {"value": 1.0 / (dt_b * wl.T * wl.C), "unit": UNIT, "cores": _cpu_cores(),
-                   "kind": "oracle",
-                   "sample": f"one (task, cluster) pair of the E-step ({wl.K + 1} FP64 CG solves "
-                             f"+ refinement to the same tolerance), {dt_b:.1f} s, EM iteration "
-                             f"extrapolated x{wl.T * wl.C} pairs"}
+            from oracle import philox
+            alpha0 = philox.alpha_init(wl.seed, wl.C, wl.D)
+            pairs = _cpu_pairs(wl)
+            times = [_oracle_pair(wl, alpha0, 0, t, c, a.refine_tol, a.refine_max, **variant)[1]
+                     for t, c in pairs]
+            cpu = _cpu_sample(wl, pairs, times, a.refine_tol, a.refine_max)
 
     # end to end through the public API with host buffers: create from pinned host Phi and y
     # (H2D inside), set alpha, one EM iteration, read q, alpha and the reconstructions (D2H)
@@ -402,42 +580,41 @@ def run_ours(a):
 
     ctx.close()
 
-    def timed_leg(**over):
-        """EM iterations/s of another form on the same workload (same warm-up and steps)."""
+    def timed_leg(warmup=None, steps=None, **over):
+        """EM iterations/s of another form on the same workload (same warm-up and steps unless
+        given)."""
+        w_ = a.warmup if warmup is None else warmup
+        n_ = a.steps if steps is None else steps
         kw2 = dict(kw)
         kw2.update(over)
         c3 = (cmcs.Context.from_fourier(wl, device=True, **kw2) if fourier
               else cmcs.Context(Phi_d, y_d, wl.N, **kw2))
-        for _ in range(a.warmup):
-            c3.em_iter(1)
-        c3.profile(True)
-        torch.cuda.synchronize()
-        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        f0.record()
-        for _ in range(a.steps):
-            c3.em_iter(1)
-        f1.record()
-        torch.cuda.synchronize()
-        ms3 = f0.elapsed_time(f1)
-        pr = c3.profile_read()
-        sm3 = c3.summary()
+        out = _time_ctx(c3, w_, n_)
         c3.close()
-        return {"value": a.steps / (ms3 / 1e3), "unit": UNIT, "ms_per_step": ms3 / a.steps,
-                "cg_steps_mean": sm3["cg_steps_mean"], "cg_capped": sm3["cg_capped"],
-                "operator_applies": sm3["operator_applies"],
-                "operator_ms_per_application": pr["operator_ms"] / max(1, pr["operator_calls"]),
-                "operator_tflops": pr["operator_flops"] / (pr["operator_ms"] * 1e-3) / 1e12
-                if pr["operator_ms"] else None, **{k: v for k, v in over.items()}}
+        out.update({k: v for k, v in over.items()})
+        return out
 
     fp32_form = None
     if a.precision != "fp32" and not a.no_fp32_form:
-        fp32_form = timed_leg(precision="fp32")
+        # the FP32 SIMT form is ~7x slower: a shorter sample (stated in the line)
+        fp32_form = timed_leg(warmup=min(a.warmup, 1), steps=min(a.steps, 3), precision="fp32")
+        peak32 = _fp32_sgemm_peak()
+        fp32_form["fp32_peak_tflops"] = peak32
+        fp32_form["fp32_peak_source"] = "measured here: cuBLAS SGEMM 8192^3, TF32 off, best of 10"
+        if fp32_form["operator_tflops"]:
+            fp32_form["alu_frac"] = fp32_form["operator_tflops"] / peak32
     per_task = None
     if a.compare_schedule:
         per_task = timed_leg(schedule="per_task")
     precond_form = None
     if a.compare_precond and not a.precond:
         precond_form = timed_leg(precond=True)
+    legs = {}
+    if rank == 0 and world == 1 and not a.no_legs and a.workload == "plain-scale" and not a.tasks:
+        del Phi_d, y_d
+        torch.cuda.empty_cache()
+        legs["precision_workload"] = precision_leg(a, peaks)
+        legs["batching_workload"] = batching_leg(a)
     if rank == 0:
         line = {"metric": _metric(a.workload), "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms_max / a.steps,
@@ -456,7 +633,11 @@ def run_ours(a):
                                   if fourier else
                                   f"inputs larger than L2 (Phi {wl.Phi.nbytes / 1e9:.1f} GB)")},
                 "cg_solves_per_s": value * systems,
+                "cg_solves_counted": "refined solves: every system of the E-step, counted once "
+                                     "whether its first CG solve converged or stopped at "
+                                     "max_iter and was finished by refinement",
                 "cg_steps_mean": summ["cg_steps_mean"], "cg_capped": summ["cg_capped"],
+                "cg_capped_frac": summ["cg_capped"] / systems,
                 "refine_sweeps_max": summ["refine_sweeps_max"],
                 "refine_diverged": summ["refine_diverged"], "resid_rel_max": summ["resid_rel_max"],
                 "operator_share": prof["operator_ms"] / ms if ms else None,
@@ -465,7 +646,7 @@ def run_ours(a):
                 "roofline": roof, "cpu_baseline": cpu, "err_vs_fp64": err, "e2e": e2e,
                 "clocks": clk, "gpu_launches": prof["kernel_launches"],
                 "fp32_form": fp32_form, "per_task_schedule": per_task,
-                "precond_form": precond_form}
+                "precond_form": precond_form, **legs}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

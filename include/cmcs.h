@@ -272,12 +272,15 @@ cmcs_status cmcs_profile_read(const cmcs_ctx *ctx, cmcs_profile_data *out);
  * no allocating routine: the intermediate Phi V is kept in a fixed 16 MiB device array inside
  * the library, so m * N must not exceed 4,194,304 (larger requests return
  * CMCS_ERR_INVALID_ARG with a message for cmcs_last_error(NULL)).
- * Phi: float [N][D] row-major, alpha: float [D], V and Z: float [m][D]; all device pointers on
- * the current device; beta > 0.  stream: cudaStream_t or NULL; the call returns after the work
- * has completed.  Every call shares that one array (per device), which keeps the previous
- * call's contents; calls whose GPU work overlaps (other host threads, other streams) race on it.
- * The first call on each device looks up the array's device address with that device current;
- * make that first call before capturing a stream into a CUDA graph. */
+ * Phi: float [N][D] row-major, alpha: float [D], V and Z: float [m][D]; all device memory of
+ * the current device (a host pointer or another device's memory returns CMCS_ERR_INVALID_ARG
+ * before anything is launched); beta > 0.  stream: cudaStream_t or NULL; the call synchronises
+ * that stream before it returns, so the host waits for its two kernels.  Every call shares that
+ * one array (per device), which keeps the previous call's contents; calls whose GPU work
+ * overlaps (other host threads, other streams) race on it.  The first call on each device looks
+ * up the array's device address with that device current and keeps it; make that first call
+ * before any stream capture.  The kept address does not survive cudaDeviceReset: do not call
+ * this entry point on a device after resetting it. */
 cmcs_status cmcs_apply_noalloc(const float *Phi, int N, int D, const float *alpha, double beta,
                                const float *V, int m, float *Z, void *stream);
 

@@ -332,10 +332,44 @@ class Context:
         return out
 
 
+def _check_noalloc_args(Phi, alpha, V, Z):
+    """Shapes, dtypes, contiguity and device of apply_noalloc's tensors, checked before the
+    library is called (a wrong one would make its kernels read or write out of bounds)."""
+    import torch
+    named = [("Phi", Phi), ("alpha", alpha), ("V", V)] + ([("Z", Z)] if Z is not None else [])
+    for name, x in named:
+        if not isinstance(x, torch.Tensor):
+            raise ValueError(f"{name} must be a torch tensor")
+        if x.dtype != torch.float32:
+            raise ValueError(f"{name} must be float32, got {x.dtype}")
+        if not x.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+    if Phi.dim() != 2 or V.dim() != 2:
+        raise ValueError("Phi must be [N][D] and V [m][D]")
+    N, D = Phi.shape
+    if N < 1 or D < 1 or V.shape[0] < 1:
+        raise ValueError("Phi and V must not be empty")
+    if V.shape[1] != D:
+        raise ValueError(f"V has {V.shape[1]} columns, Phi has D = {D}")
+    if alpha.numel() != D:
+        raise ValueError(f"alpha has {alpha.numel()} entries, expected D = {D}")
+    if Z is not None and tuple(Z.shape) != tuple(V.shape):
+        raise ValueError(f"Z must have V's shape {tuple(V.shape)}, got {tuple(Z.shape)}")
+    for name, x in named:
+        if not x.is_cuda:
+            raise ValueError(f"{name} must be on a CUDA device")
+    dev = torch.cuda.current_device()
+    for name, x in named:
+        if x.device.index != dev:
+            raise ValueError(f"{name} is on cuda:{x.device.index}, the current device is cuda:{dev}")
+
+
 def apply_noalloc(Phi, alpha, beta: float, V, Z=None, stream=None):
     """Z = beta Phi^T (Phi V) + alpha * V for one task without any device allocation inside
-    the library (Phi [N][D], alpha [D], V [m][D]: float32 CUDA tensors)."""
+    the library (Phi [N][D], alpha [D], V [m][D]: contiguous float32 tensors on the current
+    CUDA device; ValueError otherwise)."""
     import torch
+    _check_noalloc_args(Phi, alpha, V, Z)
     N, D = Phi.shape
     m = V.shape[0]
     if Z is None:

@@ -28,7 +28,9 @@ float* g_noalloc_ptr[kMaxDevices] = {};
 
 // Device address of the scratch array on the current device, looked up once per device (with
 // that device current).  Host code must not pass the symbol itself to a kernel: on the host it
-// names a stand-in, not device memory.
+// names a stand-in, not device memory.  The cached address belongs to the device's primary
+// context: after cudaDeviceReset the module is loaded again and the cache is stale, so a process
+// that resets a device must not call this entry point on it afterwards.
 cudaError_t noalloc_scratch(float** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -113,6 +115,18 @@ k_noalloc_phitw(const float* __restrict__ phi, const float* __restrict__ W,
     }
 }
 
+// true when p is device memory (or managed memory) that kernels on device dev can address; a
+// host pointer, or memory of another device, is rejected before any launch.  The query
+// allocates nothing.
+bool device_pointer(const void* p, int dev) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == dev;
+}
+
 }  // namespace
 
 extern "C" cmcs_status cmcs_apply_noalloc(const float* Phi, int N, int D, const float* alpha,
@@ -133,6 +147,22 @@ extern "C" cmcs_status cmcs_apply_noalloc(const float* Phi, int N, int D, const 
              (size_t)m * (size_t)N, kNoAllocScratchFloats);
     cmcs::set_global_error(msg);
     return CMCS_ERR_INVALID_ARG;
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    cmcs::set_global_error("cmcs_apply_noalloc: no current CUDA device");
+    return CMCS_ERR_CUDA;
+  }
+  const void* ptrs[4] = {Phi, alpha, V, Z};
+  const char* names[4] = {"Phi", "alpha", "V", "Z"};
+  for (int i = 0; i < 4; ++i) {
+    if (!device_pointer(ptrs[i], dev)) {
+      snprintf(msg, sizeof(msg),
+               "cmcs_apply_noalloc: %s is not device memory of the current device %d", names[i], dev);
+      cmcs::set_global_error(msg);
+      return CMCS_ERR_INVALID_ARG;
+    }
   }
   float* W = nullptr;
   cudaError_t e = noalloc_scratch(&W);

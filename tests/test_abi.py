@@ -166,3 +166,29 @@ def test_calls_on_null_context_are_rejected(L):
     assert L.cmcs_probes(None, 0, None, 0) == cmcs.ERR_INVALID_ARG
     assert L.cmcs_lanczos_quadrature(None, None, None, 1, 1, None, None, None) == cmcs.ERR_INVALID_ARG
     L.cmcs_destroy(None)
+
+
+def test_apply_noalloc_binding_validates_before_calling():
+    """The binding of cmcs_apply_noalloc rejects tensors whose dtype, layout, shape or device
+    would make the kernels read or write out of bounds, before anything reaches the library
+    (these CPU tensors never get past the checks)."""
+    import torch
+    from paper_2310_00420_gb300 import cmcs
+    N, D, m = 6, 5, 3
+    Phi = torch.zeros((N, D))
+    alpha = torch.ones(D)
+    V = torch.zeros((m, D))
+    bad = [
+        dict(Phi=Phi.double()),                       # dtype
+        dict(V=torch.zeros((D, m)).t()),              # non-contiguous
+        dict(Phi=torch.zeros(N * D)),                 # not 2-D
+        dict(V=torch.zeros((m, D + 1))),              # columns != D
+        dict(alpha=torch.ones(D - 1)),                # short alpha
+        dict(Z=torch.zeros((m + 1, D))),              # Z shape
+        dict(),                                       # all valid but on the host
+    ]
+    for over in bad:
+        args = dict(Phi=Phi, alpha=alpha, V=V, Z=None)
+        args.update(over)
+        with pytest.raises(ValueError):
+            cmcs.apply_noalloc(args["Phi"], args["alpha"], 1.0, args["V"], Z=args["Z"])

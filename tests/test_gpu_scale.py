@@ -1,6 +1,8 @@
-"""Parity at the benchmark's full size and launch configuration (plain-scale workload:
-T=32, C=4, D=8192, N=2048, K=32; FP32 path, refine_max 8, refine_tol 1e-5), on outputs the
-oracle can compute one (task, cluster) pair at a time, plus properties that hold at any size."""
+"""Parity at the benchmark's full size (plain-scale workload: T=32, C=4, D=8192, N=2048, K=32;
+refine_max 8, refine_tol 1e-5), on outputs the oracle can compute one (task, cluster) pair at
+a time, plus properties that hold at any size.  Two launch configurations: the plain FP32 SIMT
+form, and the configuration the benchmark times (the tcgen05 operator with Phi and the vectors
+as BF16 pairs, CMCS_BF16X3)."""
 import numpy as np
 import pytest
 
@@ -12,12 +14,11 @@ from gpu_helpers import make_ctx, rel_err_rows
 pytestmark = pytest.mark.gpu
 
 BENCH = dict(refine_max=8, refine_tol=1e-5)
+BENCH_TC = dict(precision="bf16x3", refine_max=8, refine_tol=1e-5)   # the timed configuration
 
 
-@pytest.fixture(scope="module")
-def scale():
-    wl = synth.plain_scale()
-    with make_ctx(wl, **BENCH) as ctx:
+def _run(wl, kw):
+    with make_ctx(wl, **kw) as ctx:
         ctx.em_iter(2)                                 # move away from the initial draw
         alpha = ctx.read(cmcs.OUT_ALPHA)
         it = ctx.summary()["em_iters_done"]
@@ -34,9 +35,18 @@ def scale():
     return wl, alpha, it, out
 
 
-@pytest.mark.parametrize("pair", [(0, 0), (19, 3)])
-def test_sampled_pairs_match_oracle(scale, pair):
-    wl, alpha, it, g = scale
+@pytest.fixture(scope="module")
+def scale():
+    return _run(synth.plain_scale(), BENCH)
+
+
+@pytest.fixture(scope="module")
+def scale_tc():
+    return _run(synth.plain_scale(), BENCH_TC)
+
+
+def _check_sampled_pair(run, pair):
+    wl, alpha, it, g = run
     t, c = pair
     o = cofem.cofem_estep([wl.phi(t).astype(np.float64)], [wl.yt(t).astype(np.float64)],
                           alpha[c:c + 1].astype(np.float64), np.array([1.0]), wl.beta, wl.K,
@@ -55,16 +65,54 @@ def test_sampled_pairs_match_oracle(scale, pair):
     assert abs(g["logdet"][t, c] - o["logdet"][0, 0]) <= 1e-4 * abs(o["logdet"][0, 0])
 
 
-def test_softmax_and_assignments_follow_ell(scale):
-    wl, alpha, it, g = scale
+@pytest.mark.parametrize("pair", [(0, 0), (19, 3)])
+def test_sampled_pairs_match_oracle(scale, pair):
+    _check_sampled_pair(scale, pair)
+
+
+@pytest.mark.parametrize("pair", [(0, 0), (19, 3)])
+def test_headline_sampled_pairs_match_oracle(scale_tc, pair):
+    """The benchmark's configuration (tensor-core operator, BF16 pairs, refined): mu and s of
+    the sampled pairs at 1e-4 against the oracle's refined FP64 solves, nu and ell in replay."""
+    _check_sampled_pair(scale_tc, pair)
+
+
+def test_headline_assignments_follow_replay_q(scale_tc):
+    """All T = 32 assignments of the benchmark's configuration against the argmax of the
+    responsibilities the oracle forms from the GPU's own CG coefficients (Eqs. 9-11 in
+    replay) and the GPU's refined means (Eq. 3), and those responsibilities at 1e-4."""
+    wl, alpha, it, g = scale_tc
+    T, C = wl.T, wl.C
+    ell = np.zeros((T, C))
+    for t in range(T):
+        b0 = cofem.rhs_mean(wl.phi(t).astype(np.float64), wl.yt(t).astype(np.float64), wl.beta)
+        for c in range(C):
+            nu = cofem.logdet_estimate(g["gamma"][t, c].astype(np.float64),
+                                       g["xi"][t, c].astype(np.float64), g["steps"][t, c, 1:],
+                                       wl.D)
+            ell[t, c] = cofem.ell(nu, alpha[c].astype(np.float64), b0,
+                                  g["mu"][t, c].astype(np.float64))
+    q_rep = cofem.responsibilities(ell, wl.pi)
+    np.testing.assert_allclose(g["ell"], ell, rtol=1e-6)
+    assert np.max(np.abs(g["q"] - q_rep)) <= 1e-4
+    assert np.array_equal(g["assign"], np.argmax(q_rep, axis=1))
+    # the timed path refines every system: the returned means meet the residual it reports
+    assert g["summary"]["resid_rel_max"] <= 1e-6
+    assert g["summary"]["refine_diverged"] == 0
+
+
+@pytest.mark.parametrize("run", ["scale", "scale_tc"])
+def test_softmax_and_assignments_follow_ell(request, run):
+    wl, alpha, it, g = request.getfixturevalue(run)
     q = cofem.responsibilities(g["ell"], wl.pi)
     assert np.max(np.abs(q - g["q"])) <= 1e-12
     assert np.array_equal(g["assign"], np.argmax(g["q"], axis=1))
     np.testing.assert_allclose(g["q"].sum(axis=1), 1.0, atol=1e-12)
 
 
-def test_mstep_at_scale(scale):
-    wl, alpha, it, g = scale
+@pytest.mark.parametrize("run", ["scale", "scale_tc"])
+def test_mstep_at_scale(request, run):
+    wl, alpha, it, g = request.getfixturevalue(run)
     ref = cofem.m_step(g["q"], g["mu"].astype(np.float64), g["s"].astype(np.float64),
                        alpha.astype(np.float64))
     np.testing.assert_allclose(g["alpha_next"], ref, rtol=2e-7)
@@ -72,8 +120,9 @@ def test_mstep_at_scale(scale):
     assert np.array_equal(g["mu2"], g["mu"])
 
 
-def test_lanczos_first_entry_identity_at_scale(scale):
+@pytest.mark.parametrize("run", ["scale", "scale_tc"])
+def test_lanczos_first_entry_identity_at_scale(request, run):
     """||p||^2 / gamma_1 = p^T A p > 0 and every recorded step count is within the cap."""
-    wl, alpha, it, g = scale
+    wl, alpha, it, g = request.getfixturevalue(run)
     assert g["steps"].min() >= 1 and g["steps"].max() <= wl.cg_max_iter
     assert np.all(g["gamma"][..., 0] > 0)
