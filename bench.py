@@ -15,8 +15,10 @@ batching workload (T=256 uneven tasks: one launch per pass against a per-task la
 each on a short stated sample.
 
 Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on a bounded
-sample of the same workload instead.  Multi-GPU (torchrun): every rank runs an independent
-replica (its own seed); value is the replicas' total throughput (weak scaling).
+sample of the same workload instead.  Multi-GPU (torchrun): the tasks of the one problem are
+split over the ranks (Sec. 3.3; every E-step needs only its own tasks, the M-step's sums are
+exchanged in one all-gather per EM iteration), and value is that problem's EM iterations/s
+(strong scaling); --replicas runs an independent problem per rank instead (weak scaling).
 """
 from __future__ import annotations
 
@@ -38,9 +40,10 @@ import numpy as np  # noqa: E402
 METRIC = "CoFEM EM iterations/s (plain-scale workload, one replica per GPU)"
 
 
-def _metric(workload: str) -> str:
+def _metric(workload: str, sharded: bool = False) -> str:
     """The metric's name for the workload timed (the default is plain-scale)."""
-    return METRIC if workload == "plain-scale" else METRIC.replace("plain-scale", workload)
+    m = METRIC if workload == "plain-scale" else METRIC.replace("plain-scale", workload)
+    return m.replace("one replica per GPU", "tasks split over the GPUs") if sharded else m
 UNIT = "EM iters/s"
 
 
@@ -65,6 +68,9 @@ def _args():
     ap.add_argument("--refine-tol", type=float, default=1e-5)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--replicas", action="store_true",
+                    help="with several GPUs, run independent replicas instead of splitting "
+                         "the tasks of one problem over them")
     ap.add_argument("--no-legs", action="store_true",
                     help="skip the precision and batching workload legs of the default run")
     ap.add_argument("--precond", action="store_true",
@@ -151,9 +157,10 @@ class Clocks:
                 "power_w_max": max(pw) if pw else None}
 
 
-def aggregate(ms_local: float, steps: int, world: int, device: str = "cuda"):
-    """Whole-job throughput over ranks: the slowest rank's time, every rank's steps.
-    Returns (value in steps/s, max ms over ranks)."""
+def aggregate(ms_local: float, steps: int, world: int, device: str = "cuda", units=None):
+    """Whole-job throughput over ranks: the slowest rank's time and the units all ranks
+    processed (default: every rank's steps, i.e. independent replicas; one problem split over
+    the ranks passes units = steps).  Returns (value in units/s, max ms over ranks)."""
     ms_max = ms_local
     if world > 1:
         import torch
@@ -161,7 +168,8 @@ def aggregate(ms_local: float, steps: int, world: int, device: str = "cuda"):
         t = torch.tensor([ms_local], dtype=torch.float64, device=device)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms_max = float(t.item())
-    return world * steps / (ms_max / 1e3), ms_max
+    total = world * steps if units is None else units
+    return total / (ms_max / 1e3), ms_max
 
 
 # DRAM bytes (read + write) of one operator application of the tensor-core operator (k_tc<1> +
@@ -422,7 +430,16 @@ def run_ours(a):
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
-    wl = _workload(a.workload, rank, a.tasks)
+    # several GPUs: the tasks of one problem split over them (Sec. 3.3), one all-gather of the
+    # M-step rows per EM iteration; or, with --replicas, an independent problem per GPU
+    sharded = world > 1 and not a.replicas
+    wl = _workload(a.workload, 0 if sharded else rank, a.tasks)
+    wl_full = wl
+    ranges = None
+    if sharded:
+        from paper_2310_00420_gb300 import shard
+        ranges = shard.partition(wl.N, world)
+        wl = wl_full.subset(range(*ranges[rank]))
     fourier = hasattr(wl, "mask")        # Phi_t = Omega_t F, applied by FFT (FP32 only)
     if fourier:
         a.precision = "fp32"
@@ -431,6 +448,8 @@ def run_ours(a):
               seed=wl.seed, precision=a.precision, refine_max=a.refine_max, refine_tol=a.refine_tol,
               schedule=a.schedule, graphs=not a.no_graphs, precond=a.precond,
               learn_pi=a.learn_pi, probe_share=a.probe_share, warm_start=a.warm_start)
+    if sharded:
+        kw.update(task_offset=ranges[rank][0], T_total=wl_full.T)
     variant = dict(precond=a.precond, probe_share=a.probe_share)
     if fourier:
         ctx = cmcs.Context.from_fourier(wl, device=True, **kw)
@@ -438,8 +457,17 @@ def run_ours(a):
         Phi_d = torch.from_numpy(wl.Phi).cuda()
         y_d = torch.from_numpy(wl.y).cuda()
         ctx = cmcs.Context(Phi_d, y_d, wl.N, **kw)
+
+    def driver(c_):
+        """One EM iteration of the problem: the context's own, or the split one."""
+        if not sharded:
+            return lambda: c_.em_iter(1)
+        em = shard.ShardedEM(c_, ranges, rank, device=True)
+        return lambda: em.em_iter(1)
+
+    step = driver(ctx)
     for _ in range(a.warmup):
-        ctx.em_iter(1)
+        step()
     ctx.profile(True)
 
     def barrier():
@@ -453,7 +481,7 @@ def run_ours(a):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(a.steps):
-        ctx.em_iter(1)
+        step()
     e1.record()
     torch.cuda.synchronize()
     barrier()
@@ -462,8 +490,8 @@ def run_ours(a):
     prof = ctx.profile_read()
     summ = ctx.summary()
     ctx.profile(False)
-    value, ms_max = aggregate(ms, a.steps, world)
-    systems = wl.T * wl.C * (wl.K + 1)
+    value, ms_max = aggregate(ms, a.steps, world, units=a.steps if sharded else None)
+    systems = wl_full.T * wl.C * (wl.K + 1) if sharded else wl.T * wl.C * (wl.K + 1)
 
     # operator roofline: algorithmic FLOPs / measured device time of the operator applications
     peaks, src = _peaks()
@@ -520,7 +548,7 @@ def run_ours(a):
     # error vs the FP64 oracle on one sampled (task, cluster) pair, and the CPU baseline
     cpu = None
     err = None
-    if rank == 0 and not a.no_cpu:
+    if rank == 0 and not a.no_cpu and not sharded:
         alpha = ctx.read(cmcs.OUT_ALPHA)
         it = summ["em_iters_done"]
         ctx.set_alpha(alpha, it)
@@ -565,14 +593,15 @@ def run_ours(a):
             else:
                 c2 = cmcs.Context(Phi_h, y_h, wl.N, **kw)
             c2.set_alpha(alpha_h, it)
-            c2.em_iter(1)
+            driver(c2)()
             c2.read(cmcs.OUT_Q, out=outs["q"])
             c2.read(cmcs.OUT_ALPHA, out=outs["alpha"])
             c2.read(cmcs.OUT_RECON, out=outs["recon"])
             c2.close()
         torch.cuda.synchronize()
         barrier()
-        e2e_value, _ = aggregate((time.perf_counter() - t0) * 1e3, a.steps, world)
+        e2e_value, _ = aggregate((time.perf_counter() - t0) * 1e3, a.steps, world,
+                                 units=a.steps if sharded else None)
         e2e = {"value": e2e_value, "unit": UNIT,
                "h2d_bytes_per_step": int(Phi_h.numel() * Phi_h.element_size() +
                                          y_h.numel() * y_h.element_size() + wl.C * wl.D * 4),
@@ -595,7 +624,7 @@ def run_ours(a):
         return out
 
     fp32_form = None
-    if a.precision != "fp32" and not a.no_fp32_form:
+    if a.precision != "fp32" and not a.no_fp32_form and world == 1:
         # the FP32 SIMT form is ~7x slower: a shorter sample (stated in the line)
         fp32_form = timed_leg(warmup=min(a.warmup, 1), steps=min(a.steps, 3), precision="fp32")
         peak32 = _fp32_sgemm_peak()
@@ -616,15 +645,21 @@ def run_ours(a):
         legs["precision_workload"] = precision_leg(a, peaks)
         legs["batching_workload"] = batching_leg(a)
     if rank == 0:
-        line = {"metric": _metric(a.workload), "value": value, "unit": UNIT, "n_gpus": world,
+        line = {"metric": _metric(a.workload, sharded), "value": value, "unit": UNIT,
+                "n_gpus": world,
                 "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms_max / a.steps,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "higher_is_better": True, "scaling": "strong" if sharded else "weak",
+                "vs_baseline": None,
                 "dtype": {"fp32": "f32", "bf16": "bf16+f32", "bf16x3": "bf16x2+f32"}[a.precision],
                 "data": "synthetic",
-                "config": {"workload": f"{wl.name} T={wl.T} C={wl.C} D={wl.D} N={int(wl.N[0])} "
-                                       f"K={wl.K} tol={wl.cg_tol} max_iter={wl.cg_max_iter}",
+                "config": {"workload": f"{wl_full.name} T={wl_full.T} C={wl.C} D={wl.D} "
+                                       f"N={int(wl.N[0])} K={wl.K} tol={wl.cg_tol} "
+                                       f"max_iter={wl.cg_max_iter}",
                            "precision": a.precision, "refine_max": a.refine_max,
-                           "refine_tol": a.refine_tol, "parallelism": f"{world} replicas",
+                           "refine_tol": a.refine_tol,
+                           "parallelism": (f"tasks split over {world} GPUs {ranges}, one "
+                                           f"all-gather of the M-step rows per EM iteration"
+                                           if sharded else f"{world} replicas"),
                            "variants": [v for v, on in (("precond", a.precond),
                                                         ("learn_pi", a.learn_pi),
                                                         ("probe_share", a.probe_share),

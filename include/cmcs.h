@@ -100,6 +100,13 @@ typedef struct {
                              probe systems keep x_1 = 0, which the Lanczos estimate needs.
                              cmcs_set_alpha keeps the previous means as the start (any start
                              is valid); cmcs_set_data and a failed E-step drop them          */
+  /* Tasks split across contexts, one per GPU (Sec. 3.3: the E-step of task t needs only Phi_t,
+     y_t and every alpha_c; the M-step of Eq. 5 sums over tasks).  0 and 0 for a whole problem. */
+  int task_offset;        /* global index of this context's first task, >= 0: the probes of its
+                             task t are those of task task_offset + t of the whole problem     */
+  int T_total;            /* tasks of the whole problem (0: T); task_offset + T <= T_total.
+                             With T_total > T, cmcs_em_iter is refused: the M-step goes through
+                             cmcs_mstep_terms and cmcs_mstep_apply                            */
 } cmcs_config;
 
 /* Summary of the most recent E-step and the EM state. */
@@ -187,6 +194,25 @@ cmcs_status cmcs_estep(cmcs_ctx *ctx);
  * increment of the iteration counter.  After the call, mu/q/assign are those of the last
  * E-step and alpha is the result of the last M-step. */
 cmcs_status cmcs_em_iter(cmcs_ctx *ctx, int n);
+
+/* Per-task terms of the M-step (Eq. 5) and of L(theta) (Sec. 2) from the last E-step, for EM
+ * with the tasks split across contexts (Sec. 3.3).  terms: double [T][W] with W = C (D + 1) + 1,
+ * host or device per on_device; row t (this context's task t) holds
+ *   [c (D + 1)]         q_tc                                   (Eq. 3)
+ *   [c (D + 1) + 1 + d] q_tc max(mu_tcd^2 + s_tcd, 0)           (Eq. 5 with s for diag Sigma)
+ *   [C (D + 1)]         log sum_c pi_c p(y_t | alpha_c)          (the task's term of L(theta))
+ * The rows of every context, stacked in global task order, are what cmcs_mstep_apply takes. */
+cmcs_status cmcs_mstep_terms(cmcs_ctx *ctx, double *terms, int on_device);
+
+/* The M-step from the terms of all T_total tasks of the problem (double [T_total][W] in global
+ * task order, host or device per on_device): alpha_cd = sum_t q_tc / sum_t q_tc max(mu^2 + s, 0)
+ * with the sums taken over t in order (then the clamps of cmcs_config; a cluster with
+ * sum_t q_tc < 1e-300 keeps its alpha), pi_c = max((1/T_total) sum_t q_tc, 1e-300) renormalised
+ * when learned, L(theta) = (1/T_total) sum_t of the last column; then the iteration counter is
+ * incremented.  Because the sums run over the same rows in the same order, contexts holding
+ * any split of the tasks reach the same alpha bit for bit as one context holding them all
+ * (cmcs_em_iter goes through the same two steps). */
+cmcs_status cmcs_mstep_apply(cmcs_ctx *ctx, const double *terms, int on_device);
 
 /* Replace Phi and y (same shapes as at create; host or device per on_device) and recompute
  * b0 = beta Phi^T y.  alpha, the iteration counter and the settings are kept; outputs of earlier

@@ -27,7 +27,8 @@ PRECISIONS = {"fp32": FP32, "bf16": BF16_REFINE, "bf16_refine": BF16_REFINE, "bf
 EXPORTS = ("cmcs_create", "cmcs_create_dft", "cmcs_set_alpha", "cmcs_estep", "cmcs_em_iter", "cmcs_read",
            "cmcs_result", "cmcs_apply", "cmcs_probes", "cmcs_lanczos_quadrature",
            "cmcs_profile", "cmcs_profile_read", "cmcs_apply_noalloc", "cmcs_set_data",
-           "cmcs_adjoint", "cmcs_test_stall", "cmcs_last_error", "cmcs_destroy")
+           "cmcs_adjoint", "cmcs_test_stall", "cmcs_mstep_terms", "cmcs_mstep_apply",
+           "cmcs_last_error", "cmcs_destroy")
 
 
 class Config(ctypes.Structure):
@@ -39,7 +40,8 @@ class Config(ctypes.Structure):
                 ("alpha_min", ctypes.c_double), ("alpha_max", ctypes.c_double),
                 ("schedule", ctypes.c_int), ("graphs", ctypes.c_int), ("autotune", ctypes.c_int),
                 ("learn_pi", ctypes.c_int), ("probe_share", ctypes.c_int),
-                ("precond", ctypes.c_int), ("warm_start", ctypes.c_int)]
+                ("precond", ctypes.c_int), ("warm_start", ctypes.c_int),
+                ("task_offset", ctypes.c_int), ("T_total", ctypes.c_int)]
 
 
 class Summary(ctypes.Structure):
@@ -92,6 +94,8 @@ def lib():
     L.cmcs_set_data.argtypes = [vp, vp, vp, i]
     L.cmcs_adjoint.argtypes = [vp, vp, vp, vp, vp, i]
     L.cmcs_test_stall.argtypes = [vp, i]
+    L.cmcs_mstep_terms.argtypes = [vp, vp, i]
+    L.cmcs_mstep_apply.argtypes = [vp, vp, i]
     L.cmcs_last_error.argtypes = [vp]
     L.cmcs_last_error.restype = ctypes.c_char_p
     L.cmcs_destroy.argtypes = [vp]
@@ -161,14 +165,18 @@ class Context:
                  refine_tol: float = 1e-6, alpha_min: float = 1e-10, alpha_max: float = 1e10,
                  schedule: str = "batched", graphs: bool = True, autotune: bool = False,
                  learn_pi: bool = False, probe_share: bool = False, precond: bool = False,
-                 warm_start: bool = False, mask=None, stream=None):
+                 warm_start: bool = False, task_offset: int = 0, T_total: int = 0, mask=None,
+                 stream=None):
         """Dense Phi [sum N_t][D] with y [sum N_t]; or, with Phi None and mask given, the
         Fourier operator of cmcs_create_dft: mask uint8 [T][D], y float32 [sum N_t][2].
         learn_pi, probe_share, precond and warm_start switch on the method variants of
-        cmcs_config."""
+        cmcs_config; task_offset and T_total place the context's tasks in a problem whose tasks
+        are split across contexts (see shard.py)."""
         N = np.ascontiguousarray(np.asarray(N, dtype=np.int64))
         D = int(mask.shape[1]) if mask is not None else int(Phi.shape[1])
         self.T, self.C, self.D, self.K = int(len(N)), int(C), D, int(K)
+        self.task_offset = int(task_offset)
+        self.T_total = int(T_total) if T_total else self.T
         self.U = int(cg_max_iter)
         pi = np.full(C, 1.0 / C) if pi is None else np.ascontiguousarray(np.asarray(pi, np.float64))
         self._N, self._pi = N, pi                     # keep alive during create
@@ -180,7 +188,7 @@ class Context:
                      float(refine_tol), float(alpha_min), float(alpha_max),
                      {"batched": 0, "per_task": 1}[schedule], 1 if graphs else 0,
                      1 if autotune else 0, 1 if learn_pi else 0, 1 if probe_share else 0,
-                     1 if precond else 0, 1 if warm_start else 0)
+                     1 if precond else 0, 1 if warm_start else 0, int(task_offset), int(T_total))
         self.cfg = cfg
         self.fourier = mask is not None
         p_phi, dev1 = _ptr(mask if self.fourier else Phi)
@@ -294,6 +302,37 @@ class Context:
         _check(lib().cmcs_adjoint(self.h, pg, _ptr(dy)[0], _ptr(da)[0],
                                   _ptr(dP)[0] if dP is not None else None, dev), self.h)
         return dy, da, dP
+
+    @property
+    def mterm_width(self) -> int:
+        """Doubles per task row of the M-step terms, C (D + 1) + 1."""
+        return self.C * (self.D + 1) + 1
+
+    def mstep_terms(self, out=None, device: bool = False):
+        """This context's rows of the M-step terms [T][C (D + 1) + 1] (cmcs_mstep_terms)."""
+        shape = (self.T, self.mterm_width)
+        if out is None:
+            if device:
+                import torch
+                out = torch.empty(shape, dtype=torch.float64, device="cuda")
+            else:
+                out = np.empty(shape, dtype=np.float64)
+        p, dev = _ptr(out)
+        _check(lib().cmcs_mstep_terms(self.h, p, dev), self.h)
+        return out
+
+    def mstep_apply(self, terms):
+        """The M-step from every task's terms [T_total][C (D + 1) + 1] in global task order
+        (cmcs_mstep_apply)."""
+        if _is_torch(terms):
+            if tuple(terms.shape) != (self.T_total, self.mterm_width) or not terms.is_contiguous():
+                raise ValueError("terms must be a contiguous [T_total][C (D + 1) + 1] tensor")
+        else:
+            terms = np.ascontiguousarray(terms, dtype=np.float64)
+            if terms.shape != (self.T_total, self.mterm_width):
+                raise ValueError("terms must be [T_total][C (D + 1) + 1]")
+        p, dev = _ptr(terms)
+        _check(lib().cmcs_mstep_apply(self.h, p, dev), self.h)
 
     def test_stall(self, enable: bool):
         _check(lib().cmcs_test_stall(self.h, 1 if enable else 0), self.h)

@@ -52,7 +52,7 @@ void free_ctx(Ctx* c) {
                   c->sumlogalpha, c->logpi, c->tconst, c->x, c->r, c->d, c->ad, c->xacc,
                   c->w, c->wlo, c->part, c->rr, c->bb, c->steps, c->steps0, c->active,
                   c->ractive, c->sweeps, c->rrel, c->rres, c->task_active, c->counters, c->gam, c->xi,
-                  c->psteps, c->sest, c->quad, c->logdet, c->ell, c->q, c->assign, c->stats,
+                  c->psteps, c->sest, c->quad, c->logdet, c->ell, c->q, c->assign, c->stats, c->lltask, c->mterms,
                   c->dN, c->opcount, c->dorow, c->stall_flag, c->adj_g, c->adj_x, c->adj_wl, c->adj_wm,
                   c->adj_wl_lo, c->adj_wm_lo, c->adj_dy, c->adj_da, c->pi, c->colnorm, c->pminv,
                   c->pw, c->sumlogm};
@@ -376,6 +376,10 @@ cmcs_status validate(const cmcs_config* cfg) {
   if (cfg->probe_share != 0 && cfg->probe_share != 1) return CMCS_ERR_INVALID_ARG;
   if (cfg->precond != 0 && cfg->precond != 1) return CMCS_ERR_INVALID_ARG;
   if (cfg->warm_start != 0 && cfg->warm_start != 1) return CMCS_ERR_INVALID_ARG;
+  if (cfg->task_offset < 0 || cfg->T_total < 0) return CMCS_ERR_INVALID_ARG;
+  const int64_t ttot = cfg->T_total == 0 ? cfg->T : cfg->T_total;
+  if ((int64_t)cfg->task_offset + cfg->T > ttot) return CMCS_ERR_INVALID_ARG;
+  if (ttot * cfg->C >= ((int64_t)1 << 31)) return CMCS_ERR_INVALID_ARG;   // probe counter word
   return CMCS_OK;
 }
 
@@ -434,6 +438,9 @@ cmcs_status create_ctx(const cmcs_config* cfg, const float* Phi, const float* y,
   c->precond = cfg->precond;
   c->warm_start = cfg->warm_start;
   c->seed = cfg->seed;
+  c->toff = cfg->task_offset;
+  c->T_total = cfg->T_total == 0 ? cfg->T : cfg->T_total;
+  c->mterm_w = cfg->C * (cfg->D + 1) + 1;
   c->op = mask ? 1 : 0;
   c->em_iter = 0;
   c->stream = static_cast<cudaStream_t>(stream);
@@ -549,6 +556,8 @@ cmcs_status create_ctx(const cmcs_config* cfg, const float* Phi, const float* y,
   CKC(dalloc(&c->q, (size_t)(T * C)));
   CKC(dalloc(&c->assign, (size_t)T));
   CKC(dalloc(&c->stats, 4));
+  CKC(dalloc(&c->lltask, (size_t)T));
+  CKC(dalloc(&c->mterms, (size_t)c->T_total * (size_t)c->mterm_w));
   CKC(dalloc(&c->opcount, (size_t)T));
   CKC(dalloc(&c->dorow, (size_t)(T + 1)));
   CKC(dalloc(&c->stall_flag, 1));
@@ -861,14 +870,41 @@ cmcs_status cmcs_estep(cmcs_ctx* h) {
 cmcs_status cmcs_em_iter(cmcs_ctx* h, int n) {
   if (!h || n < 0) return CMCS_ERR_INVALID_ARG;
   Ctx* c = &h->c;
+  if (c->T_total != c->T) {
+    set_err(c, "the context holds tasks %d..%d of %d: its M-step needs every task's terms "
+               "(cmcs_mstep_terms, then cmcs_mstep_apply with all rows)", c->toff,
+            c->toff + c->T - 1, c->T_total);
+    return CMCS_ERR_INVALID_ARG;
+  }
   for (int i = 0; i < n; ++i) {
     cmcs_status s = estep(c);
     if (s != CMCS_OK) return s;
-    CK(launch_mstep(c));
+    CK(launch_mstep_terms(c));
+    CK(launch_mstep_apply(c));
     CK(launch_sumlogalpha(c));
-    if (c->learn_pi) CK(launch_pi_update(c));
     c->em_iter++;
   }
+  return sync_check(c);
+}
+
+cmcs_status cmcs_mstep_terms(cmcs_ctx* h, double* terms, int on_device) {
+  if (!h || !terms || (on_device != 0 && on_device != 1)) return CMCS_ERR_INVALID_ARG;
+  Ctx* c = &h->c;
+  CK(launch_mstep_terms(c));
+  const size_t w = (size_t)c->mterm_w;
+  CK(cudaMemcpyAsync(terms, c->mterms + (size_t)c->toff * w, sizeof(double) * w * c->T,
+                     kind_out(on_device), c->stream));
+  return sync_check(c);
+}
+
+cmcs_status cmcs_mstep_apply(cmcs_ctx* h, const double* terms, int on_device) {
+  if (!h || !terms || (on_device != 0 && on_device != 1)) return CMCS_ERR_INVALID_ARG;
+  Ctx* c = &h->c;
+  CK(cudaMemcpyAsync(c->mterms, terms, sizeof(double) * (size_t)c->mterm_w * c->T_total,
+                     kind_in(on_device), c->stream));
+  CK(launch_mstep_apply(c));
+  CK(launch_sumlogalpha(c));
+  c->em_iter++;
   return sync_check(c);
 }
 

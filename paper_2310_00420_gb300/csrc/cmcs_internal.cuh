@@ -79,6 +79,9 @@ struct Ctx {
   int have_prev;     // xacc holds the means of an earlier E-step of this problem
   uint64_t seed;
   int64_t em_iter;
+  int toff;          // global index of this context's first task (keys its probes)
+  int T_total;       // tasks of the whole problem (T unless the tasks are split over contexts)
+  int mterm_w;       // doubles per row of the M-step terms, C (D + 1) + 1
   cudaStream_t stream;
   int own_stream;      // the context created its stream (caller passed NULL)
   cudaStream_t side;   // runs the Lanczos eigen step while refinement proceeds on stream
@@ -146,6 +149,8 @@ struct Ctx {
   double *logdet, *ell, *q;  // [T][C]
   int* assign;         // [T]
   double* stats;       // [4]: 0 loglik, 1 min margin
+  double* lltask;      // [T] log sum_c pi_c p(y_t | alpha_c) of the last E-step
+  double* mterms;      // [T_total][mterm_w] M-step terms of every task of the problem
   int64_t op_applies;
 
   // profiling (cmcs_profile): events around operator applications, per-task application
@@ -194,8 +199,6 @@ cudaError_t launch_sest(Ctx* c);
 cudaError_t launch_precond(Ctx* c);
 // column norms of Phi_t for the preconditioner (dense Phi; Fourier contexts fill N_t / D)
 cudaError_t launch_colnorm(Ctx* c);
-// learned priors from the responsibilities of the last E-step (pi and logpi)
-cudaError_t launch_pi_update(Ctx* c);
 // operator (kernels_op.cu): AD = A D for all active tasks
 cudaError_t launch_operator(Ctx* c, const float* V, float* Z, int with_dots);
 // accurate residual: r = B - A xacc, B = b0 (k = 0) or the probe (k >= 1) when Bext == null
@@ -238,7 +241,10 @@ cudaError_t launch_quadrature(const float* gam, const float* xi, const int* step
                               int ld, double* out, int* status, cudaStream_t st);
 cudaError_t launch_quadrature_ctx(Ctx* c, cudaStream_t st);
 cudaError_t launch_ell_softmax(Ctx* c, const float* rmu /* residuals for the correction, or null */);
-cudaError_t launch_mstep(Ctx* c);
+// M-step: this context's per-task terms into its rows of mterms, then alpha (and pi, L) from
+// all T_total rows summed in task order
+cudaError_t launch_mstep_terms(Ctx* c);
+cudaError_t launch_mstep_apply(Ctx* c);
 
 // tensor-core operator hooks (kernels_tc.cu)
 int tc_create(Ctx* c);      // returns 0 on success

@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(256)
 k_cg_init(int mode, float* __restrict__ x, float* __restrict__ r, float* __restrict__ d,
           const float* __restrict__ b0hi, float* rr, float* bb, int* steps, int* active,
           int* ractive, int* sweeps, float* rrel, int* task_active, int* counters, int R,
-          int K, int C, int Dp, int D, uint64_t seed, int64_t em_iter, int refine,
+          int K, int C, int Dp, int D, uint64_t seed, int64_t em_iter, int toff, int refine,
           __nv_bfloat16* dhi, __nv_bfloat16* dlo, const float* __restrict__ pminv,
           const float* __restrict__ pw, int pshare, int warm, float tol2) {
   __shared__ float sh[33];
@@ -109,7 +109,7 @@ k_cg_init(int mode, float* __restrict__ x, float* __restrict__ r, float* __restr
       } else if (k == 0) {
         b = *reinterpret_cast<const float4*>(b0hi + (int64_t)t * Dp + i);
       } else {
-        b = probe4(seed, em_iter, t, probe_cluster(c, pshare), C, k - 1, i, D);
+        b = probe4(seed, em_iter, t + toff, probe_cluster(c, pshare), C, k - 1, i, D);
         if (pw != nullptr) {
           const float4 w = *reinterpret_cast<const float4*>(pw + tcoff + i);
           b = make_float4(b.x * w.x, b.y * w.y, b.z * w.z, b.w * w.w);
@@ -409,7 +409,8 @@ __global__ void __launch_bounds__(128)
 // With the Jacobi preconditioner the probe systems solve A x_k = sqrt(m) p_k, and
 // s = (1/K) sum_k p_k x_k / sqrt(m) (pw = sqrt(m); null: plain probes).
 k_sest(const float* __restrict__ xacc, float* __restrict__ sest, int R, int K, int C, int Dp,
-       int D, uint64_t seed, int64_t em_iter, const float* __restrict__ pw, int pshare) {
+       int D, uint64_t seed, int64_t em_iter, int toff, const float* __restrict__ pw,
+       int pshare) {
   const int tc = blockIdx.y;
   const int t = tc / C, c = tc % C;
   const int i = (blockIdx.x * 128 + threadIdx.x) * 4;
@@ -417,7 +418,7 @@ k_sest(const float* __restrict__ xacc, float* __restrict__ sest, int R, int K, i
   float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
   const int64_t base = ((int64_t)t * R + (int64_t)c * (K + 1)) * Dp;
   for (int k = 1; k <= K; ++k) {
-    const float4 p = probe4(seed, em_iter, t, probe_cluster(c, pshare), C, k - 1, i, D);
+    const float4 p = probe4(seed, em_iter, t + toff, probe_cluster(c, pshare), C, k - 1, i, D);
     const float4 xv = *reinterpret_cast<const float4*>(xacc + base + (int64_t)k * Dp + i);
     acc.x = fmaf(p.x, xv.x, acc.x);
     acc.y = fmaf(p.y, xv.y, acc.y);
@@ -529,14 +530,15 @@ k_tconst(const float* y, const int64_t* drow, const int64_t* Nt, double* out, do
 
 // ---- probes as +-1 floats [T][C][K][D] ----------------------------------------------------
 __global__ void k_probes_out(float* dst, int T, int C, int K, int D, uint64_t seed,
-                             int64_t em_iter, int pshare) {
+                             int64_t em_iter, int toff, int pshare) {
   const int64_t tck = blockIdx.y;
   const int k = (int)(tck % K);
   const int c = (int)((tck / K) % C);
   const int t = (int)(tck / ((int64_t)K * C));
   const int d = blockIdx.x * 256 + threadIdx.x;
   if (d >= D) return;
-  const uint32_t bits = probe_bits32(seed, em_iter, t, probe_cluster(c, pshare), C, k, d & ~31);
+  const uint32_t bits = probe_bits32(seed, em_iter, t + toff, probe_cluster(c, pshare), C, k,
+                                     d & ~31);
   dst[tck * D + d] = ((bits >> (d & 31)) & 1u) ? -1.f : 1.f;
 }
 
@@ -546,7 +548,8 @@ cudaError_t launch_cg_init(Ctx* c, int mode, int warm) {
   k_cg_init<<<c->S, 256, 0, c->stream>>>(mode, c->x, c->r, c->d, c->b0hi, c->rr, c->bb,
                                          c->steps, c->active, c->ractive, c->sweeps, c->rrel,
                                          c->task_active, c->counters, c->R, c->K, c->C, c->Dp,
-                                         c->D, c->seed, c->em_iter, c->refine_max > 0 ? 1 : 0,
+                                         c->D, c->seed, c->em_iter, c->toff,
+                                         c->refine_max > 0 ? 1 : 0,
                                          static_cast<__nv_bfloat16*>(c->dhi),
                                          static_cast<__nv_bfloat16*>(c->dlo),
                                          c->precond ? c->pminv : nullptr,
@@ -607,7 +610,8 @@ cudaError_t launch_sest(Ctx* c) {
   c->launches += 1;
   dim3 grid((c->Dp / 4 + 127) / 128, c->T * c->C);
   k_sest<<<grid, 128, 0, c->stream>>>(c->xacc, c->sest, c->R, c->K, c->C, c->Dp, c->D, c->seed,
-                                      c->em_iter, c->precond ? c->pw : nullptr, c->pshare);
+                                      c->em_iter, c->toff, c->precond ? c->pw : nullptr,
+                                      c->pshare);
   return cudaGetLastError();
 }
 
@@ -668,7 +672,7 @@ cudaError_t launch_tconst_dev(Ctx* c, const int64_t* dN) {
 cudaError_t launch_probes_out(const Ctx* c, int64_t em_iter, float* dst) {
   dim3 grid((c->D + 255) / 256, (unsigned)((int64_t)c->T * c->C * c->K));
   k_probes_out<<<grid, 256, 0, c->stream>>>(dst, c->T, c->C, c->K, c->D, c->seed, em_iter,
-                                            c->pshare);
+                                            c->toff, c->pshare);
   return cudaGetLastError();
 }
 

@@ -410,7 +410,7 @@ k_dft_residual(const float* __restrict__ X, const float* __restrict__ Bext,
                float* __restrict__ Rout, const int* __restrict__ ractive,
                const float* __restrict__ mask_br, const double2* __restrict__ tw,
                const float* __restrict__ alpha, int R, int K, int C, int Dp, int D, int L, int Rc,
-               int jstride, int npair, double beta, uint64_t seed, int64_t em_iter,
+               int jstride, int npair, double beta, uint64_t seed, int64_t em_iter, int toff,
                const float* __restrict__ pw, int pshare) {
   extern __shared__ double2 Xd[];
   const int t = blockIdx.x / npair, p = blockIdx.x - t * npair;
@@ -455,8 +455,8 @@ k_dft_residual(const float* __restrict__ X, const float* __restrict__ Bext,
         } else if (k == 0) {
           b = b0;
         } else {
-          const uint32_t bits = probe_bits32(seed, em_iter, t, probe_cluster(c, pshare), C, k - 1,
-                                             i & ~31);
+          const uint32_t bits = probe_bits32(seed, em_iter, t + toff, probe_cluster(c, pshare),
+                                             C, k - 1, i & ~31);
           b = ((bits >> (i & 31)) & 1u) ? -1.0 : 1.0;
           if (pw != nullptr) b *= (double)pw[((int64_t)t * C + c) * Dp + i];   // sqrt(m) p
         }
@@ -612,7 +612,8 @@ cudaError_t launch_dft_residual(Ctx* c, const float* X, const float* Bext, float
   k_dft_residual<<<c->T * npair, kDftThreads, sizeof(double2) * (c->D + c->D / 32), c->stream>>>(
       X, Bext, c->b0hi, c->b0lo, Rout, (Bext || all_systems) ? nullptr : c->ractive, c->dft_mask,
       static_cast<const double2*>(c->dft_tw64), c->alpha, c->R, c->K, c->C, c->Dp, c->D, c->dft_L,
-      Rc, js, npair, c->beta, c->seed, c->em_iter, c->precond ? c->pw : nullptr, c->pshare);
+      Rc, js, npair, c->beta, c->seed, c->em_iter, c->toff, c->precond ? c->pw : nullptr,
+      c->pshare);
   return cudaGetLastError();
 }
 

@@ -331,6 +331,7 @@ struct FsEpi {
   int pshare;
   uint64_t seed;
   int64_t em_iter;
+  int toff;               // global index of the context's first task (probe counters)
   double beta;
   // kFsB0: b0 = beta Re(F^H y) as an FP32 pair
   float* hi;
@@ -439,7 +440,7 @@ k_fs_cols_inv(const CT* __restrict__ Y, const CT* __restrict__ tab1, FsPlan pl, 
         } else if (k == 0) {
           b = (double)ep.b0hi[(int64_t)q.t * Dp + n] + (double)ep.b0lo[(int64_t)q.t * Dp + n];
         } else {
-          const uint32_t bits = probe_bits32(ep.seed, ep.em_iter, q.t, probe_cluster(c, ep.pshare),
+          const uint32_t bits = probe_bits32(ep.seed, ep.em_iter, q.t + ep.toff, probe_cluster(c, ep.pshare),
                                              pp.C, k - 1, (int)(n & ~(int64_t)31));
           b = ((bits >> (n & 31)) & 1u) ? -1.0 : 1.0;
           if (ep.pw != nullptr) b *= (double)ep.pw[((int64_t)q.t * pp.C + c) * Dp + n];
@@ -724,6 +725,7 @@ cudaError_t fs_residual(Ctx* c, const float* X, const float* Bext, float* Rout, 
   ep.pshare = c->pshare;
   ep.seed = c->seed;
   ep.em_iter = c->em_iter;
+  ep.toff = c->toff;
   ep.beta = c->beta;
   const FsPairs pp = means_only ? pairs_of(c, c->C, c->K + 1) : pairs_of(c, c->R, 1);
   const int* flags = (Bext || all_systems) ? nullptr : c->ractive;

@@ -172,8 +172,8 @@ k_ell(const float* __restrict__ xacc, const float* __restrict__ b0hi,
 // ---- q_t = softmax_c(ell_tc / 2 + log pi_c), L(theta), a_t = argmax_c q_tc --------------
 __global__ void __launch_bounds__(256)
 k_softmax(const double* __restrict__ ell, const double* __restrict__ logpi,
-          const double* __restrict__ tconst, double* q, int* assign, double* stats, int* status,
-          int T, int C) {
+          const double* __restrict__ tconst, double* q, int* assign, double* stats,
+          double* lltask, int* status, int T, int C) {
   __shared__ double sh[33];
   __shared__ double smin[256];
   double ll = 0.0, mn = 1.0;
@@ -199,7 +199,9 @@ k_softmax(const double* __restrict__ ell, const double* __restrict__ logpi,
     assign[t] = arg;
     const double margin = q[(int64_t)t * C + arg] - best2;
     mn = fmin(mn, margin);
-    ll += mx + log(se) - tconst[t];
+    const double lt = mx + log(se) - tconst[t];   // log sum_c pi_c p(y_t | alpha_c)
+    lltask[t] = lt;
+    ll += lt;
   }
   const double tot = block_sum256(ll, sh);
   smin[threadIdx.x] = mn;
@@ -220,15 +222,53 @@ cudaError_t launch_ell_softmax(Ctx* c, const float* rmu) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_softmax<<<1, 256, 0, c->stream>>>(c->ell, c->logpi, c->tconst, c->q, c->assign, c->stats,
-                                      &c->counters[2], c->T, c->C);
+                                      c->lltask, &c->counters[2], c->T, c->C);
   return cudaGetLastError();
 }
 
-// ---- M-step, Eq. 5 with s for diag Sigma: alpha_cd = sum_t q_tc / sum_t q_tc (mu^2 + s) ---
+// ---- M-step, Eq. 5 with s for diag Sigma, split into per-task terms and their ordered sum ---
+// Row t of the term matrix (W = C (D + 1) + 1 doubles): q_tc at c (D + 1), q_tc max(mu_tcd^2 +
+// s_tcd, 0) at c (D + 1) + 1 + d, and log sum_c pi_c p(y_t | alpha_c) at C (D + 1).  The
+// M-step sums the rows of all tasks of the problem in task order, so contexts that each hold a
+// range of tasks (one per GPU) reach the same alpha bit for bit as one context holding them all.
 __global__ void __launch_bounds__(256)
-k_mstep(const float* __restrict__ xacc, const float* __restrict__ sest,
-        const double* __restrict__ q, float* alpha, int T, int C, int R, int K, int Dp, int D,
-        double amin, double amax) {
+k_mstep_terms(const float* __restrict__ xacc, const float* __restrict__ sest,
+              const double* __restrict__ q, const double* __restrict__ lltask,
+              double* __restrict__ terms, int C, int R, int K, int Dp, int D) {
+  const int t = blockIdx.y / C, c = blockIdx.y % C;
+  const int64_t W = (int64_t)C * (D + 1) + 1;
+  double* row = terms + (int64_t)t * W;
+  const double qt = q[(int64_t)t * C + c];
+  const float* mu = xacc + ((int64_t)t * R + (int64_t)c * (K + 1)) * Dp;
+  const float* sv = sest + ((int64_t)t * C + c) * Dp;
+  for (int d = blockIdx.x * 256 + threadIdx.x; d < D; d += gridDim.x * 256) {
+    const double m = (double)mu[d];
+    const double f = fmax(__fma_rn(m, m, (double)sv[d]), 0.0);
+    row[(int64_t)c * (D + 1) + 1 + d] = __dmul_rn(qt, f);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    row[(int64_t)c * (D + 1)] = qt;
+    if (c == 0) row[(int64_t)C * (D + 1)] = lltask[t];
+  }
+}
+
+cudaError_t launch_mstep_terms(Ctx* c) {
+  c->launches += 1;
+  int bx = (c->D + 255) / 256;
+  if (bx > 64) bx = 64;
+  dim3 grid(bx, c->T * c->C);
+  k_mstep_terms<<<grid, 256, 0, c->stream>>>(c->xacc, c->sest, c->q, c->lltask,
+                                             c->mterms + (int64_t)c->toff * c->mterm_w, c->C, c->R,
+                                             c->K, c->Dp, c->D);
+  return cudaGetLastError();
+}
+
+// alpha_cd = sum_t q_tc / sum_t q_tc max(mu^2 + s, 0) over the T_total rows in task order
+// (one thread per (c, d): reads of one row are coalesced across d), clamped; an empty cluster
+// (sum_t q_tc < 1e-300) keeps its alpha
+__global__ void __launch_bounds__(256)
+k_mstep_apply(const double* __restrict__ terms, float* alpha, int Ttot, int C, int Dp, int D,
+              double amin, double amax) {
   const int c = blockIdx.y;
   const int d = blockIdx.x * 256 + threadIdx.x;
   if (d >= Dp) return;
@@ -236,55 +276,53 @@ k_mstep(const float* __restrict__ xacc, const float* __restrict__ sest,
     alpha[(int64_t)c * Dp + d] = 1.0f;
     return;
   }
+  const int64_t W = (int64_t)C * (D + 1) + 1;
+  const double* col = terms + (int64_t)c * (D + 1);
   double num = 0.0, den = 0.0;
-  for (int t = 0; t < T; ++t) {
-    const double qt = q[(int64_t)t * C + c];
-    const double mu = (double)xacc[((int64_t)t * R + (int64_t)c * (K + 1)) * Dp + d];
-    const double s = (double)sest[((int64_t)t * C + c) * Dp + d];
-    num += qt;
-    den += qt * fmax(mu * mu + s, 0.0);
+  for (int t = 0; t < Ttot; ++t) {
+    num = __dadd_rn(num, col[(int64_t)t * W]);
+    den = __dadd_rn(den, col[(int64_t)t * W + 1 + d]);
   }
-  if (num < 1e-300) return;                        // empty cluster keeps its alpha
+  if (num < 1e-300) return;
   double a = (den <= num / amax) ? amax : num / den;
   a = fmin(fmax(a, amin), amax);
   alpha[(int64_t)c * Dp + d] = (float)a;
 }
 
-cudaError_t launch_mstep(Ctx* c) {
-  c->launches += 1;
-  dim3 grid((c->Dp + 255) / 256, c->C);
-  k_mstep<<<grid, 256, 0, c->stream>>>(c->xacc, c->sest, c->q, c->alpha, c->T, c->C, c->R, c->K,
-                                       c->Dp, c->D, c->alpha_min, c->alpha_max);
-  return cudaGetLastError();
-}
-
-// ---- learned priors: pi_c = max((1/T) sum_t q_tc, 1e-300), renormalised -----------------
-// (the maximiser of sum_tc q_tc log pi_c over the simplex; the floor keeps log pi finite)
-__global__ void __launch_bounds__(256)
-k_pi_update(const double* __restrict__ q, double* pi, double* logpi, int T, int C) {
-  __shared__ double tot;
-  for (int c = threadIdx.x; c < C; c += 256) {
-    double s = 0.0;
-    for (int t = 0; t < T; ++t) s += q[(int64_t)t * C + c];
-    pi[c] = fmax(s / (double)T, 1e-300);
+// L(theta) = (1/T_total) sum_t ll_t in task order, and (learned priors) pi_c = max((1/T_total)
+// sum_t q_tc, 1e-300) renormalised: the maximiser of sum_tc q_tc log pi_c over the simplex,
+// the floor keeps log pi finite
+__global__ void k_mstep_scalars(const double* __restrict__ terms, double* stats, double* pi,
+                                double* logpi, int Ttot, int C, int D, int learn_pi) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int64_t W = (int64_t)C * (D + 1) + 1;
+  double ll = 0.0;
+  for (int t = 0; t < Ttot; ++t) ll = __dadd_rn(ll, terms[(int64_t)t * W + (int64_t)C * (D + 1)]);
+  stats[0] = ll / (double)Ttot;
+  if (!learn_pi) return;
+  double tot = 0.0;
+  for (int c = 0; c < C; ++c) {
+    double sq = 0.0;
+    for (int t = 0; t < Ttot; ++t) sq = __dadd_rn(sq, terms[(int64_t)t * W + (int64_t)c * (D + 1)]);
+    pi[c] = fmax(sq / (double)Ttot, 1e-300);
+    tot += pi[c];
   }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double a = 0.0;
-    for (int c = 0; c < C; ++c) a += pi[c];
-    tot = a;
-  }
-  __syncthreads();
-  for (int c = threadIdx.x; c < C; c += 256) {
+  for (int c = 0; c < C; ++c) {
     const double v = pi[c] / tot;
     pi[c] = v;
     logpi[c] = log(v);
   }
 }
 
-cudaError_t launch_pi_update(Ctx* c) {
-  c->launches += 1;
-  k_pi_update<<<1, 256, 0, c->stream>>>(c->q, c->pi, c->logpi, c->T, c->C);
+cudaError_t launch_mstep_apply(Ctx* c) {
+  c->launches += 2;
+  dim3 grid((c->Dp + 255) / 256, c->C);
+  k_mstep_apply<<<grid, 256, 0, c->stream>>>(c->mterms, c->alpha, c->T_total, c->C, c->Dp, c->D,
+                                             c->alpha_min, c->alpha_max);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_mstep_scalars<<<1, 32, 0, c->stream>>>(c->mterms, c->stats, c->pi, c->logpi, c->T_total, c->C,
+                                           c->D, c->learn_pi);
   return cudaGetLastError();
 }
 

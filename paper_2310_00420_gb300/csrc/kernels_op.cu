@@ -215,6 +215,7 @@ struct P2Args {
   double beta_d;
   uint64_t seed;
   int64_t em_iter;
+  int toff;               // global index of the context's first task (probe counters)
   const float* pw;        // DS: sqrt(m) [T*C][Dp] scaling the probe right-hand sides, or null
   int pshare;             // DS: probes shared across clusters
 };
@@ -350,7 +351,7 @@ __global__ void __launch_bounds__(256, DS ? kP2MinBlocksDS : 1) k_pass2(P2Args p
             const bool on = (p.ractive == nullptr) || (p.ractive[sys] != 0);
             uint32_t bits = 0;
             if (on && p.Bext == nullptr && k > 0)
-              bits = probe_bits32(p.seed, p.em_iter, t, probe_cluster(c, p.pshare), p.C, k - 1,
+              bits = probe_bits32(p.seed, p.em_iter, t + p.toff, probe_cluster(c, p.pshare), p.C, k - 1,
                                   dd & ~31);
             const float* wv = (p.pw != nullptr && k > 0)
                                   ? p.pw + ((int64_t)t * p.C + c) * p.Dp : nullptr;
@@ -471,6 +472,7 @@ P2Args base_args(Ctx* c) {
   a.beta_d = c->beta;
   a.seed = c->seed;
   a.em_iter = c->em_iter;
+  a.toff = c->toff;
   a.pw = c->precond ? c->pw : nullptr;
   a.pshare = c->pshare;
   a.Rc = c->R;

@@ -55,7 +55,8 @@ int main(void) {
   O(cmcs_config, refine_max); O(cmcs_config, refine_tol); O(cmcs_config, alpha_min);
   O(cmcs_config, alpha_max); O(cmcs_config, schedule); O(cmcs_config, graphs);
   O(cmcs_config, autotune); O(cmcs_config, learn_pi); O(cmcs_config, probe_share);
-  O(cmcs_config, precond); O(cmcs_config, warm_start);
+  O(cmcs_config, precond); O(cmcs_config, warm_start); O(cmcs_config, task_offset);
+  O(cmcs_config, T_total);
   O(cmcs_summary, loglik); O(cmcs_summary, cg_steps_max); O(cmcs_summary, cg_steps_mean);
   O(cmcs_summary, cg_capped); O(cmcs_summary, refine_sweeps_max);
   O(cmcs_summary, refine_rel_max); O(cmcs_summary, min_margin);
@@ -91,6 +92,8 @@ def _cfg(**kw):
                       pi.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), base["cg_max_iter"],
                       base["cg_tol"], base["seed"], base["precision"], base["refine_max"],
                       base["refine_tol"], base["alpha_min"], base["alpha_max"], 0, 0, 0)
+    cfg.task_offset = base.get("task_offset", 0)
+    cfg.T_total = base.get("T_total", 0)
     return cfg, (N, pi)
 
 
@@ -98,7 +101,9 @@ def _cfg(**kw):
                                  dict(beta=-1.0), dict(cg_max_iter=0), dict(cg_max_iter=513),
                                  dict(cg_tol=-1.0), dict(precision=7), dict(precision=-1), dict(refine_max=-1),
                                  dict(refine_max=65), dict(alpha_min=0.0),
-                                 dict(alpha_min=2.0, alpha_max=1.0)])
+                                 dict(alpha_min=2.0, alpha_max=1.0), dict(task_offset=-1),
+                                 dict(T_total=-1), dict(task_offset=1, T_total=2),
+                                 dict(task_offset=3)])
 def test_create_rejects_invalid_config_without_cuda(L, bad):
     cfg, keep = _cfg(**bad)
     phi = np.zeros((128, 32), np.float32)
@@ -165,6 +170,8 @@ def test_calls_on_null_context_are_rejected(L):
     assert L.cmcs_set_alpha(None, None, 0, 0) == cmcs.ERR_INVALID_ARG
     assert L.cmcs_probes(None, 0, None, 0) == cmcs.ERR_INVALID_ARG
     assert L.cmcs_lanczos_quadrature(None, None, None, 1, 1, None, None, None) == cmcs.ERR_INVALID_ARG
+    assert L.cmcs_mstep_terms(None, None, 0) == cmcs.ERR_INVALID_ARG
+    assert L.cmcs_mstep_apply(None, None, 0) == cmcs.ERR_INVALID_ARG
     L.cmcs_destroy(None)
 
 

@@ -66,3 +66,12 @@ def test_workload_subsets_for_the_bench():
     assert wl.T == 2 and wl.mask.shape == (2, 256)
     wl = bench._workload("plain-small", 0, tasks=3)
     assert wl.T == 3
+
+
+def test_split_problem_aggregation_counts_one_problem():
+    """With the tasks of one problem split over the ranks, the whole job makes one EM
+    iteration per step: value = steps / slowest rank's time."""
+    import bench
+    value, ms_max = bench.aggregate(500.0, steps=4, world=1, device="cpu", units=4)
+    assert value == 8.0
+    assert "tasks split over the GPUs" in bench._metric("plain-scale", sharded=True)
