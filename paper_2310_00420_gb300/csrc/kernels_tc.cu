@@ -30,6 +30,7 @@
 #include <stdio.h>
 #include <stdlib.h>
 
+#include <algorithm>
 #include <new>
 #include <vector>
 
@@ -81,6 +82,14 @@ struct TcArgs {
                            // application)
   int* tile_ctr;           // early pass 2: next tile to hand out (zeroed per launch)
   const int* n1;           // fused or early launches: pass-1 tiles per task
+  // one-read schedule (PASS 4): work units in order, pass-1 units split along K
+  const int* u_code;       // per unit: (g << 4) | (split << 1) for pass 1, (d-tile << 1) | 1 for pass 2
+  const int* u_task;       // per unit: its task
+  int splitk;              // K splits of a pass-1 row tile
+  int nslot;               // row tiles whose partial sums can be held at once
+  float* wpart;            // [nslot][splitk][Rpad][128] FP32 partial W of pass-1 units
+  int* p1cnt;              // [row tiles] finished pass-1 units per row tile (zeroed per launch)
+  int* wready;             // [row tiles] 1 once the row tile's W is reduced and stored
 };
 
 // all tensor maps of the operator: a[pass-1][hi/lo] (pass 2 reads Phi MN-major), b[pass-1][hi/lo]
@@ -211,6 +220,7 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 struct TileInfo {
   int pass;                       // 1: W = Phi V;  2: Z = beta Phi^T W + alpha V
   int t, a_row, b_row, kx, nk, dtile, col0;
+  int split;                      // PASS 4 pass-1 unit: which K split of row tile dtile
 };
 
 // Tile decoding.  Single-pass launches (PASS 1, 2 or 3; 3 is pass 2 reading Phi MN-major):
@@ -218,8 +228,37 @@ struct TileInfo {
 // neighbouring CTAs at the same time and the second read of the A tile is served by L2.
 // Fused launches (PASS 0): tile_code[tile] = (local << 2) | (pass - 1) with tasks in order,
 // each task's pass-1 tiles before its pass-2 tiles; task = tile_task2[tile].
+// One-read launches (PASS 4): unit u of task u_task[u] is either the K split `split` of pass-1
+// row tile g (global index; k-blocks [split nkb / splitk, (split + 1) nkb / splitk) of the
+// nkb = D_pad / 64) or the whole pass-2 tile of d-tile `local`.
 template <int PASS>
 __device__ __forceinline__ bool tile_info(const TcArgs& p, int tile_in, TileInfo& ti) {
+  if (PASS == 4) {
+    const int code = p.u_code[tile_in];
+    ti.t = p.u_task[tile_in];
+    ti.col0 = 0;
+    ti.split = 0;
+    if ((code & 1) == 0) {
+      const int g = code >> 4, sp = (code >> 1) & 7;
+      const int nkb = p.Dp / kBK;
+      const int kb0 = sp * nkb / p.splitk, kb1 = (sp + 1) * nkb / p.splitk;
+      ti.pass = 1;
+      ti.a_row = g * kBM;
+      ti.b_row = ti.t * p.R;
+      ti.kx = kb0 * kBK;
+      ti.nk = kb1 - kb0;
+      ti.dtile = g;
+      ti.split = sp;
+    } else {
+      ti.pass = 2;
+      ti.dtile = code >> 1;
+      ti.a_row = ti.dtile * kBM;
+      ti.b_row = 0;
+      ti.kx = (int)p.drow[ti.t];
+      ti.nk = (int)((p.drow[ti.t + 1] - p.drow[ti.t]) / kBK);
+    }
+    return p.task_active == nullptr || p.task_active[ti.t] != 0;
+  }
   int pass = PASS == 1 ? 1 : 2, local = tile_in;
   if (PASS == 0) {
     const int code = p.tile_code[tile_in];
@@ -262,6 +301,20 @@ __device__ __forceinline__ bool wait_pass1_done(const int* cnt, int want) {
   if (*v < want) {
     const uint64_t t0 = global_ns();
     for (uint32_t i = 1; *v < want; ++i)
+      if ((i & 255u) == 0 && global_ns() - t0 > kWaitNs) return false;
+  }
+  __threadfence();
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+  return true;
+}
+
+// bounded wait until *f becomes nonzero (a row tile of W published with the release pattern
+// of signal_pass1_done); the fences order the later reads, TMA (async proxy) included
+__device__ __forceinline__ bool wait_flag(const int* f) {
+  const volatile int* v = f;
+  if (*v == 0) {
+    const uint64_t t0 = global_ns();
+    for (uint32_t i = 1; *v == 0; ++i)
       if ((i & 255u) == 0 && global_ns() - t0 > kWaitNs) return false;
   }
   __threadfence();
@@ -329,7 +382,7 @@ k_tc(const __grid_constant__ TcMaps maps, const TcArgs p) {
   uint64_t* tq_full = reinterpret_cast<uint64_t*>(red + 4 * p.Rpad);
   uint64_t* tq_empty = tq_full + kTq;
   volatile int* tq = reinterpret_cast<volatile int*>(tq_empty + kTq);
-  const bool dyn = PASS == 3 && p.early;
+  const bool dyn = (PASS == 3 && p.early) || PASS == 4;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // once a wait has expired in this E-step, later launches do nothing (the host reports it)
   if (*reinterpret_cast<volatile int*>(p.status) & 8) return;
@@ -402,7 +455,7 @@ k_tc(const __grid_constant__ TcMaps maps, const TcArgs p) {
           atomicOr(p.status, 8);
           break;
         }
-        const bool a_mn = PASS == 3 || (PASS == 0 && ti.pass == 2);
+        const bool a_mn = PASS == 3 || ((PASS == 0 || PASS == 4) && ti.pass == 2);
         const int pi = ti.pass - 1;
         if (((PASS == 0 && ti.pass == 2) || (PASS == 3 && p.early)) &&
             !wait_pass1_done(&p.p1done[ti.t], p.n1[ti.t])) {
@@ -419,6 +472,15 @@ k_tc(const __grid_constant__ TcMaps maps, const TcArgs p) {
             break;
           }
           if (*abort_flag) {
+            stop = true;
+            break;
+          }
+          // one-read pass 2: each 128-row tile of W (two k-blocks) is used once its pass-1
+          // units have been reduced
+          if (PASS == 4 && ti.pass == 2 && (kb & 1) == 0 &&
+              !wait_flag(&p.wready[(ti.kx + kb * kBK) / kBM])) {
+            *abort_flag = 1;
+            atomicOr(p.status, 8);
             stop = true;
             break;
           }
@@ -472,7 +534,7 @@ k_tc(const __grid_constant__ TcMaps maps, const TcArgs p) {
            tile = dyn ? tq_pop(qm) : tile + (int)gridDim.x) {
         TileInfo ti;
         if (!tile_info<PASS>(p, tile, ti)) continue;
-        const bool a_mn = PASS == 3 || (PASS == 0 && ti.pass == 2);
+        const bool a_mn = PASS == 3 || ((PASS == 0 || PASS == 4) && ti.pass == 2);
         const uint32_t idesc = a_mn ? idesc_mn : idesc_k;
         const int b = (int)(lt % p.nbuf);
         if (lt >= (uint32_t)p.nbuf && !mbar_wait(&tempty[b], ((lt / p.nbuf) - 1) & 1)) {
@@ -533,6 +595,58 @@ k_tc(const __grid_constant__ TcMaps maps, const TcArgs p) {
       if (epi_bar_any(!ok || *abort_flag)) break;   // uniform across the epilogue warps
       tc_fence_after();
       const uint32_t trow = tmem + (uint32_t)b * p.tmem_cols + ((uint32_t)(32 * lg) << 16);
+      if (PASS == 4 && ti.pass == 1) {
+        // K split of a pass-1 row tile: store the FP32 partial in the row tile's slot; the last
+        // of its splitk units to finish sums the partials in split order (the same sums
+        // whichever unit that is) and stores the row tile of W as BF16 hi + lo
+        const int g = ti.dtile, row = 32 * lg + lane;
+        const int slot = g % p.nslot;
+        volatile int* bc = reinterpret_cast<volatile int*>(tmem_slot + 2);
+        if (g >= p.nslot && (p.task_active == nullptr || p.task_active[p.tile_task[g - p.nslot]])) {
+          // the slot's previous row tile must have been reduced (its partials read)
+          bool okw = true;
+          if (etid == 0) okw = wait_flag(&p.wready[g - p.nslot]);
+          if (epi_bar_any(!okw)) {
+            *abort_flag = 1;
+            if (etid == 0) atomicOr(p.status, 8);
+            break;
+          }
+        }
+        float* part = p.wpart + (size_t)slot * p.splitk * p.Rpad * kBM;
+        float* mine = part + (size_t)ti.split * p.Rpad * kBM;
+        for (int c0 = 0; c0 < p.Rpad; c0 += 16) {
+          float v[16];
+          tmem_ld16(trow + c0, v);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) mine[(size_t)(c0 + i) * kBM + row] = v[i];
+        }
+        // the accumulator is drained: the MMA warp may reuse it during the reduction
+        tc_fence_before();
+        mbar_arrive(&tempty[b]);
+        ++lt;
+        __threadfence();
+        epi_bar();
+        if (etid == 0) *bc = atomicAdd(&p.p1cnt[g], 1);
+        epi_bar();
+        if (*bc == p.splitk - 1) {
+          __threadfence();
+          const int64_t n = (int64_t)ti.a_row + row;
+          for (int j = 0; j < p.R; ++j) {
+            float acc = 0.f;
+            for (int sp = 0; sp < p.splitk; ++sp)
+              acc += __ldcg(part + ((size_t)sp * p.Rpad + j) * kBM + row);
+            const __nv_bfloat16 hi = __float2bfloat16_rn(acc);
+            const __nv_bfloat16 lo = __float2bfloat16_rn(acc - __bfloat162float(hi));
+            p.w_hi[(int64_t)j * p.rows_total + n] = hi;
+            p.w_lo[(int64_t)j * p.rows_total + n] = lo;
+          }
+          asm volatile("fence.proxy.async.global;" ::: "memory");
+          __threadfence();
+          epi_bar();
+          if (etid == 0) atomicExch(&p.wready[g], 1);
+        }
+        continue;
+      }
       if (ti.pass == 1) {
         const int64_t n = (int64_t)ti.a_row + 32 * lg + lane;     // global row of Phi
         for (int c0 = 0; c0 < p.Rpad; c0 += 16) {
@@ -669,6 +783,11 @@ struct TcState {
   int *tile_code, *tile_task2, *n1, *p1done;   // fused tile list; per-task counts [T] + tile counter
   int early;                                   // mode 3: pass 2 launched programmatically
   std::vector<int> tstart;                     // first fused tile of each task (host)
+  // mode 4 (one read of Phi per application): unit list, split-K partials and counters
+  int *u_code, *u_task, nunits, splitk, nslot;
+  std::vector<int> ustart;                     // first unit of each task (per-task launches)
+  float* wpart;
+  int* m4;                                     // [2 row tiles + 1]: p1cnt, wready, unit counter
 };
 
 PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
@@ -760,6 +879,37 @@ cudaError_t run_passes(Ctx* c, TcState* s, const float* V, float* Z, int with_do
   maps.b[0][1] = s->tm_d[NB - 1];
   maps.b[1][0] = s->tm_w[0];
   maps.b[1][1] = s->tm_w[NB - 1];
+  if (s->mode == 4) {
+    // one persistent launch per application: pass-1 units split along K and pass-2 tiles,
+    // task after task, handed out in order from a counter; a task's Phi is read from HBM by
+    // its pass-1 units and again, from L2, by its pass-2 tiles shortly after
+    const int ntl = (int)(c->rows_total / kBM);
+    cudaError_t e = cudaMemsetAsync(s->m4, 0, sizeof(int) * (2 * (size_t)ntl + 1), c->stream);
+    if (e != cudaSuccess) return e;
+    a.u_code = s->u_code;
+    a.u_task = s->u_task;
+    a.splitk = s->splitk;
+    a.nslot = s->nslot;
+    a.wpart = s->wpart;
+    a.p1cnt = s->m4;
+    a.wready = s->m4 + ntl;
+    a.tile_ctr = s->m4 + 2 * ntl;
+    for (int t = 0; t < nloop; ++t) {
+      // every unit in one launch, or (comparison schedule) the units of one task per launch
+      a.tile_lo = c->per_task ? s->ustart[(size_t)t] : 0;
+      a.ntiles = c->per_task ? s->ustart[(size_t)t + 1] : s->nunits;
+      const int n = a.ntiles - a.tile_lo;
+      if (c->per_task && t > 0) {    // the unit counter restarts at each task's first unit
+        e = cudaMemsetAsync(a.tile_ctr, 0, sizeof(int), c->stream);
+        if (e != cudaSuccess) return e;
+      }
+      k_tc<4, NA, NB><<<n < sms ? n : sms, kTcThreads, s->smem_bytes, c->stream>>>(maps, a);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+      c->launches += 1;
+    }
+    return cudaSuccess;
+  }
   for (int t = 0; t < nloop; ++t) {
     // all tasks in one persistent launch, or (comparison schedule) one launch per task
     if (s->mode == 0) {
@@ -853,7 +1003,9 @@ int tc_create(Ctx* c) {
   {
     const char* mv = getenv("CMCS_TC_MODE");     // evaluation switch between the schedules
     s->mode = mv ? atoi(mv) : 3;
-    if (s->mode != 0 && s->mode != 2) s->mode = 3;
+    if (s->mode != 0 && s->mode != 2 && s->mode != 4) s->mode = 3;
+    // the one-read schedule handles one column tile and the batched launch
+    if (s->mode == 4 && s->ncol != 1) s->mode = 3;
     const char* ev = getenv("CMCS_TC_EARLY");    // evaluation switch: 0 launches pass 2 plainly
     s->early = ev ? atoi(ev) != 0 : 1;
   }
@@ -906,6 +1058,61 @@ int tc_create(Ctx* c) {
       cudaStreamSynchronize(c->stream);    // the host vectors go out of scope
     }
   }
+  if (okm && s->mode == 4) {
+    // unit list: all pass-1 units of task 0, then per task t the first L pass-1 units of task
+    // t + 1, the pass-2 tiles of task t and the rest of task t + 1's pass-1 units (a pass-2
+    // tile only ever waits on units earlier in the list)
+    const char* kv = getenv("CMCS_TC_SPLITK");   // evaluation switches of the one-read schedule
+    const char* lv = getenv("CMCS_TC_LOOKAHEAD");
+    const int nkb = (int)(Dp / kBK);
+    s->splitk = kv ? atoi(kv) : 4;
+    if (s->splitk < 1) s->splitk = 1;
+    if (s->splitk > 8) s->splitk = 8;
+    if (s->splitk > nkb) s->splitk = nkb;
+    int L = lv ? atoi(lv) : 64;
+    if (L < 0 || c->per_task) L = 0;   // per-task launches: each task's units contiguous
+    const int ndt = (int)(Dp / kBM);
+    std::vector<std::vector<int>> p1((size_t)c->T);
+    for (int t = 0; t < c->T; ++t)
+      for (int64_t g = c->hrow[t] / kBM; g < c->hrow[t + 1] / kBM; ++g)
+        for (int sp = 0; sp < s->splitk; ++sp) p1[(size_t)t].push_back((int)(g << 4) | (sp << 1));
+    std::vector<int> code, task;
+    auto put = [&](int t, int v) {
+      code.push_back(v);
+      task.push_back(t);
+    };
+    s->ustart.assign((size_t)c->T + 1, 0);
+    for (int v : p1[0]) put(0, v);
+    for (int t = 0; t < c->T; ++t) {
+      const bool nxt = t + 1 < c->T;
+      const size_t l = nxt ? std::min((size_t)L, p1[(size_t)t + 1].size()) : 0;
+      for (size_t i = 0; i < l; ++i) put(t + 1, p1[(size_t)t + 1][i]);
+      for (int j = 0; j < ndt; ++j) put(t, (j << 1) | 1);
+      if (nxt)
+        for (size_t i = l; i < p1[(size_t)t + 1].size(); ++i) put(t + 1, p1[(size_t)t + 1][i]);
+    }
+    s->nunits = (int)code.size();
+    // first unit of each task (meaningful with L = 0, where a task's units are contiguous)
+    for (int t = 0, u = 0; t < c->T; ++t) {
+      while (u < s->nunits && task[(size_t)u] != t) ++u;
+      s->ustart[(size_t)t] = u;
+    }
+    s->ustart[(size_t)c->T] = s->nunits;
+    // partials of about three tasks' row tiles in flight (a slot waits for its previous row
+    // tile's reduction, so fewer only costs time)
+    const int ntl = (int)(rows / kBM);
+    s->nslot = std::min(ntl, 64);
+    okm = cudaMalloc(reinterpret_cast<void**>(&s->u_code), sizeof(int) * code.size()) == cudaSuccess &&
+          cudaMalloc(reinterpret_cast<void**>(&s->u_task), sizeof(int) * task.size()) == cudaSuccess &&
+          cudaMalloc(reinterpret_cast<void**>(&s->m4), sizeof(int) * (2 * (size_t)ntl + 1)) == cudaSuccess &&
+          cudaMalloc(reinterpret_cast<void**>(&s->wpart),
+                     sizeof(float) * (size_t)s->nslot * s->splitk * s->Rpad * kBM) == cudaSuccess;
+    if (okm) {
+      cudaMemcpyAsync(s->u_code, code.data(), sizeof(int) * code.size(), cudaMemcpyHostToDevice, c->stream);
+      cudaMemcpyAsync(s->u_task, task.data(), sizeof(int) * task.size(), cudaMemcpyHostToDevice, c->stream);
+      cudaStreamSynchronize(c->stream);    // the host vectors go out of scope
+    }
+  }
   if (!okm) {
     snprintf(c->err, sizeof(c->err), "tensor-core operator: device allocation failed");
     return 1;
@@ -936,6 +1143,8 @@ int tc_create(Ctx* c) {
     e = s->NA == 2 ? set_smem_attr<3, 2, 2>(s->smem_bytes) : set_smem_attr<3, 1, 2>(s->smem_bytes);
   if (e == cudaSuccess)
     e = s->NA == 2 ? set_smem_attr<0, 2, 2>(s->smem_bytes) : set_smem_attr<0, 1, 2>(s->smem_bytes);
+  if (e == cudaSuccess)
+    e = s->NA == 2 ? set_smem_attr<4, 2, 2>(s->smem_bytes) : set_smem_attr<4, 1, 2>(s->smem_bytes);
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) {
     snprintf(c->err, sizeof(c->err), "tensor-core operator set-up: %s", cudaGetErrorString(e));
@@ -949,7 +1158,8 @@ void tc_destroy(Ctx* c) {
   TcState* s = static_cast<TcState*>(c->tc);
   if (!s) return;
   void* ptrs[] = {s->phi_hi, s->phi_lo, s->phit_hi, s->phit_lo, s->w_hi, s->w_lo, c->dhi, c->dlo,
-                  s->tile_code, s->tile_task2, s->n1, s->p1done};
+                  s->tile_code, s->tile_task2, s->n1, s->p1done, s->u_code, s->u_task, s->m4,
+                  s->wpart};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   c->dhi = c->dlo = nullptr;
