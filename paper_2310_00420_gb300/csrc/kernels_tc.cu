@@ -88,7 +88,8 @@ struct TcArgs {
   int splitk;              // K splits of a pass-1 row tile
   int nslot;               // row tiles whose partial sums can be held at once
   float* wpart;            // [nslot][splitk][Rpad][128] FP32 partial W of pass-1 units
-  int* p1cnt;              // [row tiles] finished pass-1 units per row tile (zeroed per launch)
+  int* p1cnt;              // [row tiles] pass-1 units that reached their epilogue (zeroed per launch)
+  int* p1st;               // [row tiles] pass-1 units whose partial is stored (zeroed per launch)
   int* wready;             // [row tiles] 1 once the row tile's W is reduced and stored
 };
 
@@ -320,6 +321,65 @@ __device__ __forceinline__ bool wait_flag(const int* f) {
   __threadfence();
   asm volatile("fence.proxy.async.global;" ::: "memory");
   return true;
+}
+
+// bounded wait until *f >= want (peers that have already arrived finishing their stores)
+__device__ __forceinline__ bool wait_count(const int* f, int want) {
+  const volatile int* v = f;
+  if (*v < want) {
+    const uint64_t t0 = global_ns();
+    for (uint32_t i = 1; *v < want; ++i)
+      if ((i & 255u) == 0 && global_ns() - t0 > kWaitNs) return false;
+  }
+  __threadfence();
+  return true;
+}
+
+// acc[0..15] = sum over splits sp = 0..SK-1 in order of the partials of columns c0..c0+15 of
+// `row` ([split][row][Rpad] FP32), with split `mine` taken from own[] (still in TMEM when the
+// others were stored).  SK = 0: run-time split count sk.
+template <int SK>
+__device__ __forceinline__ void reduce_chunk(const float* part, int Rpad, int row, int c0, int mine,
+                                             const float* own, float* acc, int sk = SK) {
+  const int nsp = SK > 0 ? SK : sk;
+  float4 buf[(SK > 0 ? SK : 1) * 4];
+  if (SK > 0) {
+#pragma unroll
+    for (int sp = 0; sp < (SK > 0 ? SK : 1); ++sp) {
+      if (sp == mine) continue;
+      const float4* src = reinterpret_cast<const float4*>(part + ((size_t)sp * kBM + row) * Rpad + c0);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) buf[sp * 4 + i] = __ldcg(src + i);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 16; ++i) acc[i] = 0.f;
+  for (int sp = 0; sp < nsp; ++sp) {
+    float v[16];
+    if (sp == mine) {
+#pragma unroll
+      for (int i = 0; i < 16; ++i) v[i] = own[i];
+    } else {
+      float4 q[4];
+      if (SK > 0) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) q[i] = buf[(SK > 0 ? sp : 0) * 4 + i];
+      } else {
+        const float4* src = reinterpret_cast<const float4*>(part + ((size_t)sp * kBM + row) * Rpad + c0);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) q[i] = __ldcg(src + i);
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        v[4 * i] = q[i].x;
+        v[4 * i + 1] = q[i].y;
+        v[4 * i + 2] = q[i].z;
+        v[4 * i + 3] = q[i].w;
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 16; ++i) acc[i] += v[i];
+  }
 }
 
 __device__ __forceinline__ float warp_reduce16(float* v, int lane) {
@@ -596,55 +656,78 @@ k_tc(const __grid_constant__ TcMaps maps, const TcArgs p) {
       tc_fence_after();
       const uint32_t trow = tmem + (uint32_t)b * p.tmem_cols + ((uint32_t)(32 * lg) << 16);
       if (PASS == 4 && ti.pass == 1) {
-        // K split of a pass-1 row tile: store the FP32 partial in the row tile's slot; the last
-        // of its splitk units to finish sums the partials in split order (the same sums
-        // whichever unit that is) and stores the row tile of W as BF16 hi + lo
+        // K split of a pass-1 row tile.  The last of the row tile's splitk units to arrive sums
+        // the partials in split order (its own still in TMEM, the others' stored by them) and
+        // stores the row tile of W as BF16 hi + lo; the others store their FP32 partials.  The
+        // sums are the same whichever unit arrives last.
         const int g = ti.dtile, row = 32 * lg + lane;
         const int slot = g % p.nslot;
         volatile int* bc = reinterpret_cast<volatile int*>(tmem_slot + 2);
-        if (g >= p.nslot && (p.task_active == nullptr || p.task_active[p.tile_task[g - p.nslot]])) {
+        float* part = p.wpart + (size_t)slot * p.splitk * kBM * p.Rpad;   // [split][row][Rpad]
+        if (etid == 0) *bc = atomicAdd(&p.p1cnt[g], 1);
+        epi_bar();
+        const bool last = *bc == p.splitk - 1;
+        epi_bar();                                 // every thread has read the role
+        bool ok = true;
+        if (!last) {
           // the slot's previous row tile must have been reduced (its partials read)
-          bool okw = true;
-          if (etid == 0) okw = wait_flag(&p.wready[g - p.nslot]);
-          if (epi_bar_any(!okw)) {
-            *abort_flag = 1;
-            if (etid == 0) atomicOr(p.status, 8);
-            break;
+          if (etid == 0 && g >= p.nslot &&
+              (p.task_active == nullptr || p.task_active[p.tile_task[g - p.nslot]]))
+            ok = wait_flag(&p.wready[g - p.nslot]);
+        } else {
+          // the other units have arrived, so they are storing: wait for all of them
+          if (etid == 0) ok = wait_count(&p.p1st[g], p.splitk - 1);
+        }
+        if (epi_bar_any(!ok)) {
+          *abort_flag = 1;
+          if (etid == 0) atomicOr(p.status, 8);
+          break;
+        }
+        if (!last) {
+          float4* mine = reinterpret_cast<float4*>(part + ((size_t)ti.split * kBM + row) * p.Rpad);
+          for (int c0 = 0; c0 < p.Rpad; c0 += 16) {
+            float v[16];
+            tmem_ld16(trow + c0, v);
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+              mine[c0 / 4 + i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+          }
+          tc_fence_before();
+          mbar_arrive(&tempty[b]);
+          ++lt;
+          __threadfence();
+          epi_bar();
+          if (etid == 0) atomicAdd(&p.p1st[g], 1);
+          continue;
+        }
+        __threadfence();
+        const int64_t n = (int64_t)ti.a_row + row;
+        for (int c0 = 0; c0 < p.Rpad; c0 += 16) {
+          float own[16], acc[16];
+          tmem_ld16(trow + c0, own);
+          switch (p.splitk) {
+            case 2: reduce_chunk<2>(part, p.Rpad, row, c0, ti.split, own, acc); break;
+            case 4: reduce_chunk<4>(part, p.Rpad, row, c0, ti.split, own, acc); break;
+            default: reduce_chunk<0>(part, p.Rpad, row, c0, ti.split, own, acc, p.splitk); break;
+          }
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const int j = c0 + i;
+            if (j < p.R) {
+              const __nv_bfloat16 hi = __float2bfloat16_rn(acc[i]);
+              const __nv_bfloat16 lo = __float2bfloat16_rn(acc[i] - __bfloat162float(hi));
+              p.w_hi[(int64_t)j * p.rows_total + n] = hi;
+              p.w_lo[(int64_t)j * p.rows_total + n] = lo;
+            }
           }
         }
-        float* part = p.wpart + (size_t)slot * p.splitk * p.Rpad * kBM;
-        float* mine = part + (size_t)ti.split * p.Rpad * kBM;
-        for (int c0 = 0; c0 < p.Rpad; c0 += 16) {
-          float v[16];
-          tmem_ld16(trow + c0, v);
-#pragma unroll
-          for (int i = 0; i < 16; ++i) mine[(size_t)(c0 + i) * kBM + row] = v[i];
-        }
-        // the accumulator is drained: the MMA warp may reuse it during the reduction
         tc_fence_before();
         mbar_arrive(&tempty[b]);
         ++lt;
+        asm volatile("fence.proxy.async.global;" ::: "memory");
         __threadfence();
         epi_bar();
-        if (etid == 0) *bc = atomicAdd(&p.p1cnt[g], 1);
-        epi_bar();
-        if (*bc == p.splitk - 1) {
-          __threadfence();
-          const int64_t n = (int64_t)ti.a_row + row;
-          for (int j = 0; j < p.R; ++j) {
-            float acc = 0.f;
-            for (int sp = 0; sp < p.splitk; ++sp)
-              acc += __ldcg(part + ((size_t)sp * p.Rpad + j) * kBM + row);
-            const __nv_bfloat16 hi = __float2bfloat16_rn(acc);
-            const __nv_bfloat16 lo = __float2bfloat16_rn(acc - __bfloat162float(hi));
-            p.w_hi[(int64_t)j * p.rows_total + n] = hi;
-            p.w_lo[(int64_t)j * p.rows_total + n] = lo;
-          }
-          asm volatile("fence.proxy.async.global;" ::: "memory");
-          __threadfence();
-          epi_bar();
-          if (etid == 0) atomicExch(&p.wready[g], 1);
-        }
+        if (etid == 0) atomicExch(&p.wready[g], 1);
         continue;
       }
       if (ti.pass == 1) {
@@ -787,7 +870,7 @@ struct TcState {
   int *u_code, *u_task, nunits, splitk, nslot;
   std::vector<int> ustart;                     // first unit of each task (per-task launches)
   float* wpart;
-  int* m4;                                     // [2 row tiles + 1]: p1cnt, wready, unit counter
+  int* m4;                                     // [3 row tiles + 1]: p1cnt, wready, p1st, unit counter
 };
 
 PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
@@ -884,7 +967,7 @@ cudaError_t run_passes(Ctx* c, TcState* s, const float* V, float* Z, int with_do
     // task after task, handed out in order from a counter; a task's Phi is read from HBM by
     // its pass-1 units and again, from L2, by its pass-2 tiles shortly after
     const int ntl = (int)(c->rows_total / kBM);
-    cudaError_t e = cudaMemsetAsync(s->m4, 0, sizeof(int) * (2 * (size_t)ntl + 1), c->stream);
+    cudaError_t e = cudaMemsetAsync(s->m4, 0, sizeof(int) * (3 * (size_t)ntl + 1), c->stream);
     if (e != cudaSuccess) return e;
     a.u_code = s->u_code;
     a.u_task = s->u_task;
@@ -893,7 +976,8 @@ cudaError_t run_passes(Ctx* c, TcState* s, const float* V, float* Z, int with_do
     a.wpart = s->wpart;
     a.p1cnt = s->m4;
     a.wready = s->m4 + ntl;
-    a.tile_ctr = s->m4 + 2 * ntl;
+    a.p1st = s->m4 + 2 * ntl;
+    a.tile_ctr = s->m4 + 3 * ntl;
     for (int t = 0; t < nloop; ++t) {
       // every unit in one launch, or (comparison schedule) the units of one task per launch
       a.tile_lo = c->per_task ? s->ustart[(size_t)t] : 0;
@@ -1104,7 +1188,7 @@ int tc_create(Ctx* c) {
     s->nslot = std::min(ntl, 64);
     okm = cudaMalloc(reinterpret_cast<void**>(&s->u_code), sizeof(int) * code.size()) == cudaSuccess &&
           cudaMalloc(reinterpret_cast<void**>(&s->u_task), sizeof(int) * task.size()) == cudaSuccess &&
-          cudaMalloc(reinterpret_cast<void**>(&s->m4), sizeof(int) * (2 * (size_t)ntl + 1)) == cudaSuccess &&
+          cudaMalloc(reinterpret_cast<void**>(&s->m4), sizeof(int) * (3 * (size_t)ntl + 1)) == cudaSuccess &&
           cudaMalloc(reinterpret_cast<void**>(&s->wpart),
                      sizeof(float) * (size_t)s->nslot * s->splitk * s->Rpad * kBM) == cudaSuccess;
     if (okm) {

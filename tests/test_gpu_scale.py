@@ -80,18 +80,23 @@ def test_headline_sampled_pairs_match_oracle(scale_tc, pair):
 def test_headline_assignments_follow_replay_q(scale_tc):
     """All T = 32 assignments of the benchmark's configuration against the argmax of the
     responsibilities the oracle forms from the GPU's own CG coefficients (Eqs. 9-11 in
-    replay) and the GPU's refined means (Eq. 3), and those responsibilities at 1e-4."""
+    replay) and the GPU's refined means (Eq. 3), and those responsibilities at 1e-4.  The data
+    term b0^T A^-1 b0 of ell is evaluated from the means as b0^T mu + mu^T (b0 - A mu), the
+    second-order form the library uses, here with the oracle's FP64 residual."""
     wl, alpha, it, g = scale_tc
     T, C = wl.T, wl.C
     ell = np.zeros((T, C))
     for t in range(T):
-        b0 = cofem.rhs_mean(wl.phi(t).astype(np.float64), wl.yt(t).astype(np.float64), wl.beta)
+        P = wl.phi(t).astype(np.float64)
+        b0 = cofem.rhs_mean(P, wl.yt(t).astype(np.float64), wl.beta)
+        mu = g["mu"][t].astype(np.float64)                                   # [C, D]
         for c in range(C):
             nu = cofem.logdet_estimate(g["gamma"][t, c].astype(np.float64),
                                        g["xi"][t, c].astype(np.float64), g["steps"][t, c, 1:],
                                        wl.D)
-            ell[t, c] = cofem.ell(nu, alpha[c].astype(np.float64), b0,
-                                  g["mu"][t, c].astype(np.float64))
+            a = alpha[c].astype(np.float64)
+            r = b0 - cofem.apply_A(P, wl.beta, a, mu[c])
+            ell[t, c] = cofem.ell(nu, a, b0, mu[c]) + float(mu[c] @ r)
     q_rep = cofem.responsibilities(ell, wl.pi)
     np.testing.assert_allclose(g["ell"], ell, rtol=1e-6)
     assert np.max(np.abs(g["q"] - q_rep)) <= 1e-4
