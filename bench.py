@@ -66,8 +66,12 @@ def _args():
     ap.add_argument("--no-graphs", action="store_true")
     ap.add_argument("--refine-max", type=int, default=8)
     ap.add_argument("--refine-tol", type=float, default=1e-5)
+    ap.add_argument("--refine-steps", type=int, default=0,
+                    help="step cap of the refinement sweeps' CG solves (0: the first solve's)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true",
+                    help="keep the error against FP64 but skip timing the CPU oracle")
     ap.add_argument("--replicas", action="store_true",
                     help="with several GPUs, run independent replicas instead of splitting "
                          "the tasks of one problem over them")
@@ -355,7 +359,8 @@ def precision_leg(a, peaks) -> dict:
     from paper_2310_00420_gb300 import cmcs
     wl = _workload("precision", 0)
     kw = dict(C=wl.C, K=wl.K, beta=wl.beta, pi=wl.pi, cg_max_iter=wl.cg_max_iter,
-              cg_tol=wl.cg_tol, seed=wl.seed, refine_max=a.refine_max, refine_tol=a.refine_tol)
+              cg_tol=wl.cg_tol, seed=wl.seed, refine_max=a.refine_max, refine_tol=a.refine_tol,
+              refine_steps=a.refine_steps)
     Phi_d = torch.from_numpy(wl.Phi).cuda()
     y_d = torch.from_numpy(wl.y).cuda()
     out = {"workload": f"{wl.name} T={wl.T} C={wl.C} D={wl.D} N={int(wl.N[0])} K={wl.K} "
@@ -416,7 +421,7 @@ def batching_leg(a) -> dict:
     wl = _workload("batching", 0)
     kw = dict(C=wl.C, K=wl.K, beta=wl.beta, pi=wl.pi, cg_max_iter=wl.cg_max_iter,
               cg_tol=wl.cg_tol, seed=wl.seed, refine_max=a.refine_max, refine_tol=a.refine_tol,
-              precision="bf16x3")
+              refine_steps=a.refine_steps, precision="bf16x3")
     Phi_d = torch.from_numpy(wl.Phi).cuda()
     y_d = torch.from_numpy(wl.y).cuda()
     out = {"workload": f"{wl.name} T={wl.T} C={wl.C} D={wl.D} N_t in [{int(wl.N.min())}, "
@@ -456,6 +461,7 @@ def run_ours(a):
         a.no_fp32_form = True
     kw = dict(C=wl.C, K=wl.K, beta=wl.beta, pi=wl.pi, cg_max_iter=wl.cg_max_iter, cg_tol=wl.cg_tol,
               seed=wl.seed, precision=a.precision, refine_max=a.refine_max, refine_tol=a.refine_tol,
+              refine_steps=a.refine_steps,
               schedule=a.schedule, graphs=not a.no_graphs, precond=a.precond,
               learn_pi=a.learn_pi, probe_share=a.probe_share, warm_start=a.warm_start)
     if sharded:
@@ -570,7 +576,7 @@ def run_ours(a):
         rel = lambda g_, r_: float(np.linalg.norm(g_ - r_) / np.linalg.norm(r_))
         err = {"pair": [t_s, c_s], "mu_rel": rel(mu_g[t_s, c_s], o["mu"][0, 0]),
                "s_rel": rel(s_g[t_s, c_s], o["s"][0, 0])}
-        if world == 1:
+        if world == 1 and not a.no_cpu_baseline:
             from oracle import philox
             alpha0 = philox.alpha_init(wl.seed, wl.C, wl.D)
             pairs = _cpu_pairs(wl)
@@ -666,7 +672,7 @@ def run_ours(a):
                                        f"N={int(wl.N[0])} K={wl.K} tol={wl.cg_tol} "
                                        f"max_iter={wl.cg_max_iter}",
                            "precision": a.precision, "refine_max": a.refine_max,
-                           "refine_tol": a.refine_tol,
+                           "refine_tol": a.refine_tol, "refine_steps": a.refine_steps or wl.cg_max_iter,
                            "parallelism": (f"tasks split over {world} GPUs {ranges}, one "
                                            f"all-gather of the M-step rows per EM iteration"
                                            if sharded else f"{world} replicas"),

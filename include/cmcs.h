@@ -107,6 +107,10 @@ typedef struct {
   int T_total;            /* tasks of the whole problem (0: T); task_offset + T <= T_total.
                              With T_total > T, cmcs_em_iter is refused: the M-step goes through
                              cmcs_mstep_terms and cmcs_mstep_apply                            */
+  int refine_steps;       /* step cap of the CG solves inside the refinement sweeps, 0..cg_max_iter
+                             (0: cg_max_iter).  Only the first solve feeds the Lanczos estimate
+                             (Eqs. 9-11); a sweep only has to shrink the error, and refine_tol
+                             still decides when the sweeps stop                               */
 } cmcs_config;
 
 /* Summary of the most recent E-step and the EM state. */

@@ -41,7 +41,8 @@ class Config(ctypes.Structure):
                 ("schedule", ctypes.c_int), ("graphs", ctypes.c_int), ("autotune", ctypes.c_int),
                 ("learn_pi", ctypes.c_int), ("probe_share", ctypes.c_int),
                 ("precond", ctypes.c_int), ("warm_start", ctypes.c_int),
-                ("task_offset", ctypes.c_int), ("T_total", ctypes.c_int)]
+                ("task_offset", ctypes.c_int), ("T_total", ctypes.c_int),
+                ("refine_steps", ctypes.c_int)]
 
 
 class Summary(ctypes.Structure):
@@ -165,8 +166,8 @@ class Context:
                  refine_tol: float = 1e-6, alpha_min: float = 1e-10, alpha_max: float = 1e10,
                  schedule: str = "batched", graphs: bool = True, autotune: bool = False,
                  learn_pi: bool = False, probe_share: bool = False, precond: bool = False,
-                 warm_start: bool = False, task_offset: int = 0, T_total: int = 0, mask=None,
-                 stream=None):
+                 warm_start: bool = False, task_offset: int = 0, T_total: int = 0,
+                 refine_steps: int = 0, mask=None, stream=None):
         """Dense Phi [sum N_t][D] with y [sum N_t]; or, with Phi None and mask given, the
         Fourier operator of cmcs_create_dft: mask uint8 [T][D], y float32 [sum N_t][2].
         learn_pi, probe_share, precond and warm_start switch on the method variants of
@@ -188,7 +189,8 @@ class Context:
                      float(refine_tol), float(alpha_min), float(alpha_max),
                      {"batched": 0, "per_task": 1}[schedule], 1 if graphs else 0,
                      1 if autotune else 0, 1 if learn_pi else 0, 1 if probe_share else 0,
-                     1 if precond else 0, 1 if warm_start else 0, int(task_offset), int(T_total))
+                     1 if precond else 0, 1 if warm_start else 0, int(task_offset), int(T_total),
+                     int(refine_steps))
         self.cfg = cfg
         self.fourier = mask is not None
         p_phi, dev1 = _ptr(mask if self.fourier else Phi)

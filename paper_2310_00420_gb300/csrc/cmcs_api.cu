@@ -66,8 +66,9 @@ void free_ctx(Ctx* c) {
   }
   if (c->hcounters) cudaFreeHost(c->hcounters);
   for (int r = 0; r < 2; ++r)
-    for (int q = 0; q < 2; ++q)
-      if (c->graph[r][q]) cudaGraphExecDestroy(c->graph[r][q]);
+    for (int k = 0; k < 2; ++k)
+      for (int q = 0; q < 2; ++q)
+        if (c->graph[r][k][q]) cudaGraphExecDestroy(c->graph[r][k][q]);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   if (c->side) cudaStreamDestroy(c->side);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
@@ -152,8 +153,8 @@ cmcs_status cg_steps_direct(Ctx* c, int record, int n) {
 
 // the graph replaying kCheckEvery CG steps, captured on first use
 cudaGraphExec_t chunk_graph(Ctx* c, int record) {
-  cudaGraphExec_t& g = c->graph[record][c->prof_on];
-  if (g != nullptr || c->graph_failed[record][c->prof_on]) return g;
+  cudaGraphExec_t& g = c->graph[record][c->capsel][c->prof_on];
+  if (g != nullptr || c->graph_failed[record][c->capsel][c->prof_on]) return g;
   const int64_t l0 = c->launches, a0 = c->op_applies, p0 = c->prof_calls;
   cudaGraph_t graph = nullptr;
   if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return nullptr;
@@ -170,7 +171,7 @@ cudaGraphExec_t chunk_graph(Ctx* c, int record) {
   if (s != CMCS_OK || e != cudaSuccess || graph == nullptr) {
     cudaGetLastError();
     if (graph) cudaGraphDestroy(graph);
-    c->graph_failed[record][c->prof_on] = 1;    // run this variant with direct launches
+    c->graph_failed[record][c->capsel][c->prof_on] = 1;   // run this variant directly
     c->err[0] = 0;
     return nullptr;
   }
@@ -179,16 +180,17 @@ cudaGraphExec_t chunk_graph(Ctx* c, int record) {
   if (e != cudaSuccess) {
     cudaGetLastError();
     g = nullptr;
-    c->graph_failed[record][c->prof_on] = 1;
+    c->graph_failed[record][c->capsel][c->prof_on] = 1;
   }
   return g;
 }
 
-// Alg. 1 for every active system until all have stopped (or the step cap), in chunks of
-// kCheckEvery steps between host polls of the number of active systems
+// Alg. 1 for every active system until all have stopped (or the step cap in force), in
+// chunks of kCheckEvery steps between host polls of the number of active systems
 cmcs_status run_cg(Ctx* c, int record) {
-  for (int u = 0; u < c->U; u += kCheckEvery) {
-    const int n = c->U - u < kCheckEvery ? c->U - u : kCheckEvery;
+  const int cap = cg_cap(c);
+  for (int u = 0; u < cap; u += kCheckEvery) {
+    const int n = cap - u < kCheckEvery ? cap - u : kCheckEvery;
     cudaGraphExec_t g = (c->use_graphs && n == kCheckEvery) ? chunk_graph(c, record) : nullptr;
     if (g != nullptr) {
       CK(cudaGraphLaunch(g, c->stream));
@@ -230,7 +232,9 @@ cmcs_status refine_sweeps(Ctx* c, const float* Bext) {
     CK(cudaMemsetAsync(c->task_active, 0, sizeof(int) * c->T, c->stream));
     CK(cudaMemsetAsync(c->counters, 0, sizeof(int) * 2, c->stream));
     CK(launch_cg_init(c, 1));
+    c->capsel = 1;                     // the sweeps' own step cap
     cmcs_status s = run_cg(c, 0);
+    c->capsel = 0;
     if (s != CMCS_OK) return s;
     CK(cudaMemsetAsync(c->counters + 1, 0, sizeof(int), c->stream));
     CK(launch_refine_update(c));
@@ -377,6 +381,7 @@ cmcs_status validate(const cmcs_config* cfg) {
   if (cfg->precond != 0 && cfg->precond != 1) return CMCS_ERR_INVALID_ARG;
   if (cfg->warm_start != 0 && cfg->warm_start != 1) return CMCS_ERR_INVALID_ARG;
   if (cfg->task_offset < 0 || cfg->T_total < 0) return CMCS_ERR_INVALID_ARG;
+  if (cfg->refine_steps < 0 || cfg->refine_steps > cfg->cg_max_iter) return CMCS_ERR_INVALID_ARG;
   const int64_t ttot = cfg->T_total == 0 ? cfg->T : cfg->T_total;
   if ((int64_t)cfg->task_offset + cfg->T > ttot) return CMCS_ERR_INVALID_ARG;
   if (ttot * cfg->C >= ((int64_t)1 << 31)) return CMCS_ERR_INVALID_ARG;   // probe counter word
@@ -426,6 +431,7 @@ cmcs_status create_ctx(const cmcs_config* cfg, const float* Phi, const float* y,
   c->S = cfg->T * c->R;
   c->Dp = (int)round_up(cfg->D, kDAlign);
   c->U = cfg->cg_max_iter;
+  c->refine_steps = cfg->refine_steps == 0 ? cfg->cg_max_iter : cfg->refine_steps;
   c->beta = cfg->beta;
   c->cg_tol = cfg->cg_tol;
   c->refine_tol = cfg->refine_tol;

@@ -87,9 +87,12 @@ struct Ctx {
   cudaStream_t side;   // runs the Lanczos eigen step while refinement proceeds on stream
   cudaEvent_t ev_fork, ev_join;
   // captured CG chunks: [record][profiling]
-  cudaGraphExec_t graph[2][2];
+  // captured CG chunks: [record][cap in force][profiling]
+  cudaGraphExec_t graph[2][2][2];
   int64_t graph_launches;  // kernels in one captured chunk
-  int graph_failed[2][2];  // capture of that variant failed: use direct launches
+  int graph_failed[2][2][2];  // capture of that variant failed: use direct launches
+  int refine_steps;        // step cap of the refinement sweeps' CG solves
+  int capsel;              // cap in force: 0 cg_max_iter (first solves), 1 refine_steps
   int capturing;           // a chunk is being captured
   int* stall_flag;         // device int, test hook of the bounded-wait path (cmcs_test_stall)
   int device;
@@ -254,6 +257,8 @@ cudaError_t tc_split_vectors(Ctx* c, const float* V);   // V -> dhi, dlo
 cudaError_t tc_refresh(Ctx* c);                         // recompute the BF16 copies of Phi
 
 inline int64_t round_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
+// CG step cap in force: cg_max_iter, or refine_steps during the refinement sweeps
+inline int cg_cap(const Ctx* c) { return c->capsel ? c->refine_steps : c->U; }
 int pick_tn(int R, int max_tn);
 int tc_set_stages(Ctx* c, int stages);   // returns the stages in force (0: not a TC context)
 int tc_max_stages(Ctx* c);

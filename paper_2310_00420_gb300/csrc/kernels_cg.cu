@@ -165,7 +165,7 @@ k_cg_update(float* __restrict__ x, float* __restrict__ r, float* __restrict__ d,
             const float* __restrict__ ad, const float* __restrict__ part,
             const float* __restrict__ alpha, int ndt, float* rr, const float* bb, int* steps,
             int* active, int* task_active, int* counters, float* gam, float* xih, int* psteps,
-            int record, int R, int K, int C, int Dp, int S, int U, float tol2,
+            int record, int R, int K, int C, int Dp, int S, int U, int cap, float tol2,
             __nv_bfloat16* dhi, __nv_bfloat16* dlo, const float* __restrict__ pminv) {
   __shared__ float sh[33];
   __shared__ float s_dad;
@@ -304,7 +304,7 @@ k_cg_update(float* __restrict__ x, float* __restrict__ r, float* __restrict__ d,
     steps[sys] = u + 1;
     rr[sys] = rr1;
     if (!isfinite(rr1)) atomicOr(&counters[2], 1);
-    const bool done = (rr1 <= tol2 * bb[sys]) || (rr1 == 0.f) || (u + 1 >= U) || !isfinite(rr1);
+    const bool done = (rr1 <= tol2 * bb[sys]) || (rr1 == 0.f) || (u + 1 >= cap) || !isfinite(rr1);
     if (done) {
       active[sys] = 0;
       atomicSub(&task_active[t], 1);
@@ -581,13 +581,13 @@ cudaError_t launch_cg_update(Ctx* c, int record) {
     k_cg_update<NV, true><<<c->S, 256, 0, c->stream>>>(                                          \
         c->x, c->r, c->d, c->ad, c->part, c->alpha, c->op == 1 ? c->dft_ndt : c->Dp / 128, c->rr, c->bb, c->steps,        \
         c->active, c->task_active, c->counters, c->gam, c->xi, c->psteps, record, c->R, c->K,    \
-        c->C, c->Dp, c->S, c->U, tol2, static_cast<__nv_bfloat16*>(c->dhi),                      \
+        c->C, c->Dp, c->S, c->U, cg_cap(c), tol2, static_cast<__nv_bfloat16*>(c->dhi),         \
         static_cast<__nv_bfloat16*>(c->dlo), c->precond ? c->pminv : nullptr);                   \
   else                                                                                           \
     k_cg_update<NV, false><<<c->S, 256, 0, c->stream>>>(                                         \
         c->x, c->r, c->d, c->ad, c->part, c->alpha, c->op == 1 ? c->dft_ndt : c->Dp / 128, c->rr, c->bb, c->steps,        \
         c->active, c->task_active, c->counters, c->gam, c->xi, c->psteps, record, c->R, c->K,    \
-        c->C, c->Dp, c->S, c->U, tol2, static_cast<__nv_bfloat16*>(c->dhi),                      \
+        c->C, c->Dp, c->S, c->U, cg_cap(c), tol2, static_cast<__nv_bfloat16*>(c->dhi),         \
         static_cast<__nv_bfloat16*>(c->dlo), c->precond ? c->pminv : nullptr)
   if (nv <= 1) { UPD(1); }
   else if (nv <= 2) { UPD(2); }

@@ -270,7 +270,7 @@ k_dft_cg_step(float* __restrict__ x, float* __restrict__ r, float* __restrict__ 
               const float* __restrict__ alpha, float* rr, const float* __restrict__ bb,
               int* steps, int* active, int* task_active, int* counters, float* gam, float* xih,
               int* psteps, unsigned long long* opcount, int record, int R, int K, int C, int Dp,
-              int D, int L, int npair, int U, float beta, float tol2,
+              int D, int L, int npair, int U, int cap, float beta, float tol2,
               const float* __restrict__ pminv) {
   extern __shared__ float2 Xf[];
   __shared__ float sh[33];
@@ -390,7 +390,7 @@ k_dft_cg_step(float* __restrict__ x, float* __restrict__ r, float* __restrict__ 
       steps[sys] = u + 1;
       rr[sys] = rr1;
       if (!isfinite(rr1)) atomicOr(&counters[2], 1);
-      const bool done = (rr1 <= tol2 * bb[sys]) || (rr1 == 0.f) || (u + 1 >= U) || !isfinite(rr1);
+      const bool done = (rr1 <= tol2 * bb[sys]) || (rr1 == 0.f) || (u + 1 >= cap) || !isfinite(rr1);
       if (done) {
         active[sys] = 0;
         atomicSub(&task_active[t], 1);
@@ -625,7 +625,7 @@ cudaError_t launch_dft_cg_step(Ctx* c, int record) {
       c->x, c->r, c->d, c->dft_mask, static_cast<const float2*>(c->dft_tw32), c->alpha, c->rr,
       c->bb, c->steps, c->active, c->task_active, c->counters, c->gam, c->xi, c->psteps,
       c->prof_on ? reinterpret_cast<unsigned long long*>(c->opcount) : nullptr, record, c->R,
-      c->K, c->C, c->Dp, c->D, c->dft_L, npair, c->U, (float)c->beta,
+      c->K, c->C, c->Dp, c->D, c->dft_L, npair, c->U, cg_cap(c), (float)c->beta,
       (float)(c->cg_tol * c->cg_tol), c->precond ? c->pminv : nullptr);
   return cudaGetLastError();
 }

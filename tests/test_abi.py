@@ -56,7 +56,7 @@ int main(void) {
   O(cmcs_config, alpha_max); O(cmcs_config, schedule); O(cmcs_config, graphs);
   O(cmcs_config, autotune); O(cmcs_config, learn_pi); O(cmcs_config, probe_share);
   O(cmcs_config, precond); O(cmcs_config, warm_start); O(cmcs_config, task_offset);
-  O(cmcs_config, T_total);
+  O(cmcs_config, T_total); O(cmcs_config, refine_steps);
   O(cmcs_summary, loglik); O(cmcs_summary, cg_steps_max); O(cmcs_summary, cg_steps_mean);
   O(cmcs_summary, cg_capped); O(cmcs_summary, refine_sweeps_max);
   O(cmcs_summary, refine_rel_max); O(cmcs_summary, min_margin);
@@ -94,6 +94,7 @@ def _cfg(**kw):
                       base["refine_tol"], base["alpha_min"], base["alpha_max"], 0, 0, 0)
     cfg.task_offset = base.get("task_offset", 0)
     cfg.T_total = base.get("T_total", 0)
+    cfg.refine_steps = base.get("refine_steps", 0)
     return cfg, (N, pi)
 
 
@@ -103,7 +104,8 @@ def _cfg(**kw):
                                  dict(refine_max=65), dict(alpha_min=0.0),
                                  dict(alpha_min=2.0, alpha_max=1.0), dict(task_offset=-1),
                                  dict(T_total=-1), dict(task_offset=1, T_total=2),
-                                 dict(task_offset=3)])
+                                 dict(task_offset=3), dict(refine_steps=-1),
+                                 dict(refine_steps=51)])
 def test_create_rejects_invalid_config_without_cuda(L, bad):
     cfg, keep = _cfg(**bad)
     phi = np.zeros((128, 32), np.float32)
