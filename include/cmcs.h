@@ -59,7 +59,13 @@ typedef enum {
   CMCS_BF16_REFINE = 1,
   /* operator on the tensor cores with Phi and the vectors both split into BF16 hi + lo pairs
      (three MMAs per step: about 16 significant bits per product, FP32 accumulation) */
-  CMCS_BF16X3 = 2
+  CMCS_BF16X3 = 2,
+  /* the first CG solve (the one whose coefficients feed the log-det estimate of Eqs. 9-11)
+     with Phi held in BF16 on the tensor cores, as CMCS_BF16_REFINE (half the bytes of Phi per
+     application); the refinement sweeps' inner solves with the CMCS_BF16X3 operator and the
+     compensated residual, so the returned solutions reach the same accuracy.  cmcs_apply with
+     accurate = 0 applies the CMCS_BF16X3 operator */
+  CMCS_BF16_MIXED = 3
 } cmcs_precision;
 
 typedef struct {
@@ -285,6 +291,10 @@ typedef struct {
   int64_t residual_calls;    /* compensated residual applications                            */
   double residual_ms;        /* their summed device time                                     */
   int64_t kernel_launches;   /* all kernels the library launched                             */
+  int64_t operator_calls_bf16; /* of the operator applications, those with Phi held as one
+                                  BF16 plane (CMCS_BF16_REFINE; the first solve of
+                                  CMCS_BF16_MIXED)                                            */
+  double operator_ms_bf16;   /* their summed device time                                     */
 } cmcs_profile_data;
 
 /* enable = 1 resets and starts the profile (events bracket every operator application, which

@@ -17,8 +17,9 @@ LIB_PATH = os.path.join(HERE, "_build", "libcmcs.so")
 OK, ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_NUMERIC, ERR_TIMEOUT, ERR_UNSUPPORTED = range(7)
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "NUMERIC", 5: "TIMEOUT",
                 6: "UNSUPPORTED"}
-FP32, BF16_REFINE, BF16X3 = 0, 1, 2
-PRECISIONS = {"fp32": FP32, "bf16": BF16_REFINE, "bf16_refine": BF16_REFINE, "bf16x3": BF16X3}
+FP32, BF16_REFINE, BF16X3, BF16_MIXED = 0, 1, 2, 3
+PRECISIONS = {"fp32": FP32, "bf16": BF16_REFINE, "bf16_refine": BF16_REFINE, "bf16x3": BF16X3,
+              "bf16_mixed": BF16_MIXED}
 
 (OUT_MU, OUT_S, OUT_Q, OUT_LOGDET, OUT_ELL, OUT_ALPHA, OUT_ASSIGN, OUT_RECON, OUT_STEPS,
  OUT_GAMMA, OUT_XI, OUT_B0, OUT_SWEEPS, OUT_RESID, OUT_PI) = range(15)
@@ -58,7 +59,8 @@ class ProfileData(ctypes.Structure):
     _fields_ = [("operator_calls", ctypes.c_int64), ("operator_ms", ctypes.c_double),
                 ("operator_flops", ctypes.c_double), ("operator_bytes", ctypes.c_double),
                 ("residual_calls", ctypes.c_int64), ("residual_ms", ctypes.c_double),
-                ("kernel_launches", ctypes.c_int64)]
+                ("kernel_launches", ctypes.c_int64), ("operator_calls_bf16", ctypes.c_int64),
+                ("operator_ms_bf16", ctypes.c_double)]
 
 
 class CmcsError(RuntimeError):

@@ -63,6 +63,7 @@ void free_ctx(Ctx* c) {
     cudaEventDestroy(c->res_ev[0]);
     cudaEventDestroy(c->res_ev[1]);
     free(c->prof_ev);
+    free(c->prof_tag);
   }
   if (c->hcounters) cudaFreeHost(c->hcounters);
   for (int r = 0; r < 2; ++r)
@@ -117,6 +118,7 @@ cudaError_t timed_operator(Ctx* c, int record) {
   if (ev) {
     cudaError_t er = cudaEventRecordWithFlags(c->prof_ev[2 * c->prof_nev], c->stream, flags);
     if (er != cudaSuccess) return er;
+    c->prof_tag[c->prof_nev] = (unsigned char)one_plane(c);
   }
   // Fourier with D in one CTA: the operator and the CG update are one kernel
   cudaError_t e = (c->op == 1 && !c->dft_large) ? launch_dft_cg_step(c, record)
@@ -125,7 +127,10 @@ cudaError_t timed_operator(Ctx* c, int record) {
     e = cudaEventRecordWithFlags(c->prof_ev[2 * c->prof_nev + 1], c->stream, flags);
     c->prof_nev++;
   }
-  if (c->prof_on) c->prof_calls++;
+  if (c->prof_on) {
+    c->prof_calls++;
+    if (one_plane(c)) c->prof_calls1++;
+  }
   return e;
 }
 
@@ -133,8 +138,10 @@ cudaError_t timed_operator(Ctx* c, int record) {
 void fold_events(Ctx* c) {
   for (int i = 0; i < c->prof_nev; ++i) {
     float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, c->prof_ev[2 * i], c->prof_ev[2 * i + 1]) == cudaSuccess)
+    if (cudaEventElapsedTime(&ms, c->prof_ev[2 * i], c->prof_ev[2 * i + 1]) == cudaSuccess) {
       c->prof_ms += ms;
+      if (c->prof_tag[i]) c->prof_ms1 += ms;
+    }
     else
       cudaGetLastError();     // a missing timing must not surface as a failure of the E-step
   }
@@ -199,6 +206,9 @@ cmcs_status run_cg(Ctx* c, int record) {
       if (c->prof_on) {
         c->prof_calls += n;
         c->prof_nev = n;
+        const int op1 = one_plane(c);
+        if (op1) c->prof_calls1 += n;
+        for (int i = 0; i < n; ++i) c->prof_tag[i] = (unsigned char)op1;
       }
     } else {
       c->prof_nev = 0;
@@ -264,9 +274,12 @@ cmcs_status estep(Ctx* c) {
     CK(launch_residual(c, c->xacc, nullptr, c->r, 1, 1));
     c->op_applies++;
   }
-  // first solve: Alg. 1 from x = 0 on b0 and the probes, recording gamma and xi
+  // first solve: Alg. 1 from x = 0 on b0 and the probes, recording gamma and xi (with
+  // CMCS_BF16_MIXED, Phi held as one BF16 plane)
   CK(launch_cg_init(c, 0, warm));
+  c->first_solve = 1;
   cmcs_status s = run_cg(c, 1);
+  c->first_solve = 0;
   if (s != CMCS_OK) return s;
   if (warm) CK(launch_add_means(c));  // mu = mu_prev + delta
   CK(cudaMemcpyAsync(c->steps0, c->steps, sizeof(int) * c->S, cudaMemcpyDeviceToDevice, c->stream));
@@ -358,7 +371,7 @@ cmcs_status validate(const cmcs_config* cfg) {
   if (cfg->cg_max_iter < 1 || cfg->cg_max_iter > 512) return CMCS_ERR_INVALID_ARG;
   if (!(cfg->cg_tol >= 0.0)) return CMCS_ERR_INVALID_ARG;
   if (cfg->precision != CMCS_FP32 && cfg->precision != CMCS_BF16_REFINE &&
-      cfg->precision != CMCS_BF16X3)
+      cfg->precision != CMCS_BF16X3 && cfg->precision != CMCS_BF16_MIXED)
     return CMCS_ERR_INVALID_ARG;
   if (cfg->refine_max < 0 || cfg->refine_max > 64) return CMCS_ERR_INVALID_ARG;
   if (!(cfg->refine_tol >= 0.0)) return CMCS_ERR_INVALID_ARG;
@@ -564,7 +577,7 @@ cmcs_status create_ctx(const cmcs_config* cfg, const float* Phi, const float* y,
   CKC(dalloc(&c->stats, 4));
   CKC(dalloc(&c->lltask, (size_t)T));
   CKC(dalloc(&c->mterms, (size_t)c->T_total * (size_t)c->mterm_w));
-  CKC(dalloc(&c->opcount, (size_t)T));
+  CKC(dalloc(&c->opcount, (size_t)(2 * T)));   // [all-plane applications][one-plane ones]
   CKC(dalloc(&c->dorow, (size_t)(T + 1)));
   CKC(dalloc(&c->stall_flag, 1));
   CKC(cudaMemsetAsync(c->stall_flag, 0, sizeof(int), c->stream));
@@ -576,7 +589,7 @@ cmcs_status create_ctx(const cmcs_config* cfg, const float* Phi, const float* y,
   CKC(dalloc(&c->adj_wm_lo, (size_t)(C * c->rows_total)));
   CKC(dalloc(&c->adj_dy, (size_t)c->hrow[c->T]));
   CKC(dalloc(&c->adj_da, (size_t)(C * Dp)));
-  CKC(cudaMemsetAsync(c->opcount, 0, sizeof(int64_t) * T, c->stream));
+  CKC(cudaMemsetAsync(c->opcount, 0, sizeof(int64_t) * 2 * T, c->stream));
 
   // zero everything that padding relies on
   if (!mask) CKC(cudaMemsetAsync(c->phi, 0, sizeof(float) * c->rows_total * Dp, c->stream));
@@ -630,7 +643,8 @@ cmcs_status create_ctx(const cmcs_config* cfg, const float* Phi, const float* y,
   CKC(launch_alpha_init(c));
   CKC(launch_sumlogalpha(c));
   CKC(launch_tconst_dev(c, c->dN));
-  if (c->precision == CMCS_BF16_REFINE || c->precision == CMCS_BF16X3) {
+  if (c->precision == CMCS_BF16_REFINE || c->precision == CMCS_BF16X3 ||
+      c->precision == CMCS_BF16_MIXED) {
     if (tc_create(c) != 0) {
       if (c->err[0] == 0) set_err(c, "BF16 tensor-core operator unavailable");
       return fail(CMCS_ERR_UNSUPPORTED);
@@ -696,15 +710,20 @@ cmcs_status cmcs_profile(cmcs_ctx* h, int enable) {
   if (enable) {
     if (!c->prof_ev) {
       c->prof_ev = static_cast<cudaEvent_t*>(calloc(2 * kProfEvents, sizeof(cudaEvent_t)));
+      c->prof_tag = static_cast<unsigned char*>(calloc(kProfEvents, 1));
+      if (!c->prof_tag) {
+        set_err(c, "host allocation failed");
+        return CMCS_ERR_OOM;
+      }
       if (!c->prof_ev) return CMCS_ERR_OOM;
       for (int i = 0; i < 2 * kProfEvents; ++i) CK(cudaEventCreate(&c->prof_ev[i]));
       CK(cudaEventCreate(&c->res_ev[0]));
       CK(cudaEventCreate(&c->res_ev[1]));
     }
-    CK(cudaMemsetAsync(c->opcount, 0, sizeof(int64_t) * c->T, c->stream));
+    CK(cudaMemsetAsync(c->opcount, 0, sizeof(int64_t) * 2 * c->T, c->stream));
     c->prof_nev = 0;
-    c->prof_calls = c->res_calls = c->launches = 0;
-    c->prof_ms = c->res_ms = 0.0;
+    c->prof_calls = c->res_calls = c->launches = c->prof_calls1 = 0;
+    c->prof_ms = c->res_ms = c->prof_ms1 = 0.0;
   }
   c->prof_on = enable;
   return sync_check(c);
@@ -713,12 +732,12 @@ cmcs_status cmcs_profile(cmcs_ctx* h, int enable) {
 cmcs_status cmcs_profile_read(const cmcs_ctx* hc, cmcs_profile_data* out) {
   if (!hc || !out) return CMCS_ERR_INVALID_ARG;
   Ctx* c = const_cast<Ctx*>(&hc->c);
-  std::vector<int64_t> cnt(c->T);
-  CK(cudaMemcpyAsync(cnt.data(), c->opcount, sizeof(int64_t) * c->T, cudaMemcpyDeviceToHost, c->stream));
+  std::vector<int64_t> cnt(2 * (size_t)c->T);
+  CK(cudaMemcpyAsync(cnt.data(), c->opcount, sizeof(int64_t) * 2 * c->T, cudaMemcpyDeviceToHost,
+                     c->stream));
   cmcs_status s = sync_check(c);
   if (s != CMCS_OK) return s;
   fold_events(c);
-  const double sphi = c->precision == CMCS_BF16_REFINE ? 2.0 : 4.0;
   double fl = 0.0, by = 0.0;
   for (int t = 0; t < c->T; ++t) {
     const double n = (double)c->hN[t], D = (double)c->D, R = (double)c->R;
@@ -734,8 +753,11 @@ cmcs_status cmcs_profile_read(const cmcs_ctx* hc, cmcs_profile_data* out) {
       fl += (double)cnt[t] * R * (5.0 * D * (double)c->dft_L + 12.0 * D);
       by += (double)cnt[t] * (24.0 * R * D + 4.0 * D);
     } else {
-      fl += (double)cnt[t] * 4.0 * n * D * R;
-      by += (double)cnt[t] * (sphi * n * D + 4.0 * R * (2.0 * D + 2.0 * n));
+      // Phi counted once per application: 4 bytes per element as FP32 or a BF16 pair (first
+      // T counters), 2 as one BF16 plane (second T counters)
+      const double a4 = (double)cnt[(size_t)t], a2 = (double)cnt[(size_t)c->T + t];
+      fl += (a4 + a2) * 4.0 * n * D * R;
+      by += a4 * 4.0 * n * D + a2 * 2.0 * n * D + (a4 + a2) * 4.0 * R * (2.0 * D + 2.0 * n);
     }
   }
   out->operator_calls = c->prof_calls;
@@ -745,6 +767,8 @@ cmcs_status cmcs_profile_read(const cmcs_ctx* hc, cmcs_profile_data* out) {
   out->residual_calls = c->res_calls;
   out->residual_ms = c->res_ms;
   out->kernel_launches = c->launches;
+  out->operator_calls_bf16 = c->prof_calls1;
+  out->operator_ms_bf16 = c->prof_ms1;
   return CMCS_OK;
 }
 

@@ -164,6 +164,10 @@ struct Ctx {
   int64_t* opcount;              // [T] device: operator applications per task
   int64_t prof_calls, res_calls, launches;
   double prof_ms, res_ms;
+  int64_t prof_calls1;           // applications with Phi as one BF16 plane, and their time
+  double prof_ms1;
+  unsigned char* prof_tag;       // [kProfEvents] the recorded application used one plane
+  int first_solve;               // the E-step's first solve (Lanczos coefficients) is running
   cudaEvent_t res_ev[2];
 
   // tensor-core operator (precision 1 and 2); null otherwise
@@ -259,6 +263,12 @@ cudaError_t tc_refresh(Ctx* c);                         // recompute the BF16 co
 inline int64_t round_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
 // CG step cap in force: cg_max_iter, or refine_steps during the refinement sweeps
 inline int cg_cap(const Ctx* c) { return c->capsel ? c->refine_steps : c->U; }
+// the tensor-core operator holds Phi as one BF16 plane now: always with CMCS_BF16_REFINE, in
+// the first solve with CMCS_BF16_MIXED
+inline int one_plane(const Ctx* c) {
+  return c->tc != nullptr && (c->precision == CMCS_BF16_REFINE ||
+                              (c->precision == CMCS_BF16_MIXED && c->first_solve));
+}
 int pick_tn(int R, int max_tn);
 int tc_set_stages(Ctx* c, int stages);   // returns the stages in force (0: not a TC context)
 int tc_max_stages(Ctx* c);

@@ -939,8 +939,13 @@ TcArgs base_args(Ctx* c, TcState* s) {
 template <int NA, int NB>
 cudaError_t run_passes(Ctx* c, TcState* s, const float* V, float* Z, int with_dots) {
   TcArgs a = base_args(c, s);
+  // the bytes one stage receives: NA planes of the Phi tile and NB of the vector tile (a
+  // CMCS_BF16_MIXED context runs NA = 1 in its first solve inside stages sized for NA = 2)
+  a.stage_bytes = NA * kBM * kBK * 2 + NB * s->Rpad * kBK * 2;
   a.task_active = with_dots ? c->task_active : nullptr;
-  a.opcount = c->prof_on ? reinterpret_cast<unsigned long long*>(c->opcount) : nullptr;
+  // per-task application counts: the first T for the BF16 pair, the next T for one plane
+  a.opcount = c->prof_on ? reinterpret_cast<unsigned long long*>(c->opcount) + (NA == 1 ? c->T : 0)
+                         : nullptr;
   a.V = V;
   a.Z = Z;
   a.raw = with_dots;             // the CG step: its update kernel completes A d and d^T A d
@@ -1054,7 +1059,7 @@ int tc_create(Ctx* c) {
   TcState* s = new (std::nothrow) TcState();
   if (!s) return 1;
   c->tc = s;
-  s->NA = c->precision == CMCS_BF16X3 ? 2 : 1;
+  s->NA = (c->precision == CMCS_BF16X3 || c->precision == CMCS_BF16_MIXED) ? 2 : 1;
   s->NB = 2;
   // columns: tiles of at most 256 (one MMA width), so two accumulators always fit in TMEM
   s->ncol = (c->R + 255) / 256;
@@ -1291,7 +1296,10 @@ cudaError_t tc_split_vectors(Ctx* c, const float* V) {
 cudaError_t tc_operator(Ctx* c, const float* V, float* Z, int with_dots) {
   TcState* s = static_cast<TcState*>(c->tc);
   if (!s) return cudaErrorNotSupported;
-  return s->NA == 2 ? run_passes<2, 2>(c, s, V, Z, with_dots) : run_passes<1, 2>(c, s, V, Z, with_dots);
+  // one BF16 plane of Phi (CMCS_BF16_REFINE; the first solve of CMCS_BF16_MIXED, whose storage
+  // keeps both planes) or the BF16 pair
+  return (s->NA == 2 && !one_plane(c)) ? run_passes<2, 2>(c, s, V, Z, with_dots)
+                                        : run_passes<1, 2>(c, s, V, Z, with_dots);
 }
 
 }  // namespace cmcs

@@ -49,7 +49,11 @@ def test_struct_layout_matches_header():
 #include "cmcs.h"
 #define O(s, f) printf(#s "." #f " %zu\n", offsetof(s, f))
 int main(void) {
-  printf("cmcs_config %zu\ncmcs_summary %zu\n", sizeof(cmcs_config), sizeof(cmcs_summary));
+  printf("cmcs_config %zu\ncmcs_summary %zu\ncmcs_profile_data %zu\n", sizeof(cmcs_config),
+         sizeof(cmcs_summary), sizeof(cmcs_profile_data));
+  O(cmcs_profile_data, operator_ms); O(cmcs_profile_data, operator_bytes);
+  O(cmcs_profile_data, residual_ms); O(cmcs_profile_data, kernel_launches);
+  O(cmcs_profile_data, operator_calls_bf16); O(cmcs_profile_data, operator_ms_bf16);
   O(cmcs_config, N); O(cmcs_config, beta); O(cmcs_config, pi); O(cmcs_config, cg_max_iter);
   O(cmcs_config, cg_tol); O(cmcs_config, seed); O(cmcs_config, precision);
   O(cmcs_config, refine_max); O(cmcs_config, refine_tol); O(cmcs_config, alpha_min);
@@ -74,10 +78,12 @@ int main(void) {
     got = dict(l.rsplit(" ", 1) for l in lines if l.strip())
     assert int(got["cmcs_config"]) == ctypes.sizeof(cmcs.Config)
     assert int(got["cmcs_summary"]) == ctypes.sizeof(cmcs.Summary)
+    assert int(got["cmcs_profile_data"]) == ctypes.sizeof(cmcs.ProfileData)
     for key, val in got.items():
         if "." in key:
             s, f = key.split(".")
-            cls = cmcs.Config if s == "cmcs_config" else cmcs.Summary
+            cls = {"cmcs_config": cmcs.Config, "cmcs_summary": cmcs.Summary,
+                   "cmcs_profile_data": cmcs.ProfileData}[s]
             assert getattr(cls, f).offset == int(val), key
 
 

@@ -77,8 +77,11 @@ def test_bf16_phi_refinement_divergence_is_detected(small):
     assert np.all(np.isfinite(mu))
 
 
-@pytest.mark.parametrize("precision,tol", [("bf16x3", 1e-4)])
+@pytest.mark.parametrize("precision,tol", [("bf16x3", 1e-4), ("bf16_mixed", 1e-4)])
 def test_tc_estep_parity(small, precision, tol):
+    """E-step on the tensor-core operator against the oracle's refined FP64 solves.  The mixed
+    path runs its first solve (the Lanczos coefficients) with Phi as one BF16 plane and refines
+    with the BF16 pair, so its solutions meet the same bound; nu is graded in replay."""
     P, Y = task_lists(small)
     alpha = synth.uniform_alpha(small.C, small.D, seed=3)
     with make_ctx(small, precision=precision, refine_max=16, refine_tol=1e-6) as ctx:
@@ -121,3 +124,58 @@ def test_operator_schedules_agree(precision, monkeypatch):
     assert np.array_equal(Z["0"], Z["31"])
     assert np.array_equal(Z["31"], Z["30"])          # pass 2 launched early or after pass 1
     np.testing.assert_allclose(Z["2"], Z["0"], rtol=1e-5, atol=1e-5 * np.abs(Z["0"]).max())
+
+
+def test_mixed_precision_em_parity(small):
+    """Ten EM iterations of the mixed path (first solves with Phi as one BF16 plane, BF16-pair
+    refinement) against the oracle's EM loop: the reduced-precision bar of 1e-3 for alpha and
+    the reconstructions, bit-exact assignments, responsibilities at 1e-4 except the named soft
+    task.  The profile counts the one-plane applications (the first solves)."""
+    from gpu_helpers import check_free_q
+    P, Y = task_lists(small)
+    with make_ctx(small, precision="bf16_mixed", refine_max=12, refine_tol=1e-6) as ctx:
+        ctx.profile(True)
+        ctx.em_iter(small.em_iters)
+        prof = ctx.profile_read()
+        a_g, q_g = ctx.read(cmcs.OUT_ALPHA), ctx.read(cmcs.OUT_Q)
+        asg, recon = ctx.read(cmcs.OUT_ASSIGN), ctx.read(cmcs.OUT_RECON)
+        summ = ctx.summary()
+    o = cofem.em(P, Y, small.pi, small.beta, small.em_iters, K=small.K, seed=small.seed,
+                 tol=small.cg_tol, max_iter=small.cg_max_iter, C=small.C, D=small.D,
+                 refine_tol=1e-12, refine_max=40)
+    assert summ["refine_diverged"] == 0
+    assert np.array_equal(asg, o["assign"])
+    check_free_q(q_g, o["last"]["q"], soft_tasks=(2,))      # task 2: q = (0.992, 0.008)
+    assert rel_err_rows(a_g, o["alpha"]).max() <= 1e-3
+    assert rel_err_rows(recon, o["recon"]).max() <= 1e-3
+    assert 0 < prof["operator_calls_bf16"] < prof["operator_calls"]
+
+
+@pytest.mark.parametrize("splitk", ["4", "2", "3"])
+def test_one_read_schedule_matches_oracle(splitk, monkeypatch):
+    """The one-read schedule (CMCS_TC_MODE=4: pass-1 row tiles split along K, reduced in split
+    order by the last unit, each task's pass-2 tiles following its pass-1 units in one launch)
+    against the oracle's operator, uneven N_t, and its E-step against the refined FP64 solves.
+    It is an evaluation switch, slower than the default two launches (Phi is not held in L2
+    long enough), kept under test."""
+    monkeypatch.setenv("CMCS_TC_MODE", "4")
+    monkeypatch.setenv("CMCS_TC_SPLITK", splitk)
+    wl = synth.make_workload("ragged", 4, 3, 640, (100, 700), nnz=8, sigma=0.01, K=9, seed=19)
+    P, Y = task_lists(wl)
+    R = wl.C * (wl.K + 1)
+    V = np.random.default_rng(24).standard_normal((wl.T, R, wl.D)).astype(np.float32)
+    with make_ctx(wl, precision="bf16x3", refine_max=12, refine_tol=1e-6) as ctx:
+        alpha = ctx.read(cmcs.OUT_ALPHA).astype(np.float64)
+        Z = ctx.apply(V)
+        assert np.array_equal(Z, ctx.apply(V))           # fixed summation order
+        ctx.estep()
+        mu, s_ = ctx.read(cmcs.OUT_MU), ctx.read(cmcs.OUT_S)
+    for t in range(wl.T):
+        for j in range(R):
+            c = j // (wl.K + 1)
+            ref = cofem.apply_A(P[t], wl.beta, alpha[c], V[t, j].astype(np.float64))
+            assert rel_err_rows(Z[t, j], ref) < 1e-4, (t, j)
+    o = cofem.cofem_estep(P, Y, alpha, wl.pi, wl.beta, wl.K, wl.seed, 0, wl.cg_tol,
+                          wl.cg_max_iter, refine_tol=1e-12, refine_max=40)
+    assert rel_err_rows(mu, o["mu"]).max() <= 1e-4
+    assert rel_err_rows(s_, o["s"]).max() <= 1e-4
