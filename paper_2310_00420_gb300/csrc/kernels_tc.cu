@@ -1225,15 +1225,17 @@ int tc_create(Ctx* c) {
     snprintf(c->err, sizeof(c->err), "tensor-core operator: tensor map encoding failed");
     return 1;
   }
-  cudaError_t e = s->NA == 2 ? set_smem_attr<1, 2, 2>(s->smem_bytes) : set_smem_attr<1, 1, 2>(s->smem_bytes);
-  if (e == cudaSuccess)
-    e = s->NA == 2 ? set_smem_attr<2, 2, 2>(s->smem_bytes) : set_smem_attr<2, 1, 2>(s->smem_bytes);
-  if (e == cudaSuccess)
-    e = s->NA == 2 ? set_smem_attr<3, 2, 2>(s->smem_bytes) : set_smem_attr<3, 1, 2>(s->smem_bytes);
-  if (e == cudaSuccess)
-    e = s->NA == 2 ? set_smem_attr<0, 2, 2>(s->smem_bytes) : set_smem_attr<0, 1, 2>(s->smem_bytes);
-  if (e == cudaSuccess)
-    e = s->NA == 2 ? set_smem_attr<4, 2, 2>(s->smem_bytes) : set_smem_attr<4, 1, 2>(s->smem_bytes);
+  // both plane counts: a CMCS_BF16_MIXED context (NA = 2 storage) also runs the one-plane kernels
+  cudaError_t e = set_smem_attr<1, 1, 2>(s->smem_bytes);
+  if (e == cudaSuccess) e = set_smem_attr<2, 1, 2>(s->smem_bytes);
+  if (e == cudaSuccess) e = set_smem_attr<3, 1, 2>(s->smem_bytes);
+  if (e == cudaSuccess) e = set_smem_attr<0, 1, 2>(s->smem_bytes);
+  if (e == cudaSuccess) e = set_smem_attr<4, 1, 2>(s->smem_bytes);
+  if (e == cudaSuccess && s->NA == 2) e = set_smem_attr<1, 2, 2>(s->smem_bytes);
+  if (e == cudaSuccess && s->NA == 2) e = set_smem_attr<2, 2, 2>(s->smem_bytes);
+  if (e == cudaSuccess && s->NA == 2) e = set_smem_attr<3, 2, 2>(s->smem_bytes);
+  if (e == cudaSuccess && s->NA == 2) e = set_smem_attr<0, 2, 2>(s->smem_bytes);
+  if (e == cudaSuccess && s->NA == 2) e = set_smem_attr<4, 2, 2>(s->smem_bytes);
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) {
     snprintf(c->err, sizeof(c->err), "tensor-core operator set-up: %s", cudaGetErrorString(e));

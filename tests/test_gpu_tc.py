@@ -151,21 +151,24 @@ def test_mixed_precision_em_parity(small):
     assert 0 < prof["operator_calls_bf16"] < prof["operator_calls"]
 
 
-@pytest.mark.parametrize("splitk", ["4", "2", "3"])
+@pytest.mark.parametrize("splitk", ["4", "2", "3", "default"])
 def test_one_read_schedule_matches_oracle(splitk, monkeypatch):
     """The one-read schedule (CMCS_TC_MODE=4: pass-1 row tiles split along K, reduced in split
     order by the last unit, each task's pass-2 tiles following its pass-1 units in one launch)
     against the oracle's operator, uneven N_t, and its E-step against the refined FP64 solves.
     It is an evaluation switch, slower than the default two launches (Phi is not held in L2
     long enough), kept under test."""
-    monkeypatch.setenv("CMCS_TC_MODE", "4")
-    monkeypatch.setenv("CMCS_TC_SPLITK", splitk)
+    if splitk != "default":                               # "default": the two-launch schedule
+        monkeypatch.setenv("CMCS_TC_MODE", "4")
+        monkeypatch.setenv("CMCS_TC_SPLITK", splitk)
     wl = synth.make_workload("ragged", 4, 3, 640, (100, 700), nnz=8, sigma=0.01, K=9, seed=19)
     P, Y = task_lists(wl)
     R = wl.C * (wl.K + 1)
     V = np.random.default_rng(24).standard_normal((wl.T, R, wl.D)).astype(np.float32)
+    a32 = synth.uniform_alpha(wl.C, wl.D, seed=8) + np.float32(0.05)
+    alpha = a32.astype(np.float64)
     with make_ctx(wl, precision="bf16x3", refine_max=12, refine_tol=1e-6) as ctx:
-        alpha = ctx.read(cmcs.OUT_ALPHA).astype(np.float64)
+        ctx.set_alpha(a32, 0)
         Z = ctx.apply(V)
         assert np.array_equal(Z, ctx.apply(V))           # fixed summation order
         ctx.estep()
