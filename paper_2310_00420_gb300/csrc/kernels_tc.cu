@@ -91,6 +91,7 @@ struct TcArgs {
   int* p1cnt;              // [row tiles] pass-1 units that reached their epilogue (zeroed per launch)
   int* p1st;               // [row tiles] pass-1 units whose partial is stored (zeroed per launch)
   int* wready;             // [row tiles] 1 once the row tile's W is reduced and stored
+  int pf;                  // prefetch the Phi tile this many k-blocks ahead into L2 (0: off)
 };
 
 // all tensor maps of the operator: a[pass-1][hi/lo] (pass 2 reads Phi MN-major), b[pass-1][hi/lo]
@@ -145,6 +146,12 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tm, in
       " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
       "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(smem_u32(bar))
       : "memory");
+}
+// prefetch a tile of the tensor into L2 (no shared memory, no barrier)
+__device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap* tm, int x, int y) {
+  asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(
+                   reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y)
+               : "memory");
 }
 __device__ __forceinline__ void tc_fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -560,6 +567,21 @@ k_tc(const __grid_constant__ TcMaps maps, const TcArgs p) {
               tma_load_2d(ad, &maps.a[0][h], kcol, ti.a_row, &full[s]);
             }
           }
+          // the Phi tile pf k-blocks ahead into L2, so that its load then comes from L2
+          if (p.pf > 0 && kb + p.pf < ti.nk) {
+            const int kpf = kcol + p.pf * kBK;
+#pragma unroll
+            for (int h = 0; h < NA; ++h) {
+              if (a_mn) {
+                tma_prefetch_2d(&maps.a[1][h], ti.a_row, kpf);
+                tma_prefetch_2d(&maps.a[1][h], ti.a_row + 64, kpf);
+              } else if (PASS == 2 || (PASS == 0 && pi == 1)) {
+                tma_prefetch_2d(&maps.a[1][h], kpf, ti.a_row);
+              } else {
+                tma_prefetch_2d(&maps.a[0][h], kpf, ti.a_row);
+              }
+            }
+          }
           // constant indices into the parameter block keep the maps in parameter space
           uint8_t* bst = st + NA * a_bytes;
           const int brow = ti.b_row + ti.col0;
@@ -865,6 +887,7 @@ struct TcState {
   uint32_t mn_lbo, mn_sbo;
   int *tile_code, *tile_task2, *n1, *p1done;   // fused tile list; per-task counts [T] + tile counter
   int early;                                   // mode 3: pass 2 launched programmatically
+  int pf;                                      // L2 prefetch distance of the Phi tiles (k-blocks)
   std::vector<int> tstart;                     // first fused tile of each task (host)
   // mode 4 (one read of Phi per application): unit list, split-K partials and counters
   int *u_code, *u_task, nunits, splitk, nslot;
@@ -933,6 +956,7 @@ TcArgs base_args(Ctx* c, TcState* s) {
   a.beta = (float)c->beta;
   a.status = &c->counters[2];
   a.stall = c->stall_flag;
+  a.pf = s->pf;
   return a;
 }
 
@@ -1097,6 +1121,9 @@ int tc_create(Ctx* c) {
     if (s->mode == 4 && s->ncol != 1) s->mode = 3;
     const char* ev = getenv("CMCS_TC_EARLY");    // evaluation switch: 0 launches pass 2 plainly
     s->early = ev ? atoi(ev) != 0 : 1;
+    const char* pv = getenv("CMCS_TC_PREFETCH"); // evaluation switch: L2 prefetch distance
+    s->pf = pv ? atoi(pv) : 0;
+    if (s->pf < 0) s->pf = 0;
   }
   s->mn_lbo = 8192;      // 64-column halves of the MN-major A tile are 8 KiB apart
   s->mn_sbo = 1024;      // groups of 8 k rows are 1 KiB apart

@@ -161,7 +161,8 @@ def test_one_read_schedule_matches_oracle(splitk, monkeypatch):
     if splitk != "default":                               # "default": the two-launch schedule
         monkeypatch.setenv("CMCS_TC_MODE", "4")
         monkeypatch.setenv("CMCS_TC_SPLITK", splitk)
-    wl = synth.make_workload("ragged", 4, 3, 640, (100, 700), nnz=8, sigma=0.01, K=9, seed=19)
+    # N_t well below D, as in the paper's workloads (the BF16-pair refinement contracts)
+    wl = synth.make_workload("ragged", 4, 3, 640, (60, 300), nnz=8, sigma=0.01, K=9, seed=19)
     P, Y = task_lists(wl)
     R = wl.C * (wl.K + 1)
     V = np.random.default_rng(24).standard_normal((wl.T, R, wl.D)).astype(np.float32)
