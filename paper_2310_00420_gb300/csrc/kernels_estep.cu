@@ -31,41 +31,45 @@ __device__ __forceinline__ Tv block_sum256(Tv v, Tv* sh) {
 // unreduced block (Golub & Van Loan, "Matrix Computations", Sec. 8.3), accumulating only the
 // first row of the rotation product (the Golub-Welsch observation).  Returns
 // sum_u S_{u,1}^2 log lambda_u; sets *fail if the sweep cap is hit or an eigenvalue is <= 0.
-template <int UB>
+// The diagonal a, the off-diagonal b and the first row z of the rotations live in shared
+// memory at stride `st` (the thread's own column of its block's arrays): the QR sweep is a
+// chain of dependent FP64 operations, and shared memory keeps each step's loads short where
+// per-thread local arrays of this size would fall out of L1.
 __device__ double lanczos_log_quad(const float* __restrict__ g, const float* __restrict__ xi,
-                                   int U, int* fail) {
-  double a[UB], b[UB], z[UB];
+                                   int U, double* a, double* b, double* z, int st, int* fail) {
   for (int i = 0; i < U; ++i) {
     const double gi = (double)g[i];
-    a[i] = 1.0 / gi + (i > 0 ? (double)xi[i - 1] / (double)g[i - 1] : 0.0);
-    b[i] = (i + 1 < U) ? sqrt((double)xi[i]) / gi : 0.0;
-    z[i] = (i == 0) ? 1.0 : 0.0;
+    a[i * st] = 1.0 / gi + (i > 0 ? (double)xi[i - 1] / (double)g[i - 1] : 0.0);
+    b[i * st] = (i + 1 < U) ? sqrt((double)xi[i]) / gi : 0.0;
+    z[i * st] = (i == 0) ? 1.0 : 0.0;
   }
   const double eps = DBL_EPSILON;
   int m = U - 1;
   int iters = 0;
   const int max_iters = 60 * U + 60;
   while (m > 0) {
-    if (fabs(b[m - 1]) <= eps * (fabs(a[m - 1]) + fabs(a[m]))) {
-      b[m - 1] = 0.0;
+    if (fabs(b[(m - 1) * st]) <= eps * (fabs(a[(m - 1) * st]) + fabs(a[m * st]))) {
+      b[(m - 1) * st] = 0.0;
       --m;
       continue;
     }
     int l = m - 1;
-    while (l > 0 && fabs(b[l - 1]) > eps * (fabs(a[l - 1]) + fabs(a[l]))) --l;
-    if (l > 0) b[l - 1] = 0.0;
+    while (l > 0 && fabs(b[(l - 1) * st]) > eps * (fabs(a[(l - 1) * st]) + fabs(a[l * st]))) --l;
+    if (l > 0) b[(l - 1) * st] = 0.0;
     if (++iters > max_iters) {
       *fail = 1;
       break;
     }
     // Wilkinson shift: eigenvalue of the trailing 2x2 block closer to a[m]
-    const double dd = 0.5 * (a[m - 1] - a[m]);
-    const double bm = b[m - 1];
+    const double dd = 0.5 * (a[(m - 1) * st] - a[m * st]);
+    const double bm = b[(m - 1) * st];
     // entries of these matrices lie within about 1e-12 .. 1e12, far from overflow, so the
     // plain square root replaces the (slower) scaled hypot
     const double den = dd + copysign(sqrt(dd * dd + bm * bm), dd);
-    const double mu = a[m] - bm * bm / den;
-    double x = a[l] - mu, y = b[l];
+    const double mu = a[m * st] - bm * bm / den;
+    double x = a[l * st] - mu, y = b[l * st];
+    // the chase carries a[k], b[k] and z[k] in registers from one rotation to the next
+    double ak = a[l * st], bk = b[l * st], zk = z[l * st];
     for (int k = l; k < m; ++k) {
       const double r = sqrt(x * x + y * y);
       double c = 1.0, s = 0.0;
@@ -73,39 +77,54 @@ __device__ double lanczos_log_quad(const float* __restrict__ g, const float* __r
         c = x / r;
         s = -y / r;
       }
-      if (k > l) b[k - 1] = r;
-      const double ak = a[k], ak1 = a[k + 1], bk = b[k];
-      a[k] = c * c * ak - 2.0 * c * s * bk + s * s * ak1;
-      a[k + 1] = s * s * ak + 2.0 * c * s * bk + c * c * ak1;
-      b[k] = c * s * (ak - ak1) + (c * c - s * s) * bk;
+      if (k > l) b[(k - 1) * st] = r;
+      const double ak1 = a[(k + 1) * st];
+      const double nak = c * c * ak - 2.0 * c * s * bk + s * s * ak1;
+      const double nak1 = s * s * ak + 2.0 * c * s * bk + c * c * ak1;
+      const double nbk = c * s * (ak - ak1) + (c * c - s * s) * bk;
+      a[k * st] = nak;
+      const double zk1 = z[(k + 1) * st];
+      z[k * st] = c * zk - s * zk1;
+      zk = s * zk + c * zk1;
+      ak = nak1;
+      bk = nbk;
       if (k + 1 < m) {
-        const double bulge = -s * b[k + 1];
-        b[k + 1] = c * b[k + 1];
-        x = b[k];
+        const double bk1 = b[(k + 1) * st];
+        const double bulge = -s * bk1;
+        x = nbk;
         y = bulge;
+        b[k * st] = nbk;
+        bk = c * bk1;                      // b[k + 1] for the next rotation
+      } else {
+        b[k * st] = nbk;
       }
-      const double zk = z[k], zk1 = z[k + 1];
-      z[k] = c * zk - s * zk1;
-      z[k + 1] = s * zk + c * zk1;
     }
+    a[m * st] = ak;
+    z[m * st] = zk;
   }
   double sum = 0.0;
   for (int i = 0; i < U; ++i) {
-    if (!(a[i] > 0.0)) *fail = 1;
-    sum += z[i] * z[i] * log(a[i]);
+    const double ai = a[i * st], zi = z[i * st];
+    if (!(ai > 0.0)) *fail = 1;
+    sum += zi * zi * log(ai);
   }
   return sum;
 }
 
 }  // namespace
 
-constexpr int kQuadThreads = 32;   // one serial eigen solve per thread: spread over all SMs
+// threads per block of k_quad for matrices up to UB: their arrays (3 UB doubles each) in at
+// most 192 KiB of shared memory
+template <int UB>
+constexpr int quad_threads() { return UB <= 256 ? 32 : 16; }
 
 template <int UB>
-__global__ void __launch_bounds__(kQuadThreads)
+__global__ void __launch_bounds__(quad_threads<UB>())
 k_quad(const float* __restrict__ gam, const float* __restrict__ xi, const int* __restrict__ steps,
        int nsys, int ld, double* out, int* status) {
-  const int i = blockIdx.x * kQuadThreads + threadIdx.x;
+  extern __shared__ double qsm[];                 // [3][UB][threads]
+  constexpr int NT = quad_threads<UB>();
+  const int i = blockIdx.x * NT + threadIdx.x;
   if (i >= nsys) return;
   int U = steps[i];
   if (U <= 0) {
@@ -118,21 +137,37 @@ k_quad(const float* __restrict__ gam, const float* __restrict__ xi, const int* _
     return;
   }
   int fail = 0;
-  out[i] = lanczos_log_quad<UB>(gam + (int64_t)i * ld, xi + (int64_t)i * ld, U, &fail);
+  double* a = qsm + threadIdx.x;
+  double* b = a + UB * NT;
+  double* z = b + UB * NT;
+  out[i] = lanczos_log_quad(gam + (int64_t)i * ld, xi + (int64_t)i * ld, U, a, b, z, NT, &fail);
   if (fail) atomicOr(status, 1);
+}
+
+template <int UB>
+cudaError_t launch_quad(const float* gam, const float* xi, const int* steps, int nsys, int ld,
+                        double* out, int* status, cudaStream_t st) {
+  constexpr int NT = quad_threads<UB>();
+  const size_t smem = sizeof(double) * 3 * UB * NT;
+  static bool attr = false;                       // set once per kernel instance
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_quad<UB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  k_quad<UB><<<(nsys + NT - 1) / NT, NT, smem, st>>>(gam, xi, steps, nsys, ld, out, status);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_quadrature(const float* gam, const float* xi, const int* steps, int nsys,
                               int ld, double* out, int* status, cudaStream_t st) {
   if (nsys <= 0) return cudaSuccess;
-  const int blocks = (nsys + kQuadThreads - 1) / kQuadThreads;
-  const int nt = kQuadThreads;
-  if (ld <= 64) k_quad<64><<<blocks, nt, 0, st>>>(gam, xi, steps, nsys, ld, out, status);
-  else if (ld <= 128) k_quad<128><<<blocks, nt, 0, st>>>(gam, xi, steps, nsys, ld, out, status);
-  else if (ld <= 256) k_quad<256><<<blocks, nt, 0, st>>>(gam, xi, steps, nsys, ld, out, status);
-  else if (ld <= 512) k_quad<512><<<blocks, nt, 0, st>>>(gam, xi, steps, nsys, ld, out, status);
-  else return cudaErrorInvalidValue;
-  return cudaGetLastError();
+  if (ld <= 64) return launch_quad<64>(gam, xi, steps, nsys, ld, out, status, st);
+  if (ld <= 128) return launch_quad<128>(gam, xi, steps, nsys, ld, out, status, st);
+  if (ld <= 256) return launch_quad<256>(gam, xi, steps, nsys, ld, out, status, st);
+  if (ld <= 512) return launch_quad<512>(gam, xi, steps, nsys, ld, out, status, st);
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_quadrature_ctx(Ctx* c, cudaStream_t st) {
