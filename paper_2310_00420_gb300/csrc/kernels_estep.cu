@@ -2,6 +2,7 @@
 // by an FP64 log-sum-exp (Eq. 3), hard assignments (Alg. 2), and the alpha update (Eq. 5).
 #include <float.h>
 #include <math.h>
+#include <stdlib.h>
 
 #include "cmcs_internal.cuh"
 
@@ -71,11 +72,19 @@ __device__ double lanczos_log_quad(const float* __restrict__ g, const float* __r
     // the chase carries a[k], b[k] and z[k] in registers from one rotation to the next
     double ak = a[l * st], bk = b[l * st], zk = z[l * st];
     for (int k = l; k < m; ++k) {
-      const double r = sqrt(x * x + y * y);
-      double c = 1.0, s = 0.0;
-      if (r > 0.0) {
-        c = x / r;
-        s = -y / r;
+      // r = sqrt(x^2 + y^2) and 1 / r: a single-precision reciprocal square root refined by two
+      // Newton-Raphson steps for 1 / sqrt(q) (each y <- y (3 - q y^2) / 2 doubles the correct
+      // bits: 24 -> 48 -> beyond double precision), in place of a square root and two
+      // divisions per rotation
+      const double q = x * x + y * y;
+      double c = 1.0, s = 0.0, r = 0.0;
+      if (q > 0.0) {
+        double ir = (double)rsqrtf((float)q);
+        ir = ir * (1.5 - 0.5 * q * ir * ir);
+        ir = ir * (1.5 - 0.5 * q * ir * ir);
+        r = q * ir;
+        c = x * ir;
+        s = -y * ir;
       }
       if (k > l) b[(k - 1) * st] = r;
       const double ak1 = a[(k + 1) * st];
@@ -113,17 +122,13 @@ __device__ double lanczos_log_quad(const float* __restrict__ g, const float* __r
 
 }  // namespace
 
-// threads per block of k_quad for matrices up to UB: their arrays (3 UB doubles each) in at
-// most 192 KiB of shared memory
-template <int UB>
-constexpr int quad_threads() { return UB <= 256 ? 32 : 16; }
-
-template <int UB>
-__global__ void __launch_bounds__(quad_threads<UB>())
+// k_quad: one Lanczos matrix per thread, NT threads per block, arrays of 3 UB doubles per
+// thread in shared memory
+template <int UB, int NT>
+__global__ void __launch_bounds__(NT)
 k_quad(const float* __restrict__ gam, const float* __restrict__ xi, const int* __restrict__ steps,
        int nsys, int ld, double* out, int* status) {
-  extern __shared__ double qsm[];                 // [3][UB][threads]
-  constexpr int NT = quad_threads<UB>();
+  extern __shared__ double qsm[];                 // [3][UB][NT]
   const int i = blockIdx.x * NT + threadIdx.x;
   if (i >= nsys) return;
   int U = steps[i];
@@ -144,30 +149,45 @@ k_quad(const float* __restrict__ gam, const float* __restrict__ xi, const int* _
   if (fail) atomicOr(status, 1);
 }
 
-template <int UB>
+template <int UB, int NT>
 cudaError_t launch_quad(const float* gam, const float* xi, const int* steps, int nsys, int ld,
                         double* out, int* status, cudaStream_t st) {
-  constexpr int NT = quad_threads<UB>();
   const size_t smem = sizeof(double) * 3 * UB * NT;
   static bool attr = false;                       // set once per kernel instance
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_quad<UB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_quad<UB, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  k_quad<UB><<<(nsys + NT - 1) / NT, NT, smem, st>>>(gam, xi, steps, nsys, ld, out, status);
+  k_quad<UB, NT><<<(nsys + NT - 1) / NT, NT, smem, st>>>(gam, xi, steps, nsys, ld, out, status);
   return cudaGetLastError();
+}
+
+template <int NT>
+cudaError_t launch_quad_nt(const float* gam, const float* xi, const int* steps, int nsys, int ld,
+                           double* out, int* status, cudaStream_t st) {
+  if (ld <= 64) return launch_quad<64, NT>(gam, xi, steps, nsys, ld, out, status, st);
+  if (ld <= 128) return launch_quad<128, NT>(gam, xi, steps, nsys, ld, out, status, st);
+  if (ld <= 256) return launch_quad<256, NT>(gam, xi, steps, nsys, ld, out, status, st);
+  if (ld <= 512) return launch_quad<512, (NT < 16 ? NT : 16)>(gam, xi, steps, nsys, ld, out, status, st);
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_quadrature(const float* gam, const float* xi, const int* steps, int nsys,
                               int ld, double* out, int* status, cudaStream_t st) {
   if (nsys <= 0) return cudaSuccess;
-  if (ld <= 64) return launch_quad<64>(gam, xi, steps, nsys, ld, out, status, st);
-  if (ld <= 128) return launch_quad<128>(gam, xi, steps, nsys, ld, out, status, st);
-  if (ld <= 256) return launch_quad<256>(gam, xi, steps, nsys, ld, out, status, st);
-  if (ld <= 512) return launch_quad<512>(gam, xi, steps, nsys, ld, out, status, st);
-  return cudaErrorInvalidValue;
+  static int nt = -1;                             // evaluation switch CMCS_QUAD_NT: 4, 8, 16, 32
+  if (nt < 0) {
+    const char* v = getenv("CMCS_QUAD_NT");
+    nt = v ? atoi(v) : 32;
+  }
+  switch (nt) {
+    case 4: return launch_quad_nt<4>(gam, xi, steps, nsys, ld, out, status, st);
+    case 16: return launch_quad_nt<16>(gam, xi, steps, nsys, ld, out, status, st);
+    case 8: return launch_quad_nt<8>(gam, xi, steps, nsys, ld, out, status, st);
+    default: return launch_quad_nt<32>(gam, xi, steps, nsys, ld, out, status, st);
+  }
 }
 
 cudaError_t launch_quadrature_ctx(Ctx* c, cudaStream_t st) {
