@@ -564,6 +564,22 @@ def run_ours(a):
                     "frac": op_tflops / pk_t, **common}
         roof["hbm_gbs_achieved"] = op_gbs
 
+    # the Lanczos eigen step (Eqs. 9-10) alone, on this E-step's own probe coefficients, through
+    # the stand-alone entry point (it runs on a side stream inside the E-step)
+    quad_ms = None
+    if not fourier:
+        gam = ctx.read(cmcs.OUT_GAMMA, device=True).reshape(-1, wl.cg_max_iter)
+        xis = ctx.read(cmcs.OUT_XI, device=True).reshape(-1, wl.cg_max_iter)
+        stp = ctx.read(cmcs.OUT_STEPS, device=True)[:, :, 1:].contiguous().reshape(-1)
+        cmcs.lanczos_quadrature(gam, xis, stp)
+        q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        q0.record()
+        for _ in range(3):
+            cmcs.lanczos_quadrature(gam, xis, stp)
+        q1.record()
+        torch.cuda.synchronize()
+        quad_ms = q0.elapsed_time(q1) / 3
+
     # error vs the FP64 oracle on one sampled (task, cluster) pair, and the CPU baseline
     cpu = None
     err = None
@@ -724,6 +740,7 @@ def run_ours(a):
                 "operator_share": prof["operator_ms"] / ms if ms else None,
                 "residual_ms_per_step": prof["residual_ms"] / a.steps,
                 "operator_applies_per_step": prof["operator_calls"] / a.steps,
+                "lanczos_quadrature_ms": quad_ms,
                 "roofline": roof, "cpu_baseline": cpu, "err_vs_fp64": err, "e2e": e2e,
                 "clocks": clk, "gpu_launches": prof["kernel_launches"],
                 "fp32_form": fp32_form, "bf16_mixed_form": mixed_form,
