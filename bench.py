@@ -66,7 +66,7 @@ def _args():
     ap.add_argument("--no-graphs", action="store_true")
     ap.add_argument("--refine-max", type=int, default=8)
     ap.add_argument("--refine-tol", type=float, default=1e-5)
-    ap.add_argument("--refine-steps", type=int, default=0,
+    ap.add_argument("--refine-steps", type=int, default=70,
                     help="step cap of the refinement sweeps' CG solves (0: the first solve's)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -363,7 +363,7 @@ def precision_leg(a, peaks) -> dict:
     wl = _workload("precision", 0)
     kw = dict(C=wl.C, K=wl.K, beta=wl.beta, pi=wl.pi, cg_max_iter=wl.cg_max_iter,
               cg_tol=wl.cg_tol, seed=wl.seed, refine_max=a.refine_max, refine_tol=a.refine_tol,
-              refine_steps=a.refine_steps)
+              refine_steps=0)
     Phi_d = torch.from_numpy(wl.Phi).cuda()
     y_d = torch.from_numpy(wl.y).cuda()
     out = {"workload": f"{wl.name} T={wl.T} C={wl.C} D={wl.D} N={int(wl.N[0])} K={wl.K} "
@@ -424,7 +424,7 @@ def batching_leg(a) -> dict:
     wl = _workload("batching", 0)
     kw = dict(C=wl.C, K=wl.K, beta=wl.beta, pi=wl.pi, cg_max_iter=wl.cg_max_iter,
               cg_tol=wl.cg_tol, seed=wl.seed, refine_max=a.refine_max, refine_tol=a.refine_tol,
-              refine_steps=a.refine_steps, precision="bf16x3")
+              refine_steps=0, precision="bf16x3")
     Phi_d = torch.from_numpy(wl.Phi).cuda()
     y_d = torch.from_numpy(wl.y).cuda()
     out = {"workload": f"{wl.name} T={wl.T} C={wl.C} D={wl.D} N_t in [{int(wl.N.min())}, "
