@@ -106,7 +106,8 @@ cmcs_status read_counters(Ctx* c) {
   return sync_check(c);
 }
 
-constexpr int kCheckEvery = 8;   // CG steps between host polls of the active-system count
+// CG steps between host polls of the active-system count (evaluation switch CMCS_CG_CHUNK)
+constexpr int kCheckEvery = 8;
 static_assert(kCheckEvery <= kProfEvents, "events of one chunk");
 
 // operator application, bracketed by profiling events when enabled (pair prof_nev of the
@@ -158,7 +159,7 @@ cmcs_status cg_steps_direct(Ctx* c, int record, int n) {
   return CMCS_OK;
 }
 
-// the graph replaying kCheckEvery CG steps, captured on first use
+// the graph replaying c->chunk CG steps, captured on first use
 cudaGraphExec_t chunk_graph(Ctx* c, int record) {
   cudaGraphExec_t& g = c->graph[record][c->capsel][c->prof_on];
   if (g != nullptr || c->graph_failed[record][c->capsel][c->prof_on]) return g;
@@ -167,7 +168,7 @@ cudaGraphExec_t chunk_graph(Ctx* c, int record) {
   if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return nullptr;
   c->prof_nev = 0;
   c->capturing = 1;
-  cmcs_status s = cg_steps_direct(c, record, kCheckEvery);
+  cmcs_status s = cg_steps_direct(c, record, c->chunk);
   c->capturing = 0;
   cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
   c->graph_launches = c->launches - l0;
@@ -193,12 +194,12 @@ cudaGraphExec_t chunk_graph(Ctx* c, int record) {
 }
 
 // Alg. 1 for every active system until all have stopped (or the step cap in force), in
-// chunks of kCheckEvery steps between host polls of the number of active systems
+// chunks of c->chunk steps between host polls of the number of active systems
 cmcs_status run_cg(Ctx* c, int record) {
   const int cap = cg_cap(c);
-  for (int u = 0; u < cap; u += kCheckEvery) {
-    const int n = cap - u < kCheckEvery ? cap - u : kCheckEvery;
-    cudaGraphExec_t g = (c->use_graphs && n == kCheckEvery) ? chunk_graph(c, record) : nullptr;
+  for (int u = 0; u < cap; u += c->chunk) {
+    const int n = cap - u < c->chunk ? cap - u : c->chunk;
+    cudaGraphExec_t g = (c->use_graphs && n == c->chunk) ? chunk_graph(c, record) : nullptr;
     if (g != nullptr) {
       CK(cudaGraphLaunch(g, c->stream));
       c->launches += c->graph_launches;
@@ -444,6 +445,11 @@ cmcs_status create_ctx(const cmcs_config* cfg, const float* Phi, const float* y,
   c->S = cfg->T * c->R;
   c->Dp = (int)round_up(cfg->D, kDAlign);
   c->U = cfg->cg_max_iter;
+  {
+    const char* cv = getenv("CMCS_CG_CHUNK");
+    const int ch = cv ? atoi(cv) : kCheckEvery;
+    c->chunk = (ch >= 1 && ch <= 64) ? ch : kCheckEvery;
+  }
   c->refine_steps = cfg->refine_steps == 0 ? cfg->cg_max_iter : cfg->refine_steps;
   c->beta = cfg->beta;
   c->cg_tol = cfg->cg_tol;

@@ -92,6 +92,7 @@ struct Ctx {
   int64_t graph_launches;  // kernels in one captured chunk
   int graph_failed[2][2][2];  // capture of that variant failed: use direct launches
   int refine_steps;        // step cap of the refinement sweeps' CG solves
+  int chunk;               // CG steps per host poll (and per captured graph)
   int capsel;              // cap in force: 0 cg_max_iter (first solves), 1 refine_steps
   int capturing;           // a chunk is being captured
   int* stall_flag;         // device int, test hook of the bounded-wait path (cmcs_test_stall)
