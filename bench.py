@@ -180,8 +180,8 @@ def aggregate(ms_local: float, steps: int, world: int, device: str = "cuda", uni
 # k_tc<3>) on plain-scale with BF16X3, from one ncu capture on the 8-task slice scaled by
 # 32 / 8 tasks, keyed to the SHA-256 prefix of the kernel source it was taken on: once that
 # source changes the figure no longer describes the kernel and traffic is reported as null.
-_TRAFFIC = {"kernels_tc.cu": "acb0f4231cdbee5b",
-            "plain-scale/bf16x3": 4 * ((571.656704 + 3.679744) + (548.578048 + 25.114368)) * 1e6}
+_TRAFFIC = {"kernels_tc.cu": "bb5dfc6409c729ac",
+            "plain-scale/bf16x3": 4 * ((571.582976 + 0.119552) + (548.570368 + 24.364544)) * 1e6}
 
 
 def _source_sha(name: str) -> str:
