@@ -18,6 +18,7 @@
 // passes (natural order in and out), twiddles from tables evaluated in FP64 on the host.
 // The CG operator runs in FP32, the residual and b0 in FP64.  No CTA waits on another.
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <new>
@@ -74,7 +75,8 @@ struct FsPlan {
   int n1, n2;
   int nb;     // columns i2 per CTA in the FP64 column passes (divides n2, a power of two)
   int nb32;   // the same for the FP32 column passes
-  int nbr;    // rows k1 per CTA in the row pass (the last block may be partial)
+  int nbr;    // rows k1 per CTA in the FP64 row pass (the last block may be partial)
+  int nbr32;  // the same for the FP32 row pass
   uint64_t mn2;   // reciprocal of n2
   FsRadix p1, p2;
 };
@@ -267,20 +269,21 @@ k_fs_rows(CT* __restrict__ Y, const CT* __restrict__ spec, const CT* __restrict_
           const int* __restrict__ flags, const int* __restrict__ task_active) {
   extern __shared__ __align__(16) unsigned char fs_sm[];
   const int ls = pl.n2 + 1;
+  const int nbr = sizeof(CT) == sizeof(float2) ? pl.nbr32 : pl.nbr;
   CT* A = reinterpret_cast<CT*>(fs_sm);
-  CT* B = A + pl.nbr * ls;
-  CT* tw = B + pl.nbr * ls;
+  CT* B = A + nbr * ls;
+  CT* tw = B + nbr * ls;
   CT* tw3 = tw + pl.n2;
   const int pi = blockIdx.x;
   const FsSys q = fs_sys(pp, pi, flags);
   if (task_active != nullptr && task_active[q.t] == 0) return;     // block-uniform
   if (!q.on1 && !q.on2) return;
   fs_stage_tables(tw, tw3, tab2, pl.n2, tabD, pp.D);
-  const int r0 = blockIdx.y * pl.nbr;
+  const int r0 = blockIdx.y * nbr;
   CT* Yp = Y + (int64_t)pi * pp.D;
   // the last row block may run past n1: its extra rows transform zeros and are not stored
 #pragma unroll 4
-  for (int idx = threadIdx.x; idx < pl.nbr * pl.n2; idx += blockDim.x) {
+  for (int idx = threadIdx.x; idx < nbr * pl.n2; idx += blockDim.x) {
     const int rr = fs_div(idx, pl.mn2), i2 = idx - rr * pl.n2, k1 = r0 + rr;
     CT v = Cx<CT>::mk(0, 0);
     if (k1 < pl.n1)
@@ -291,10 +294,10 @@ k_fs_rows(CT* __restrict__ Y, const CT* __restrict__ spec, const CT* __restrict_
   CT* cur = A;
   CT* oth = B;
   if constexpr (!SPEC) {
-    cur = fs_fft<CT, false>(A, B, pl.p2, pl.nbr, ls, tw);
+    cur = fs_fft<CT, false>(A, B, pl.p2, nbr, ls, tw);
     oth = cur == A ? B : A;
     const float* mt = mask + (int64_t)q.t * pp.D;
-    for (int idx = threadIdx.x; idx < pl.nbr * pl.n2; idx += blockDim.x) {
+    for (int idx = threadIdx.x; idx < nbr * pl.n2; idx += blockDim.x) {
       const int rr = fs_div(idx, pl.mn2), k2 = idx - rr * pl.n2, k1 = r0 + rr;
       if (k1 >= pl.n1) continue;
       const typename Cx<CT>::R mk = (typename Cx<CT>::R)mt[k1 + (int64_t)pl.n1 * k2];
@@ -303,8 +306,8 @@ k_fs_rows(CT* __restrict__ Y, const CT* __restrict__ spec, const CT* __restrict_
     }
     __syncthreads();
   }
-  const CT* res = fs_fft<CT, true>(cur, oth, pl.p2, pl.nbr, ls, tw);
-  for (int idx = threadIdx.x; idx < pl.nbr * pl.n2; idx += blockDim.x) {
+  const CT* res = fs_fft<CT, true>(cur, oth, pl.p2, nbr, ls, tw);
+  for (int idx = threadIdx.x; idx < nbr * pl.n2; idx += blockDim.x) {
     const int rr = fs_div(idx, pl.mn2), i2 = idx - rr * pl.n2, k1 = r0 + rr;
     if (k1 < pl.n1)
       Yp[(int64_t)k1 * pl.n2 + i2] = fs_mulc(res[rr * ls + i2], fs_twD(tw3, (int64_t)i2 * k1));
@@ -556,6 +559,20 @@ bool make_plan(int D, FsPlan* out) {
   pl.nbr = 1;
   while (pl.nbr < 8 && (size_t)2 * (pl.nbr * 2) * (pl.n2 + 1) * sizeof(double2) <= kFsSmemBudget)
     pl.nbr *= 2;
+  pl.nbr32 = pl.nbr;
+  {
+    // evaluation switches: FP32 columns per column-pass CTA and rows per row-pass CTA
+    const char* v = getenv("CMCS_FS_NB32");
+    const int nbv = v ? atoi(v) : 0;
+    if (nbv >= 1 && nbv <= 16 && (nbv & (nbv - 1)) == 0 && pl.n2 % nbv == 0 &&
+        (int64_t)pl.n1 * nbv >= 128 &&
+        (size_t)2 * nbv * (pl.n1 + 1) * sizeof(float2) <= kFsSmemBudget)
+      pl.nb32 = nbv;
+    const char* r = getenv("CMCS_FS_NBR32");
+    const int nr = r ? atoi(r) : 0;
+    if (nr >= 1 && nr <= 32 && (size_t)2 * nr * (pl.n2 + 1) * sizeof(float2) <= kFsSmemBudget)
+      pl.nbr32 = nr;
+  }
   pl.mn2 = recip(pl.n2);
   pl.p1 = make_radix(pl.n1);
   pl.p2 = make_radix(pl.n2);
@@ -571,7 +588,8 @@ size_t cols_smem(const FsPlan& pl, size_t cs) {
   return (2 * (size_t)cols_nb(pl, cs) * (pl.n1 + 1) + pl.n1 + kFsTwSmem) * cs;
 }
 size_t rows_smem(const FsPlan& pl, size_t cs) {
-  return (2 * (size_t)pl.nbr * (pl.n2 + 1) + pl.n2 + kFsTwSmem) * cs;
+  const int nbr = cs == sizeof(float2) ? pl.nbr32 : pl.nbr;
+  return (2 * (size_t)nbr * (pl.n2 + 1) + pl.n2 + kFsTwSmem) * cs;
 }
 
 template <typename CT>
@@ -617,7 +635,8 @@ cudaError_t run_passes(Ctx* c, const FsPairs& pp, const float* X, const CT* spec
         X, Y, tab1, tabD, pl, pp, flags, task_active);
     c->launches += 1;
   }
-  k_fs_rows<CT, SPEC><<<dim3(np, (pl.n1 + pl.nbr - 1) / pl.nbr), kFsThreads, sr, c->stream>>>(
+  const int nbr = f64 ? pl.nbr : pl.nbr32;
+  k_fs_rows<CT, SPEC><<<dim3(np, (pl.n1 + nbr - 1) / nbr), kFsThreads, sr, c->stream>>>(
       Y, spec, tab2, tabD, fs->mask, pl, pp, flags, task_active);
   k_fs_cols_inv<CT, MODE><<<dim3(np, pl.n2 / cols_nb(pl, sizeof(CT))), kFsThreads, sc, c->stream>>>(
       Y, tab1, pl, pp, flags, task_active, ep);
