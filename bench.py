@@ -464,7 +464,7 @@ def run_ours(a):
         a.no_fp32_form = True
     kw = dict(C=wl.C, K=wl.K, beta=wl.beta, pi=wl.pi, cg_max_iter=wl.cg_max_iter, cg_tol=wl.cg_tol,
               seed=wl.seed, precision=a.precision, refine_max=a.refine_max, refine_tol=a.refine_tol,
-              refine_steps=a.refine_steps,
+              refine_steps=min(a.refine_steps, wl.cg_max_iter),
               schedule=a.schedule, graphs=not a.no_graphs, precond=a.precond,
               learn_pi=a.learn_pi, probe_share=a.probe_share, warm_start=a.warm_start)
     if sharded:
@@ -734,7 +734,7 @@ def run_ours(a):
                                        f"N={int(wl.N[0])} K={wl.K} tol={wl.cg_tol} "
                                        f"max_iter={wl.cg_max_iter}",
                            "precision": a.precision, "refine_max": a.refine_max,
-                           "refine_tol": a.refine_tol, "refine_steps": a.refine_steps or wl.cg_max_iter,
+                           "refine_tol": a.refine_tol, "refine_steps": min(a.refine_steps, wl.cg_max_iter) or wl.cg_max_iter,
                            "parallelism": (f"tasks split over {world} GPUs {ranges}, one "
                                            f"all-gather of the M-step rows per EM iteration"
                                            if sharded else f"{world} replicas"),
