@@ -75,16 +75,22 @@ __device__ double lanczos_log_quad(const float* __restrict__ g, const float* __r
       // r = sqrt(x^2 + y^2) and 1 / r: a single-precision reciprocal square root refined by two
       // Newton-Raphson steps for 1 / sqrt(q) (each y <- y (3 - q y^2) / 2 doubles the correct
       // bits: 24 -> 48 -> beyond double precision), in place of a square root and two
-      // divisions per rotation
+      // divisions per rotation.  The seed needs q inside single precision's normal range;
+      // outside it (the last rotations of a converging block can have q far below 1e-38)
+      // the square root and division are taken in double precision.
       const double q = x * x + y * y;
       double c = 1.0, s = 0.0, r = 0.0;
-      if (q > 0.0) {
+      if (q > 1e-30 && q < 1e30) {
         double ir = (double)rsqrtf((float)q);
         ir = ir * (1.5 - 0.5 * q * ir * ir);
         ir = ir * (1.5 - 0.5 * q * ir * ir);
         r = q * ir;
         c = x * ir;
         s = -y * ir;
+      } else if (q > 0.0) {
+        r = sqrt(q);
+        c = x / r;
+        s = -y / r;
       }
       if (k > l) b[(k - 1) * st] = r;
       const double ak1 = a[(k + 1) * st];

@@ -129,6 +129,31 @@ def test_quadrature_matches_oracle_on_same_coefficients(small):
         assert abs(out[i] - ref) <= 1e-9 * scale, (i, out[i], ref)
 
 
+@pytest.mark.parametrize("scale", [1e-30, 1e-20, 1e20, 1e30])
+def test_quadrature_at_extreme_scales(small, scale):
+    """The eigen step on Lanczos matrices scaled by `scale` (the CG coefficients of scale * A:
+    gamma / scale, the same xi), whose chased rotations leave single precision's range, against
+    LAPACK: sum_u S_u1^2 log lambda_u shifts by exactly log(scale)."""
+    import torch
+    P, Y = task_lists(small)
+    alpha = philox.alpha_init(0, small.C, small.D)
+    Pk = philox.probes(0, 0, 0, 0, small.C, 8, small.D)
+    r = cofem.cg(lambda V, idx: cofem.apply_A(P[0], small.beta, alpha[0], V), Pk.T, 0.0, 100)
+    g = np.stack([(r.gamma[k] / scale).astype(np.float32) for k in range(8)])
+    x = np.stack([r.xi[k].astype(np.float32) for k in range(8)])
+    st = r.steps.astype(np.int32)
+    out, status = cmcs.lanczos_quadrature(torch.from_numpy(g).cuda(), torch.from_numpy(x).cuda(),
+                                          torch.from_numpy(st).cuda())
+    assert status == 0
+    out = out.cpu().numpy()
+    for i in range(8):
+        G = cofem.lanczos_tridiag(g[i].astype(np.float64), x[i].astype(np.float64), int(st[i]))
+        lam, V = np.linalg.eigh(G)
+        ref = float(np.sum(V[0] ** 2 * np.log(lam)))
+        mag = float(np.sum(V[0] ** 2 * np.abs(np.log(lam)))) + 1.0
+        assert abs(out[i] - ref) <= 1e-9 * mag, (scale, i, out[i], ref)
+
+
 def replay_q(wl, g, o, alpha32):
     """Responsibilities the oracle computes from the GPU's own CG coefficients (replay of the
     Lanczos coefficients, Eqs. 9-11) and the oracle's refined means: q, ell, nu."""
