@@ -553,13 +553,21 @@ bool make_plan(int D, FsPlan* out) {
   pl.n2 = best2;
   pl.n1 = D / best2;
   pl.nb = pow2_share(pl.n2, 16, pl.n1);
-  // FP32 column passes: 8 columns (32-byte rows) for more CTAs per SM, where that still
-  // leaves n2 / nb32 partial sums within the D / 128 slots
+  // FP32 column passes: 8 columns (32-byte rows) unless the rule below picks another, as long
+  // as n2 / nb32 partial sums fit the D / 128 slots
   pl.nb32 = (pl.nb >= 8 && pl.n1 * 8 >= 128) ? 8 : pl.nb;
   pl.nbr = 1;
   while (pl.nbr < 8 && (size_t)2 * (pl.nbr * 2) * (pl.n2 + 1) * sizeof(double2) <= kFsSmemBudget)
     pl.nbr *= 2;
-  pl.nbr32 = pl.nbr;
+  // FP32 passes: about 2048 complex values per CTA (two 16 KiB buffers), so that several CTAs
+  // share an SM; measured best at n2 = 400 (4 rows) and at 128 x 128 (16 rows, 16 columns)
+  pl.nbr32 = 1;
+  while (pl.nbr32 < 32 && pl.nbr32 < pl.n1 && pl.nbr32 * 2 * pl.n2 <= 2048) pl.nbr32 *= 2;
+  {
+    int nb = 1;
+    while (nb < 16 && pl.n2 % (nb * 2) == 0 && nb * 2 * pl.n1 <= 2048) nb *= 2;
+    if ((int64_t)pl.n1 * nb >= 128) pl.nb32 = nb;
+  }
   {
     // evaluation switches: FP32 columns per column-pass CTA and rows per row-pass CTA
     const char* v = getenv("CMCS_FS_NB32");
