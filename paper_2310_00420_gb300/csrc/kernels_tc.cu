@@ -92,6 +92,9 @@ struct TcArgs {
   int* p1st;               // [row tiles] pass-1 units whose partial is stored (zeroed per launch)
   int* wready;             // [row tiles] 1 once the row tile's W is reduced and stored
   int pf;                  // prefetch the Phi tile this many k-blocks ahead into L2 (0: off)
+  int tiled;               // the Phi planes are stored blocked ([row tile][k-block][128][64]):
+                           // every A tile of pass 1 is one contiguous 16 KiB and every
+                           // MN-major box of pass 2 one contiguous 8 KiB (4-D tensor maps)
 };
 
 // all tensor maps of the operator: a[pass-1][hi/lo] (pass 2 reads Phi MN-major), b[pass-1][hi/lo]
@@ -146,6 +149,20 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tm, in
       " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
       "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(smem_u32(bar))
       : "memory");
+}
+// 4-D tile (the blocked layout of Phi: [row tile][k-block][128 rows][64 columns])
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* tm, int x, int y, int z,
+                                            int w, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(z), "r"(w), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tma_prefetch_4d(const CUtensorMap* tm, int x, int y, int z, int w) {
+  asm volatile("cp.async.bulk.prefetch.tensor.4d.L2.global.tile [%0, {%1, %2, %3, %4}];" ::"l"(
+                   reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(z), "r"(w)
+               : "memory");
 }
 // prefetch a tile of the tensor into L2 (no shared memory, no barrier)
 __device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap* tm, int x, int y) {
@@ -559,10 +576,18 @@ k_tc(const __grid_constant__ TcMaps maps, const TcArgs p) {
             uint8_t* ad = st + h * a_bytes;
             if (a_mn) {
               // Phi itself (rows n = kcol .., columns d = a_row ..): two 64-column boxes
-              tma_load_2d(ad, &maps.a[1][h], ti.a_row, kcol, &full[s]);
-              tma_load_2d(ad + a_bytes / 2, &maps.a[1][h], ti.a_row + 64, kcol, &full[s]);
+              if (p.tiled) {
+                tma_load_4d(ad, &maps.a[1][h], 0, kcol & (kBM - 1), ti.a_row / kBK, kcol / kBM, &full[s]);
+                tma_load_4d(ad + a_bytes / 2, &maps.a[1][h], 0, kcol & (kBM - 1), ti.a_row / kBK + 1,
+                            kcol / kBM, &full[s]);
+              } else {
+                tma_load_2d(ad, &maps.a[1][h], ti.a_row, kcol, &full[s]);
+                tma_load_2d(ad + a_bytes / 2, &maps.a[1][h], ti.a_row + 64, kcol, &full[s]);
+              }
             } else if (PASS == 2 || (PASS == 0 && pi == 1)) {
               tma_load_2d(ad, &maps.a[1][h], kcol, ti.a_row, &full[s]);
+            } else if (p.tiled) {
+              tma_load_4d(ad, &maps.a[0][h], 0, 0, kcol / kBK, ti.a_row / kBM, &full[s]);
             } else {
               tma_load_2d(ad, &maps.a[0][h], kcol, ti.a_row, &full[s]);
             }
@@ -572,11 +597,16 @@ k_tc(const __grid_constant__ TcMaps maps, const TcArgs p) {
             const int kpf = kcol + p.pf * kBK;
 #pragma unroll
             for (int h = 0; h < NA; ++h) {
-              if (a_mn) {
+              if (a_mn && p.tiled) {
+                tma_prefetch_4d(&maps.a[1][h], 0, kpf & (kBM - 1), ti.a_row / kBK, kpf / kBM);
+                tma_prefetch_4d(&maps.a[1][h], 0, kpf & (kBM - 1), ti.a_row / kBK + 1, kpf / kBM);
+              } else if (a_mn) {
                 tma_prefetch_2d(&maps.a[1][h], ti.a_row, kpf);
                 tma_prefetch_2d(&maps.a[1][h], ti.a_row + 64, kpf);
               } else if (PASS == 2 || (PASS == 0 && pi == 1)) {
                 tma_prefetch_2d(&maps.a[1][h], kpf, ti.a_row);
+              } else if (p.tiled) {
+                tma_prefetch_4d(&maps.a[0][h], 0, 0, kpf / kBK, ti.a_row / kBM);
               } else {
                 tma_prefetch_2d(&maps.a[0][h], kpf, ti.a_row);
               }
@@ -854,6 +884,24 @@ __global__ void k_split_bf16(const float* __restrict__ src, __nv_bfloat16* __res
   }
 }
 
+// the same split written blocked: element (n, d) of Phi [rows][Dp] at
+// ((n / 128) (Dp / 64) + d / 64) 8192 + (n % 128) 64 + d % 64
+__global__ void k_split_bf16_tiled(const float* __restrict__ src, __nv_bfloat16* __restrict__ hi,
+                                   __nv_bfloat16* __restrict__ lo, int64_t rows, int Dp) {
+  const int64_t n_el = rows * Dp;
+  const int nkb = Dp / 64;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_el;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t n = i / Dp;
+    const int d = (int)(i - n * Dp);
+    const int64_t o = ((n >> 7) * nkb + (d >> 6)) * 8192 + (n & 127) * 64 + (d & 63);
+    const float x = src[i];
+    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+    hi[o] = h;
+    if (lo) lo[o] = __float2bfloat16_rn(x - __bfloat162float(h));
+  }
+}
+
 // PhiT[d][n] = Phi[n][d] split into BF16 pairs, 32 x 32 tiles through shared memory
 __global__ void k_transpose_split(const float* __restrict__ phi, __nv_bfloat16* __restrict__ thi,
                                   __nv_bfloat16* __restrict__ tlo, int64_t rows, int Dp) {
@@ -888,6 +936,7 @@ struct TcState {
   int *tile_code, *tile_task2, *n1, *p1done;   // fused tile list; per-task counts [T] + tile counter
   int early;                                   // mode 3: pass 2 launched programmatically
   int pf;                                      // L2 prefetch distance of the Phi tiles (k-blocks)
+  int tiled;                                   // Phi planes stored blocked (see TcArgs)
   std::vector<int> tstart;                     // first fused tile of each task (host)
   // mode 4 (one read of Phi per application): unit list, split-K partials and counters
   int *u_code, *u_task, nunits, splitk, nslot;
@@ -918,6 +967,23 @@ bool encode_2d(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer,
   cuuint32_t box[2] = {(cuuint32_t)kBK, box_rows};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box,
+                  estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+// the blocked Phi plane as a 4-D tensor [rows / 128][Dp / 64][128][64] (innermost last in the
+// dims below), box [1][1][box_rows][64]: the same 128-byte-swizzled shared-memory image as the
+// 2-D box of encode_2d, read from one contiguous block
+bool encode_blocked(CUtensorMap* m, const void* base, uint64_t Dp, uint64_t rows, uint32_t box_rows) {
+  auto fn = get_encode();
+  if (!fn || base == nullptr) return false;
+  cuuint64_t dims[4] = {(cuuint64_t)kBK, (cuuint64_t)kBM, Dp / kBK, rows / kBM};
+  cuuint64_t strides[3] = {(cuuint64_t)kBK * 2, (cuuint64_t)kBK * kBM * 2,
+                           (Dp / kBK) * (cuuint64_t)kBK * kBM * 2};
+  cuuint32_t box[4] = {(cuuint32_t)kBK, box_rows, 1, 1};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(base), dims, strides, box,
                   estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
@@ -957,6 +1023,7 @@ TcArgs base_args(Ctx* c, TcState* s) {
   a.status = &c->counters[2];
   a.stall = c->stall_flag;
   a.pf = s->pf;
+  a.tiled = s->tiled;
   return a;
 }
 
@@ -1124,6 +1191,8 @@ int tc_create(Ctx* c) {
     const char* pv = getenv("CMCS_TC_PREFETCH"); // evaluation switch: L2 prefetch distance
     s->pf = pv ? atoi(pv) : 0;
     if (s->pf < 0) s->pf = 0;
+    const char* tv = getenv("CMCS_TC_TILED");    // evaluation switch: 0 keeps Phi row-major
+    s->tiled = tv ? atoi(tv) != 0 : 0;
   }
   s->mn_lbo = 8192;      // 64-column halves of the MN-major A tile are 8 KiB apart
   s->mn_sbo = 1024;      // groups of 8 k rows are 1 KiB apart
@@ -1233,21 +1302,27 @@ int tc_create(Ctx* c) {
     snprintf(c->err, sizeof(c->err), "tensor-core operator: device allocation failed");
     return 1;
   }
-  k_split_bf16<<<4096, 256, 0, c->stream>>>(c->phi, s->phi_hi, s->phi_lo, rows * Dp);
+  if (s->tiled)
+    k_split_bf16_tiled<<<4096, 256, 0, c->stream>>>(c->phi, s->phi_hi, s->phi_lo, rows, (int)Dp);
+  else
+    k_split_bf16<<<4096, 256, 0, c->stream>>>(c->phi, s->phi_hi, s->phi_lo, rows * Dp);
   if (s->mode == 2)
     k_transpose_split<<<dim3(Dp / 32, (unsigned)(rows / 32)), dim3(32, 8), 0, c->stream>>>(
         c->phi, s->phit_hi, s->phit_lo, rows, (int)Dp);
   cudaMemsetAsync(c->dhi, 0, sizeof(__nv_bfloat16) * S * Dp, c->stream);
   cudaMemsetAsync(c->dlo, 0, sizeof(__nv_bfloat16) * S * Dp, c->stream);
-  bool ok = encode_2d(&s->tm_phi[0], s->phi_hi, Dp, rows, kBM) &&
+  auto enc_phi = [&](CUtensorMap* m, const __nv_bfloat16* base, uint32_t box_rows) {
+    return s->tiled ? encode_blocked(m, base, Dp, rows, box_rows) : encode_2d(m, base, Dp, rows, box_rows);
+  };
+  bool ok = enc_phi(&s->tm_phi[0], s->phi_hi, kBM) &&
             (s->mode != 2 || encode_2d(&s->tm_phit[0], s->phit_hi, rows, Dp, kBM)) &&
             encode_2d(&s->tm_d[0], c->dhi, Dp, S, s->BR) && encode_2d(&s->tm_d[1], c->dlo, Dp, S, s->BR) &&
             encode_2d(&s->tm_w[0], s->w_hi, rows, R, s->BR) && encode_2d(&s->tm_w[1], s->w_lo, rows, R, s->BR);
   if (ok && s->NA == 2)
-    ok = encode_2d(&s->tm_phi[1], s->phi_lo, Dp, rows, kBM) &&
+    ok = enc_phi(&s->tm_phi[1], s->phi_lo, kBM) &&
          (s->mode != 2 || encode_2d(&s->tm_phit[1], s->phit_lo, rows, Dp, kBM));
-  if (ok) ok = encode_2d(&s->tm_phimn[0], s->phi_hi, Dp, rows, 64);
-  if (ok && s->NA == 2) ok = encode_2d(&s->tm_phimn[1], s->phi_lo, Dp, rows, 64);
+  if (ok) ok = enc_phi(&s->tm_phimn[0], s->phi_hi, 64);
+  if (ok && s->NA == 2) ok = enc_phi(&s->tm_phimn[1], s->phi_lo, 64);
   if (!ok) {
     snprintf(c->err, sizeof(c->err), "tensor-core operator: tensor map encoding failed");
     return 1;
@@ -1307,7 +1382,10 @@ cudaError_t tc_refresh(Ctx* c) {
   TcState* s = static_cast<TcState*>(c->tc);
   if (!s) return cudaSuccess;
   const int64_t rows = c->rows_total, Dp = c->Dp;
-  k_split_bf16<<<4096, 256, 0, c->stream>>>(c->phi, s->phi_hi, s->phi_lo, rows * Dp);
+  if (s->tiled)
+    k_split_bf16_tiled<<<4096, 256, 0, c->stream>>>(c->phi, s->phi_hi, s->phi_lo, rows, (int)Dp);
+  else
+    k_split_bf16<<<4096, 256, 0, c->stream>>>(c->phi, s->phi_hi, s->phi_lo, rows * Dp);
   if (s->mode == 2)
     k_transpose_split<<<dim3(Dp / 32, (unsigned)(rows / 32)), dim3(32, 8), 0, c->stream>>>(
         c->phi, s->phit_hi, s->phit_lo, rows, (int)Dp);
