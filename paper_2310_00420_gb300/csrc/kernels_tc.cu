@@ -1192,7 +1192,7 @@ int tc_create(Ctx* c) {
     s->pf = pv ? atoi(pv) : 0;
     if (s->pf < 0) s->pf = 0;
     const char* tv = getenv("CMCS_TC_TILED");    // evaluation switch: 0 keeps Phi row-major
-    s->tiled = tv ? atoi(tv) != 0 : 0;
+    s->tiled = tv ? atoi(tv) != 0 : 1;
   }
   s->mn_lbo = 8192;      // 64-column halves of the MN-major A tile are 8 KiB apart
   s->mn_sbo = 1024;      // groups of 8 k rows are 1 KiB apart
