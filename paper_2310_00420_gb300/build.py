@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libcmcs.so")
 SOURCES = ["cmcs_api.cu", "kernels_op.cu", "kernels_cg.cu", "kernels_estep.cu", "kernels_tc.cu",
-           "noalloc.cu", "adjoint.cu", "kernels_dft.cu", "kernels_dft_large.cu"]
+           "kernels_ozaki.cu", "noalloc.cu", "adjoint.cu", "kernels_dft.cu", "kernels_dft_large.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]

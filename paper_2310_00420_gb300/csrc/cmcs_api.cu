@@ -75,6 +75,7 @@ void free_ctx(Ctx* c) {
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
   if (c->tc) tc_destroy(c);
+  if (c->oz) oz_destroy(c);
   dft_destroy(c);
   free(c->hN);
   free(c->hNp);
@@ -655,6 +656,13 @@ cmcs_status create_ctx(const cmcs_config* cfg, const float* Phi, const float* y,
       if (c->err[0] == 0) set_err(c, "BF16 tensor-core operator unavailable");
       return fail(CMCS_ERR_UNSUPPORTED);
     }
+    // the refinement residual on the tensor cores (digit planes of Phi); CMCS_OZ=0 keeps the
+    // double-single SIMT residual (evaluation switch)
+    const char* ov = getenv("CMCS_OZ");
+    if ((ov == nullptr || atoi(ov) != 0) && oz_create(c) != 0) {
+      if (c->err[0] == 0) set_err(c, "tensor-core residual unavailable");
+      return fail(CMCS_ERR_UNSUPPORTED);
+    }
   }
   CKC(cudaStreamSynchronize(c->stream));
   CKC(cudaGetLastError());
@@ -819,6 +827,7 @@ cmcs_status cmcs_set_data(cmcs_ctx* h, const float* Phi, const float* y, int on_
   CK(launch_colnorm(c));
   c->have_prev = 0;                   // the previous means belong to the old data
   if (c->tc != nullptr) CK(tc_refresh(c));
+  if (c->oz != nullptr) CK(oz_refresh(c));
   return sync_check(c);
 }
 

@@ -171,8 +171,10 @@ struct Ctx {
   int first_solve;               // the E-step's first solve (Lanczos coefficients) is running
   cudaEvent_t res_ev[2];
 
-  // tensor-core operator (precision 1 and 2); null otherwise
+  // tensor-core operator (precision 1, 2 and 3); null otherwise
   void* tc;
+  // tensor-core refinement residual (digit planes of Phi, kernels_ozaki.cu); null otherwise
+  void* oz;
   // structured sensing of Sec. 4 (op == 1): Phi_t = Omega_t F applied by FFT (kernels_dft.cu)
   int op;
   int dft_L;              // log2 D
@@ -213,6 +215,11 @@ cudaError_t launch_operator(Ctx* c, const float* V, float* Z, int with_dots);
 cudaError_t launch_residual(Ctx* c, const float* X, const float* Bext, float* Rout,
                             int all_systems = 0, int means_only = 0);
 cudaError_t launch_resid_norm(Ctx* c);
+// the same residual (all systems, dense Phi) on the tensor cores by error-free digit splitting
+int oz_create(Ctx* c);
+cudaError_t oz_refresh(Ctx* c);      // Phi changed: its column scales and digit planes
+void oz_destroy(Ctx* c);
+cudaError_t oz_residual(Ctx* c, const float* X, const float* Bext, float* Rout);
 // W[t][j'][n] = (Phi_t V_{t, j' * jstride})[n] for j' < Rc (FP32 SIMT pass 1 only)
 // W = Phi V for Rc columns (systems j = j' * jstride); with Wlo, as a compensated pair W + Wlo
 cudaError_t launch_phi_v(Ctx* c, const float* V, float* W, float* Wlo, int Rc, int jstride);

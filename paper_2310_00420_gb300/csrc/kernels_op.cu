@@ -522,6 +522,7 @@ cudaError_t launch_phi_v(Ctx* c, const float* V, float* W, float* Wlo, int Rc, i
 cudaError_t launch_residual(Ctx* c, const float* X, const float* Bext, float* Rout,
                             int all_systems, int means_only) {
   if (c->op == 1) return launch_dft_residual(c, X, Bext, Rout, all_systems, means_only);
+  if (c->oz != nullptr && !means_only) return oz_residual(c, X, Bext, Rout);
   const int Rc = means_only ? c->C : c->R;
   const int js = means_only ? c->K + 1 : 1;
   const int tn = c->tn_ds > 0 ? c->tn_ds : pick_tn(Rc, 4);
