@@ -66,7 +66,7 @@ def _args():
     ap.add_argument("--no-graphs", action="store_true")
     ap.add_argument("--refine-max", type=int, default=8)
     ap.add_argument("--refine-tol", type=float, default=1e-5)
-    ap.add_argument("--refine-steps", type=int, default=70,
+    ap.add_argument("--refine-steps", type=int, default=50,
                     help="step cap of the refinement sweeps' CG solves (0: the first solve's)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -439,6 +439,59 @@ def batching_leg(a) -> dict:
     return out
 
 
+def differentiation_leg(a, n_steps: int = 100) -> dict:
+    """The differentiation workload (T=64, C=4, D=2048, N=512, K=32): Phi learned by Adam on
+    sum_t ||mu_{t, a_t} - z_t||^2 through PosteriorMeans (forward: one E-step on the current Phi;
+    backward: the batched adjoint solve), n_steps timed steps after two warm-up steps, at the
+    responsibilities and alpha of the first E-step."""
+    import torch
+    from paper_2310_00420_gb300 import cmcs
+    from paper_2310_00420_gb300.adjoint import posterior_means
+    wl = _workload("differentiation", 0)
+    kw = dict(C=wl.C, K=wl.K, beta=wl.beta, pi=wl.pi, cg_max_iter=wl.cg_max_iter,
+              cg_tol=wl.cg_tol, seed=wl.seed, refine_max=a.refine_max, refine_tol=a.refine_tol,
+              refine_steps=0, precision="bf16x3")
+    Phi = torch.from_numpy(wl.Phi).cuda().requires_grad_(True)
+    y = torch.from_numpy(wl.y).cuda()
+    z = torch.from_numpy(wl.z).cuda()
+    ctx = cmcs.Context(Phi.detach(), y, wl.N, **kw)
+    ctx.estep()
+    al = torch.from_numpy(ctx.read(cmcs.OUT_ALPHA)).cuda()
+    assign = torch.from_numpy(ctx.read(cmcs.OUT_ASSIGN).astype(np.int64)).cuda()
+    rows = torch.arange(wl.T, device="cuda")
+    opt = torch.optim.Adam([Phi], lr=1e-4)
+
+    def step():
+        mu = posterior_means(ctx, Phi, y, al, 0)
+        loss = ((mu[rows, assign] - z) ** 2).sum()
+        opt.zero_grad()
+        loss.backward()
+        opt.step()
+        return loss.detach()
+
+    for _ in range(2):
+        step()
+    losses = []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(n_steps):
+        losses.append(step())
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    ctx.close()
+    lv = [float(v) for v in losses]
+    out = {"workload": f"{wl.name} T={wl.T} C={wl.C} D={wl.D} N={int(wl.N[0])} K={wl.K}",
+           "adam_steps": n_steps, "lr": 1e-4, "value": n_steps / (ms / 1000.0),
+           "unit": "Adam steps/s", "ms_per_step": ms / n_steps,
+           "loss_first": lv[0], "loss_last": lv[-1], "loss_min": min(lv),
+           "per_step": "set_data(Phi), E-step (all systems, refined), adjoint solve, Adam update"}
+    del Phi, y, z
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(a):
     import torch
     from paper_2310_00420_gb300 import cmcs
@@ -721,6 +774,7 @@ def run_ours(a):
         torch.cuda.empty_cache()
         legs["precision_workload"] = precision_leg(a, peaks)
         legs["batching_workload"] = batching_leg(a)
+        legs["differentiation_workload"] = differentiation_leg(a)
     if rank == 0:
         line = {"metric": _metric(a.workload, sharded), "value": value, "unit": UNIT,
                 "n_gpus": world,

@@ -129,54 +129,102 @@ __device__ double lanczos_log_quad(const float* __restrict__ g, const float* __r
 }  // namespace
 
 // k_quad: one Lanczos matrix per thread, NT threads per block, arrays of 3 UB doubles per
-// thread in shared memory
+// thread in shared memory; a grid smaller than the matrix count loops over them
 template <int UB, int NT>
 __global__ void __launch_bounds__(NT)
 k_quad(const float* __restrict__ gam, const float* __restrict__ xi, const int* __restrict__ steps,
        int nsys, int ld, double* out, int* status) {
   extern __shared__ double qsm[];                 // [3][UB][NT]
-  const int i = blockIdx.x * NT + threadIdx.x;
-  if (i >= nsys) return;
-  int U = steps[i];
-  if (U <= 0) {
-    out[i] = 0.0;
-    return;
-  }
-  if (U > UB || U > ld) {
-    atomicOr(status, 2);
-    out[i] = 0.0;
-    return;
-  }
-  int fail = 0;
   double* a = qsm + threadIdx.x;
   double* b = a + UB * NT;
   double* z = b + UB * NT;
-  out[i] = lanczos_log_quad(gam + (int64_t)i * ld, xi + (int64_t)i * ld, U, a, b, z, NT, &fail);
-  if (fail) atomicOr(status, 1);
+  for (int i = blockIdx.x * NT + threadIdx.x; i < nsys; i += gridDim.x * NT) {
+    const int U = steps[i];
+    if (U <= 0) {
+      out[i] = 0.0;
+      continue;
+    }
+    if (U > UB || U > ld) {
+      atomicOr(status, 2);
+      out[i] = 0.0;
+      continue;
+    }
+    int fail = 0;
+    out[i] = lanczos_log_quad(gam + (int64_t)i * ld, xi + (int64_t)i * ld, U, a, b, z, NT, &fail);
+    if (fail) atomicOr(status, 1);
+  }
+}
+
+// the same with the arrays in per-thread local memory (no shared memory: the blocks fit beside
+// kernels that hold most of an SM's shared memory)
+template <int UB>
+__global__ void __launch_bounds__(32)
+k_quad_local(const float* __restrict__ gam, const float* __restrict__ xi, const int* __restrict__ steps,
+             int nsys, int ld, double* out, int* status) {
+  double a[UB], b[UB], z[UB];
+  for (int i = blockIdx.x * 32 + threadIdx.x; i < nsys; i += gridDim.x * 32) {
+    const int U = steps[i];
+    if (U <= 0) {
+      out[i] = 0.0;
+      continue;
+    }
+    if (U > UB || U > ld) {
+      atomicOr(status, 2);
+      out[i] = 0.0;
+      continue;
+    }
+    int fail = 0;
+    out[i] = lanczos_log_quad(gam + (int64_t)i * ld, xi + (int64_t)i * ld, U, a, b, z, 1, &fail);
+    if (fail) atomicOr(status, 1);
+  }
+}
+
+template <int UB>
+cudaError_t launch_quad_local(const float* gam, const float* xi, const int* steps, int nsys, int ld,
+                              double* out, int* status, cudaStream_t st, int max_blocks) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_quad_local<UB>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  int grid = (nsys + 31) / 32;
+  if (max_blocks > 0 && grid > max_blocks) grid = max_blocks;
+  k_quad_local<UB><<<grid, 32, 0, st>>>(gam, xi, steps, nsys, ld, out, status);
+  return cudaGetLastError();
 }
 
 template <int UB, int NT>
 cudaError_t launch_quad(const float* gam, const float* xi, const int* steps, int nsys, int ld,
-                        double* out, int* status, cudaStream_t st) {
+                        double* out, int* status, cudaStream_t st, int max_blocks) {
   const size_t smem = sizeof(double) * 3 * UB * NT;
   static bool attr = false;                       // set once per kernel instance
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(k_quad<UB, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
+    // an SM that takes a block of this kernel keeps its whole shared memory available, so the
+    // tensor-core kernels running meanwhile can still be placed beside it
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_quad<UB, NT>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                               cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  k_quad<UB, NT><<<(nsys + NT - 1) / NT, NT, smem, st>>>(gam, xi, steps, nsys, ld, out, status);
+  int grid = (nsys + NT - 1) / NT;
+  if (max_blocks > 0 && grid > max_blocks) grid = max_blocks;
+  k_quad<UB, NT><<<grid, NT, smem, st>>>(gam, xi, steps, nsys, ld, out, status);
   return cudaGetLastError();
 }
 
 template <int NT>
 cudaError_t launch_quad_nt(const float* gam, const float* xi, const int* steps, int nsys, int ld,
-                           double* out, int* status, cudaStream_t st) {
-  if (ld <= 64) return launch_quad<64, NT>(gam, xi, steps, nsys, ld, out, status, st);
-  if (ld <= 128) return launch_quad<128, NT>(gam, xi, steps, nsys, ld, out, status, st);
-  if (ld <= 256) return launch_quad<256, NT>(gam, xi, steps, nsys, ld, out, status, st);
-  if (ld <= 512) return launch_quad<512, (NT < 16 ? NT : 16)>(gam, xi, steps, nsys, ld, out, status, st);
+                           double* out, int* status, cudaStream_t st, int max_blocks = 0) {
+  if (ld <= 64) return launch_quad<64, NT>(gam, xi, steps, nsys, ld, out, status, st, max_blocks);
+  if (ld <= 128) return launch_quad<128, NT>(gam, xi, steps, nsys, ld, out, status, st, max_blocks);
+  if (ld <= 256) return launch_quad<256, NT>(gam, xi, steps, nsys, ld, out, status, st, max_blocks);
+  if (ld <= 512)
+    return launch_quad<512, (NT < 16 ? NT : 16)>(gam, xi, steps, nsys, ld, out, status, st, max_blocks);
   return cudaErrorInvalidValue;
 }
 
@@ -196,10 +244,22 @@ cudaError_t launch_quadrature(const float* gam, const float* xi, const int* step
   }
 }
 
+// In the E-step the eigen step runs on a side stream beside the refinement, whose tensor-core
+// kernels hold most of each SM's shared memory.  There it uses the local-memory kernel, with the
+// SMs it lands on kept at their full shared-memory carve-out, so it fits beside them: the
+// shared-memory kernel (96 KiB per block) made the first refinement residual wait for it.
+// CMCS_QUAD_SIDE=0 (evaluation switch) launches the shared-memory kernel instead.
 cudaError_t launch_quadrature_ctx(Ctx* c, cudaStream_t st) {
   c->launches += 1;
-  return launch_quadrature(c->gam, c->xi, c->psteps, c->T * c->C * c->K, c->U, c->quad,
-                           &c->counters[2], st);
+  static int side = -1;
+  if (side < 0) {
+    const char* v = getenv("CMCS_QUAD_SIDE");
+    side = v ? atoi(v) != 0 : 1;
+  }
+  const int nsys = c->T * c->C * c->K;
+  if (side && nsys > 0 && c->U <= 128)
+    return launch_quad_local<128>(c->gam, c->xi, c->psteps, nsys, c->U, c->quad, &c->counters[2], st, 0);
+  return launch_quadrature(c->gam, c->xi, c->psteps, nsys, c->U, c->quad, &c->counters[2], st);
 }
 
 // ---- ell_tc = nu + sum_d log alpha_cd + b0^T mu (Eq. 3), nu from Eq. 11 ------------------

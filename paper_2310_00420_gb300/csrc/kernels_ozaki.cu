@@ -8,14 +8,15 @@
 //   Phi[n][d] = u_td 2^-7 sum_{k<5} q_k[n][d],  q_k = e_k 2^-8k,  e_k integer in [-128, 128],
 // with u_td the smallest power of two >= max_n |Phi_t[n][d]| (column d of task t), so every FP32
 // entry of Phi within 2^-15 of its column's largest is represented exactly, and the vector
-// operand v (x' = u_t * x in pass 1, W in pass 2) likewise with one scale per system over the
-// contraction index and three planes (24 bits below that system's largest entry).  The product
-// of two digit planes (k, l) is an integer multiple of 2^-8(k+l), each product of digits has at
-// most 14 bits, so the FP32 sum of up to 1024 of them in tensor memory is exact.  Per tile the
-// five Phi planes are multiplied by the three stacked vector planes (one MMA of N = 3 * 32
-// columns per Phi plane, five accumulators of 96 columns in TMEM); after every `chunk` k-blocks
-// the epilogue warps add the 15 exact sums into a double-single accumulator per output
-// (Knuth's TwoSum) and the MMA issuer starts the next chunk from zero.
+// operand likewise with one scale per system over the contraction index: x' = u_t * x in pass 1
+// with four planes (32 bits below the system's largest |x'|), W in pass 2 with three (24 bits).
+// The product of two digit planes (k, l) is an integer multiple of 2^-8(k+l), each product of
+// digits has at most 14 bits, so the FP32 sum of up to 1024 of them in tensor memory is exact.
+// The pairs with k + l <= 4 are formed (the rest lie below 2^-32 of the leading pair): per tile
+// Phi plane k is multiplied by the first nl(k) stacked vector planes in one MMA of N = 32 nl(k)
+// columns into its own TMEM accumulator; after every `chunk` k-blocks the epilogue warps add the
+// exact sums into a double-single accumulator per output (Knuth's TwoSum) and the MMA issuer
+// starts the next chunk from zero.
 //
 // Pass 1: W[j][n] = sum_d Phi[n][d] x[j][d]      A = Phi digit planes, K-major (blocked layout)
 // Pass 2: R[j][d] = B - alpha x - beta sum_n Phi[n][d] W[j][n]
@@ -49,22 +50,33 @@ using namespace tcx;
 namespace {
 
 constexpr int kOzK = 5;                          // digit planes of Phi
-constexpr int kOzL = 3;                          // digit planes of the vector operand
+constexpr int kOzL1 = 4;                         // digit planes of x' (pass 1)
+constexpr int kOzL2 = 3;                         // digit planes of W (pass 2)
 constexpr int kOzJT = 32;                        // systems per tile
-constexpr int kOzN = kOzL * kOzJT;               // MMA N: three planes of 32 systems
-constexpr int kOzTmem = 512;                     // TMEM columns allocated (5 x 96 used)
+constexpr int kOzTmem = 512;                     // TMEM columns allocated (448 or 384 used)
 constexpr int kOzEpiWarps = 8;
 constexpr int kOzThreads = 64 + 32 * kOzEpiWarps;
 constexpr int kOzStages = 2;
 constexpr int kOzABytes = kTileM * kTileK * 2;   // 16 KiB per Phi plane
 constexpr int kOzBBytes = kOzJT * kTileK * 2;    // 4 KiB per vector plane
-constexpr int kOzStageBytes = kOzK * kOzABytes + kOzL * kOzBBytes;
-constexpr int kOzSmem = kOzStages * kOzStageBytes + 1024 + 128;
+__host__ __device__ constexpr int oz_nl_max(int pass) { return pass == 1 ? kOzL1 : kOzL2; }
+__host__ __device__ constexpr int oz_stage_bytes(int pass) {
+  return kOzK * kOzABytes + oz_nl_max(pass) * kOzBBytes;
+}
+// vector planes multiplied by Phi plane k (pairs k + l <= 4) and its accumulator's first column
+__host__ __device__ constexpr int oz_nl(int pass, int k) {
+  return oz_nl_max(pass) < 5 - k ? oz_nl_max(pass) : 5 - k;
+}
+__host__ __device__ constexpr int oz_col(int pass, int k) {
+  return k == 0 ? 0 : oz_col(pass, k - 1) + kOzJT * oz_nl(pass, k - 1);
+}
+static_assert(oz_col(1, kOzK) <= kOzTmem && oz_col(2, kOzK) <= kOzTmem, "TMEM columns");
+constexpr int kOzSmem = kOzStages * oz_stage_bytes(1) + 1024 + 128;
 constexpr int kOzMaxChunk = 16;                  // k-blocks per exact chunk: 16 x 64 x 2^14 = 2^24
 
 struct OzMaps {
   CUtensorMap a[kOzK];
-  CUtensorMap b[kOzL];
+  CUtensorMap b[kOzL1];        // pass 2 uses the first kOzL2
 };
 
 struct OzArgs {
@@ -166,7 +178,7 @@ __global__ void __launch_bounds__(256) k_oz_x_digits(const float* __restrict__ X
   const int e = scale_exp(m);
   if (threadIdx.x == 0) xs[sys] = ldexpf(1.f, e);
   for (int d = threadIdx.x; d < Dp; d += blockDim.x)
-    make_digits<kOzL>(ut[d] * x[d], e, dig + sys * Dp + d, plane);
+    make_digits<kOzL1>(ut[d] * x[d], e, dig + sys * Dp + d, plane);
 }
 
 __global__ void k_oz_w_digits(const float* __restrict__ wf, const unsigned int* __restrict__ wmax,
@@ -178,7 +190,7 @@ __global__ void k_oz_w_digits(const float* __restrict__ wf, const unsigned int* 
     const int64_t j = i / rows, n = i - j * rows;
     const int t = tile_task[n >> 7];
     const int e = scale_exp(__uint_as_float(wmax[(int64_t)t * R + j]));
-    make_digits<kOzL>(wf[i], e, dig + i, n_el);
+    make_digits<kOzL2>(wf[i], e, dig + i, n_el);
   }
 }
 
@@ -236,7 +248,9 @@ k_oz(const __grid_constant__ OzMaps maps, const OzArgs p) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~static_cast<uintptr_t>(1023));
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)kOzStages * kOzStageBytes);
+  constexpr int kStage = oz_stage_bytes(PASS);
+  constexpr int NL = oz_nl_max(PASS);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)kOzStages * kStage);
   uint64_t* empty = full + kOzStages;
   uint64_t* tfull = empty + kOzStages;        // a chunk's sums are ready for the epilogue
   uint64_t* tempty = tfull + 1;               // the epilogue has read them
@@ -284,8 +298,8 @@ k_oz(const __grid_constant__ OzMaps maps, const OzArgs p) {
             stop = true;
             break;
           }
-          uint8_t* st = smem + (size_t)s * kOzStageBytes;
-          mbar_expect_tx(&full[s], (uint32_t)kOzStageBytes);
+          uint8_t* st = smem + (size_t)s * kStage;
+          mbar_expect_tx(&full[s], (uint32_t)kStage);
           const int kcol = ti.kx + kb * kTileK;
 #pragma unroll
           for (int k = 0; k < kOzK; ++k) {
@@ -302,7 +316,7 @@ k_oz(const __grid_constant__ OzMaps maps, const OzArgs p) {
           }
           uint8_t* bst = st + kOzK * kOzABytes;
 #pragma unroll
-          for (int l = 0; l < kOzL; ++l) tma_load_2d(bst + l * kOzBBytes, &maps.b[l], kcol, brow, &full[s]);
+          for (int l = 0; l < NL; ++l) tma_load_2d(bst + l * kOzBBytes, &maps.b[l], kcol, brow, &full[s]);
           issued = it + 1;
         }
       }
@@ -310,7 +324,7 @@ k_oz(const __grid_constant__ OzMaps maps, const OzArgs p) {
   } else if (warp == 1) {
     // ---- MMA issuer
     if (lane == 0) {
-      const uint32_t idesc = idesc_bf16(kTileM, kOzN) | (PASS == 2 ? (1u << 15) : 0u);
+      const uint32_t amaj = PASS == 2 ? (1u << 15) : 0u;      // A MN-major in pass 2
       uint32_t it = 0, q = 0;
       bool stop = false;
       for (int tile = blockIdx.x; tile < p.ntiles && !stop && !*abort_flag; tile += gridDim.x) {
@@ -335,7 +349,7 @@ k_oz(const __grid_constant__ OzMaps maps, const OzArgs p) {
             break;
           }
           tc_fence_after();
-          const uint32_t st = smem_u32(smem + (size_t)s * kOzStageBytes);
+          const uint32_t st = smem_u32(smem + (size_t)s * kStage);
 #pragma unroll
           for (int kk = 0; kk < kTileK / 16; ++kk) {
             const uint64_t bd = smem_desc(st + kOzK * kOzABytes + kk * 32);
@@ -343,7 +357,8 @@ k_oz(const __grid_constant__ OzMaps maps, const OzArgs p) {
             for (int k = 0; k < kOzK; ++k) {
               const uint64_t ad = PASS == 1 ? smem_desc(st + k * kOzABytes + kk * 32)
                                             : smem_desc_mn(st + k * kOzABytes + kk * 2048, 8192, 1024);
-              mma_bf16(tmem + (uint32_t)(k * kOzN), ad, bd, idesc, (cstart && kk == 0) ? 0u : 1u);
+              mma_bf16(tmem + (uint32_t)oz_col(PASS, k), ad, bd,
+                       idesc_bf16(kTileM, kOzJT * oz_nl(PASS, k)) | amaj, (cstart && kk == 0) ? 0u : 1u);
             }
           }
           mma_commit(&empty[s]);
@@ -380,13 +395,13 @@ k_oz(const __grid_constant__ OzMaps maps, const OzArgs p) {
           break;
         }
         tc_fence_after();
-        // the 15 exact sums, most significant planes first
+        // the exact sums of the pairs (k, l), most significant Phi planes first
 #pragma unroll
         for (int k = 0; k < kOzK; ++k) {
 #pragma unroll
-          for (int l = 0; l < kOzL; ++l) {
+          for (int l = 0; l < oz_nl(PASS, k); ++l) {
             float v[16];
-            tmem_ld16(trow + (uint32_t)(k * kOzN + l * kOzJT), v);
+            tmem_ld16(trow + (uint32_t)(oz_col(PASS, k) + l * kOzJT), v);
 #pragma unroll
             for (int i = 0; i < 16; ++i) two_sum_acc(hi[i], lo[i], v[i]);
           }
@@ -479,7 +494,7 @@ k_oz(const __grid_constant__ OzMaps maps, const OzArgs p) {
 struct OzState {
   __nv_bfloat16* phid;        // [5][rows][Dp] digit planes of Phi, blocked
   float* u;                   // [T][Dp]
-  __nv_bfloat16* xd;          // [3][S][Dp]
+  __nv_bfloat16* xd;          // [4][S][Dp]
   float* xs;                  // [S]
   float* wf;                  // [R][rows]
   unsigned int* wmax;         // [S]
@@ -503,11 +518,11 @@ int oz_create(Ctx* c) {
   auto al = [&](void** p, size_t bytes) { return cudaMalloc(p, bytes) == cudaSuccess; };
   bool ok = al(reinterpret_cast<void**>(&s->phid), sizeof(__nv_bfloat16) * (size_t)(kOzK * rows * Dp)) &&
             al(reinterpret_cast<void**>(&s->u), sizeof(float) * (size_t)(c->T * Dp)) &&
-            al(reinterpret_cast<void**>(&s->xd), sizeof(__nv_bfloat16) * (size_t)(kOzL * S * Dp)) &&
+            al(reinterpret_cast<void**>(&s->xd), sizeof(__nv_bfloat16) * (size_t)(kOzL1 * S * Dp)) &&
             al(reinterpret_cast<void**>(&s->xs), sizeof(float) * (size_t)S) &&
             al(reinterpret_cast<void**>(&s->wf), sizeof(float) * (size_t)(R * rows)) &&
             al(reinterpret_cast<void**>(&s->wmax), sizeof(unsigned int) * (size_t)S) &&
-            al(reinterpret_cast<void**>(&s->wd), sizeof(__nv_bfloat16) * (size_t)(kOzL * R * rows));
+            al(reinterpret_cast<void**>(&s->wd), sizeof(__nv_bfloat16) * (size_t)(kOzL2 * R * rows));
   if (!ok) {
     snprintf(c->err, sizeof(c->err), "tensor-core residual: device allocation failed");
     return 1;
@@ -516,9 +531,8 @@ int oz_create(Ctx* c) {
     const __nv_bfloat16* base = s->phid + (size_t)k * rows * Dp;
     ok = encode_blocked(&s->m1.a[k], base, Dp, rows, kTileM) && encode_blocked(&s->m2.a[k], base, Dp, rows, 64);
   }
-  for (int l = 0; l < kOzL && ok; ++l)
-    ok = encode_2d(&s->m1.b[l], s->xd + (size_t)l * S * Dp, Dp, S, kOzJT) &&
-         encode_2d(&s->m2.b[l], s->wd + (size_t)l * R * rows, rows, R, kOzJT);
+  for (int l = 0; l < kOzL1 && ok; ++l) ok = encode_2d(&s->m1.b[l], s->xd + (size_t)l * S * Dp, Dp, S, kOzJT);
+  for (int l = 0; l < kOzL2 && ok; ++l) ok = encode_2d(&s->m2.b[l], s->wd + (size_t)l * R * rows, rows, R, kOzJT);
   if (!ok) {
     snprintf(c->err, sizeof(c->err), "tensor-core residual: tensor map encoding failed");
     return 1;

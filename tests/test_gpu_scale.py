@@ -15,7 +15,7 @@ pytestmark = pytest.mark.gpu
 
 BENCH = dict(refine_max=8, refine_tol=1e-5)
 # the timed configuration: refinement sweeps' CG solves capped at 70 steps
-BENCH_TC = dict(precision="bf16x3", refine_max=8, refine_tol=1e-5, refine_steps=70)
+BENCH_TC = dict(precision="bf16x3", refine_max=8, refine_tol=1e-5, refine_steps=50)
 
 
 def _run(wl, kw):

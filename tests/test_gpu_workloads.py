@@ -128,7 +128,7 @@ def test_differentiation_workload_adjoint(diff_wl):
 
 def test_differentiation_workload_adam_steps(diff_wl):
     """The differentiation workload's loss sum_t ||mu_{t, a_t} - z_t||^2 through PosteriorMeans:
-    a few Adam steps on Phi at full size lower it."""
+    the workload's 100 Adam steps on Phi at full size lower it."""
     import torch
     from paper_2310_00420_gb300.adjoint import posterior_means
     wl = diff_wl
@@ -142,7 +142,7 @@ def test_differentiation_workload_adam_steps(diff_wl):
         al = torch.tensor(ctx.read(cmcs.OUT_ALPHA), device="cuda")
         assign = torch.tensor(ctx.read(cmcs.OUT_ASSIGN).astype(np.int64), device="cuda")
         rows = torch.arange(wl.T, device="cuda")
-        for _ in range(5):
+        for _ in range(100):
             mu = posterior_means(ctx, Phi, y, al, 0)
             loss = ((mu[rows, assign] - z) ** 2).sum()
             opt.zero_grad()
