@@ -848,6 +848,7 @@ cmcs_status cmcs_adjoint(cmcs_ctx* h, const float* g, float* dy, float* dalpha, 
   a.K = 0;
   a.S = c->T * c->C;
   a.tc = nullptr;
+  a.oz = nullptr;                     // the tensor-core residual's buffers are sized for R systems
   a.dhi = a.dlo = nullptr;
   a.prof_on = 0;
   a.xacc = c->adj_x;
