@@ -180,20 +180,22 @@ def aggregate(ms_local: float, steps: int, world: int, device: str = "cuda", uni
 # k_tc<3>) on plain-scale with BF16X3, from one ncu capture on the 8-task slice scaled by
 # 32 / 8 tasks, keyed to the SHA-256 prefix of the kernel source it was taken on: once that
 # source changes the figure no longer describes the kernel and traffic is reported as null.
-_TRAFFIC = {"kernels_tc.cu": "bb5dfc6409c729ac",
-            "plain-scale/bf16x3": 4 * ((571.582976 + 0.119552) + (548.570368 + 24.364544)) * 1e6}
+_TRAFFIC = {"kernels_tc.cu+tc_ptx.cuh": "cd8ab4ddca22cb16",
+            "plain-scale/bf16x3": 4 * ((571.588096 + 0.462336) + (548.529408 + 25.012480)) * 1e6}
 
 
-def _source_sha(name: str) -> str:
+def _source_sha(*names: str) -> str:
     import hashlib
-    path = os.path.join(ROOT, "paper_2310_00420_gb300", "csrc", name)
-    with open(path, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for name in names:
+        with open(os.path.join(ROOT, "paper_2310_00420_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def _operator_traffic(wl, precision: str):
     if wl.name == "plain-scale" and wl.T == 32 and precision == "bf16x3":
-        if _source_sha("kernels_tc.cu") == _TRAFFIC["kernels_tc.cu"]:
+        if _source_sha("kernels_tc.cu", "tc_ptx.cuh") == _TRAFFIC["kernels_tc.cu+tc_ptx.cuh"]:
             return _TRAFFIC["plain-scale/bf16x3"]
     return None
 
@@ -740,8 +742,10 @@ def run_ours(a):
     if a.precision == "bf16x3" and not a.no_fp32_form and world == 1 and not fourier:
         # the mixed path: first solves with Phi as one BF16 plane (half its bytes), refinement
         # with the BF16 pair; its one-plane operator against the measured HBM bandwidth
+        # (its refinement keeps the first solve's step cap: with shorter inner solves some
+        # systems' refinement diverges from the one-plane first solve)
         mixed_form = timed_leg(warmup=min(a.warmup, 2), steps=min(a.steps, 5),
-                               precision="bf16_mixed")
+                               precision="bf16_mixed", refine_steps=0)
         one = sum(2.0 * int(n) * wl.D + 4.0 * wl.C * (wl.K + 1) * (2.0 * wl.D + 2.0 * int(n))
                   for n in wl.N)
         if mixed_form["bf16_plane_ms_per_application"]:
@@ -750,7 +754,7 @@ def run_ours(a):
             mixed_form["bf16_plane_hbm_gbs"] = gbs
             mixed_form["bf16_plane_hbm_frac"] = gbs / peaks["hbm_gbs"]
         if rank == 0 and not a.no_cpu:
-            c4 = cmcs.Context(Phi_d, y_d, wl.N, **dict(kw, precision="bf16_mixed"))
+            c4 = cmcs.Context(Phi_d, y_d, wl.N, **dict(kw, precision="bf16_mixed", refine_steps=0))
             c4.em_iter(2)
             al4 = c4.read(cmcs.OUT_ALPHA)
             it4 = c4.summary()["em_iters_done"]
