@@ -384,6 +384,130 @@ __global__ void __launch_bounds__(256, DS ? kP2MinBlocksDS : 1) k_pass2(P2Args p
 }
 
 // --------------------------------------------------------------------------------------
+// Narrow right-hand-side blocks (R <= 8, e.g. the adjoint's C systems per task): the operator
+// as two GEMVs.  With so few columns the GEMM tiles above would mostly compute padding, and
+// the work is bound by reading Phi: each pass streams Phi once, row segments as float4 loads
+// coalesced across the warp.
+// Pass 1: a warp takes 8 rows of one task; for every float4 of d it loads the R vectors once
+// (L1-cached) and the 8 rows' Phi, keeps 8 x R accumulators and reduces them across the warp.
+// Pass 2: a CTA of 128 threads takes 512 coordinates of one task, each thread four of them
+// for all R systems; the task's W is staged in shared memory 256 rows at a time.  Epilogue as
+// in k_pass2: Z = beta Phi^T W + alpha_c V and the per-128-coordinate partials of v^T A v.
+// --------------------------------------------------------------------------------------
+constexpr int kGemvMaxR = 8;        // widest right-hand-side block run as two GEMVs
+constexpr int kGvRows = 8;          // rows per warp in pass 1
+constexpr int kGvWarps = 4;         // warps per CTA in pass 1
+constexpr int kGvChunk = 256;       // rows of W staged per step of pass 2
+
+template <int NR>
+__global__ void __launch_bounds__(32 * kGvWarps)
+k_gemv1(const float* __restrict__ phi, const float* __restrict__ V, float* __restrict__ W,
+        const int64_t* __restrict__ drow, const int* __restrict__ tile_task,
+        const int* __restrict__ task_active, int R, int Dp, int64_t rows_total) {
+  const int lane = threadIdx.x & 31;
+  const int64_t n0 = ((int64_t)blockIdx.x * kGvWarps + (threadIdx.x >> 5)) * kGvRows;
+  if (n0 >= rows_total) return;
+  const int t = tile_task[n0 >> 7];
+  if (task_active != nullptr && task_active[t] == 0) return;
+  const float* Vt = V + (int64_t)t * R * Dp;
+  float acc[kGvRows][NR];
+#pragma unroll
+  for (int i = 0; i < kGvRows; ++i)
+#pragma unroll
+    for (int j = 0; j < NR; ++j) acc[i][j] = 0.f;
+  for (int d = lane * 4; d < Dp; d += 128) {
+    float4 v[NR];
+#pragma unroll
+    for (int j = 0; j < NR; ++j) v[j] = __ldg(reinterpret_cast<const float4*>(Vt + (int64_t)j * Dp + d));
+#pragma unroll
+    for (int i = 0; i < kGvRows; ++i) {
+      const float4 a = __ldcs(reinterpret_cast<const float4*>(phi + (n0 + i) * Dp + d));
+#pragma unroll
+      for (int j = 0; j < NR; ++j) {
+        acc[i][j] = fmaf(a.x, v[j].x, acc[i][j]);
+        acc[i][j] = fmaf(a.y, v[j].y, acc[i][j]);
+        acc[i][j] = fmaf(a.z, v[j].z, acc[i][j]);
+        acc[i][j] = fmaf(a.w, v[j].w, acc[i][j]);
+      }
+    }
+  }
+  // fixed-order butterfly over the lanes: every lane ends with the full sums
+#pragma unroll
+  for (int i = 0; i < kGvRows; ++i)
+#pragma unroll
+    for (int j = 0; j < NR; ++j)
+#pragma unroll
+      for (int m = 16; m > 0; m >>= 1) acc[i][j] += __shfl_xor_sync(0xffffffffu, acc[i][j], m);
+  const int64_t rbeg = drow[t], Np = drow[t + 1] - rbeg;
+  float* Wt = W + rbeg * R;
+  if (lane < kGvRows) {
+#pragma unroll
+    for (int i = 0; i < kGvRows; ++i)
+      if (i == lane)
+#pragma unroll
+        for (int j = 0; j < NR; ++j) Wt[(int64_t)j * Np + (n0 - rbeg) + i] = acc[i][j];
+  }
+}
+
+template <int NR>
+__global__ void __launch_bounds__(128) k_gemv2(P2Args p) {
+  __shared__ float Ws[NR][kGvChunk];
+  const int t = blockIdx.y;
+  if (p.task_active != nullptr && p.task_active[t] == 0) return;
+  const int d = blockIdx.x * 512 + threadIdx.x * 4;
+  const bool on = d < p.Dp;          // warp-uniform: D_pad is a multiple of 128
+  if (p.opcount != nullptr && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&p.opcount[t], 1ull);
+  const int64_t rbeg = p.drow[t], Np = p.drow[t + 1] - rbeg;
+  const float* Wt = p.W + rbeg * p.R;
+  float4 acc[NR];
+#pragma unroll
+  for (int j = 0; j < NR; ++j) acc[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int64_t c0 = 0; c0 < Np; c0 += kGvChunk) {
+    const int nc = (int)(Np - c0 < kGvChunk ? Np - c0 : kGvChunk);
+    __syncthreads();
+    for (int i = threadIdx.x; i < NR * nc; i += 128) {
+      const int j = i / nc, n = i - j * nc;
+      Ws[j][n] = Wt[(int64_t)j * Np + c0 + n];
+    }
+    __syncthreads();
+    const float* prow = p.phi + (rbeg + c0) * p.Dp + d;
+    for (int n = 0; on && n < nc; ++n) {
+      const float4 a = __ldcs(reinterpret_cast<const float4*>(prow + (int64_t)n * p.Dp));
+#pragma unroll
+      for (int j = 0; j < NR; ++j) {
+        const float w = Ws[j][n];
+        acc[j].x = fmaf(a.x, w, acc[j].x);
+        acc[j].y = fmaf(a.y, w, acc[j].y);
+        acc[j].z = fmaf(a.z, w, acc[j].z);
+        acc[j].w = fmaf(a.w, w, acc[j].w);
+      }
+    }
+  }
+  const int lane = threadIdx.x & 31;
+  if (!on) return;
+#pragma unroll
+  for (int j = 0; j < NR; ++j) {
+    if (j >= p.R) break;
+    const int64_t sys = (int64_t)t * p.R + j;
+    const int c = j / (p.K + 1);
+    const float4 v = *reinterpret_cast<const float4*>(p.V + sys * p.Dp + d);
+    const float4 al = *reinterpret_cast<const float4*>(p.alpha + (int64_t)c * p.Dp + d);
+    float4 z;
+    z.x = fmaf(p.beta_f, acc[j].x, al.x * v.x);
+    z.y = fmaf(p.beta_f, acc[j].y, al.y * v.y);
+    z.z = fmaf(p.beta_f, acc[j].z, al.z * v.z);
+    z.w = fmaf(p.beta_f, acc[j].w, al.w * v.w);
+    *reinterpret_cast<float4*>(p.Z + sys * p.Dp + d) = z;
+    if (p.part != nullptr) {
+      float dot = fmaf(v.x, z.x, fmaf(v.y, z.y, fmaf(v.z, z.z, v.w * z.w)));
+#pragma unroll
+      for (int m = 16; m > 0; m >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, m);
+      if (lane == 0) p.part[(int64_t)(d >> 7) * p.S + sys] = dot;
+    }
+  }
+}
+
+// --------------------------------------------------------------------------------------
 // host launchers
 // --------------------------------------------------------------------------------------
 namespace {
@@ -453,6 +577,27 @@ cudaError_t pass2(Ctx* c, int tn, const P2Args& a0, int nt = -1) {
   return cudaGetLastError();
 }
 
+// the two GEMV passes for R <= kGemvMaxR (every task in one launch per pass)
+cudaError_t gemv_operator(Ctx* c, const P2Args& a, const float* V, const int* mask) {
+  const int64_t nwarps = c->rows_total / kGvRows;
+  const unsigned g1 = (unsigned)((nwarps + kGvWarps - 1) / kGvWarps);
+  const dim3 g2((unsigned)((c->Dp + 511) / 512), (unsigned)c->T);
+  cudaStream_t st = c->stream;
+#define GVCASE(NR)                                                                              \
+  case NR:                                                                                      \
+    k_gemv1<NR><<<g1, 32 * kGvWarps, 0, st>>>(c->phi, V, c->w, c->drow, c->tile_task, mask, c->R, \
+                                             c->Dp, c->rows_total);                              \
+    k_gemv2<NR><<<g2, 128, 0, st>>>(a);                                                         \
+    break;
+  switch (c->R) {
+    GVCASE(1) GVCASE(2) GVCASE(3) GVCASE(4) GVCASE(5) GVCASE(6) GVCASE(7) GVCASE(8)
+    default: return cudaErrorInvalidValue;
+  }
+#undef GVCASE
+  c->launches += 2;
+  return cudaGetLastError();
+}
+
 P2Args base_args(Ctx* c) {
   P2Args a{};
   a.phi = c->phi;
@@ -507,6 +652,12 @@ cudaError_t launch_operator(Ctx* c, const float* V, float* Z, int with_dots) {
     }
     return cudaSuccess;
   }
+  static int gemv = -1;                // evaluation switch CMCS_GEMV=0: the GEMM tiles at any R
+  if (gemv < 0) {
+    const char* v = getenv("CMCS_GEMV");
+    gemv = v ? atoi(v) != 0 : 1;
+  }
+  if (gemv && c->R <= kGemvMaxR) return gemv_operator(c, a, V, mask);
   cudaError_t e = pass1<false>(c, tn, V, c->w, nullptr, mask, c->R, 1);
   if (e != cudaSuccess) return e;
   c->launches += 2;
