@@ -18,18 +18,20 @@
 // exact sums into a double-single accumulator per output (Knuth's TwoSum) and the MMA issuer
 // starts the next chunk from zero.
 //
-// Pass 1: W[j][n] = sum_d Phi[n][d] x[j][d]      A = Phi digit planes, K-major (blocked layout)
+// Pass 1: W[j][n] = sum_d Phi[n][d] x[j][d]      A = the three leading Phi digit planes, K-major
+//                                               (blocked layout)
 // Pass 2: R[j][d] = B - alpha x - beta sum_n Phi[n][d] W[j][n]
-//                                               A = the same planes read MN-major
-// W's digits carry 24 bits below each system's largest |W|: the rounding this adds to W is an
-// error in Phi x, which the solution of A delta = r sees only through beta Phi^T (amplified by
-// about the condition of Phi_t, not of A_tc); Phi^T W itself, whose rounding A^-1 amplifies by
-// kappa(A_tc), is formed without rounding.  The final combine b - alpha x - beta z runs in
+//                                               A = all five planes read MN-major
+// W carries rounding of FP32 size: its digits keep 24 bits below each system's largest |W|, and
+// pass 1 takes Phi to 23 bits below its column's largest entry.  Such an error in Phi x reaches
+// the solution of A delta = r only through beta Phi^T (amplified by about the condition of Phi_t,
+// not of A_tc); Phi^T W itself, whose rounding A^-1 amplifies by kappa(A_tc), is formed without
+// rounding from all five planes.  The final combine b - alpha x - beta z runs in
 // double-single arithmetic (TwoProduct by FMA, TwoSum), the output is rounded to FP32 once.
 //
 // Persistent kernels, one CTA (10 warps) per SM: warp 0 lane 0 streams the tiles with TMA
-// (128-byte swizzle) through two shared-memory stages, warp 1 lane 0 issues tcgen05.mma, warps
-// 2-9 drain TMEM (two per 32-lane quarter, 16 systems each).  Every wait is bounded; on expiry
+// (128-byte swizzle) through three (pass 1) or two (pass 2) shared-memory stages, warp 1 lane 0
+// issues tcgen05.mma, warps 2-9 drain TMEM (two per 32-lane quarter, 16 systems each).  Every wait is bounded; on expiry
 // the kernel records status bit 8, stops issuing, waits (bounded) for its copies in flight and
 // still frees its TMEM.
 #include <cuda.h>
@@ -53,15 +55,18 @@ constexpr int kOzK = 5;                          // digit planes of Phi
 constexpr int kOzL1 = 4;                         // digit planes of x' (pass 1)
 constexpr int kOzL2 = 3;                         // digit planes of W (pass 2)
 constexpr int kOzJT = 32;                        // systems per tile
-constexpr int kOzTmem = 512;                     // TMEM columns allocated (448 or 384 used)
+constexpr int kOzTmem = 512;                     // TMEM columns allocated (352 or 384 used)
 constexpr int kOzEpiWarps = 8;
 constexpr int kOzThreads = 64 + 32 * kOzEpiWarps;
-constexpr int kOzStages = 2;
+// pass 1 forms W, whose errors the refinement sees only through beta Phi^T (see above), from
+// the three leading Phi planes in three 64 KiB stages; pass 2 uses all five in two of 92 KiB
+__host__ __device__ constexpr int oz_nk(int pass) { return pass == 1 ? 3 : kOzK; }
+__host__ __device__ constexpr int oz_stages(int pass) { return pass == 1 ? 3 : 2; }
 constexpr int kOzABytes = kTileM * kTileK * 2;   // 16 KiB per Phi plane
 constexpr int kOzBBytes = kOzJT * kTileK * 2;    // 4 KiB per vector plane
 __host__ __device__ constexpr int oz_nl_max(int pass) { return pass == 1 ? kOzL1 : kOzL2; }
 __host__ __device__ constexpr int oz_stage_bytes(int pass) {
-  return kOzK * kOzABytes + oz_nl_max(pass) * kOzBBytes;
+  return oz_nk(pass) * kOzABytes + oz_nl_max(pass) * kOzBBytes;
 }
 // vector planes multiplied by Phi plane k (pairs k + l <= 4) and its accumulator's first column
 __host__ __device__ constexpr int oz_nl(int pass, int k) {
@@ -70,8 +75,10 @@ __host__ __device__ constexpr int oz_nl(int pass, int k) {
 __host__ __device__ constexpr int oz_col(int pass, int k) {
   return k == 0 ? 0 : oz_col(pass, k - 1) + kOzJT * oz_nl(pass, k - 1);
 }
-static_assert(oz_col(1, kOzK) <= kOzTmem && oz_col(2, kOzK) <= kOzTmem, "TMEM columns");
-constexpr int kOzSmem = kOzStages * oz_stage_bytes(1) + 1024 + 128;
+static_assert(oz_col(1, oz_nk(1)) <= kOzTmem && oz_col(2, oz_nk(2)) <= kOzTmem, "TMEM columns");
+constexpr int kOzSmem1 = oz_stages(1) * oz_stage_bytes(1) + 1024 + 128;
+constexpr int kOzSmem2 = oz_stages(2) * oz_stage_bytes(2) + 1024 + 128;
+static_assert(kOzSmem1 <= 227 * 1024 && kOzSmem2 <= 227 * 1024, "shared memory per CTA");
 constexpr int kOzMaxChunk = 16;                  // k-blocks per exact chunk: 16 x 64 x 2^14 = 2^24
 
 struct OzMaps {
@@ -250,6 +257,8 @@ k_oz(const __grid_constant__ OzMaps maps, const OzArgs p) {
                                              ~static_cast<uintptr_t>(1023));
   constexpr int kStage = oz_stage_bytes(PASS);
   constexpr int NL = oz_nl_max(PASS);
+  constexpr int NK = oz_nk(PASS);
+  constexpr int kOzStages = oz_stages(PASS);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)kOzStages * kStage);
   uint64_t* empty = full + kOzStages;
   uint64_t* tfull = empty + kOzStages;        // a chunk's sums are ready for the epilogue
@@ -302,7 +311,7 @@ k_oz(const __grid_constant__ OzMaps maps, const OzArgs p) {
           mbar_expect_tx(&full[s], (uint32_t)kStage);
           const int kcol = ti.kx + kb * kTileK;
 #pragma unroll
-          for (int k = 0; k < kOzK; ++k) {
+          for (int k = 0; k < NK; ++k) {
             uint8_t* ad = st + k * kOzABytes;
             if (PASS == 1) {
               tma_load_4d(ad, &maps.a[k], 0, 0, kcol / kTileK, ti.a_row / kTileM, &full[s]);
@@ -314,7 +323,7 @@ k_oz(const __grid_constant__ OzMaps maps, const OzArgs p) {
                           kcol / kTileM, &full[s]);
             }
           }
-          uint8_t* bst = st + kOzK * kOzABytes;
+          uint8_t* bst = st + NK * kOzABytes;
 #pragma unroll
           for (int l = 0; l < NL; ++l) tma_load_2d(bst + l * kOzBBytes, &maps.b[l], kcol, brow, &full[s]);
           issued = it + 1;
@@ -352,9 +361,9 @@ k_oz(const __grid_constant__ OzMaps maps, const OzArgs p) {
           const uint32_t st = smem_u32(smem + (size_t)s * kStage);
 #pragma unroll
           for (int kk = 0; kk < kTileK / 16; ++kk) {
-            const uint64_t bd = smem_desc(st + kOzK * kOzABytes + kk * 32);
+            const uint64_t bd = smem_desc(st + NK * kOzABytes + kk * 32);
 #pragma unroll
-            for (int k = 0; k < kOzK; ++k) {
+            for (int k = 0; k < NK; ++k) {
               const uint64_t ad = PASS == 1 ? smem_desc(st + k * kOzABytes + kk * 32)
                                             : smem_desc_mn(st + k * kOzABytes + kk * 2048, 8192, 1024);
               mma_bf16(tmem + (uint32_t)oz_col(PASS, k), ad, bd,
@@ -397,7 +406,7 @@ k_oz(const __grid_constant__ OzMaps maps, const OzArgs p) {
         tc_fence_after();
         // the exact sums of the pairs (k, l), most significant Phi planes first
 #pragma unroll
-        for (int k = 0; k < kOzK; ++k) {
+        for (int k = 0; k < NK; ++k) {
 #pragma unroll
           for (int l = 0; l < oz_nl(PASS, k); ++l) {
             float v[16];
@@ -537,8 +546,8 @@ int oz_create(Ctx* c) {
     snprintf(c->err, sizeof(c->err), "tensor-core residual: tensor map encoding failed");
     return 1;
   }
-  cudaError_t e = cudaFuncSetAttribute(k_oz<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kOzSmem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_oz<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kOzSmem);
+  cudaError_t e = cudaFuncSetAttribute(k_oz<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kOzSmem1);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_oz<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kOzSmem2);
   if (e == cudaSuccess) e = oz_refresh(c);
   if (e != cudaSuccess) {
     snprintf(c->err, sizeof(c->err), "tensor-core residual set-up: %s", cudaGetErrorString(e));
@@ -607,10 +616,10 @@ cudaError_t oz_residual(Ctx* c, const float* X, const float* Bext, float* Rout) 
   k_oz_x_digits<<<(unsigned)c->S, 256, 0, c->stream>>>(X, s->u, s->xd, s->xs, c->R, c->Dp,
                                                        (int64_t)c->S * c->Dp);
   a.ntiles = (int)(rows / kTileM) * a.njt;
-  k_oz<1><<<a.ntiles < sms ? a.ntiles : sms, kOzThreads, kOzSmem, c->stream>>>(s->m1, a);
+  k_oz<1><<<a.ntiles < sms ? a.ntiles : sms, kOzThreads, kOzSmem1, c->stream>>>(s->m1, a);
   k_oz_w_digits<<<4096, 256, 0, c->stream>>>(s->wf, s->wmax, c->tile_task, s->wd, c->R, rows);
   a.ntiles = c->T * (c->Dp / kTileM) * a.njt;
-  k_oz<2><<<a.ntiles < sms ? a.ntiles : sms, kOzThreads, kOzSmem, c->stream>>>(s->m2, a);
+  k_oz<2><<<a.ntiles < sms ? a.ntiles : sms, kOzThreads, kOzSmem2, c->stream>>>(s->m2, a);
   c->launches += 4;
   return cudaGetLastError();
 }
