@@ -816,11 +816,27 @@ cmcs_status cmcs_set_data(cmcs_ctx* h, const float* Phi, const float* y, int on_
   }
   const cudaMemcpyKind kin = kind_in(on_device);
   int64_t src_row = 0;
-  for (int t = 0; t < c->T; ++t) {
+  for (int t = 0; t < c->T;) {
+    if (c->D == c->Dp) {
+      // unpadded rows: consecutive tasks without padding rows are one contiguous block on both
+      // sides, copied in one piece
+      int t1 = t + 1;
+      int64_t rows = c->hN[t];
+      while (c->hN[t1 - 1] == c->hNp[t1 - 1] && t1 < c->T) rows += c->hN[t1++];
+      CK(cudaMemcpyAsync(c->phi + c->hrow[t] * c->Dp, Phi + src_row * c->D, sizeof(float) * rows * c->D,
+                         kin, c->stream));
+      for (int u = t; u < t1; ++u) {
+        CK(cudaMemcpyAsync(c->y + c->hrow[u], y + src_row, sizeof(float) * c->hN[u], kin, c->stream));
+        src_row += c->hN[u];
+      }
+      t = t1;
+      continue;
+    }
     CK(cudaMemcpy2DAsync(c->phi + c->hrow[t] * c->Dp, sizeof(float) * c->Dp, Phi + src_row * c->D,
                          sizeof(float) * c->D, sizeof(float) * c->D, (size_t)c->hN[t], kin, c->stream));
     CK(cudaMemcpyAsync(c->y + c->hrow[t], y + src_row, sizeof(float) * c->hN[t], kin, c->stream));
     src_row += c->hN[t];
+    ++t;
   }
   CK(launch_b0(c));
   CK(launch_tconst_dev(c, c->dN));
