@@ -102,7 +102,7 @@ cmcs_status sync_check(Ctx* c) {
 }
 
 cmcs_status read_counters(Ctx* c) {
-  CK(cudaMemcpyAsync(c->hcounters, c->counters, 4 * sizeof(int), cudaMemcpyDeviceToHost,
+  CK(cudaMemcpyAsync(c->hcounters, c->counters, 5 * sizeof(int), cudaMemcpyDeviceToHost,
                      c->stream));
   return sync_check(c);
 }
@@ -196,7 +196,34 @@ cudaGraphExec_t chunk_graph(Ctx* c, int record) {
 
 // Alg. 1 for every active system until all have stopped (or the step cap in force), in
 // chunks of c->chunk steps between host polls of the number of active systems
+// Fourier operator within one CTA: the whole solve as one persistent launch (each CTA loops its
+// pair's CG steps); CMCS_DFT_PERSIST=0 (evaluation switch) keeps one launch per step
+cmcs_status run_cg_persistent(Ctx* c, int record) {
+  CK(cudaMemsetAsync(c->counters + 4, 0, sizeof(int), c->stream));
+  const bool ev = c->prof_on;
+  if (ev) CK(cudaEventRecord(c->prof_ev[0], c->stream));
+  CK(launch_dft_cg_solve(c, record));
+  if (ev) CK(cudaEventRecord(c->prof_ev[1], c->stream));
+  cmcs_status s = read_counters(c);
+  if (s != CMCS_OK) return s;
+  const int n = c->hcounters[4];        // steps of the longest solve: operator applications
+  c->op_applies += n;
+  if (ev) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->prof_ev[0], c->prof_ev[1]) == cudaSuccess) c->prof_ms += ms;
+    else cudaGetLastError();
+    c->prof_calls += n;
+  }
+  return CMCS_OK;
+}
+
 cmcs_status run_cg(Ctx* c, int record) {
+  static int persist = -1;
+  if (persist < 0) {
+    const char* v = getenv("CMCS_DFT_PERSIST");
+    persist = v ? atoi(v) != 0 : 1;
+  }
+  if (persist && c->op == 1 && !c->dft_large) return run_cg_persistent(c, record);
   const int cap = cg_cap(c);
   for (int u = 0; u < cap; u += c->chunk) {
     const int n = cap - u < c->chunk ? cap - u : c->chunk;
@@ -570,8 +597,8 @@ cmcs_status create_ctx(const cmcs_config* cfg, const float* Phi, const float* y,
   CKC(dalloc(&c->rres, (size_t)S));
   CKC(cudaMemsetAsync(c->rres, 0, sizeof(float) * S, c->stream));
   CKC(dalloc(&c->task_active, (size_t)T));
-  CKC(dalloc(&c->counters, 4));
-  CKC(cudaMallocHost(reinterpret_cast<void**>(&c->hcounters), 4 * sizeof(int)));
+  CKC(dalloc(&c->counters, 5));
+  CKC(cudaMallocHost(reinterpret_cast<void**>(&c->hcounters), 5 * sizeof(int)));
   CKC(dalloc(&c->gam, (size_t)(T * C * K * c->U)));
   CKC(dalloc(&c->xi, (size_t)(T * C * K * c->U)));
   CKC(dalloc(&c->psteps, (size_t)(T * C * K)));

@@ -142,10 +142,11 @@ struct Ctx {
   float* rrel;         // [S] last ||delta|| / ||x||
   float* rres;         // [S] ||b - A x|| / ||b|| of the returned solution
   int* task_active;    // [T]
-  int* counters;       // [4]: 0 active systems, 1 refine-active systems, 2 status flags,
-                       //      3 systems whose refinement diverged (reverted) in this E-step
+  int* counters;       // [5]: 0 active systems, 1 refine-active systems, 2 status flags,
+                       //      3 systems whose refinement diverged (reverted) in this E-step,
+                       //      4 steps of the longest solve of a persistent CG launch
   int last_diverged;   // host copy of counters[3] after the last E-step
-  int* hcounters;      // pinned host mirror [4]
+  int* hcounters;      // pinned host mirror [5]
   float *gam, *xi;     // [T*C*K][U]
   int* psteps;         // [T*C*K] CG steps of the probe systems' first solve
   float* sest;         // [T][C][Dp]
@@ -235,6 +236,8 @@ cudaError_t launch_dft_residual(Ctx* c, const float* X, const float* Bext, float
 cudaError_t launch_dft_b0(Ctx* c);
 // one whole CG step (operator and update) for every active system of a Fourier context
 cudaError_t launch_dft_cg_step(Ctx* c, int record);
+// a whole CG solve in one persistent launch (counters[4]: steps of the longest solve)
+cudaError_t launch_dft_cg_solve(Ctx* c, int record);
 // four-step transforms for D = 2^a 5^b (16 | D, D <= 2^20) beyond one CTA (kernels_dft_large.cu)
 bool dft_large_ok(int D);
 int fs_create(Ctx* c, const uint8_t* hmask);   // hmask: host [T][D]

@@ -400,6 +400,158 @@ k_dft_cg_step(float* __restrict__ x, float* __restrict__ r, float* __restrict__ 
   }
 }
 
+// ---- a whole CG solve (Alg. 1) for pairs of systems, persistent -----------------------------
+// The same step as k_dft_cg_step (the same operations in the same order, so the same results
+// bit for bit), looped inside the CTA until both systems stop (convergence,
+// breakdown or the step cap): the CTA keeps its pair for the whole solve, so the pair's x, r
+// and d (192 KiB at D = 8192) stay in L2 between steps and r^T r, the step counts and the
+// convergence state stay in registers; no host poll and no launch per step.  maxsteps
+// (counters[4]) receives the most steps any pair took, the operator applications the solve
+// cost.
+__global__ void __launch_bounds__(kDftThreads)
+k_dft_cg_solve(float* __restrict__ x, float* __restrict__ r, float* __restrict__ d,
+               const float* __restrict__ mask_br, const float2* __restrict__ tw,
+               const float* __restrict__ alpha, float* rr, const float* __restrict__ bb,
+               int* steps, int* active, int* task_active, int* counters, float* gam, float* xih,
+               int* psteps, unsigned long long* opcount, int record, int R, int K, int C, int Dp,
+               int D, int L, int npair, int U, int cap, float beta, float tol2,
+               const float* __restrict__ pminv) {
+  extern __shared__ float2 Xf[];
+  __shared__ float sh[33];
+  __shared__ int s_go[2];
+  const int t = blockIdx.x / npair, p = blockIdx.x - t * npair;
+  const int j1 = 2 * p, j2 = 2 * p + 1;
+  const bool has2 = j2 < R;
+  const int64_t s1 = (int64_t)t * R + j1, s2 = has2 ? s1 + 1 : s1;
+  bool go1 = active[s1] != 0, go2 = has2 && active[s2] != 0;
+  if (!go1 && !go2) return;                          // block-uniform
+  float* x1 = x + s1 * Dp;
+  float* x2 = x + s2 * Dp;
+  float* r1 = r + s1 * Dp;
+  float* r2 = r + s2 * Dp;
+  float* d1 = d + s1 * Dp;
+  float* d2 = d + s2 * Dp;
+  const float* m = mask_br + (int64_t)t * D;
+  const float scale = beta / (float)D;
+  const float* a1 = alpha + (int64_t)(j1 / (K + 1)) * Dp;
+  const float* a2 = alpha + (int64_t)((has2 ? j2 : j1) / (K + 1)) * Dp;
+  const float* mi1 = pminv != nullptr ? pminv + ((int64_t)t * C + j1 / (K + 1)) * Dp : nullptr;
+  const float* mi2 = (pminv != nullptr && has2) ? pminv + ((int64_t)t * C + j2 / (K + 1)) * Dp
+                                                : nullptr;
+  float rr01 = rr[s1], rr02 = rr[s2];
+  int u1 = steps[s1], u2 = steps[s2];
+  int nstep = 0;
+  while (go1 || go2) {                               // block-uniform
+    if (opcount != nullptr && p == 0 && threadIdx.x == 0) atomicAdd(&opcount[t], 1ull);
+    ++nstep;
+    for (int i = threadIdx.x; i < D; i += blockDim.x) Xf[pad(i)] = make_float2(d1[i], has2 ? d2[i] : 0.f);
+    __syncthreads();
+    fft_dif(Xf, tw, D, L);
+    for (int i = threadIdx.x; i < D; i += blockDim.x) {
+      const float mk = m[i];
+      const float2 v = Xf[pad(i)];
+      Xf[pad(i)] = make_float2(v.x * mk, v.y * mk);
+    }
+    __syncthreads();
+    ifft_dit(Xf, tw, D, L);
+    float dad1 = 0.f, dad2 = 0.f;
+    for (int i = threadIdx.x; i < D; i += blockDim.x) {
+      const float2 xf = Xf[pad(i)];
+      const float dv1 = d1[i], dv2 = has2 ? d2[i] : 0.f;
+      const float ad1 = fmaf(scale, xf.x, a1[i] * dv1);
+      const float ad2 = has2 ? fmaf(scale, xf.y, a2[i] * dv2) : 0.f;
+      Xf[pad(i)] = make_float2(ad1, ad2);
+      dad1 = fmaf(dv1, ad1, dad1);
+      dad2 = fmaf(dv2, ad2, dad2);
+    }
+    dad1 = dft_block_sum(dad1, sh);
+    dad2 = dft_block_sum(dad2, sh);
+    // breakdown (d^T A d <= 0 or not finite): stop the system
+    if (threadIdx.x == 0) {
+      for (int q = 0; q < 2; ++q) {
+        const bool act = q == 0 ? go1 : go2;
+        const float dad = q == 0 ? dad1 : dad2;
+        const int64_t sys = q == 0 ? s1 : s2;
+        bool go = act;
+        if (act && (!(dad > 0.f) || !isfinite(dad))) {
+          active[sys] = 0;
+          atomicSub(&task_active[t], 1);
+          atomicSub(&counters[0], 1);
+          if (!isfinite(dad)) atomicOr(&counters[2], 1);
+          go = false;
+        }
+        s_go[q] = go ? 1 : 0;
+      }
+    }
+    __syncthreads();
+    go1 = s_go[0] != 0;
+    go2 = s_go[1] != 0;
+    if (!go1 && !go2) break;                         // block-uniform
+    const float g1 = go1 ? rr01 / dad1 : 0.f, g2 = go2 ? rr02 / dad2 : 0.f;   // gamma_u
+    float q1 = 0.f, q2 = 0.f;
+    for (int i = threadIdx.x; i < D; i += blockDim.x) {
+      const float2 ad = Xf[pad(i)];
+      float zv1 = 0.f, zv2 = 0.f;
+      if (go1) {
+        x1[i] = fmaf(g1, d1[i], x1[i]);
+        const float rv1 = fmaf(-g1, ad.x, r1[i]);
+        r1[i] = rv1;
+        zv1 = mi1 != nullptr ? rv1 * mi1[i] : rv1;
+        q1 = fmaf(rv1, zv1, q1);
+      }
+      if (go2) {
+        x2[i] = fmaf(g2, d2[i], x2[i]);
+        const float rv2 = fmaf(-g2, ad.y, r2[i]);
+        r2[i] = rv2;
+        zv2 = mi2 != nullptr ? rv2 * mi2[i] : rv2;
+        q2 = fmaf(rv2, zv2, q2);
+      }
+      Xf[pad(i)] = make_float2(zv1, zv2);
+    }
+    const float rr11 = dft_block_sum(q1, sh);
+    const float rr12 = dft_block_sum(q2, sh);
+    const float xi1 = go1 ? rr11 / rr01 : 0.f, xi2 = go2 ? rr12 / rr02 : 0.f;   // xi_u
+    for (int i = threadIdx.x; i < D; i += blockDim.x) {
+      const float2 rv = Xf[pad(i)];
+      if (go1) d1[i] = fmaf(xi1, d1[i], rv.x);
+      if (go2) d2[i] = fmaf(xi2, d2[i], rv.y);
+    }
+    // per-system bookkeeping, as in the step kernel; every thread takes the same decisions
+    bool done1 = false, done2 = false;
+    for (int q = 0; q < 2; ++q) {
+      if (!(q == 0 ? go1 : go2)) continue;
+      const int64_t sys = q == 0 ? s1 : s2;
+      const int j = q == 0 ? j1 : j2;
+      const float g = q == 0 ? g1 : g2, xi = q == 0 ? xi1 : xi2, rr1 = q == 0 ? rr11 : rr12;
+      const int u = q == 0 ? u1 : u2;
+      const bool done = (rr1 <= tol2 * bb[sys]) || (rr1 == 0.f) || (u + 1 >= cap) || !isfinite(rr1);
+      if (threadIdx.x == 0) {
+        const int c = j / (K + 1), k = j % (K + 1);
+        if (record && k > 0) {
+          const int64_t pidx = ((int64_t)t * C + c) * K + (k - 1);
+          gam[pidx * U + u] = g;
+          xih[pidx * U + u] = xi;
+          psteps[pidx] = u + 1;
+        }
+        steps[sys] = u + 1;
+        rr[sys] = rr1;
+        if (!isfinite(rr1)) atomicOr(&counters[2], 1);
+        if (done) {
+          active[sys] = 0;
+          atomicSub(&task_active[t], 1);
+          atomicSub(&counters[0], 1);
+        }
+      }
+      if (q == 0) { u1 = u + 1; rr01 = rr11; done1 = done; }
+      else { u2 = u + 1; rr02 = rr12; done2 = done; }
+    }
+    go1 = go1 && !done1;
+    go2 = go2 && !done2;
+    __syncthreads();                                 // d and Xf complete before the next step
+  }
+  if (threadIdx.x == 0) atomicMax(&counters[4], nstep);
+}
+
 // ---- refinement residual b - A x in FP64 ------------------------------------------------
 // Columns j' < Rc of each task are systems j = j' * jstride (all R, or the means only); pairs
 // (2p, 2p+1) share a transform.  b is Bext when given, else b0 (k = 0) or the probe.  Systems
@@ -577,6 +729,7 @@ int dft_create(Ctx* c, const uint8_t* mask, const float* y, int on_device) {
   const int sm32 = (int)sizeof(float2) * (D + D / 32), sm64 = (int)sizeof(double2) * (D + D / 32);
   if (cudaFuncSetAttribute(k_dft_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, sm32) != cudaSuccess ||
       cudaFuncSetAttribute(k_dft_cg_step, cudaFuncAttributeMaxDynamicSharedMemorySize, sm32) != cudaSuccess ||
+      cudaFuncSetAttribute(k_dft_cg_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, sm32) != cudaSuccess ||
       cudaFuncSetAttribute(k_dft_residual, cudaFuncAttributeMaxDynamicSharedMemorySize, sm64) != cudaSuccess ||
       cudaFuncSetAttribute(k_dft_b0, cudaFuncAttributeMaxDynamicSharedMemorySize, sm64) != cudaSuccess)
     return 4;
@@ -622,6 +775,19 @@ cudaError_t launch_dft_cg_step(Ctx* c, int record) {
   const int npair = (c->R + 1) / 2;
   c->launches += 1;
   k_dft_cg_step<<<c->T * npair, kDftThreads, sizeof(float2) * (c->D + c->D / 32), c->stream>>>(
+      c->x, c->r, c->d, c->dft_mask, static_cast<const float2*>(c->dft_tw32), c->alpha, c->rr,
+      c->bb, c->steps, c->active, c->task_active, c->counters, c->gam, c->xi, c->psteps,
+      c->prof_on ? reinterpret_cast<unsigned long long*>(c->opcount) : nullptr, record, c->R,
+      c->K, c->C, c->Dp, c->D, c->dft_L, npair, c->U, cg_cap(c), (float)c->beta,
+      (float)(c->cg_tol * c->cg_tol), c->precond ? c->pminv : nullptr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dft_cg_solve(Ctx* c, int record) {
+  if (c->dft_large) return cudaErrorInvalidValue;
+  const int npair = (c->R + 1) / 2;
+  c->launches += 1;
+  k_dft_cg_solve<<<c->T * npair, kDftThreads, sizeof(float2) * (c->D + c->D / 32), c->stream>>>(
       c->x, c->r, c->d, c->dft_mask, static_cast<const float2*>(c->dft_tw32), c->alpha, c->rr,
       c->bb, c->steps, c->active, c->task_active, c->counters, c->gam, c->xi, c->psteps,
       c->prof_on ? reinterpret_cast<unsigned long long*>(c->opcount) : nullptr, record, c->R,
