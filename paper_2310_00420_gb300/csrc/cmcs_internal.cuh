@@ -220,7 +220,8 @@ cudaError_t launch_resid_norm(Ctx* c);
 int oz_create(Ctx* c);
 cudaError_t oz_refresh(Ctx* c);      // Phi changed: its column scales and digit planes
 void oz_destroy(Ctx* c);
-cudaError_t oz_residual(Ctx* c, const float* X, const float* Bext, float* Rout);
+// columns j' < Rc of every task, systems j = j' jstride (all R, or the C means with K + 1)
+cudaError_t oz_residual(Ctx* c, const float* X, const float* Bext, float* Rout, int Rc, int jstride);
 // W[t][j'][n] = (Phi_t V_{t, j' * jstride})[n] for j' < Rc (FP32 SIMT pass 1 only)
 // W = Phi V for Rc columns (systems j = j' * jstride); with Wlo, as a compensated pair W + Wlo
 cudaError_t launch_phi_v(Ctx* c, const float* V, float* W, float* Wlo, int Rc, int jstride);

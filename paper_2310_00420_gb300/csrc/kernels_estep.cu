@@ -257,6 +257,8 @@ cudaError_t launch_quadrature_ctx(Ctx* c, cudaStream_t st) {
     side = v ? atoi(v) != 0 : 1;
   }
   const int nsys = c->T * c->C * c->K;
+  if (side && nsys > 0 && c->U <= 64)
+    return launch_quad_local<64>(c->gam, c->xi, c->psteps, nsys, c->U, c->quad, &c->counters[2], st, 0);
   if (side && nsys > 0 && c->U <= 128)
     return launch_quad_local<128>(c->gam, c->xi, c->psteps, nsys, c->U, c->quad, &c->counters[2], st, 0);
   return launch_quadrature(c->gam, c->xi, c->psteps, nsys, c->U, c->quad, &c->counters[2], st);

@@ -673,9 +673,12 @@ cudaError_t launch_phi_v(Ctx* c, const float* V, float* W, float* Wlo, int Rc, i
 cudaError_t launch_residual(Ctx* c, const float* X, const float* Bext, float* Rout,
                             int all_systems, int means_only) {
   if (c->op == 1) return launch_dft_residual(c, X, Bext, Rout, all_systems, means_only);
-  if (c->oz != nullptr && !means_only) return oz_residual(c, X, Bext, Rout);
   const int Rc = means_only ? c->C : c->R;
   const int js = means_only ? c->K + 1 : 1;
+  // the residual of the means feeds ell's data term mu^T (b0 - A mu), where the tensor-core
+  // residual's rounding of W (beta Phi^T dW, harmless to refinement) would shift the value by
+  // beta (Phi mu)^T dW: it stays on the double-single kernels
+  if (c->oz != nullptr && !means_only) return oz_residual(c, X, Bext, Rout, Rc, js);
   const int tn = c->tn_ds > 0 ? c->tn_ds : pick_tn(Rc, 4);
   // systems no longer refining: their tiles are skipped, their residual entries not read
   const int* ractive = (Bext || all_systems) ? nullptr : c->ractive;

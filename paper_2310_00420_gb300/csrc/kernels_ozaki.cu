@@ -90,8 +90,10 @@ struct OzArgs {
   const int* tile_task;       // [rows / 128]
   const int64_t* drow;        // [T + 1] padded row offsets
   int R, K, C, Dp, D, S;
+  int Rc, jstride;            // columns j' < Rc of a task: systems j = j' jstride (all R systems,
+                              // or the C means); digits, W and scales are indexed compactly
   int64_t rows_total;
-  int njt;                    // system tiles per task
+  int njt;                    // system tiles per task (of Rc columns)
   int ntiles;
   int chunk;                  // k-blocks summed exactly in TMEM before a drain
   const float* xs;            // pass 1: [S] scale of x' = u_t x
@@ -166,12 +168,12 @@ __global__ void k_oz_phi_digits(const float* __restrict__ phi, const float* __re
 __global__ void __launch_bounds__(256) k_oz_x_digits(const float* __restrict__ X,
                                                      const float* __restrict__ u,
                                                      __nv_bfloat16* __restrict__ dig,
-                                                     float* __restrict__ xs, int R, int Dp,
-                                                     int64_t plane) {
+                                                     float* __restrict__ xs, int R, int Rc,
+                                                     int jstride, int Dp, int64_t plane) {
   __shared__ float red[8];
-  const int64_t sys = blockIdx.x;
-  const int t = (int)(sys / R);
-  const float* x = X + sys * Dp;
+  const int64_t sys = blockIdx.x;                    // compact index t Rc + j'
+  const int t = (int)(sys / Rc);
+  const float* x = X + ((int64_t)t * R + (sys - (int64_t)t * Rc) * jstride) * Dp;
   const float* ut = u + (int64_t)t * Dp;
   float m = 0.f;
   for (int d = threadIdx.x; d < Dp; d += blockDim.x) m = fmaxf(m, fabsf(ut[d] * x[d]));
@@ -190,14 +192,14 @@ __global__ void __launch_bounds__(256) k_oz_x_digits(const float* __restrict__ X
 
 __global__ void k_oz_w_digits(const float* __restrict__ wf, const unsigned int* __restrict__ wmax,
                               const int* __restrict__ tile_task, __nv_bfloat16* __restrict__ dig,
-                              int R, int64_t rows) {
-  const int64_t n_el = (int64_t)R * rows;
+                              int Rc, int64_t rows, int64_t plane) {
+  const int64_t n_el = (int64_t)Rc * rows;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_el;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t j = i / rows, n = i - j * rows;
     const int t = tile_task[n >> 7];
-    const int e = scale_exp(__uint_as_float(wmax[(int64_t)t * R + j]));
-    make_digits<kOzL2>(wf[i], e, dig + i, n_el);
+    const int e = scale_exp(__uint_as_float(wmax[(int64_t)t * Rc + j]));
+    make_digits<kOzL2>(wf[i], e, dig + i, plane);
   }
 }
 
@@ -294,7 +296,7 @@ k_oz(const __grid_constant__ OzMaps maps, const OzArgs p) {
       bool stop = false;
       for (int tile = blockIdx.x; tile < p.ntiles && !stop && !*abort_flag; tile += gridDim.x) {
         const OzTile ti = oz_tile<PASS>(p, tile);
-        const int brow = PASS == 1 ? ti.t * p.R + ti.j0 : ti.j0;
+        const int brow = PASS == 1 ? ti.t * p.Rc + ti.j0 : ti.j0;
         for (int kb = 0; kb < ti.nk; ++kb, ++it) {
           const int s = (int)(it % kOzStages);
           if (it >= (uint32_t)kOzStages && !mbar_wait(&empty[s], ((it / kOzStages) - 1) & 1)) {
@@ -424,8 +426,8 @@ k_oz(const __grid_constant__ OzMaps maps, const OzArgs p) {
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
           const int j = ti.j0 + 16 * jh + i;
-          if (j >= p.R) break;                      // uniform across the warp
-          const int64_t sys = (int64_t)ti.t * p.R + j;
+          if (j >= p.Rc) break;                     // uniform across the warp
+          const int64_t sys = (int64_t)ti.t * p.Rc + j;  // compact
           // W = 2^-14 s (hi + lo): s and 2^-14 are powers of two
           const float w = __fadd_rn(hi[i], lo[i]) * (p.xs[sys] * 6.103515625e-05f);
           p.wf[(int64_t)j * p.rows_total + n] = w;
@@ -440,7 +442,7 @@ k_oz(const __grid_constant__ OzMaps maps, const OzArgs p) {
         // probe bits of the 16 systems for this warp's 32 coordinates: lane i draws system i's
         uint32_t mybits = 0;
         {
-          const int j = ti.j0 + 16 * jh + (lane & 15);
+          const int j = (ti.j0 + 16 * jh + (lane & 15)) * p.jstride;
           if (p.Bext == nullptr && j < p.R) {
             const int c = j / (p.K + 1), k = j - c * (p.K + 1);
             if (k > 0)
@@ -450,13 +452,15 @@ k_oz(const __grid_constant__ OzMaps maps, const OzArgs p) {
         }
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
-          const int j = ti.j0 + 16 * jh + i;
+          const int jc = ti.j0 + 16 * jh + i;        // compact column
           const uint32_t bits = __shfl_sync(0xffffffffu, mybits, i);
-          if (j >= p.R) break;                      // uniform across the warp
+          if (jc >= p.Rc) break;                    // uniform across the warp
+          const int j = jc * p.jstride;
           const int64_t sys = (int64_t)ti.t * p.R + j;
           const int c = j / (p.K + 1), k = j - c * (p.K + 1);
           // z = Phi^T W = 2^-14 u_d v_j (hi + lo), exact scaling by powers of two
-          const float sc = ud * ldexpf(6.103515625e-05f, scale_exp(__uint_as_float(p.wmax[sys])));
+          const float sc = ud * ldexpf(6.103515625e-05f,
+                                       scale_exp(__uint_as_float(p.wmax[(int64_t)ti.t * p.Rc + jc])));
           const float zh = hi[i] * sc, zl = lo[i] * sc;
           float bh = 0.f, bl = 0.f;
           if (p.Bext != nullptr) {
@@ -576,7 +580,7 @@ void oz_destroy(Ctx* c) {
   c->oz = nullptr;
 }
 
-cudaError_t oz_residual(Ctx* c, const float* X, const float* Bext, float* Rout) {
+cudaError_t oz_residual(Ctx* c, const float* X, const float* Bext, float* Rout, int Rc, int jstride) {
   OzState* s = static_cast<OzState*>(c->oz);
   if (!s) return cudaErrorNotSupported;
   const int64_t rows = c->rows_total;
@@ -590,7 +594,9 @@ cudaError_t oz_residual(Ctx* c, const float* X, const float* Bext, float* Rout) 
   a.D = c->D;
   a.S = c->S;
   a.rows_total = rows;
-  a.njt = (c->R + kOzJT - 1) / kOzJT;
+  a.Rc = Rc;
+  a.jstride = jstride;
+  a.njt = (Rc + kOzJT - 1) / kOzJT;
   a.chunk = s->chunk;
   a.xs = s->xs;
   a.wf = s->wf;
@@ -611,13 +617,15 @@ cudaError_t oz_residual(Ctx* c, const float* X, const float* Bext, float* Rout) 
   a.pshare = c->pshare;
   a.status = &c->counters[2];
   const int sms = c->sm_count > 0 ? c->sm_count : 1;
-  cudaError_t e = cudaMemsetAsync(s->wmax, 0, sizeof(unsigned int) * (size_t)c->S, c->stream);
+  const int nsys = c->T * Rc;
+  cudaError_t e = cudaMemsetAsync(s->wmax, 0, sizeof(unsigned int) * (size_t)nsys, c->stream);
   if (e != cudaSuccess) return e;
-  k_oz_x_digits<<<(unsigned)c->S, 256, 0, c->stream>>>(X, s->u, s->xd, s->xs, c->R, c->Dp,
-                                                       (int64_t)c->S * c->Dp);
+  k_oz_x_digits<<<(unsigned)nsys, 256, 0, c->stream>>>(X, s->u, s->xd, s->xs, c->R, Rc, jstride,
+                                                       c->Dp, (int64_t)c->S * c->Dp);
   a.ntiles = (int)(rows / kTileM) * a.njt;
   k_oz<1><<<a.ntiles < sms ? a.ntiles : sms, kOzThreads, kOzSmem1, c->stream>>>(s->m1, a);
-  k_oz_w_digits<<<4096, 256, 0, c->stream>>>(s->wf, s->wmax, c->tile_task, s->wd, c->R, rows);
+  k_oz_w_digits<<<4096, 256, 0, c->stream>>>(s->wf, s->wmax, c->tile_task, s->wd, Rc, rows,
+                                             (int64_t)c->R * rows);
   a.ntiles = c->T * (c->Dp / kTileM) * a.njt;
   k_oz<2><<<a.ntiles < sms ? a.ntiles : sms, kOzThreads, kOzSmem2, c->stream>>>(s->m2, a);
   c->launches += 4;
