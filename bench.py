@@ -619,6 +619,27 @@ def run_ours(a):
                     "frac": op_tflops / pk_t, **common}
         roof["hbm_gbs_achieved"] = op_gbs
 
+    # the refinement residual on the tensor cores (k_oz<1> + k_oz<2> and their digit kernels):
+    # live time per call and its executed digit-plane MMA work against the sustained BF16
+    # peak.  Per 32-system tile, pass 1 multiplies three Phi planes by 4 + 4 + 3 vector planes
+    # (352 MMA columns) over D_pad, pass 2 five planes by 3 + 3 + 3 + 2 + 1 (384) over the rows
+    res_tc = None
+    if (not fourier and a.precision in ("bf16x3", "bf16_mixed") and prof["residual_calls"] > 0
+            and os.environ.get("CMCS_OZ", "1") != "0"):
+        njt = -(-wl.C * (wl.K + 1) // 32)
+        rows = sum(-(-int(n) // 128) * 128 for n in wl.N)
+        dpad = -(-wl.D // 128) * 128
+        mma = 2.0 * rows * dpad * (352 + 384) * njt
+        ms_call = prof["residual_ms"] / prof["residual_calls"]
+        pk_t = peaks["bf16_tflops_sustained"]
+        res_tc = {"kernels": "k_oz<1> + k_oz<2> (tcgen05, BF16 digit planes) with k_oz_x_digits, "
+                             "k_oz_w_digits",
+                  "calls_per_step": prof["residual_calls"] / a.steps, "ms_per_call": ms_call,
+                  "executed_mma_tflop": mma / 1e12,
+                  "tflops_achieved": mma / (ms_call * 1e-3) / 1e12,
+                  "tensor_frac": mma / (ms_call * 1e-3) / 1e12 / pk_t,
+                  "peak_source": "MEASURED_PEAKS.json: BF16 sustained"}
+
     # the Lanczos eigen step (Eqs. 9-10) alone, on this E-step's own probe coefficients, through
     # the stand-alone entry point (it runs on a side stream inside the E-step)
     quad_ms = None
@@ -813,6 +834,7 @@ def run_ours(a):
                 "refine_diverged": summ["refine_diverged"], "resid_rel_max": summ["resid_rel_max"],
                 "operator_share": prof["operator_ms"] / ms if ms else None,
                 "residual_ms_per_step": prof["residual_ms"] / a.steps,
+                "residual_tc": res_tc,
                 "operator_applies_per_step": prof["operator_calls"] / a.steps,
                 "lanczos_quadrature_ms": quad_ms,
                 "roofline": roof, "cpu_baseline": cpu, "err_vs_fp64": err, "e2e": e2e,
