@@ -54,16 +54,20 @@ typedef enum {
      and sums (about twice FP32's precision) */
   CMCS_FP32 = 0,
   /* operator with Phi held in BF16 on the tcgen05 tensor cores (FP32 accumulation in TMEM);
-     CG vectors FP32 (entering the MMA as BF16 hi + lo pairs); the refinement residual uses the
-     FP32 Phi as in CMCS_FP32 */
+     CG vectors FP32 (entering the MMA as BF16 hi + lo pairs); the refinement residual is the
+     tensor-core one of CMCS_BF16X3 */
   CMCS_BF16_REFINE = 1,
   /* operator on the tensor cores with Phi and the vectors both split into BF16 hi + lo pairs
-     (three MMAs per step: about 16 significant bits per product, FP32 accumulation) */
+     (three MMAs per step: about 16 significant bits per product, FP32 accumulation); the
+     refinement residual on the tensor cores from exact BF16 digit planes of the FP32 Phi and
+     of the vectors (Ozaki's error-free splitting): Phi^T W is formed without rounding, W and x
+     are rounded at FP32 level (an error refinement sees only through beta Phi^T); the residual
+     of the returned means (for ell's data term) is the compensated one of CMCS_FP32 */
   CMCS_BF16X3 = 2,
   /* the first CG solve (the one whose coefficients feed the log-det estimate of Eqs. 9-11)
      with Phi held in BF16 on the tensor cores, as CMCS_BF16_REFINE (half the bytes of Phi per
-     application); the refinement sweeps' inner solves with the CMCS_BF16X3 operator and the
-     compensated residual, so the returned solutions reach the same accuracy.  cmcs_apply with
+     application); the refinement sweeps' inner solves with the CMCS_BF16X3 operator and its
+     refinement residual, so the returned solutions reach the same accuracy.  cmcs_apply with
      accurate = 0 applies the CMCS_BF16X3 operator */
   CMCS_BF16_MIXED = 3
 } cmcs_precision;
@@ -254,8 +258,9 @@ cmcs_status cmcs_result(const cmcs_ctx *ctx, cmcs_summary *out);
 /* Apply A_tc = beta Phi_t^T Phi_t + diag(alpha_c) (Eq. 7) to V, float [T][C*(K+1)][D] (vector
  * j of task t uses cluster c = j / (K+1)), writing Z of the same shape.  accurate = 0 uses
  * the E-step's batched operator (FP32 or BF16 per precision); accurate = 1 computes
- * B - A V with compensated products and sums (the refinement residual) for B given in Z on
- * entry.  V and Z are host or device per on_device.  The E-step's work buffers are reused,
+ * B - A V as the refinement residual of the context's precision (compensated SIMT products
+ * for CMCS_FP32, the tensor-core digit-plane residual for the BF16 precisions) for B given in
+ * Z on entry.  V and Z are host or device per on_device.  The E-step's work buffers are reused,
  * so results of a previous E-step other than alpha, b0 and the counter are invalidated. */
 cmcs_status cmcs_apply(cmcs_ctx *ctx, const float *V, float *Z, int on_device, int accurate);
 
@@ -288,7 +293,7 @@ typedef struct {
   double operator_flops;     /* algorithmic FLOPs: sum over applied tasks of 4 N_t D R        */
   double operator_bytes;     /* algorithmic bytes: per applied task s_Phi N_t D (Phi read once,
                                 s_Phi = 4 for FP32, 2 for BF16) + 4 R (2 D + 2 N_t) (V, W, Z)  */
-  int64_t residual_calls;    /* compensated residual applications                            */
+  int64_t residual_calls;    /* refinement residual applications                             */
   double residual_ms;        /* their summed device time                                     */
   int64_t kernel_launches;   /* all kernels the library launched                             */
   int64_t operator_calls_bf16; /* of the operator applications, those with Phi held as one
