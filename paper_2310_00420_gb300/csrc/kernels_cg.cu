@@ -64,19 +64,6 @@ __device__ __forceinline__ void store_split4(__nv_bfloat16* hi, __nv_bfloat16* l
   *reinterpret_cast<uint2*>(lo + i) = *reinterpret_cast<const uint2*>(l);
 }
 
-// hi + lo of four consecutive entries of a BF16 pair, in FP32
-__device__ __forceinline__ float4 load_pair4(const __nv_bfloat16* hi, const __nv_bfloat16* lo,
-                                             int64_t i) {
-  const uint2 uh = *reinterpret_cast<const uint2*>(hi + i);
-  const uint2 ul = *reinterpret_cast<const uint2*>(lo + i);
-  const __nv_bfloat16* h = reinterpret_cast<const __nv_bfloat16*>(&uh);
-  const __nv_bfloat16* l = reinterpret_cast<const __nv_bfloat16*>(&ul);
-  return make_float4(__bfloat162float(h[0]) + __bfloat162float(l[0]),
-                     __bfloat162float(h[1]) + __bfloat162float(l[1]),
-                     __bfloat162float(h[2]) + __bfloat162float(l[2]),
-                     __bfloat162float(h[3]) + __bfloat162float(l[3]));
-}
-
 }  // namespace
 
 // ---- CG initialisation: x_1 = 0, r_1 = d_1 = b (Alg. 1, first line) ---------------------
@@ -170,9 +157,7 @@ k_cg_init(int mode, float* __restrict__ x, float* __restrict__ r, float* __restr
 // phases (D_pad <= 1024 NV); NV = 0: generic loop that re-reads them.
 // RAW = false: ad = A d and d^T A d arrives as per-tile partials from the operator epilogue.
 // RAW = true (tensor-core operator): ad = beta Phi^T Phi d only; this kernel adds alpha_c * d
-// and forms d^T A d itself, so the operator's epilogue reads neither d nor alpha.  There the
-// direction is kept only as the BF16 pair d_hi + d_lo the operator multiplies: the updates use
-// exactly the vector whose A d was formed, and each step moves 4 bytes per coordinate less.
+// and forms d^T A d itself, so the operator's epilogue reads neither d nor alpha.
 // pminv != null: Jacobi-preconditioned step, z = M^-1 r, rr = r^T z, d = z + xi d.
 template <int NV, bool RAW>
 __global__ void __launch_bounds__(256)
@@ -214,7 +199,7 @@ k_cg_update(float* __restrict__ x, float* __restrict__ r, float* __restrict__ d,
   if constexpr (RAW) {
     float a2 = 0.f;
     auto pre = [&](int i, float4& dout, float4& aout) {
-      dout = load_pair4(dhi, dlo, sys * Dp + i);     // the direction the operator applied
+      dout = *reinterpret_cast<const float4*>(ds + i);
       aout = adv(i, dout);
       a2 = fmaf(dout.x, aout.x, a2); a2 = fmaf(dout.y, aout.y, a2);
       a2 = fmaf(dout.z, aout.z, a2); a2 = fmaf(dout.w, aout.w, a2);
@@ -262,7 +247,7 @@ k_cg_update(float* __restrict__ x, float* __restrict__ r, float* __restrict__ d,
       dv = dk[q];
       av = ak[q];
     } else {
-      dv = RAW ? load_pair4(dhi, dlo, sys * Dp + i) : *reinterpret_cast<const float4*>(ds + i);
+      dv = *reinterpret_cast<const float4*>(ds + i);
       av = adv(i, dv);
     }
     xv.x = fmaf(g, dv.x, xv.x); xv.y = fmaf(g, dv.y, xv.y);
@@ -293,7 +278,7 @@ k_cg_update(float* __restrict__ x, float* __restrict__ r, float* __restrict__ d,
   auto step2 = [&](int i, float4 rv, float4 dv) {  // rv: z_{u+1}
     dv.x = fmaf(xi, dv.x, rv.x); dv.y = fmaf(xi, dv.y, rv.y);
     dv.z = fmaf(xi, dv.z, rv.z); dv.w = fmaf(xi, dv.w, rv.w);
-    if (!RAW) *reinterpret_cast<float4*>(ds + i) = dv;
+    *reinterpret_cast<float4*>(ds + i) = dv;
     if (dhi != nullptr) store_split4(dhi, dlo, sys * Dp + i, dv);
   };
   if constexpr (NV > 0) {
@@ -305,7 +290,7 @@ k_cg_update(float* __restrict__ x, float* __restrict__ r, float* __restrict__ d,
   } else {
     for (int i = threadIdx.x * 4; i < Dp; i += 256 * 4)
       step2(i, zof(i, *reinterpret_cast<const float4*>(rs + i)),
-            RAW ? load_pair4(dhi, dlo, sys * Dp + i) : *reinterpret_cast<const float4*>(ds + i));
+            *reinterpret_cast<const float4*>(ds + i));
   }
   if (threadIdx.x == 0) {
     const int u = steps[sys];
