@@ -31,9 +31,9 @@
 //
 // Persistent kernels, one CTA (10 warps) per SM: warp 0 lane 0 streams the tiles with TMA
 // (128-byte swizzle) through three (pass 1) or two (pass 2) shared-memory stages, warp 1 lane 0
-// issues tcgen05.mma, warps 2-9 drain TMEM (two per 32-lane quarter, 16 systems each).  Every wait is bounded; on expiry
-// the kernel records status bit 8, stops issuing, waits (bounded) for its copies in flight and
-// still frees its TMEM.
+// issues tcgen05.mma, warps 2-9 drain TMEM (two per 32-lane quarter, 16 systems each).  Every
+// wait is bounded; on expiry the kernel records status bit 8, stops issuing, waits (bounded)
+// for its copies in flight and still frees its TMEM.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <math.h>
